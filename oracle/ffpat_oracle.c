@@ -1,0 +1,477 @@
+/*
+ * ffpat_oracle.c -- plain FP64 CPU oracle for one-step full-field photoacoustic
+ * reconstruction (Haltmeier, Zangerl, Nuster, Nguyen, "Photoacoustic image
+ * reconstruction from full field data in heterogeneous media", 2019).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls
+ * this file: only the tests, the smoke check and the benchmark's CPU baseline
+ * do.  It shares no code, header or table with the CUDA library.
+ *
+ * Every function is the plain definition, written out as slow loops in double
+ * precision (compile with -ffp-contract=off so that no multiply-add is fused).
+ *
+ * Discretisation (readings of the paper, which uses a k-space solver and
+ * Matlab's radon for its own 2D experiments):
+ *   grid      N^3 cell-centred points on [-1,1]^3, x_i = -1 + (i + 1/2) dx,
+ *             dx = 2/N, layout [z][y][x] with x fastest;
+ *   Laplacian L4 u = sum over the three axes of
+ *             (-u[-2] + 16 u[-1] - 30 u[0] + 16 u[+1] - u[+2]) / 12,
+ *             with zero ghost values outside the box (the 1/dx^2 is folded
+ *             into kappa);
+ *   time      Nt = ceil(T c_max / (cfl dx) (1 - 1e-12)), dt = T / Nt,
+ *             kappa = (c dt / dx)^2.
+ *
+ * Parity status: every function below is pinned by tests/test_oracle_pins.py
+ * (closed forms, spectral closed form of the time stepping, exact polynomial
+ * reproduction, energy conservation, dense transposes, FBP identity, KKT).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define FFO_PI 3.14159265358979323846
+
+static size_t at3(int n, int z, int y, int x) { return ((size_t)z * n + y) * n + x; }
+
+/* value of u at (z,y,x), zero outside the box (homogeneous Dirichlet ghosts) */
+static double ghost(const double *u, int n, int z, int y, int x) {
+  if (x < 0 || y < 0 || z < 0 || x >= n || y >= n || z >= n) return 0.0;
+  return u[at3(n, z, y, x)];
+}
+
+/* one axis of the fourth-order central second difference (times 12) */
+static double d2_axis(double um2, double um1, double u0, double up1, double up2) {
+  return -um2 + 16.0 * um1 - 30.0 * u0 + 16.0 * up1 - up2;
+}
+
+/* L4 u at one point: the discrete Laplacian of the wave equation (Sec. 2.1,
+ * eq. (1)), fourth order in space, dimensionless */
+static double lap4_at(const double *u, int n, int z, int y, int x) {
+  double u0 = u[at3(n, z, y, x)];
+  double ax = d2_axis(ghost(u, n, z, y, x - 2), ghost(u, n, z, y, x - 1), u0,
+                      ghost(u, n, z, y, x + 1), ghost(u, n, z, y, x + 2));
+  double ay = d2_axis(ghost(u, n, z, y - 2, x), ghost(u, n, z, y - 1, x), u0,
+                      ghost(u, n, z, y + 1, x), ghost(u, n, z, y + 2, x));
+  double az = d2_axis(ghost(u, n, z - 2, y, x), ghost(u, n, z - 1, y, x), u0,
+                      ghost(u, n, z + 1, y, x), ghost(u, n, z + 2, y, x));
+  return (ax + ay + az) / 12.0;
+}
+
+static void lap4(const double *u, int n, double *out) {
+  int z;
+#pragma omp parallel for schedule(static)
+  for (z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) out[at3(n, z, y, x)] = lap4_at(u, n, z, y, x);
+}
+
+int ffo_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void ffo_set_num_threads(int k) {
+#ifdef _OPENMP
+  if (k > 0) omp_set_num_threads(k);
+#else
+  (void)k;
+#endif
+}
+
+/* ---------------------------------------------------------------- setup -- */
+
+/* Number of leapfrog steps for final time T (wave model, Sec. 2.1): the
+ * smallest Nt with T/Nt <= cfl dx / c_max; the factor (1 - 1e-12) keeps a
+ * ratio that is an integer up to round-off from gaining a step. */
+int ffo_time_steps(int n, double T, double cfl, double cmax, double *dt_out) {
+  double dx = 2.0 / n;
+  double x = T * cmax / (cfl * dx);
+  int nt = (int)ceil(x * (1.0 - 1e-12));
+  if (nt < 1) nt = 1;
+  if (dt_out) *dt_out = T / nt;
+  return nt;
+}
+
+/* kappa = (c dt / dx)^2 for every grid point (c^2 scaling of eq. (1)) */
+void ffo_kappa(int n, double dt, const double *c, double *kappa) {
+  double dx = 2.0 / n;
+  size_t n3 = (size_t)n * n * n;
+  for (size_t i = 0; i < n3; ++i) {
+    double r = c[i] * dt / dx;
+    kappa[i] = r * r;
+  }
+}
+
+double ffo_max(size_t len, const double *a) {
+  double m = -INFINITY;
+  for (size_t i = 0; i < len; ++i)
+    if (a[i] > m) m = a[i];
+  return m;
+}
+
+/* ---------------------------------------------------- wave operator W_T -- */
+
+/* W_T h = p(., T) (eq. (3)) for the wave equation (1)-(2): p^0 = h; the zero
+ * initial velocity gives p^1 = p^0 + 1/2 kappa L4 p^0; then the leapfrog
+ * p^{n+1} = 2 p^n - p^{n-1} + kappa L4 p^n up to n + 1 = nt.  kappa carries
+ * dt, so this runs any number of steps nt >= 1 for the given kappa. */
+void ffo_wave(int n, int nt, const double *kappa, const double *h, double *out) {
+  size_t n3 = (size_t)n * n * n;
+  double *prev = malloc(n3 * sizeof(double));
+  double *cur = malloc(n3 * sizeof(double));
+  double *lap = malloc(n3 * sizeof(double));
+  memcpy(prev, h, n3 * sizeof(double));
+  lap4(prev, n, lap);
+  for (size_t i = 0; i < n3; ++i) cur[i] = prev[i] + 0.5 * kappa[i] * lap[i];
+  for (int step = 1; step < nt; ++step) {
+    lap4(cur, n, lap);
+    for (size_t i = 0; i < n3; ++i) {
+      double next = 2.0 * cur[i] - prev[i] + kappa[i] * lap[i];
+      prev[i] = cur[i];
+      cur[i] = next;
+    }
+  }
+  memcpy(out, cur, n3 * sizeof(double));
+  free(prev);
+  free(cur);
+  free(lap);
+}
+
+/* The transpose of W_T (Sec. 3.1: the adjoint runs the wave equation backwards
+ * from (q, q_t)|_T = (g, 0) to t = 0).  For the exact Euclidean transpose of
+ * the discrete W the sound speed sits inside the Laplacian, q_tt = Delta(c^2 q):
+ * q^{nt} = g, q^{nt-1} = q^{nt} + 1/2 L4(kappa q^{nt}), and
+ * q^{n-1} = 2 q^n - q^{n+1} + L4(kappa q^n) down to q^0, the output. */
+void ffo_wave_adjoint(int n, int nt, const double *kappa, const double *g, double *out) {
+  size_t n3 = (size_t)n * n * n;
+  double *later = malloc(n3 * sizeof(double)); /* q^{n+1} */
+  double *cur = malloc(n3 * sizeof(double));   /* q^n */
+  double *kq = malloc(n3 * sizeof(double));
+  double *lap = malloc(n3 * sizeof(double));
+  memcpy(later, g, n3 * sizeof(double));
+  for (size_t i = 0; i < n3; ++i) kq[i] = kappa[i] * later[i];
+  lap4(kq, n, lap);
+  for (size_t i = 0; i < n3; ++i) cur[i] = later[i] + 0.5 * lap[i];
+  for (int step = 1; step < nt; ++step) {
+    for (size_t i = 0; i < n3; ++i) kq[i] = kappa[i] * cur[i];
+    lap4(kq, n, lap);
+    for (size_t i = 0; i < n3; ++i) {
+      double earlier = 2.0 * cur[i] - later[i] + lap[i];
+      later[i] = cur[i];
+      cur[i] = earlier;
+    }
+  }
+  memcpy(out, cur, n3 * sizeof(double));
+  free(later);
+  free(cur);
+  free(kq);
+  free(lap);
+}
+
+/* ------------------------------------------------- X-ray transform X / P -- */
+
+/* theta_j = pi j / n_angles, j < n_angles (the paper's 1D set of directions,
+ * Sec. 4.1: equidistant in [0, 180 degrees)). */
+void ffo_angles(int nth, double *cs, double *sn) {
+  for (int j = 0; j < nth; ++j) {
+    double th = (FFO_PI * j) / nth;
+    cs[j] = cos(th);
+    sn[j] = sin(th);
+  }
+}
+
+/* number of ray samples: 2 ceil(N / sqrt 2), spacing dx, covering |s| <~ sqrt 2 */
+int ffo_ray_samples(int n) { return 2 * (int)ceil((double)n / sqrt(2.0)); }
+
+/* bilinear interpolation weights of the sample point (xi_k theta + s_m theta_perp)
+ * in slice coordinates; returns the lower-left corner through i0/j0 */
+static void sample_point(int n, double cs, double sn, int k, int m, int ns, int *i0, int *j0,
+                         double *fx, double *fy) {
+  double dx = 2.0 / n;
+  double xi = -1.0 + (k + 0.5) * dx;           /* detector centre xi_k */
+  double s = (m + 0.5 - ns / 2) * dx;          /* ray sample s_m */
+  double x = xi * cs - s * sn;                 /* xi theta + s theta_perp, theta_perp = (-sin, cos) */
+  double y = xi * sn + s * cs;
+  double half = n / 2.0;
+  double gx = (x + 1.0) * half - 0.5;          /* continuous grid index of x */
+  double gy = (y + 1.0) * half - 0.5;
+  double fl_x = floor(gx), fl_y = floor(gy);
+  *i0 = (int)fl_x;
+  *j0 = (int)fl_y;
+  *fx = gx - fl_x;
+  *fy = gy - fl_y;
+}
+
+/* exposes the sample arithmetic for the bit-exact index-table check */
+void ffo_sample_points(int n, int nth, int count, const int32_t *jkm, int32_t *ij, double *f) {
+  double *cs = malloc(nth * sizeof(double)), *sn = malloc(nth * sizeof(double));
+  int ns = ffo_ray_samples(n);
+  ffo_angles(nth, cs, sn);
+  for (int t = 0; t < count; ++t) {
+    int j = jkm[3 * t], k = jkm[3 * t + 1], m = jkm[3 * t + 2];
+    int i0, j0;
+    double fx, fy;
+    sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+    ij[2 * t] = i0;
+    ij[2 * t + 1] = j0;
+    f[2 * t] = fx;
+    f[2 * t + 1] = fy;
+  }
+  free(cs);
+  free(sn);
+}
+
+static double slice_at(const double *slice, int n, int iy, int ix) {
+  if (ix < 0 || iy < 0 || ix >= n || iy >= n) return 0.0;
+  return slice[(size_t)iy * n + ix];
+}
+
+/* P: g[j][l][k] = ds sum_m B(p[l]; xi_k theta_j + s_m theta_j^perp), eq. (4)
+ * applied in each horizontal plane z_l (the X-ray transform is the 2D Radon
+ * transform per plane), with zero-extended bilinear interpolation B. */
+void ffo_project(int n, int nth, const double *p, double *g) {
+  double *cs = malloc(nth * sizeof(double)), *sn = malloc(nth * sizeof(double));
+  int ns = ffo_ray_samples(n);
+  double ds = 2.0 / n;
+  ffo_angles(nth, cs, sn);
+  int jl;
+#pragma omp parallel for schedule(static)
+  for (jl = 0; jl < nth * n; ++jl) {
+    int j = jl / n, l = jl % n;
+    const double *slice = p + (size_t)l * n * n;
+    for (int k = 0; k < n; ++k) {
+      double acc = 0.0;
+      for (int m = 0; m < ns; ++m) {
+        int i0, j0;
+        double fx, fy;
+        sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+        double b = (1.0 - fx) * (1.0 - fy) * slice_at(slice, n, j0, i0) +
+                   fx * (1.0 - fy) * slice_at(slice, n, j0, i0 + 1) +
+                   (1.0 - fx) * fy * slice_at(slice, n, j0 + 1, i0) +
+                   fx * fy * slice_at(slice, n, j0 + 1, i0 + 1);
+        acc += b;
+      }
+      g[((size_t)j * n + l) * n + k] = ds * acc;
+    }
+  }
+  free(cs);
+  free(sn);
+}
+
+static void scatter(double *slice, int n, int iy, int ix, double v) {
+  if (ix < 0 || iy < 0 || ix >= n || iy >= n) return;
+  slice[(size_t)iy * n + ix] += v;
+}
+
+/* P^T: the matrix transpose of ffo_project (the discrete counterpart of the
+ * backprojection X* of Sec. 3.1): every sample spreads ds g[j][l][k] onto its
+ * four bilinear corners with the same weights. */
+void ffo_backproject(int n, int nth, const double *g, double *out) {
+  double *cs = malloc(nth * sizeof(double)), *sn = malloc(nth * sizeof(double));
+  int ns = ffo_ray_samples(n);
+  double ds = 2.0 / n;
+  ffo_angles(nth, cs, sn);
+  memset(out, 0, (size_t)n * n * n * sizeof(double));
+  int l;
+#pragma omp parallel for schedule(static)
+  for (l = 0; l < n; ++l) {
+    double *slice = out + (size_t)l * n * n;
+    for (int j = 0; j < nth; ++j)
+      for (int k = 0; k < n; ++k) {
+        double w = ds * g[((size_t)j * n + l) * n + k];
+        for (int m = 0; m < ns; ++m) {
+          int i0, j0;
+          double fx, fy;
+          sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+          scatter(slice, n, j0, i0, (1.0 - fx) * (1.0 - fy) * w);
+          scatter(slice, n, j0, i0 + 1, fx * (1.0 - fy) * w);
+          scatter(slice, n, j0 + 1, i0, (1.0 - fx) * fy * w);
+          scatter(slice, n, j0 + 1, i0 + 1, fx * fy * w);
+        }
+      }
+  }
+  free(cs);
+  free(sn);
+}
+
+/* ------------------------------------------------ preconditioner Lambda -- */
+
+/* Filter tap t_d of Lambda (Sec. 3.1, F Lambda Phi = |omega|/(4 pi) F Phi in
+ * the detector variable): half the band-limited ramp filter on the detector
+ * spacing dxi, times the quadrature weight dxi. */
+double ffo_ramp_tap(int n, int d) {
+  double dxi = 2.0 / n;
+  if (d < 0) d = -d;
+  if (d == 0) return 1.0 / (8.0 * dxi);
+  if (d % 2 == 0) return 0.0;
+  return -1.0 / (2.0 * FFO_PI * FFO_PI * (double)d * (double)d * dxi);
+}
+
+/* (Lambda r)[j][l][k] = sum_{k'} t_{k-k'} r[j][l][k'] along each detector row */
+void ffo_ramp(int n, int nth, const double *r, double *out) {
+  int row;
+  int rows = nth * n;
+#pragma omp parallel for schedule(static)
+  for (row = 0; row < rows; ++row) {
+    const double *rr = r + (size_t)row * n;
+    double *oo = out + (size_t)row * n;
+    for (int k = 0; k < n; ++k) {
+      double acc = 0.0;
+      for (int kk = 0; kk < n; ++kk) acc += ffo_ramp_tap(n, k - kk) * rr[kk];
+      oo[k] = acc;
+    }
+  }
+}
+
+/* --------------------------------------------- forward operator A = P W -- */
+
+typedef struct {
+  int n, nth, nt, precond;
+  double dt, T, cfl;
+  double *kappa;
+} ffo_setup_t;
+
+static int setup(ffo_setup_t *s, int n, double T, double cfl, int nth, int precond, const double *c) {
+  size_t n3 = (size_t)n * n * n;
+  s->n = n;
+  s->nth = nth;
+  s->T = T;
+  s->cfl = cfl;
+  s->precond = precond;
+  s->nt = ffo_time_steps(n, T, cfl, ffo_max(n3, c), &s->dt);
+  s->kappa = malloc(n3 * sizeof(double));
+  ffo_kappa(n, s->dt, c, s->kappa);
+  return s->nt;
+}
+
+/* g = P W_T h (Problem 1 with full data, M = R^2) */
+int ffo_forward(int n, double T, double cfl, int nth, const double *c, const double *h, double *g) {
+  ffo_setup_t s;
+  size_t n3 = (size_t)n * n * n;
+  setup(&s, n, T, cfl, nth, 0, c);
+  double *p = malloc(n3 * sizeof(double));
+  ffo_wave(n, s.nt, s.kappa, h, p);
+  ffo_project(n, nth, p, g);
+  free(p);
+  free(s.kappa);
+  return s.nt;
+}
+
+/* h = W_T^T P^T g */
+int ffo_adjoint(int n, double T, double cfl, int nth, const double *c, const double *g, double *h) {
+  ffo_setup_t s;
+  size_t n3 = (size_t)n * n * n;
+  setup(&s, n, T, cfl, nth, 0, c);
+  double *a = malloc(n3 * sizeof(double));
+  ffo_backproject(n, nth, g, a);
+  ffo_wave_adjoint(n, s.nt, s.kappa, a, h);
+  free(a);
+  free(s.kappa);
+  return s.nt;
+}
+
+static double dot(size_t len, const double *a, const double *b) {
+  double acc = 0.0;
+  for (size_t i = 0; i < len; ++i) acc += a[i] * b[i];
+  return acc;
+}
+
+/* grad = A^T Lambda (A h - g); r_out = A h - g; lr_out = Lambda r */
+static void data_gradient(const ffo_setup_t *s, const double *h, const double *g, double *r,
+                          double *lr, double *grad, double *work3) {
+  int n = s->n, nth = s->nth;
+  size_t nd = (size_t)nth * n * n;
+  ffo_wave(n, s->nt, s->kappa, h, work3);
+  ffo_project(n, nth, work3, r);
+  for (size_t i = 0; i < nd; ++i) r[i] = r[i] - g[i];
+  if (s->precond)
+    ffo_ramp(n, nth, r, lr);
+  else
+    memcpy(lr, r, nd * sizeof(double));
+  ffo_backproject(n, nth, lr, work3);
+  ffo_wave_adjoint(n, s->nt, s->kappa, work3, grad);
+}
+
+/* Largest eigenvalue of A^T Lambda A by power iteration from v0 (the step
+ * size bound 1/L; not in the paper, which fixes s = 0.2 for its own scaling). */
+double ffo_power(int n, double T, double cfl, int nth, int precond, const double *c,
+                 const double *v0, int iters) {
+  ffo_setup_t s;
+  size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
+  setup(&s, n, T, cfl, nth, precond, c);
+  double *v = malloc(n3 * sizeof(double)), *w = malloc(n3 * sizeof(double));
+  double *work3 = malloc(n3 * sizeof(double));
+  double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
+  double *zero = calloc(nd, sizeof(double));
+  double nv = sqrt(dot(n3, v0, v0));
+  for (size_t i = 0; i < n3; ++i) v[i] = v0[i] / nv;
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    data_gradient(&s, v, zero, r, lr, w, work3); /* w = A^T Lambda A v */
+    double nw = sqrt(dot(n3, w, w));
+    lam = nw;
+    for (size_t i = 0; i < n3; ++i) v[i] = w[i] / nw;
+  }
+  free(v);
+  free(w);
+  free(work3);
+  free(r);
+  free(lr);
+  free(zero);
+  free(s.kappa);
+  return lam;
+}
+
+/* Algorithm 8 (preconditioned proximal forward-backward, Sec. 3.2) with
+ * R = ||h||_1 + indicator(h >= 0): r_k = A^T Lambda (A h_k - g) and
+ * h_{k+1} = prox_{s lambda R}(h_k - s r_k) = max(h_k - s r_k - s lambda, 0).
+ * stats[4 k + {0,1,2,3}] = objective 1/2 <Lambda r, r> + lambda ||h_k||_1,
+ * ||A h_k - g||_2, ||h_{k+1} - h_k|| / max(||h_k||, 1e-300), ||h_{k+1}||_2.
+ * Returns the number of iterations run (stops early when tol > 0 and the
+ * relative change drops below tol). */
+int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, const double *g,
+           double lambda, double step, int iters, double tol, double *h, double *stats) {
+  ffo_setup_t s;
+  size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
+  setup(&s, n, T, cfl, nth, precond, c);
+  double *grad = malloc(n3 * sizeof(double)), *work3 = malloc(n3 * sizeof(double));
+  double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
+  int k;
+  for (k = 0; k < iters; ++k) {
+    data_gradient(&s, h, g, r, lr, grad, work3);
+    double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
+    for (size_t i = 0; i < n3; ++i) {
+      double f = h[i] - step * grad[i] - step * lambda;
+      double hn = f > 0.0 ? f : 0.0;
+      l1 += fabs(h[i]);
+      hh += h[i] * h[i];
+      dd += (hn - h[i]) * (hn - h[i]);
+      nn += hn * hn;
+      h[i] = hn;
+    }
+    double rel = sqrt(dd) / (sqrt(hh) > 1e-300 ? sqrt(hh) : 1e-300);
+    if (stats) {
+      stats[4 * k + 0] = 0.5 * dot(nd, lr, r) + lambda * l1;
+      stats[4 * k + 1] = sqrt(dot(nd, r, r));
+      stats[4 * k + 2] = rel;
+      stats[4 * k + 3] = sqrt(nn);
+    }
+    if (tol > 0.0 && rel < tol) {
+      ++k;
+      break;
+    }
+  }
+  free(grad);
+  free(work3);
+  free(r);
+  free(lr);
+  free(s.kappa);
+  return k;
+}

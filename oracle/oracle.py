@@ -1,0 +1,209 @@
+"""ctypes binding of the plain FP64 CPU oracle (``oracle/ffpat_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline / reference arm of ``bench.py`` use it; the product library never does.
+
+Every wrapper takes and returns float64 NumPy arrays in ``[z][y][x]`` (volumes)
+or ``[theta][z][xi]`` (projection data) layout.  The citations are to
+Haltmeier, Zangerl, Nuster, Nguyen (2019): wave model eq. (1)-(3), the X-ray
+transform eq. (4), the preconditioner / backprojection / adjoint of Sec. 3.1,
+and Algorithm 8 with its proximal map (Sec. 3.2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ffpat_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libffpat_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, OpenMP over planes)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+               "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.ffo_time_steps.restype = ctypes.c_int
+            L.ffo_time_steps.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, _D]
+            L.ffo_kappa.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D]
+            L.ffo_max.restype = ctypes.c_double
+            L.ffo_max.argtypes = [ctypes.c_size_t, _D]
+            L.ffo_wave.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
+            L.ffo_wave_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
+            L.ffo_angles.argtypes = [ctypes.c_int, _D, _D]
+            L.ffo_ray_samples.restype = ctypes.c_int
+            L.ffo_ray_samples.argtypes = [ctypes.c_int]
+            L.ffo_sample_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _I32, _I32, _D]
+            L.ffo_project.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_backproject.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_ramp_tap.restype = ctypes.c_double
+            L.ffo_ramp_tap.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.ffo_ramp.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_forward.restype = ctypes.c_int
+            L.ffo_forward.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      _D, _D, _D]
+            L.ffo_adjoint.restype = ctypes.c_int
+            L.ffo_adjoint.argtypes = L.ffo_forward.argtypes
+            L.ffo_power.restype = ctypes.c_double
+            L.ffo_power.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, _D, _D, ctypes.c_int]
+            L.ffo_fb.restype = ctypes.c_int
+            L.ffo_fb.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                 ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_double, _D, _D]
+            L.ffo_num_threads.restype = ctypes.c_int
+            L.ffo_set_num_threads.argtypes = [ctypes.c_int]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().ffo_num_threads()
+
+
+def set_num_threads(k: int) -> None:
+    lib().ffo_set_num_threads(int(k))
+
+
+def time_steps(n: int, T: float, cfl: float, cmax: float):
+    """(Nt, dt) of the leapfrog discretisation of eq. (1) up to time T."""
+    dt = ctypes.c_double()
+    nt = lib().ffo_time_steps(n, T, cfl, cmax, ctypes.byref(dt))
+    return nt, dt.value
+
+
+def kappa(n: int, dt: float, c) -> np.ndarray:
+    c = _f64(c)
+    out = np.empty_like(c)
+    lib().ffo_kappa(n, dt, _p(c), _p(out))
+    return out
+
+
+def wave(kap, h, nt: int) -> np.ndarray:
+    """W_T h for an explicit step count nt (kappa already holds dt)."""
+    kap, h = _f64(kap), _f64(h)
+    out = np.empty_like(h)
+    lib().ffo_wave(h.shape[0], int(nt), _p(kap), _p(h), _p(out))
+    return out
+
+
+def wave_adjoint(kap, g, nt: int) -> np.ndarray:
+    kap, g = _f64(kap), _f64(g)
+    out = np.empty_like(g)
+    lib().ffo_wave_adjoint(g.shape[0], int(nt), _p(kap), _p(g), _p(out))
+    return out
+
+
+def angles(nth: int):
+    cs = np.empty(nth)
+    sn = np.empty(nth)
+    lib().ffo_angles(nth, _p(cs), _p(sn))
+    return cs, sn
+
+
+def ray_samples(n: int) -> int:
+    return lib().ffo_ray_samples(n)
+
+
+def sample_points(n: int, nth: int, jkm) -> tuple[np.ndarray, np.ndarray]:
+    """(i0, j0) corners and (fx, fy) fractions of the ray samples (j, k, m)."""
+    jkm = np.ascontiguousarray(jkm, dtype=np.int32).reshape(-1, 3)
+    ij = np.empty((jkm.shape[0], 2), dtype=np.int32)
+    f = np.empty((jkm.shape[0], 2), dtype=np.float64)
+    lib().ffo_sample_points(n, nth, jkm.shape[0], jkm.ctypes.data_as(_I32),
+                            ij.ctypes.data_as(_I32), _p(f))
+    return ij, f
+
+
+def project(p, nth: int) -> np.ndarray:
+    p = _f64(p)
+    n = p.shape[0]
+    g = np.empty((nth, n, n))
+    lib().ffo_project(n, nth, _p(p), _p(g))
+    return g
+
+
+def backproject(g, n: int) -> np.ndarray:
+    g = _f64(g)
+    out = np.empty((n, n, n))
+    lib().ffo_backproject(n, g.shape[0], _p(g), _p(out))
+    return out
+
+
+def ramp_tap(n: int, d: int) -> float:
+    return lib().ffo_ramp_tap(n, d)
+
+
+def ramp(r) -> np.ndarray:
+    r = _f64(r)
+    out = np.empty_like(r)
+    lib().ffo_ramp(r.shape[1], r.shape[0], _p(r), _p(out))
+    return out
+
+
+def forward(c, h, T: float, nth: int, cfl: float = 0.3) -> np.ndarray:
+    """g = P W_T h (Problem 1, full data)."""
+    c, h = _f64(c), _f64(h)
+    n = h.shape[0]
+    g = np.empty((nth, n, n))
+    lib().ffo_forward(n, T, cfl, nth, _p(c), _p(h), _p(g))
+    return g
+
+
+def adjoint(c, g, T: float, cfl: float = 0.3) -> np.ndarray:
+    """h = W_T^T P^T g."""
+    c, g = _f64(c), _f64(g)
+    n = c.shape[0]
+    h = np.empty((n, n, n))
+    lib().ffo_adjoint(n, T, cfl, g.shape[0], _p(c), _p(g), _p(h))
+    return h
+
+
+def power(c, v0, T: float, nth: int, precond: int = 0, iters: int = 20, cfl: float = 0.3) -> float:
+    """Largest eigenvalue of A^T Lambda A by power iteration from v0."""
+    c, v0 = _f64(c), _f64(v0)
+    return lib().ffo_power(c.shape[0], T, cfl, nth, precond, _p(c), _p(v0), iters)
+
+
+def fb(c, g, T: float, lam: float, step: float, iters: int, h0=None, precond: int = 0,
+       tol: float = 0.0, cfl: float = 0.3):
+    """Algorithm 8 with R = l1 + positivity.  Returns (h, stats[k, 4], iters_done)."""
+    c, g = _f64(c), _f64(g)
+    n = c.shape[0]
+    h = np.zeros((n, n, n)) if h0 is None else _f64(h0).copy()
+    stats = np.zeros((max(iters, 1), 4))
+    k = lib().ffo_fb(n, T, cfl, g.shape[0], precond, _p(c), _p(g), lam, step, iters, tol,
+                     _p(h), _p(stats))
+    return h, stats[:k], k
