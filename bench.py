@@ -1,0 +1,338 @@
+"""Benchmark of the hot path: iterations of Algorithm 8 (one-step FB) on the
+single-instance 128^3 workload (90 angles, T = 1.2, FP32-Kahan wavefields).
+
+One step = one FB iteration = W (333 leapfrog steps) + P + residual + P^T +
+W^T (333 steps) + the fused prox update with FP64 norms.  The metric is
+voxel-steps per second (2 Nt N^3 per iteration over the device time), with
+FB iterations per second alongside.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload cfg2|cfg5|cfg1] [--precision fp32-kahan|fp32|fp64]
+
+Multi-GPU: the problem does not shard across GPUs in this build; N GPUs run N
+independent replicas (one reconstruction each) and `value` is the sum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "cfg2": dict(cfg=2, label="single solve N=128^3, 90 angles, T=1.2, 20 balls, GRF sound speed"),
+    "cfg5": dict(cfg=5, label="large solve N=384^3, 180 angles, T=1.5, ramp-preconditioned"),
+    "cfg1": dict(cfg=1, label="small solve N=32^3, 24 angles, T=1"),
+}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ffpat_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        finally:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_problem(args):
+    from paper_1901_06503_gb300 import ffpat as F
+    from paper_1901_06503_gb300.inputs import config
+    wl = WORKLOADS[args.workload]
+    w = config(wl["cfg"])
+    prec = {"fp32-kahan": F.FP32_KAHAN, "fp32": F.FP32, "fp64": F.FP64}[args.precision]
+    prob = F.problem(w.n, w.T, w.n_angles, prec, w.precond)
+    return w, wl, prob
+
+
+def oracle_sample(w, seconds_target=10.0):
+    """Time the oracle's wave operator (the dominant loop) on the workload's
+    grid for a bounded number of leapfrog steps; returns voxel-steps/s."""
+    import numpy as np
+    import oracle.oracle as o
+    nt, dt = o.time_steps(w.n, w.T, w.cfl, float(w.c.max()))
+    kap = o.kappa(w.n, dt, w.c)
+    t0 = time.perf_counter()
+    o.wave(kap, w.h, 2)
+    probe = time.perf_counter() - t0
+    steps = int(max(2, min(nt, seconds_target / max(probe / 2, 1e-6))))
+    t0 = time.perf_counter()
+    out = o.wave(kap, w.h, steps)
+    el = time.perf_counter() - t0
+    assert np.isfinite(out).all()
+    return steps * float(w.n) ** 3 / el, steps, el, o.num_threads()
+
+
+def run_reference(args):
+    world, rank, local = dist_init(args)
+    if rank != 0:
+        return 0
+    import oracle.oracle as o
+    o.build()
+    w, wl, prob = make_problem(args)
+    for _ in range(args.warmup):
+        oracle_sample(w, seconds_target=1.0)
+    vals, total_vs, total_s = [], 0.0, 0.0
+    for _ in range(args.steps):
+        v, steps, el, cores = oracle_sample(w, seconds_target=args.ref_seconds)
+        total_vs += steps * float(w.n) ** 3
+        total_s += el
+    value = total_vs / total_s
+    line = {
+        "impl": "reference", "metric": "voxel-steps/s", "value": value, "unit": "voxel-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["label"], "n": w.n, "n_angles": w.n_angles, "T": w.T},
+        "cpu_baseline": {"value": value, "unit": "voxel-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 CPU oracle wave operator W, {steps} leapfrog steps on "
+                                   f"the {w.n}^3 grid per step (the FB iteration's dominant loop)"},
+        "e2e": {"value": value, "unit": "voxel-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    from paper_1901_06503_gb300.inputs import add_noise
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build_lib.build()
+    F.lib()
+    w, wl, prob = make_problem(args)
+    dt = F.torch_dtype(prob)
+    c = torch.as_tensor(w.c, device=dev).to(dt)
+    h_true = torch.as_tensor(w.h, device=dev).to(dt)
+    # synthetic data g = A h + noise, computed by the library in FP64
+    p64 = F.problem(w.n, w.T, w.n_angles, F.FP64, w.precond)
+    g64 = F.forward(p64, torch.as_tensor(w.c, device=dev), torch.as_tensor(w.h, device=dev))
+    g = torch.as_tensor(add_noise(g64.cpu().numpy(), w.noise, w.noise_rel), device=dev).to(dt)
+    del g64
+    ws = F.workspace(prob, dev)
+    nt, dtime, _ = F.problem_info(prob, float(w.c.astype(np.float32).max()
+                                              if prob.precision != F.FP64 else w.c.max()))
+    v0 = torch.ones_like(h_true)
+    L = F.opnorm(prob, c, v0, iters=20, ws=ws)
+    step = 1.0 / L
+    h = torch.zeros_like(h_true)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        F.fb_solve(prob, c, g, w.lam, step, 1, h=h, ws=ws, history=False)
+    torch.cuda.synchronize()
+
+    # ---- timed region: exactly K FB iterations, L2 flushed between them
+    F.profile_enable(True)
+    F.profile_read()
+    launches0 = F.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            F.fb_solve(prob, c, g, w.lam, step, 1, h=h, ws=ws, history=False)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(world)
+    prof = F.profile_read()
+    launches = F.launch_count() - launches0
+    F.profile_enable(False)
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    dev_ms = max_over_ranks(dev_ms, world, dev)
+    vs_per_iter = 2.0 * nt * float(w.n) ** 3
+    value = world * args.steps * vs_per_iter / (dev_ms / 1e3)
+    clocks = clk.summary()
+
+    # ---- end to end through the public API with host buffers
+    c_h = torch.as_tensor(w.c).to(dt).pin_memory()
+    g_h = g.cpu().pin_memory()
+    h_h = torch.zeros_like(h_true, device="cpu").pin_memory()
+    out_h = torch.empty_like(h_h).pin_memory()
+    c_d, g_d, h_d = torch.empty_like(c), torch.empty_like(g), torch.empty_like(h)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        c_d.copy_(c_h, non_blocking=True)
+        g_d.copy_(g_h, non_blocking=True)
+        h_d.copy_(h_h, non_blocking=True)
+        F.fb_solve(prob, c_d, g_d, w.lam, step, 1, h=h_d, ws=ws, history=False)
+        out_h.copy_(h_d, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    esz = 8 if prob.precision == F.FP64 else 4
+    h2d = (2 * w.n**3 + w.n_angles * w.n**2) * esz
+    d2h = w.n**3 * esz
+
+    hbm, src = peaks()
+    achieved = prof["step_bytes"] / (prof["step_ms"] / 1e3) / 1e9 if prof["step_ms"] > 0 else None
+    launch_ms = prof["step_ms"] / max(prof["step_launches"], 1)
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, steps, el, cores = oracle_sample(w, seconds_target=args.ref_seconds)
+        cpu = {"value": v, "unit": "voxel-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 CPU oracle wave operator W: {steps} leapfrog steps on the "
+                         f"{w.n}^3 grid ({el:.1f} s)"}
+    bpp = {F.FP64: 32, F.FP32: 16, F.FP32_KAHAN: 28}[prob.precision]
+    line = {
+        "metric": "voxel-steps/s", "value": value, "unit": "voxel-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {F.FP64: "f64", F.FP32: "f32", F.FP32_KAHAN: "f32"}[prob.precision],
+        "data": "synthetic",
+        "config": {"workload": wl["label"], "n": w.n, "n_angles": w.n_angles, "T": w.T,
+                   "nt": nt, "precision": F.PRECISION_NAMES[prob.precision],
+                   "fb_iteration": "W + P + residual + P^T + W^T + prox update",
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fb_iters_per_s": world * args.steps / (dev_ms / 1e3),
+        "wall_s": wall,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_source": f"{src} hbm_gbs", "kernel": "leapfrog step",
+                     "bytes_per_point_step": bpp, "launch_ms": launch_ms,
+                     "launches_timed": prof["step_launches"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * vs_per_iter / e2e_s, "unit": "voxel-steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
+    ap.add_argument("--precision", choices=["fp32-kahan", "fp32", "fp64"], default="fp32-kahan")
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * ffpat.h -- C ABI of the GB300 (sm_103a) library for one-step full-field
+ * photoacoustic tomography with a variable sound speed (Haltmeier, Zangerl,
+ * Nuster, Nguyen, "Photoacoustic image reconstruction from full field data in
+ * heterogeneous media", 2019).
+ *
+ * Model (Sec. 2.1, eq. (1)-(3)): p_tt = c(x)^2 Delta p on [-1,1]^3,
+ * p(.,0) = h, p_t(.,0) = 0; W h = p(., T).  Data (eq. (4), Problem 1 with full
+ * data): g = P W h, where P takes line integrals in every horizontal plane
+ * z = const over the directions theta_j = pi j / n_angles, j < n_angles.
+ *
+ * Discretisation (fixed by this library):
+ *   grid     N^3 cell-centred points, x_i = -1 + (i + 1/2) dx, dx = 2/N;
+ *            volumes are [z][y][x] with x fastest, N^3 elements;
+ *   time     Nt = ceil(T c_max / (cfl dx) (1 - 1e-12)), dt = T / Nt,
+ *            kappa = (c dt / dx)^2; p^1 = p^0 + kappa L4 p^0 / 2 and
+ *            p^{n+1} = 2 p^n - p^{n-1} + kappa L4 p^n, L4 the fourth-order
+ *            central Laplacian with zero ghost values outside the box;
+ *   rays     detector xi_k = -1 + (k + 1/2) dx, k < N; samples
+ *            s_m = (m + 1/2 - Ns/2) dx, m < Ns = 2 ceil(N / sqrt 2), each
+ *            sampled bilinearly (zero outside the grid) at
+ *            xi_k theta + s_m theta_perp, theta_perp = (-sin, cos);
+ *   data     g[j][l][k] = dx sum_m B(p[l]; ...), layout [theta][z][xi],
+ *            n_angles * N * N elements.
+ * The adjoint entry points apply the exact matrix transposes of these
+ * discrete operators, so <A h, g> = <h, A^T g> up to rounding.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, of element type
+ *     double when problem.precision == FFPAT_FP64 and float otherwise.  The
+ *     library keeps no reference to them after the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is queued on it; unless stated otherwise an entry point
+ *     returns once the work is queued, and the caller synchronises the stream.
+ *   - `ws` is caller-owned device scratch of at least
+ *     ffpat_workspace_bytes(problem) bytes, 256-byte aligned; its contents on
+ *     entry do not matter.  Two calls that run concurrently need two
+ *     workspaces.
+ *   - Return value: FFPAT_OK (0) or a negative ffpat_status.  On error,
+ *     ffpat_last_error() (per host thread) describes it.  No call aborts the
+ *     process and no C++ exception crosses this boundary.
+ */
+#ifndef FFPAT_H
+#define FFPAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FFPAT_OK = 0,
+  FFPAT_EINVAL = -1,    /* invalid argument (sizes, c <= 0 or not finite, CFL > 1/2, ...) */
+  FFPAT_ENOMEM = -2,    /* workspace too small or allocation refused */
+  FFPAT_ECUDA = -3,     /* a CUDA runtime call failed */
+  FFPAT_EBUSY = -4,     /* server queue full */
+  FFPAT_ETIMEDOUT = -5, /* a bounded wait ran out */
+  FFPAT_PENDING = 1     /* server request not finished yet */
+} ffpat_status;
+
+typedef enum {
+  FFPAT_FP64 = 0,      /* double everywhere */
+  FFPAT_FP32 = 1,      /* float wavefields, three-term leapfrog */
+  FFPAT_FP32_KAHAN = 2 /* float wavefields, increment form with a Kahan-compensated position update */
+} ffpat_precision;
+
+typedef enum {
+  FFPAT_PRECOND_NONE = 0, /* Lambda = I (Algorithm 7 / 8 without preconditioning) */
+  FFPAT_PRECOND_RAMP = 1  /* Lambda: F Lambda Phi = |omega| / (4 pi) F Phi along xi (Sec. 3.1) */
+} ffpat_precond;
+
+/* Problem statement (Problem 1 of Sec. 2.1 with full data). */
+typedef struct {
+  int32_t n;         /* grid points per axis N (1..2048); N^3 volume, N detectors, N planes */
+  double T;          /* final time T > 0 */
+  double cfl;        /* dt <= cfl dx / c_max; 0 < cfl <= 0.5 (stability of L4 leapfrog) */
+  int32_t n_angles;  /* number of projection directions, >= 1 */
+  int32_t precision; /* ffpat_precision */
+  int32_t precond;   /* ffpat_precond (used by ffpat_fb_solve and ffpat_opnorm) */
+} ffpat_problem;
+
+/* Per-solve summary of Algorithm 8.  objective = 1/2 <Lambda r, r> + lambda ||h_k||_1
+ * and resid_norm = ||r||_2 with r = A h_k - g, both for the last iteration's
+ * input h_k; rel_change = ||h_{k+1} - h_k|| / max(||h_k||, 1e-300). */
+typedef struct {
+  int32_t iters_done;
+  double objective;
+  double resid_norm;
+  double rel_change;
+  double step;      /* step size s actually used */
+  double opnorm_sq; /* power-iteration estimate of ||Lambda^1/2 A||^2 (0 if not run) */
+} ffpat_fb_stats;
+
+/* Description of the last error on this host thread ("" if none). */
+const char *ffpat_last_error(void);
+
+/* Library version string. */
+const char *ffpat_version(void);
+
+/* Workspace bytes needed by every entry point below for this problem
+ * (0 if the problem is invalid; see ffpat_last_error). */
+size_t ffpat_workspace_bytes(const ffpat_problem *problem);
+
+/* Host-only: time discretisation for a given c_max (the wave model of Sec. 2.1):
+ * writes Nt, dt and Ns (ray samples).  Any output pointer may be NULL. */
+int ffpat_problem_info(const ffpat_problem *problem, double c_max, int32_t *nt, double *dt,
+                       int32_t *n_samples);
+
+/* Host-only: the angle table theta_j = pi j / n_angles as cos_sin[2 j] = cos,
+ * cos_sin[2 j + 1] = sin (host libm, double), n_angles entries. */
+int ffpat_debug_tables(const ffpat_problem *problem, double *cos_sin);
+
+/* Device: index arithmetic of `count` ray samples (j, k, m) given as int32
+ * triples in jkm (device); writes the lower-left bilinear corner (i0, j0) to
+ * ij and the fractions (fx, fy) to f (device, double).  This is the very
+ * device function the projection of an FP64 problem uses. */
+int ffpat_debug_samples(const ffpat_problem *problem, int32_t count, const int32_t *jkm,
+                        int32_t *ij, double *f, void *stream);
+
+/* g = P W h  (eq. (4) composed with W of eq. (3)).  c, h: N^3; g: n_angles N^2. */
+int ffpat_forward(const ffpat_problem *problem, const void *c, const void *h, void *g, void *ws,
+                  size_t ws_bytes, void *stream);
+
+/* h = W^T P^T g: the exact transpose of ffpat_forward (the discrete form of
+ * W_T^* X^* of Sec. 3.1, with the sound speed inside the Laplacian). */
+int ffpat_adjoint(const ffpat_problem *problem, const void *c, const void *g, void *h, void *ws,
+                  size_t ws_bytes, void *stream);
+
+/* out = W in (transpose = 0) or W^T in (transpose = 1); N^3 each (eq. (3)). */
+int ffpat_wave(const ffpat_problem *problem, const void *c, const void *in, void *out,
+               int32_t transpose, void *ws, size_t ws_bytes, void *stream);
+
+/* g = P p (eq. (4)); p: N^3, g: n_angles N^2.  No workspace. */
+int ffpat_project(const ffpat_problem *problem, const void *p, void *g, void *stream);
+
+/* h = P^T g, the exact transpose of ffpat_project (backprojection X^* of Sec. 3.1). */
+int ffpat_backproject(const ffpat_problem *problem, const void *g, void *h, void *stream);
+
+/* out = Lambda r along every detector row (Sec. 3.1): linear convolution with
+ * t_0 = 1/(8 dxi), t_d = -1/(2 pi^2 d^2 dxi) for odd d, 0 for even d != 0. */
+int ffpat_ramp(const ffpat_problem *problem, const void *r, void *out, void *stream);
+
+/* Power iteration v <- A^T Lambda A v / ||.|| from v0 (device, N^3) for `iters`
+ * steps; *opnorm_sq = the estimate of the largest eigenvalue of A^T Lambda A.
+ * Synchronises the stream. */
+int ffpat_opnorm(const ffpat_problem *problem, const void *c, const void *v0, int32_t iters,
+                 double *opnorm_sq, void *ws, size_t ws_bytes, void *stream);
+
+/* Algorithm 8 (Sec. 3.2) with R = ||h||_1 + indicator(h >= 0):
+ *   r_k = A^T Lambda (A h_k - g),  h_{k+1} = max(h_k - s r_k - s lambda, 0).
+ * h_inout: h_0 on entry (zeros per Algorithm 8), the last iterate on return.
+ * step <= 0: s = 1 / L with L from 20 power iterations from a fixed
+ * pseudo-random start.  tol > 0 stops once rel_change < tol (one 8-byte
+ * device-to-host read per iteration); tol = 0 runs max_iters with no host
+ * round trip inside the loop.  history (host, nullable): 4 doubles per
+ * iteration (objective, resid_norm, rel_change, ||h_{k+1}||).
+ * Synchronises the stream before returning. */
+int ffpat_fb_solve(const ffpat_problem *problem, const void *c, const void *g, double lambda,
+                   double step, int32_t max_iters, double tol, void *h_inout,
+                   ffpat_fb_stats *stats, double *history, void *ws, size_t ws_bytes,
+                   void *stream);
+
+/* Instrumentation.  While enabled, every wave time loop records CUDA events on
+ * its stream around its leapfrog launches; ffpat_profile_read synchronises
+ * those events and returns the number of leapfrog launches timed, their total
+ * milliseconds, and the algorithmic HBM bytes they move (one pass per step:
+ * 16 B FP32, 28 B FP32-Kahan, 32 B FP64 per grid point).  Reading resets. */
+typedef struct {
+  int64_t step_launches;
+  double step_ms;
+  double step_bytes;
+  int64_t kernel_launches; /* all kernels this library launched since the last reset */
+} ffpat_profile;
+int ffpat_profile_enable(int32_t on);
+int ffpat_profile_read(ffpat_profile *out);
+
+/* Total kernels launched by this library since load (monotone counter). */
+int64_t ffpat_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFPAT_H */

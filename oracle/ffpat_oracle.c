@@ -265,6 +265,33 @@ void ffo_project(int n, int nth, const double *p, double *g) {
   free(sn);
 }
 
+/* selected rays of ffo_project: out[t] = g[j][l][k] for jlk[3t..3t+2] = (j, l, k);
+ * the same loop as ffo_project, restricted, for spot checks on large grids */
+void ffo_project_rays(int n, int nth, const double *p, int count, const int32_t *jlk, double *out) {
+  double *cs = malloc(nth * sizeof(double)), *sn = malloc(nth * sizeof(double));
+  int ns = ffo_ray_samples(n);
+  double ds = 2.0 / n;
+  ffo_angles(nth, cs, sn);
+  for (int t = 0; t < count; ++t) {
+    int j = jlk[3 * t], l = jlk[3 * t + 1], k = jlk[3 * t + 2];
+    const double *slice = p + (size_t)l * n * n;
+    double acc = 0.0;
+    for (int m = 0; m < ns; ++m) {
+      int i0, j0;
+      double fx, fy;
+      sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+      double b = (1.0 - fx) * (1.0 - fy) * slice_at(slice, n, j0, i0) +
+                 fx * (1.0 - fy) * slice_at(slice, n, j0, i0 + 1) +
+                 (1.0 - fx) * fy * slice_at(slice, n, j0 + 1, i0) +
+                 fx * fy * slice_at(slice, n, j0 + 1, i0 + 1);
+      acc += b;
+    }
+    out[t] = ds * acc;
+  }
+  free(cs);
+  free(sn);
+}
+
 static void scatter(double *slice, int n, int iy, int ix, double v) {
   if (ix < 0 || iy < 0 || ix >= n || iy >= n) return;
   slice[(size_t)iy * n + ix] += v;

@@ -59,6 +59,7 @@ def lib():
             L.ffo_ray_samples.argtypes = [ctypes.c_int]
             L.ffo_sample_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _I32, _I32, _D]
             L.ffo_project.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_project_rays.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _I32, _D]
             L.ffo_backproject.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
             L.ffo_ramp_tap.restype = ctypes.c_double
             L.ffo_ramp_tap.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -153,6 +154,15 @@ def project(p, nth: int) -> np.ndarray:
     g = np.empty((nth, n, n))
     lib().ffo_project(n, nth, _p(p), _p(g))
     return g
+
+
+def project_rays(p, nth: int, jlk) -> np.ndarray:
+    """g[j][l][k] of project() for the listed (j, l, k) only."""
+    p = _f64(p)
+    jlk = np.ascontiguousarray(jlk, dtype=np.int32).reshape(-1, 3)
+    out = np.empty(jlk.shape[0])
+    lib().ffo_project_rays(p.shape[0], nth, _p(p), jlk.shape[0], jlk.ctypes.data_as(_I32), _p(out))
+    return out
 
 
 def backproject(g, n: int) -> np.ndarray:

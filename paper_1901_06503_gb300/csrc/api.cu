@@ -1,0 +1,561 @@
+// api.cu -- the extern "C" boundary of the library (include/ffpat.h): argument
+// validation, workspace carve, the time loops of W and W^T, and the host
+// driver of Algorithm 8 (Sec. 3.2).
+//
+// The adjoint wave operator is applied as W^T = K^-1 W K with K = diag(kap):
+// W = T_Nt(I + K L4 / 2) is a polynomial in K L4 (the leapfrog with the zero-
+// velocity start step is the Chebyshev recurrence), so its transpose is the
+// same polynomial in L4 K = K^-1 (K L4) K.  One stencil kernel therefore
+// serves both directions; the K scalings are fused into the backprojection
+// (on entry) and the gradient step (on exit).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace ffpat {
+
+static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_prof_launches{0};
+static std::atomic<int> g_prof_on{0};
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  long long steps;
+  double bytes;
+};
+static std::mutex g_prof_mu;
+static std::vector<ProfRec> g_prof;
+
+void count_launch(int k) {
+  g_launches += k;
+  if (g_prof_on.load(std::memory_order_relaxed)) g_prof_launches += k;
+}
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int check_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(FFPAT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return FFPAT_OK;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(FFPAT_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)
+
+#define TRY(expr)                \
+  do {                           \
+    const int r_ = (expr);       \
+    if (r_ != FFPAT_OK) return r_; \
+  } while (0)
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Validate the problem and fill the size fields of the plan.
+static int validate(const ffpat_problem* pr, Plan& pl) {
+  if (!pr) return fail(FFPAT_EINVAL, "problem is NULL");
+  if (pr->n < 1 || pr->n > 2048) return fail(FFPAT_EINVAL, "n = %d outside [1, 2048]", pr->n);
+  if (!(pr->T > 0.0) || !isfinite(pr->T)) return fail(FFPAT_EINVAL, "T must be finite and > 0");
+  if (!(pr->cfl > 0.0) || !(pr->cfl <= 0.5))
+    return fail(FFPAT_EINVAL, "cfl = %g outside (0, 0.5] (leapfrog stability of L4)", pr->cfl);
+  if (pr->n_angles < 1 || pr->n_angles > 65535)
+    return fail(FFPAT_EINVAL, "n_angles = %d outside [1, 65535]", pr->n_angles);
+  if (pr->precision < FFPAT_FP64 || pr->precision > FFPAT_FP32_KAHAN)
+    return fail(FFPAT_EINVAL, "unknown precision %d", pr->precision);
+  if (pr->precond < FFPAT_PRECOND_NONE || pr->precond > FFPAT_PRECOND_RAMP)
+    return fail(FFPAT_EINVAL, "unknown preconditioner %d", pr->precond);
+  pl.n = pr->n;
+  pl.nth = pr->n_angles;
+  pl.ns = 2 * (int)ceil((double)pr->n / sqrt(2.0));
+  pl.prec = pr->precision;
+  pl.precond = pr->precond;
+  pl.T = pr->T;
+  pl.cfl = pr->cfl;
+  pl.dx = 2.0 / pr->n;
+  pl.n3 = (size_t)pl.n * pl.n * pl.n;
+  pl.nd = (size_t)pl.nth * pl.n * pl.n;
+  pl.esize = pl.prec == FFPAT_FP64 ? 8 : 4;
+  return FFPAT_OK;
+}
+
+static int nstate(const Plan& pl) { return pl.prec == FFPAT_FP32_KAHAN ? 4 : 2; }
+
+// Carve the workspace (ws == nullptr: size only).
+static size_t carve(Plan& pl, void* ws) {
+  char* b = (char*)ws;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = b ? (void*)(b + off) : nullptr;
+    off += up256(bytes);
+    return p;
+  };
+  const size_t vol = pl.n3 * pl.esize, dat = pl.nd * pl.esize;
+  pl.kap = take(vol);
+  for (int i = 0; i < 4; ++i) pl.s[i] = i < nstate(pl) ? take(vol) : nullptr;
+  pl.x = take(vol);
+  pl.v = take(vol);
+  pl.r = take(dat);
+  pl.r2 = take(dat);
+  pl.partials = (double*)take(sizeof(double) * kNumQuant * kReduceBlocks);
+  pl.scal = (double*)take(sizeof(double) * kScal);
+  pl.hist = (double*)take(sizeof(double) * 8 * kMaxHist);
+  pl.tab = (double*)take(sizeof(double) * 2 * pl.nth);
+  pl.tabf = (float*)take(sizeof(float) * 2 * pl.nth);
+  return off;
+}
+
+static int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes) {
+  TRY(validate(pr, pl));
+  const size_t need = carve(pl, nullptr);
+  if (!ws) return fail(FFPAT_EINVAL, "workspace is NULL (%zu bytes needed)", need);
+  if (((uintptr_t)ws & 255) != 0) return fail(FFPAT_EINVAL, "workspace not 256-byte aligned");
+  if (ws_bytes < need)
+    return fail(FFPAT_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
+  carve(pl, ws);
+  return FFPAT_OK;
+}
+
+static void host_angles(int nth, std::vector<double>& cs_sn) {
+  cs_sn.resize(2 * (size_t)nth);
+  for (int j = 0; j < nth; ++j) {
+    const double th = (M_PI * j) / nth;
+    cs_sn[j] = cos(th);
+    cs_sn[nth + j] = sin(th);
+  }
+}
+
+static int upload_tables(Plan& pl, cudaStream_t st) {
+  std::vector<double> t;
+  host_angles(pl.nth, t);
+  std::vector<float> tf(t.size());
+  for (size_t i = 0; i < t.size(); ++i) tf[i] = (float)t[i];
+  CK(cudaMemcpyAsync(pl.tab, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(pl.tabf, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  // the host vectors die at return: make sure the copies have consumed them
+  CK(cudaStreamSynchronize(st));
+  return FFPAT_OK;
+}
+
+static int time_steps(const Plan& pl, double cmax, int* nt, double* dt) {
+  const double x = pl.T * cmax / (pl.cfl * pl.dx);
+  const double steps = ceil(x * (1.0 - 1e-12));
+  if (!(steps < 2e9)) return fail(FFPAT_EINVAL, "T c_max / (cfl dx) = %g steps is too many", x);
+  *nt = steps < 1.0 ? 1 : (int)steps;
+  *dt = pl.T / *nt;
+  return FFPAT_OK;
+}
+
+// c statistics -> Nt, dt, kappa (one device-to-host read of three doubles).
+static int setup_speed(Plan& pl, const void* c, cudaStream_t st) {
+  if (!c) return fail(FFPAT_EINVAL, "c is NULL");
+  TRY(launch_speed_stats(pl, c, pl.scal, st));
+  double h3[3];
+  CK(cudaMemcpyAsync(h3, pl.scal, sizeof h3, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h3[2] != 0.0)
+    return fail(FFPAT_EINVAL, "sound speed has %.0f entries that are not finite and > 0", h3[2]);
+  pl.cmax = h3[0];
+  TRY(time_steps(pl, pl.cmax, &pl.nt, &pl.dt));
+  TRY(launch_kappa(pl, c, st));
+  return FFPAT_OK;
+}
+
+static int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_bytes,
+                 cudaStream_t st) {
+  g_err[0] = 0;
+  TRY(attach(pr, pl, ws, ws_bytes));
+  TRY(upload_tables(pl, st));
+  TRY(setup_speed(pl, c, st));
+  return FFPAT_OK;
+}
+
+static double bytes_per_point(const Plan& pl) {
+  return pl.prec == FFPAT_FP64 ? 32.0 : (pl.prec == FFPAT_FP32 ? 16.0 : 28.0);
+}
+
+// W applied to `in` (N^3).  The result goes to `out` if non-null, else it
+// stays in a state buffer whose address is returned through *result.
+static int run_wave(const Plan& pl, const void* in, void* out, const void** result,
+                    cudaStream_t st) {
+  const int nt = pl.nt;
+  ProfRec rec{};
+  const bool prof = g_prof_on.load() && nt > 1;
+  if (pl.prec == FFPAT_FP32_KAHAN) {
+    void* d = pl.s[2];
+    void* e = pl.s[3];
+    void* first = (nt == 1 && out) ? out : pl.s[0];
+    TRY(launch_step_inc(pl, in, first, d, e, true, st));
+    const void* cur = first;
+    if (prof) {
+      CK(cudaEventCreate(&rec.a));
+      CK(cudaEventCreate(&rec.b));
+      CK(cudaEventRecord(rec.a, st));
+    }
+    for (int s = 1; s < nt; ++s) {
+      void* nxt = (s == nt - 1 && out) ? out : (cur == pl.s[0] ? pl.s[1] : pl.s[0]);
+      TRY(launch_step_inc(pl, cur, nxt, d, e, false, st));
+      cur = nxt;
+    }
+    if (prof) CK(cudaEventRecord(rec.b, st));
+    if (result) *result = cur;
+  } else {
+    void* A = pl.s[0];  // p^{n-1}
+    void* B = pl.s[1];  // p^n
+    if (nt == 1) {
+      void* dst = out ? out : B;
+      TRY(launch_step3(pl, in, nullptr, dst, true, nullptr, st));
+      if (result) *result = dst;
+    } else {
+      TRY(launch_step3(pl, in, nullptr, B, true, A, st));
+      if (prof) {
+        CK(cudaEventCreate(&rec.a));
+        CK(cudaEventCreate(&rec.b));
+        CK(cudaEventRecord(rec.a, st));
+      }
+      for (int s = 1; s < nt; ++s) {
+        void* dst = (s == nt - 1 && out) ? out : A;
+        TRY(launch_step3(pl, B, A, dst, false, nullptr, st));
+        A = B;
+        B = dst;
+      }
+      if (prof) CK(cudaEventRecord(rec.b, st));
+      if (result) *result = B;
+    }
+  }
+  if (prof) {
+    rec.steps = nt - 1;
+    rec.bytes = (double)(nt - 1) * (double)pl.n3 * bytes_per_point(pl);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.push_back(rec);
+  }
+  return FFPAT_OK;
+}
+
+// h = W^T P^T g  ->  x = K P^T g ; w = W x ; h = w / K
+static int apply_adjoint(const Plan& pl, const void* g, void* h, cudaStream_t st) {
+  TRY(launch_backproject(pl, g, pl.x, pl.kap, st));
+  const void* w = nullptr;
+  TRY(run_wave(pl, pl.x, nullptr, &w, st));
+  TRY(launch_kscale(pl, w, h, false, st));
+  return FFPAT_OK;
+}
+
+// x-domain result of A^T Lambda (A v - g) without the final 1/kap: returns the
+// state buffer holding W K P^T Lambda r.  dots[0] = <Lambda r, r>, dots[1] = <r, r>.
+static int data_gradient(const Plan& pl, const void* v, const void* g, const void** w,
+                         double* dots, cudaStream_t st) {
+  const void* pN = nullptr;
+  TRY(run_wave(pl, v, nullptr, &pN, st));
+  TRY(launch_project(pl, pN, pl.r, g, st));
+  const void* lr = pl.r;
+  if (pl.precond == FFPAT_PRECOND_RAMP) {
+    TRY(launch_ramp(pl, pl.r, pl.r2, st));
+    lr = pl.r2;
+  }
+  if (dots) TRY(launch_dot(pl, pl.nd, lr, pl.r, dots, st));
+  TRY(launch_backproject(pl, lr, pl.x, pl.kap, st));
+  TRY(run_wave(pl, pl.x, nullptr, w, st));
+  return FFPAT_OK;
+}
+
+// power iteration on A^T Lambda A, vector in pl.v; returns the estimate
+static int power_iteration(const Plan& pl, int iters, double* est, cudaStream_t st) {
+  double* sq = pl.scal + 8;
+  TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
+  TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
+  for (int it = 0; it < iters; ++it) {
+    const void* w = nullptr;
+    TRY(data_gradient(pl, pl.v, nullptr, &w, nullptr, st));
+    TRY(launch_kscale(pl, w, pl.v, false, st));
+    TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
+    TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
+  }
+  double h;
+  CK(cudaMemcpyAsync(&h, sq, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *est = sqrt(h);
+  return FFPAT_OK;
+}
+
+}  // namespace ffpat
+
+using namespace ffpat;
+
+extern "C" {
+
+const char* ffpat_last_error(void) { return g_err; }
+
+const char* ffpat_version(void) { return "ffpat 0.1 (sm_103a)"; }
+
+size_t ffpat_workspace_bytes(const ffpat_problem* problem) {
+  Plan pl;
+  if (validate(problem, pl) != FFPAT_OK) return 0;
+  return carve(pl, nullptr);
+}
+
+int ffpat_problem_info(const ffpat_problem* problem, double c_max, int32_t* nt, double* dt,
+                       int32_t* n_samples) {
+  Plan pl;
+  g_err[0] = 0;
+  TRY(validate(problem, pl));
+  if (!(c_max > 0.0) || !isfinite(c_max)) return fail(FFPAT_EINVAL, "c_max must be finite and > 0");
+  int n_t;
+  double d_t;
+  TRY(time_steps(pl, c_max, &n_t, &d_t));
+  if (nt) *nt = n_t;
+  if (dt) *dt = d_t;
+  if (n_samples) *n_samples = pl.ns;
+  return FFPAT_OK;
+}
+
+int ffpat_debug_tables(const ffpat_problem* problem, double* cos_sin) {
+  Plan pl;
+  g_err[0] = 0;
+  TRY(validate(problem, pl));
+  if (!cos_sin) return fail(FFPAT_EINVAL, "cos_sin is NULL");
+  std::vector<double> t;
+  host_angles(pl.nth, t);
+  for (int j = 0; j < pl.nth; ++j) {
+    cos_sin[2 * j] = t[j];
+    cos_sin[2 * j + 1] = t[pl.nth + j];
+  }
+  return FFPAT_OK;
+}
+
+int ffpat_debug_samples(const ffpat_problem* problem, int32_t count, const int32_t* jkm,
+                        int32_t* ij, double* f, void* stream) {
+  Plan pl;
+  g_err[0] = 0;
+  TRY(validate(problem, pl));
+  if (count < 0 || (count > 0 && (!jkm || !ij || !f)))
+    return fail(FFPAT_EINVAL, "bad sample list");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* tab = nullptr;
+  CK(cudaMallocAsync((void**)&tab, sizeof(double) * 2 * pl.nth, st));
+  pl.tab = tab;
+  std::vector<double> t;
+  host_angles(pl.nth, t);
+  CK(cudaMemcpyAsync(tab, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  TRY(launch_debug_samples(pl, count, jkm, ij, f, st));
+  CK(cudaFreeAsync(tab, st));
+  CK(cudaStreamSynchronize(st));
+  return FFPAT_OK;
+}
+
+int ffpat_forward(const ffpat_problem* problem, const void* c, const void* h, void* g, void* ws,
+                  size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  TRY(setup(problem, pl, c, ws, ws_bytes, st));
+  if (!h || !g) return fail(FFPAT_EINVAL, "h or g is NULL");
+  const void* pN = nullptr;
+  TRY(run_wave(pl, h, nullptr, &pN, st));
+  TRY(launch_project(pl, pN, g, nullptr, st));
+  return FFPAT_OK;
+}
+
+int ffpat_adjoint(const ffpat_problem* problem, const void* c, const void* g, void* h, void* ws,
+                  size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  TRY(setup(problem, pl, c, ws, ws_bytes, st));
+  if (!h || !g) return fail(FFPAT_EINVAL, "h or g is NULL");
+  TRY(apply_adjoint(pl, g, h, st));
+  return FFPAT_OK;
+}
+
+int ffpat_wave(const ffpat_problem* problem, const void* c, const void* in, void* out,
+               int32_t transpose, void* ws, size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  TRY(setup(problem, pl, c, ws, ws_bytes, st));
+  if (!in || !out) return fail(FFPAT_EINVAL, "in or out is NULL");
+  if (!transpose) {
+    TRY(run_wave(pl, in, out, nullptr, st));
+  } else {
+    TRY(launch_kscale(pl, in, pl.x, true, st));
+    const void* w = nullptr;
+    TRY(run_wave(pl, pl.x, nullptr, &w, st));
+    TRY(launch_kscale(pl, w, out, false, st));
+  }
+  return FFPAT_OK;
+}
+
+int ffpat_project(const ffpat_problem* problem, const void* p, void* g, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  g_err[0] = 0;
+  TRY(validate(problem, pl));
+  if (!p || !g) return fail(FFPAT_EINVAL, "p or g is NULL");
+  void* tabs = nullptr;
+  CK(cudaMallocAsync(&tabs, 24 * (size_t)pl.nth + 256, st));
+  pl.tab = (double*)tabs;
+  pl.tabf = (float*)((char*)tabs + 16 * (size_t)pl.nth);
+  std::vector<double> t;
+  host_angles(pl.nth, t);
+  std::vector<float> tf(t.begin(), t.end());
+  CK(cudaMemcpyAsync(pl.tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(pl.tabf, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, st));
+  TRY(launch_project(pl, p, g, nullptr, st));
+  CK(cudaFreeAsync(tabs, st));
+  CK(cudaStreamSynchronize(st));
+  return FFPAT_OK;
+}
+
+int ffpat_backproject(const ffpat_problem* problem, const void* g, void* h, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  g_err[0] = 0;
+  TRY(validate(problem, pl));
+  if (!h || !g) return fail(FFPAT_EINVAL, "g or h is NULL");
+  void* tabs = nullptr;
+  CK(cudaMallocAsync(&tabs, 24 * (size_t)pl.nth + 256, st));
+  pl.tab = (double*)tabs;
+  pl.tabf = (float*)((char*)tabs + 16 * (size_t)pl.nth);
+  std::vector<double> t;
+  host_angles(pl.nth, t);
+  std::vector<float> tf(t.begin(), t.end());
+  CK(cudaMemcpyAsync(pl.tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(pl.tabf, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, st));
+  TRY(launch_backproject(pl, g, h, nullptr, st));
+  CK(cudaFreeAsync(tabs, st));
+  CK(cudaStreamSynchronize(st));
+  return FFPAT_OK;
+}
+
+int ffpat_ramp(const ffpat_problem* problem, const void* r, void* out, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  g_err[0] = 0;
+  TRY(validate(problem, pl));
+  if (!r || !out) return fail(FFPAT_EINVAL, "r or out is NULL");
+  if (r == out) return fail(FFPAT_EINVAL, "ramp cannot run in place");
+  TRY(launch_ramp(pl, r, out, st));
+  return FFPAT_OK;
+}
+
+int ffpat_opnorm(const ffpat_problem* problem, const void* c, const void* v0, int32_t iters,
+                 double* opnorm_sq, void* ws, size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  TRY(setup(problem, pl, c, ws, ws_bytes, st));
+  if (!v0 || !opnorm_sq || iters < 1) return fail(FFPAT_EINVAL, "bad power-iteration arguments");
+  CK(cudaMemcpyAsync(pl.v, v0, pl.n3 * pl.esize, cudaMemcpyDeviceToDevice, st));
+  TRY(power_iteration(pl, iters, opnorm_sq, st));
+  return FFPAT_OK;
+}
+
+int ffpat_fb_solve(const ffpat_problem* problem, const void* c, const void* g, double lambda,
+                   double step, int32_t max_iters, double tol, void* h_inout,
+                   ffpat_fb_stats* stats, double* history, void* ws, size_t ws_bytes,
+                   void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  TRY(setup(problem, pl, c, ws, ws_bytes, st));
+  if (!g || !h_inout) return fail(FFPAT_EINVAL, "g or h is NULL");
+  if (max_iters < 0 || max_iters > kMaxHist)
+    return fail(FFPAT_EINVAL, "max_iters = %d outside [0, %d]", max_iters, kMaxHist);
+  if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(FFPAT_EINVAL, "lambda must be >= 0");
+  if (!(tol >= 0.0)) return fail(FFPAT_EINVAL, "tol must be >= 0");
+  double opn = 0.0;
+  if (!(step > 0.0)) {
+    TRY(launch_hash_fill(pl, pl.v, 0x5eed1901ull, st));
+    TRY(power_iteration(pl, 20, &opn, st));
+    if (!(opn > 0.0) || !isfinite(opn)) return fail(FFPAT_EINVAL, "operator norm estimate %g", opn);
+    step = 1.0 / opn;
+  }
+  if (!isfinite(step)) return fail(FFPAT_EINVAL, "step is not finite");
+  int k = 0;
+  for (; k < max_iters; ++k) {
+    double* hk = pl.hist + 8 * (size_t)k;
+    const void* w = nullptr;
+    TRY(data_gradient(pl, h_inout, g, &w, hk, st));
+    TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st));
+    if (tol > 0.0) {
+      double q[4];
+      CK(cudaMemcpyAsync(q, hk + 2, sizeof q, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      const double rel = sqrt(q[2]) / fmax(sqrt(q[1]), 1e-300);
+      if (rel < tol) {
+        ++k;
+        break;
+      }
+    }
+  }
+  std::vector<double> hh(8 * (size_t)(k > 0 ? k : 1), 0.0);
+  if (k > 0) CK(cudaMemcpyAsync(hh.data(), pl.hist, 8 * sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < k && history; ++i) {
+    const double* q = &hh[8 * (size_t)i];
+    history[4 * i + 0] = 0.5 * q[0] + lambda * q[2];
+    history[4 * i + 1] = sqrt(q[1]);
+    history[4 * i + 2] = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
+    history[4 * i + 3] = sqrt(q[5]);
+  }
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->iters_done = k;
+    stats->step = step;
+    stats->opnorm_sq = opn;
+    if (k > 0) {
+      const double* q = &hh[8 * (size_t)(k - 1)];
+      stats->objective = 0.5 * q[0] + lambda * q[2];
+      stats->resid_norm = sqrt(q[1]);
+      stats->rel_change = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
+    }
+  }
+  return FFPAT_OK;
+}
+
+int ffpat_profile_enable(int32_t on) {
+  g_prof_on = on ? 1 : 0;
+  return FFPAT_OK;
+}
+
+int ffpat_profile_read(ffpat_profile* out) {
+  g_err[0] = 0;
+  if (!out) return fail(FFPAT_EINVAL, "out is NULL");
+  std::vector<ProfRec> recs;
+  {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    recs.swap(g_prof);
+  }
+  memset(out, 0, sizeof *out);
+  int rc = FFPAT_OK;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    if (rc == FFPAT_OK) {
+      cudaError_t e = cudaEventSynchronize(r.b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+      if (e != cudaSuccess) rc = fail(FFPAT_ECUDA, "profile events: %s", cudaGetErrorString(e));
+    }
+    out->step_launches += r.steps;
+    out->step_ms += ms;
+    out->step_bytes += r.bytes;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  out->kernel_launches = g_prof_launches.exchange(0);
+  return rc;
+}
+
+int64_t ffpat_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,282 @@
+// fb.cu -- setup of the wave coefficients, elementwise passes and the fused
+// forward-backward update of Algorithm 8 (Sec. 3.2), with deterministic FP64
+// reductions.
+//
+// Every reduction runs on a fixed grid of kReduceBlocks CTAs with a grid-
+// stride loop; each CTA reduces its FP64 partial in a fixed shuffle tree and
+// writes it to `partials`; a single-CTA pass then sums the partials in a fixed
+// order.  Results are therefore bit-reproducible from run to run.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace ffpat {
+namespace {
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sm[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double sm[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  double t = -INFINITY;
+  if (w == 0) {
+    t = lane < (int)(blockDim.x >> 5) ? sm[lane] : -INFINITY;
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+  }
+  return t;
+}
+
+// sum `nq` rows of kReduceBlocks partials (fixed order) into dst[0..nq)
+__global__ void __launch_bounds__(kReduceThreads)
+    k_finalize(const double* __restrict__ partials, int nq, double* __restrict__ dst) {
+  for (int q = 0; q < nq; ++q) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kReduceBlocks; i += blockDim.x) acc += partials[q * kReduceBlocks + i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) dst[q] = acc;
+  }
+}
+
+// max c, -min c, count of invalid entries (not finite or <= 0)
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_speed_stats(const T* __restrict__ c, size_t len, double* __restrict__ partials) {
+  double mx = -INFINITY, mn = INFINITY, bad = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = (double)c[i];
+    if (!(v > 0.0) || !isfinite(v)) bad += 1.0;
+    mx = fmax(mx, v);
+    mn = fmin(mn, v);
+  }
+  mx = block_max(mx);
+  const double nmn = block_max(-mn);
+  bad = block_sum(bad);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = mx;
+    partials[kReduceBlocks + blockIdx.x] = nmn;
+    partials[2 * kReduceBlocks + blockIdx.x] = bad;
+  }
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+    k_speed_final(const double* __restrict__ partials, double* __restrict__ dst) {
+  double mx = -INFINITY, nmn = -INFINITY, bad = 0.0;
+  for (int i = threadIdx.x; i < kReduceBlocks; i += blockDim.x) {
+    mx = fmax(mx, partials[i]);
+    nmn = fmax(nmn, partials[kReduceBlocks + i]);
+    bad += partials[2 * kReduceBlocks + i];
+  }
+  mx = block_max(mx);
+  nmn = block_max(nmn);
+  bad = block_sum(bad);
+  if (threadIdx.x == 0) {
+    dst[0] = mx;
+    dst[1] = -nmn;
+    dst[2] = bad;
+  }
+}
+
+// kap = (c dt / dx)^2 / 12, evaluated in FP64 as ((c dt) / dx)^2 / 12
+template <typename T>
+__global__ void k_kappa(const T* __restrict__ c, T* __restrict__ kap, size_t len, double dt,
+                        double dx) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double r = (double)c[i] * dt / dx;
+    kap[i] = (T)(r * r / 12.0);
+  }
+}
+
+template <typename T>
+__global__ void k_kscale(const T* __restrict__ a, T* __restrict__ out, const T* __restrict__ kap,
+                         size_t len, bool mul) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = mul ? a[i] * kap[i] : a[i] / kap[i];
+}
+
+template <typename T>
+__global__ void k_scale_dev(const T* __restrict__ a, T* __restrict__ out, size_t len,
+                            const double* __restrict__ sq) {
+  const double s = 1.0 / sqrt(sq[0]);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (T)((double)a[i] * s);
+}
+
+// partials rows: 0 = sum a b, 1 = sum b b
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_dots(const T* __restrict__ a, const T* __restrict__ b, size_t len,
+           double* __restrict__ partials) {
+  double ab = 0.0, bb = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double x = (double)a[i], y = (double)b[i];
+    ab = fma(x, y, ab);
+    bb = fma(y, y, bb);
+  }
+  ab = block_sum(ab);
+  bb = block_sum(bb);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = ab;
+    partials[kReduceBlocks + blockIdx.x] = bb;
+  }
+}
+
+// Algorithm 8, second line, with R = ||.||_1 + indicator(>= 0):
+// grad = w / kap (the last division of W^T = K^-1 W K), h+ = max(h - s grad - s lambda, 0).
+// partial rows: 0 = sum |h|, 1 = sum h^2, 2 = sum (h+ - h)^2, 3 = sum h+^2
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_fb_update(T* __restrict__ h, const T* __restrict__ w, const T* __restrict__ kap, size_t len,
+                double step, double lambda, double* __restrict__ partials) {
+  double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
+  const T s = (T)step, sl = (T)(step * lambda);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T hv = h[i];
+    const T grad = w[i] / kap[i];
+    const T f = (hv - s * grad) - sl;
+    const T hn = f > T(0) ? f : T(0);
+    h[i] = hn;
+    const double hd = (double)hv, nd = (double)hn, df = nd - hd;
+    l1 += fabs(hd);
+    hh = fma(hd, hd, hh);
+    dd = fma(df, df, dd);
+    nn = fma(nd, nd, nn);
+  }
+  l1 = block_sum(l1);
+  hh = block_sum(hh);
+  dd = block_sum(dd);
+  nn = block_sum(nn);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = l1;
+    partials[kReduceBlocks + blockIdx.x] = hh;
+    partials[2 * kReduceBlocks + blockIdx.x] = dd;
+    partials[3 * kReduceBlocks + blockIdx.x] = nn;
+  }
+}
+
+// counter-based pseudo-random start vector (splitmix64 + Box-Muller)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+template <typename T>
+__global__ void k_hash_fill(T* __restrict__ out, size_t len, uint64_t seed) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed ^ (2 * i)), b = splitmix64(seed ^ (2 * i + 1));
+    const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
+    const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    out[i] = (T)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+  }
+}
+
+
+unsigned ew_blocks(size_t len) {
+  size_t b = (len + 255) / 256;
+  const size_t cap = 16 * kNumSMs;
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+int launch_speed_stats(const Plan& pl, const void* c, double* out3, cudaStream_t st) {
+  if (pl.prec == FFPAT_FP64)
+    k_speed_stats<double><<<kReduceBlocks, kReduceThreads, 0, st>>>((const double*)c, pl.n3, pl.partials);
+  else
+    k_speed_stats<float><<<kReduceBlocks, kReduceThreads, 0, st>>>((const float*)c, pl.n3, pl.partials);
+  k_speed_final<<<1, kReduceThreads, 0, st>>>(pl.partials, out3);
+  count_launch(2);
+  return check_launch(__func__);
+}
+
+int launch_kappa(const Plan& pl, const void* c, cudaStream_t st) {
+  const unsigned nb = ew_blocks(pl.n3);
+  if (pl.prec == FFPAT_FP64)
+    k_kappa<double><<<nb, 256, 0, st>>>((const double*)c, (double*)pl.kap, pl.n3, pl.dt, pl.dx);
+  else
+    k_kappa<float><<<nb, 256, 0, st>>>((const float*)c, (float*)pl.kap, pl.n3, pl.dt, pl.dx);
+  count_launch();
+  return check_launch(__func__);
+}
+
+int launch_kscale(const Plan& pl, const void* a, void* out, bool mul, cudaStream_t st) {
+  const unsigned nb = ew_blocks(pl.n3);
+  if (pl.prec == FFPAT_FP64)
+    k_kscale<double><<<nb, 256, 0, st>>>((const double*)a, (double*)out, (const double*)pl.kap, pl.n3, mul);
+  else
+    k_kscale<float><<<nb, 256, 0, st>>>((const float*)a, (float*)out, (const float*)pl.kap, pl.n3, mul);
+  count_launch();
+  return check_launch(__func__);
+}
+
+int launch_scale_dev(const Plan& pl, size_t len, const void* a, void* out, const double* s,
+                     cudaStream_t st) {
+  const unsigned nb = ew_blocks(len);
+  if (pl.prec == FFPAT_FP64)
+    k_scale_dev<double><<<nb, 256, 0, st>>>((const double*)a, (double*)out, len, s);
+  else
+    k_scale_dev<float><<<nb, 256, 0, st>>>((const float*)a, (float*)out, len, s);
+  count_launch();
+  return check_launch(__func__);
+}
+
+int launch_dot(const Plan& pl, size_t len, const void* a, const void* b, double* result,
+               cudaStream_t st) {
+  if (pl.prec == FFPAT_FP64)
+    k_dots<double><<<kReduceBlocks, kReduceThreads, 0, st>>>((const double*)a, (const double*)b, len, pl.partials);
+  else
+    k_dots<float><<<kReduceBlocks, kReduceThreads, 0, st>>>((const float*)a, (const float*)b, len, pl.partials);
+  k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 2, result);
+  count_launch(2);
+  return check_launch(__func__);
+}
+
+int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double lambda,
+                     double* dst, cudaStream_t st) {
+  if (pl.prec == FFPAT_FP64)
+    k_fb_update<double><<<kReduceBlocks, kReduceThreads, 0, st>>>(
+        (double*)h, (const double*)w, (const double*)pl.kap, pl.n3, step, lambda, pl.partials);
+  else
+    k_fb_update<float><<<kReduceBlocks, kReduceThreads, 0, st>>>(
+        (float*)h, (const float*)w, (const float*)pl.kap, pl.n3, step, lambda, pl.partials);
+  k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 4, dst);
+  count_launch(2);
+  return check_launch(__func__);
+}
+
+int launch_hash_fill(const Plan& pl, void* out, uint64_t seed, cudaStream_t st) {
+  const unsigned nb = ew_blocks(pl.n3);
+  if (pl.prec == FFPAT_FP64)
+    k_hash_fill<double><<<nb, 256, 0, st>>>((double*)out, pl.n3, seed);
+  else
+    k_hash_fill<float><<<nb, 256, 0, st>>>((float*)out, pl.n3, seed);
+  count_launch();
+  return check_launch(__func__);
+}
+
+}  // namespace ffpat

@@ -1,0 +1,74 @@
+// internal.cuh -- shared declarations of the ffpat CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/ffpat.h"
+
+namespace ffpat {
+
+constexpr int kNumSMs = 152;           // GB300: 2 dies x 76 SMs
+constexpr int kReduceBlocks = 4 * kNumSMs;  // fixed grid of every deterministic reduction
+constexpr int kReduceThreads = 256;
+constexpr int kNumQuant = 8;           // quantities one reduction pass can carry
+
+// Derived, validated problem plus the carve of the caller's workspace.
+struct Plan {
+  int n = 0, nth = 0, ns = 0, nt = 0, prec = 0, precond = 0;
+  double T = 0, cfl = 0, dx = 0, dt = 0, cmax = 0;
+  size_t n3 = 0, nd = 0, esize = 0;
+  // workspace carve (device)
+  void* kap = nullptr;    // kappa / 12 for every grid point
+  void* s[4] = {};        // wavefield state (2 buffers three-term form, 4 increment form)
+  void* x = nullptr;      // image-domain scratch (adjoint input / gradient)
+  void* v = nullptr;      // image-domain scratch (power iteration vector)
+  void* r = nullptr;      // data-domain scratch (residual)
+  void* r2 = nullptr;     // data-domain scratch (Lambda residual)
+  double* partials = nullptr;  // kNumQuant * kReduceBlocks doubles
+  double* scal = nullptr;      // small device scalars
+  double* hist = nullptr;      // per-iteration FB statistics (8 doubles / iteration, up to kMaxHist)
+  double* tab = nullptr;       // cos[nth], sin[nth] (double)
+  float* tabf = nullptr;       // cos[nth], sin[nth] (float)
+};
+constexpr int kMaxHist = 4096;
+constexpr int kScal = 64;
+
+// ---------------------------------------------------------------- launches --
+void count_launch(int k = 1);
+// FFPAT_OK, or FFPAT_ECUDA with the pending launch error recorded for ffpat_last_error()
+int check_launch(const char* what);
+
+// stencil.cu
+// three-term form.  start: out_p1 = p0 + kap*L(p0)/2 and copy_p0 = p0 (may be null)
+int launch_step3(const Plan& pl, const void* p, const void* qin, void* qout, bool start,
+                 void* copy_p0, cudaStream_t st);
+// increment form (FP32 only).  start: d = kap L(p)/2, e = Kahan carry, pout = p + d.
+int launch_step_inc(const Plan& pl, const void* pin, void* pout, void* d, void* e, bool start,
+                    cudaStream_t st);
+
+// xray.cu
+int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st);
+int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st);
+int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st);
+int launch_debug_samples(const Plan& pl, int count, const int32_t* jkm, int32_t* ij, double* f,
+                         cudaStream_t st);
+
+// fb.cu
+int launch_speed_stats(const Plan& pl, const void* c, double* out3, cudaStream_t st);
+int launch_kappa(const Plan& pl, const void* c, cudaStream_t st);
+// out[i] = a[i] * kap[i] (mul = true) or a[i] / kap[i]
+int launch_kscale(const Plan& pl, const void* a, void* out, bool mul, cudaStream_t st);
+// out[i] = a[i] * s  (s a device double)
+int launch_scale_dev(const Plan& pl, size_t len, const void* a, void* out, const double* s,
+                     cudaStream_t st);
+// scal[q] = deterministic FP64 dot products over `len` elements
+int launch_dot(const Plan& pl, size_t len, const void* a, const void* b, double* result,
+               cudaStream_t st);
+// FB update + partial norms; results land in dst[0..3]
+int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double lambda,
+                     double* dst, cudaStream_t st);
+int launch_hash_fill(const Plan& pl, void* out, uint64_t seed, cudaStream_t st);
+
+}  // namespace ffpat

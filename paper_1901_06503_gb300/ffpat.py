@@ -1,0 +1,304 @@
+"""Thin ctypes binding of the C ABI in ``include/ffpat.h`` (libffpat.so).
+
+Argument marshalling only: torch tensors provide device memory and the
+current CUDA stream; every step of the computation runs in the library's
+CUDA kernels.  There is no CPU fallback: a missing or unloadable library
+raises.
+
+Names follow the ABI (``ffpat_forward`` -> :func:`forward`, ...).  Volumes are
+``[z][y][x]`` tensors of shape (N, N, N); projection data are
+``[theta][z][xi]`` tensors of shape (n_angles, N, N); float64 for FFPAT_FP64
+problems, float32 otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libffpat.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ffpat.h")
+
+FP64, FP32, FP32_KAHAN = 0, 1, 2
+PRECOND_NONE, PRECOND_RAMP = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, PENDING = 0, -1, -2, -3, -4, -5, 1
+PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", FP32_KAHAN: "fp32-kahan"}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("T", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("n_angles", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("precond", ctypes.c_int32)]
+
+    def __repr__(self):
+        return (f"Problem(n={self.n}, T={self.T}, cfl={self.cfl}, n_angles={self.n_angles}, "
+                f"precision={PRECISION_NAMES.get(self.precision, self.precision)}, "
+                f"precond={self.precond})")
+
+
+class FBStats(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int32), ("objective", ctypes.c_double),
+                ("resid_norm", ctypes.c_double), ("rel_change", ctypes.c_double),
+                ("step", ctypes.c_double), ("opnorm_sq", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("step_launches", ctypes.c_int64), ("step_ms", ctypes.c_double),
+                ("step_bytes", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class FFPATError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ffpat error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+_PR = ctypes.POINTER(Problem)
+
+
+def _declare(L):
+    i32, i64, f64, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "ffpat_last_error": (ctypes.c_char_p, []),
+        "ffpat_version": (ctypes.c_char_p, []),
+        "ffpat_workspace_bytes": (sz, [_PR]),
+        "ffpat_problem_info": (ctypes.c_int, [_PR, f64, ctypes.POINTER(i32), ctypes.POINTER(f64),
+                                              ctypes.POINTER(i32)]),
+        "ffpat_debug_tables": (ctypes.c_int, [_PR, _P]),
+        "ffpat_debug_samples": (ctypes.c_int, [_PR, i32, _P, _P, _P, _P]),
+        "ffpat_forward": (ctypes.c_int, [_PR, _P, _P, _P, _P, sz, _P]),
+        "ffpat_adjoint": (ctypes.c_int, [_PR, _P, _P, _P, _P, sz, _P]),
+        "ffpat_wave": (ctypes.c_int, [_PR, _P, _P, _P, i32, _P, sz, _P]),
+        "ffpat_project": (ctypes.c_int, [_PR, _P, _P, _P]),
+        "ffpat_backproject": (ctypes.c_int, [_PR, _P, _P, _P]),
+        "ffpat_ramp": (ctypes.c_int, [_PR, _P, _P, _P]),
+        "ffpat_opnorm": (ctypes.c_int, [_PR, _P, _P, i32, ctypes.POINTER(f64), _P, sz, _P]),
+        "ffpat_fb_solve": (ctypes.c_int, [_PR, _P, _P, f64, f64, i32, f64, _P,
+                                          ctypes.POINTER(FBStats), _P, _P, sz, _P]),
+        "ffpat_profile_enable": (ctypes.c_int, [i32]),
+        "ffpat_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile)]),
+        "ffpat_launch_count": (i64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def lib():
+    """Load libffpat.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise FFPATError(ECUDA, f"{LIB_PATH} is missing: build it with "
+                                        "paper_1901_06503_gb300.build_lib.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Every function the public header declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ffpat_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc):
+    if rc < 0:
+        raise FFPATError(rc, lib().ffpat_last_error().decode())
+    return rc
+
+
+def problem(n: int, T: float, n_angles: int, precision: int = FP64, precond: int = 0,
+            cfl: float = 0.3) -> Problem:
+    return Problem(int(n), float(T), float(cfl), int(n_angles), int(precision), int(precond))
+
+
+def torch_dtype(prob: Problem):
+    import torch
+    return torch.float64 if prob.precision == FP64 else torch.float32
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, prob, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch_dtype(prob):
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {torch_dtype(prob)}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def vol_shape(prob):
+    return (prob.n, prob.n, prob.n)
+
+
+def data_shape(prob):
+    return (prob.n_angles, prob.n, prob.n)
+
+
+def workspace_bytes(prob: Problem) -> int:
+    b = lib().ffpat_workspace_bytes(ctypes.byref(prob))
+    if b == 0:
+        raise FFPATError(EINVAL, lib().ffpat_last_error().decode())
+    return int(b)
+
+
+def workspace(prob: Problem, device="cuda"):
+    import torch
+    return torch.empty(workspace_bytes(prob), dtype=torch.uint8, device=device)
+
+
+def _ws(prob, ws, device):
+    if ws is None:
+        ws = workspace(prob, device)
+    return ws, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel())
+
+
+def _empty(prob, shape, like):
+    import torch
+    return torch.empty(shape, dtype=torch_dtype(prob), device=like.device)
+
+
+def problem_info(prob: Problem, cmax: float):
+    nt, dt, ns = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().ffpat_problem_info(ctypes.byref(prob), cmax, ctypes.byref(nt), ctypes.byref(dt),
+                                    ctypes.byref(ns)))
+    return nt.value, dt.value, ns.value
+
+
+def debug_tables(prob: Problem) -> np.ndarray:
+    out = np.empty((prob.n_angles, 2), dtype=np.float64)
+    _check(lib().ffpat_debug_tables(ctypes.byref(prob), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def debug_samples(prob: Problem, jkm, device="cuda"):
+    import torch
+    jkm = torch.as_tensor(np.ascontiguousarray(jkm, dtype=np.int32).reshape(-1, 3), device=device)
+    ij = torch.empty((jkm.shape[0], 2), dtype=torch.int32, device=device)
+    f = torch.empty((jkm.shape[0], 2), dtype=torch.float64, device=device)
+    _check(lib().ffpat_debug_samples(ctypes.byref(prob), jkm.shape[0], _P(jkm.data_ptr()),
+                                     _P(ij.data_ptr()), _P(f.data_ptr()), _stream(None)))
+    return ij.cpu().numpy(), f.cpu().numpy()
+
+
+def forward(prob, c, h, g=None, ws=None, stream=None):
+    """g = P W h."""
+    g = _empty(prob, data_shape(prob), h) if g is None else g
+    ws, wp, wn = _ws(prob, ws, h.device)
+    _check(lib().ffpat_forward(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                               _dev(h, prob, vol_shape(prob), "h"),
+                               _dev(g, prob, data_shape(prob), "g"), wp, wn, _stream(stream)))
+    return g
+
+
+def adjoint(prob, c, g, h=None, ws=None, stream=None):
+    """h = W^T P^T g."""
+    h = _empty(prob, vol_shape(prob), g) if h is None else h
+    ws, wp, wn = _ws(prob, ws, g.device)
+    _check(lib().ffpat_adjoint(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                               _dev(g, prob, data_shape(prob), "g"),
+                               _dev(h, prob, vol_shape(prob), "h"), wp, wn, _stream(stream)))
+    return h
+
+
+def wave(prob, c, x, out=None, transpose=False, ws=None, stream=None):
+    """W x (or W^T x)."""
+    out = _empty(prob, vol_shape(prob), x) if out is None else out
+    ws, wp, wn = _ws(prob, ws, x.device)
+    _check(lib().ffpat_wave(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                            _dev(x, prob, vol_shape(prob), "in"),
+                            _dev(out, prob, vol_shape(prob), "out"), int(bool(transpose)), wp, wn,
+                            _stream(stream)))
+    return out
+
+
+def project(prob, p, g=None, stream=None):
+    g = _empty(prob, data_shape(prob), p) if g is None else g
+    _check(lib().ffpat_project(ctypes.byref(prob), _dev(p, prob, vol_shape(prob), "p"),
+                               _dev(g, prob, data_shape(prob), "g"), _stream(stream)))
+    return g
+
+
+def backproject(prob, g, h=None, stream=None):
+    h = _empty(prob, vol_shape(prob), g) if h is None else h
+    _check(lib().ffpat_backproject(ctypes.byref(prob), _dev(g, prob, data_shape(prob), "g"),
+                                   _dev(h, prob, vol_shape(prob), "h"), _stream(stream)))
+    return h
+
+
+def ramp(prob, r, out=None, stream=None):
+    out = _empty(prob, data_shape(prob), r) if out is None else out
+    _check(lib().ffpat_ramp(ctypes.byref(prob), _dev(r, prob, data_shape(prob), "r"),
+                            _dev(out, prob, data_shape(prob), "out"), _stream(stream)))
+    return out
+
+
+def opnorm(prob, c, v0, iters=20, ws=None, stream=None) -> float:
+    ws, wp, wn = _ws(prob, ws, v0.device)
+    est = ctypes.c_double()
+    _check(lib().ffpat_opnorm(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                              _dev(v0, prob, vol_shape(prob), "v0"), int(iters),
+                              ctypes.byref(est), wp, wn, _stream(stream)))
+    return est.value
+
+
+def fb_solve(prob, c, g, lam, step, max_iters, h=None, tol=0.0, ws=None, stream=None,
+             history=True):
+    """Algorithm 8; returns (h, stats dict, history array [k, 4] or None)."""
+    import torch
+    h = torch.zeros(vol_shape(prob), dtype=torch_dtype(prob), device=g.device) if h is None else h
+    ws, wp, wn = _ws(prob, ws, g.device)
+    st = FBStats()
+    hist = np.zeros((max(int(max_iters), 1), 4)) if history else None
+    hp = hist.ctypes.data_as(ctypes.c_void_p) if history else None
+    _check(lib().ffpat_fb_solve(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                                _dev(g, prob, data_shape(prob), "g"), float(lam), float(step),
+                                int(max_iters), float(tol), _dev(h, prob, vol_shape(prob), "h"),
+                                ctypes.byref(st), hp, wp, wn, _stream(stream)))
+    d = st.as_dict()
+    return h, d, (hist[: d["iters_done"]] if history else None)
+
+
+def profile_enable(on: bool = True) -> None:
+    _check(lib().ffpat_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    p = Profile()
+    _check(lib().ffpat_profile_read(ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in p._fields_}
+
+
+def launch_count() -> int:
+    return int(lib().ffpat_launch_count())
+
+
+def version() -> str:
+    return lib().ffpat_version().decode()

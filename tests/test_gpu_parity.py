@@ -1,0 +1,284 @@
+"""GPU parity: every hot-path step of the CUDA library against the FP64 oracle
+on the same seeded inputs.
+
+Tolerances (relative L2): 1e-10 for FP64 problems, 2e-5 for the FP32 and
+FP32-Kahan wavefields; bit-exact for the FP64 projection's index arithmetic and
+for the FP64 projection itself on identical input.
+"""
+import numpy as np
+import pytest
+
+import oracle.oracle as o
+from paper_1901_06503_gb300 import build_lib
+from paper_1901_06503_gb300 import ffpat as F
+from paper_1901_06503_gb300.inputs import (add_noise, config, random_data, random_speed,
+                                           random_volume)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {F.FP64: 1e-10, F.FP32: 2e-5, F.FP32_KAHAN: 2e-5}
+PRECS = [F.FP64, F.FP32, F.FP32_KAHAN]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build_lib.build()
+    F.lib()
+
+
+def dev(a, prob):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda").to(F.torch_dtype(prob)).contiguous()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def as_input(a, prec):
+    """What the GPU receives, in float64 (FP32 problems get rounded inputs)."""
+    return a.astype(np.float32).astype(np.float64) if prec != F.FP64 else a
+
+
+# ---------------------------------------------------------- index tables --
+
+def test_sample_index_arithmetic_bit_exact():
+    rng = np.random.default_rng(5)
+    for n, nth in [(32, 24), (33, 7), (128, 90), (384, 180)]:
+        ns = o.ray_samples(n)
+        jkm = np.stack([rng.integers(0, nth, 4000), rng.integers(0, n, 4000),
+                        rng.integers(0, ns, 4000)], axis=1).astype(np.int32)
+        prob = F.problem(n, 1.0, nth)
+        ij_g, f_g = F.debug_samples(prob, jkm)
+        ij_o, f_o = o.sample_points(n, nth, jkm)
+        assert np.array_equal(ij_g, ij_o)
+        assert np.array_equal(f_g, f_o)
+
+
+# ----------------------------------------------------------- projection --
+
+@pytest.mark.parametrize("n,nth", [(24, 6), (33, 7), (40, 13)])
+def test_project_fp64_bit_exact(n, nth):
+    p = random_volume(n, 100 + n)
+    prob = F.problem(n, 1.0, nth)
+    g = host(F.project(prob, dev(p, prob)))
+    assert np.array_equal(g, o.project(p, nth))
+
+
+@pytest.mark.parametrize("prec", [F.FP32])
+@pytest.mark.parametrize("n,nth", [(24, 6), (33, 7)])
+def test_project_fp32(n, nth, prec):
+    p = random_volume(n, 200 + n)
+    prob = F.problem(n, 1.0, nth, prec)
+    g = host(F.project(prob, dev(p, prob)))
+    assert rel(g, o.project(as_input(p, prec), nth)) < 2e-6
+
+
+@pytest.mark.parametrize("prec", [F.FP64, F.FP32])
+@pytest.mark.parametrize("n,nth", [(24, 6), (33, 7), (40, 13)])
+def test_backproject(n, nth, prec):
+    g = random_data(nth, n, 300 + n)
+    prob = F.problem(n, 1.0, nth, prec)
+    h = host(F.backproject(prob, dev(g, prob)))
+    want = o.backproject(as_input(g, prec), n)
+    assert rel(h, want) < (1e-12 if prec == F.FP64 else 2e-6)
+
+
+@pytest.mark.parametrize("prec", [F.FP64, F.FP32])
+@pytest.mark.parametrize("n,nth", [(24, 6), (33, 3), (130, 2)])
+def test_ramp(n, nth, prec):
+    r = random_data(nth, n, 400 + n)
+    prob = F.problem(n, 1.0, nth, prec)
+    out = host(F.ramp(prob, dev(r, prob)))
+    assert rel(out, o.ramp(as_input(r, prec))) < (1e-12 if prec == F.FP64 else 2e-6)
+
+
+# ----------------------------------------------------------- wave operator --
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,T", [(24, 0.6), (33, 0.45), (40, 0.02)])
+def test_wave_and_transpose(n, T, prec):
+    c = as_input(random_speed(n, 500 + n), prec)
+    h = as_input(random_volume(n, 501 + n), prec)
+    prob = F.problem(n, T, 4, prec)
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    kap = o.kappa(n, dt, c)
+    w = host(F.wave(prob, dev(c, prob), dev(h, prob)))
+    assert rel(w, o.wave(kap, h, nt)) < TOL[prec]
+    wt = host(F.wave(prob, dev(c, prob), dev(h, prob), transpose=True))
+    assert rel(wt, o.wave_adjoint(kap, h, nt)) < TOL[prec]
+
+
+# ----------------------------------------------------- composite operator --
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forward_adjoint_config1(prec):
+    w = config(1)
+    c, h = as_input(w.c, prec), as_input(w.h, prec)
+    prob = F.problem(w.n, w.T, w.n_angles, prec)
+    g_gpu = host(F.forward(prob, dev(c, prob), dev(h, prob)))
+    g_or = o.forward(c, h, w.T, w.n_angles)
+    assert rel(g_gpu, g_or) < TOL[prec]
+    gd = as_input(add_noise(g_or, w.noise, w.noise_rel), prec)
+    a_gpu = host(F.adjoint(prob, dev(c, prob), dev(gd, prob)))
+    assert rel(a_gpu, o.adjoint(c, gd, w.T)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forward_adjoint_ragged(prec):
+    n, nth, T = 37, 11, 0.5
+    c = as_input(random_speed(n, 601), prec)
+    h = as_input(random_volume(n, 602), prec)
+    g = as_input(random_data(nth, n, 603), prec)
+    prob = F.problem(n, T, nth, prec)
+    assert rel(host(F.forward(prob, dev(c, prob), dev(h, prob))), o.forward(c, h, T, nth)) < TOL[prec]
+    assert rel(host(F.adjoint(prob, dev(c, prob), dev(g, prob))), o.adjoint(c, g, T)) < TOL[prec]
+
+
+def test_dot_product_gpu_fp64():
+    n, nth, T = 36, 9, 0.7
+    prob = F.problem(n, T, nth)
+    c = dev(random_speed(n, 701), prob)
+    h = dev(random_volume(n, 702), prob)
+    g = dev(random_data(nth, n, 703), prob)
+    Ah = F.forward(prob, c, h)
+    Atg = F.adjoint(prob, c, g)
+    lhs = float((Ah * g).sum())
+    rhs = float((h * Atg).sum())
+    assert abs(lhs - rhs) <= 1e-12 * float(Ah.norm() * g.norm())
+
+
+@pytest.mark.parametrize("prec", [F.FP64, F.FP32_KAHAN])
+def test_forward_adjoint_config2_full(prec):
+    """N = 128, 90 angles, T = 1.2 (333 steps): the whole operator pair."""
+    w = config(2)
+    c, h = as_input(w.c, prec), as_input(w.h, prec)
+    prob = F.problem(w.n, w.T, w.n_angles, prec)
+    g_or = o.forward(c, h, w.T, w.n_angles)
+    g_gpu = host(F.forward(prob, dev(c, prob), dev(h, prob)))
+    assert rel(g_gpu, g_or) < TOL[prec]
+    gd = as_input(add_noise(g_or, w.noise, w.noise_rel), prec)
+    a_gpu = host(F.adjoint(prob, dev(c, prob), dev(gd, prob)))
+    assert rel(a_gpu, o.adjoint(c, gd, w.T)) < TOL[prec]
+
+
+# ------------------------------------------------------------ Algorithm 8 --
+
+def fb_case(prec, precond=0, n=None):
+    w = config(1, n=n)
+    c, htrue = as_input(w.c, prec), w.h
+    g = add_noise(o.forward(c, htrue, w.T, w.n_angles), w.noise, w.noise_rel)
+    g = as_input(g, prec)
+    L = o.power(c, random_volume(w.n, 9), w.T, w.n_angles, precond=precond, iters=20)
+    return w, c, g, 1.0 / L
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fb_config1(prec):
+    w, c, g, s = fb_case(prec)
+    prob = F.problem(w.n, w.T, w.n_angles, prec)
+    h_gpu, st, hist = F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, s, w.iters)
+    h_or, hist_or, k = o.fb(c, g, w.T, w.lam, s, w.iters)
+    assert st["iters_done"] == k == w.iters
+    assert rel(host(h_gpu), h_or) < (1e-10 if prec == F.FP64 else 5e-5)
+    tol = 1e-9 if prec == F.FP64 else 1e-4
+    for col in (0, 1, 3):
+        assert np.max(np.abs(hist[:, col] - hist_or[:, col]) / np.abs(hist_or[:, col])) < tol
+    assert abs(st["objective"] - hist_or[-1, 0]) < tol * abs(hist_or[-1, 0])
+
+
+def test_fb_preconditioned_fp64():
+    w, c, g, s = fb_case(F.FP64, precond=1, n=20)
+    prob = F.problem(w.n, w.T, w.n_angles, F.FP64, precond=1)
+    h_gpu, st, hist = F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, s, 6)
+    h_or, hist_or, k = o.fb(c, g, w.T, w.lam, s, 6, precond=1)
+    assert rel(host(h_gpu), h_or) < 1e-10
+    assert np.max(np.abs(hist[:, 0] - hist_or[:, 0]) / np.abs(hist_or[:, 0])) < 1e-9
+
+
+def test_fb_deterministic_fp64():
+    w, c, g, s = fb_case(F.FP64)
+    prob = F.problem(w.n, w.T, w.n_angles)
+    outs = [host(F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, s, 3)[0]) for _ in range(2)]
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_fb_tolerance_and_warm_start():
+    w, c, g, s = fb_case(F.FP64)
+    prob = F.problem(w.n, w.T, w.n_angles)
+    h0 = np.maximum(w.h + 0.05 * random_volume(w.n, 33), 0)
+    h_gpu, st, hist = F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, s, 50, h=dev(h0, prob),
+                                 tol=5e-3)
+    h_or, hist_or, k = o.fb(c, g, w.T, w.lam, s, 50, h0=h0, tol=5e-3)
+    assert st["iters_done"] == k < 50
+    assert rel(host(h_gpu), h_or) < 1e-10
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_opnorm_fp64(precond):
+    n, nth, T = 20, 8, 0.6
+    c = random_speed(n, 801)
+    v0 = random_volume(n, 802)
+    prob = F.problem(n, T, nth, F.FP64, precond)
+    est = F.opnorm(prob, dev(c, prob), dev(v0, prob), iters=20)
+    want = o.power(c, v0, T, nth, precond=precond, iters=20)
+    assert abs(est - want) < 1e-10 * want
+
+
+def test_fb_automatic_step():
+    w, c, g, s = fb_case(F.FP64)
+    prob = F.problem(w.n, w.T, w.n_angles)
+    _, st, _ = F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, 0.0, 1)
+    assert abs(st["step"] - s) < 0.05 * s and st["opnorm_sq"] > 0
+
+
+# --------------------------------------------------------------- errors --
+
+def test_rejects_nonpositive_speed():
+    n = 16
+    prob = F.problem(n, 0.5, 4)
+    c = random_speed(n, 1)
+    c[3, 4, 5] = 0.0
+    with pytest.raises(F.FFPATError) as e:
+        F.forward(prob, dev(c, prob), dev(random_volume(n, 2), prob))
+    assert e.value.code == F.EINVAL
+
+
+# ------------------------------------------- full sizes, bench launch shape --
+
+def test_full_size_n384_fp32_spot_checks():
+    """N = 384, 180 angles (the large solve): the stencil launch and the
+    projection in the bench's launch configuration, checked where the oracle
+    can follow -- one time step on the whole grid and a sample of rays --
+    and the transpose pair through the dot product."""
+    n, nth = 384, 180
+    rng = np.random.default_rng(11)
+    c = as_input(np.clip(1 + 0.2 * rng.standard_normal((n, n, n)), 0.75, 1.4), F.FP32)
+    h = as_input(rng.standard_normal((n, n, n)), F.FP32)
+    cmax = c.max()
+    T1 = 0.3 * (2.0 / n) / cmax * 0.999  # exactly one time step
+    for prec in (F.FP32, F.FP32_KAHAN):
+        prob = F.problem(n, T1, nth, prec)
+        nt, dt = o.time_steps(n, T1, 0.3, cmax)
+        assert nt == 1
+        w1 = host(F.wave(prob, dev(c, prob), dev(h, prob)))
+        assert rel(w1, o.wave(o.kappa(n, dt, c), h, 1)) < 1e-6
+    prob = F.problem(n, 1.0, nth, F.FP32)
+    g = host(F.project(prob, dev(h, prob)))
+    jlk = np.stack([rng.integers(0, nth, 3000), rng.integers(0, n, 3000),
+                    rng.integers(0, n, 3000)], axis=1)
+    want = o.project_rays(h, nth, jlk)
+    got = g[jlk[:, 0], jlk[:, 1], jlk[:, 2]]
+    assert rel(got, want) < 5e-6
+    gt = dev(random_data(nth, n, 12), prob)
+    bp = F.backproject(prob, gt)
+    hd = dev(h, prob)
+    lhs = float((F.project(prob, hd).double() * gt.double()).sum())
+    rhs = float((hd.double() * bp.double()).sum())
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)

@@ -213,6 +213,14 @@ def test_sample_tables():
     assert np.allclose(ij[:, 1] + f[:, 1], np.array([0, 11]) - ns // 2 + 8, atol=1e-12)
 
 
+def test_project_rays_is_project():
+    n, nth = 12, 5
+    p = random_volume(n, 13)
+    g = o.project(p, nth)
+    jlk = np.array([[j, l, k] for j in range(nth) for l in range(n) for k in range(n)])
+    assert np.array_equal(o.project_rays(p, nth, jlk), g.ravel())
+
+
 def test_projection_transpose_dense():
     """P^T is the exact matrix transpose of P (8^3 grid, 6 angles)."""
     n, nth = 8, 6
