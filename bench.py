@@ -235,6 +235,7 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("ffpat_timed")
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.fill_(float(k))
@@ -243,6 +244,7 @@ def run_ours(args):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        torch.cuda.nvtx.range_pop()
     barrier(world)
     prof = F.profile_read()
     launches = F.launch_count() - launches0

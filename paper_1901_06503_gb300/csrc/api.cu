@@ -116,8 +116,10 @@ static size_t carve(Plan& pl, void* ws) {
   pl.partials = (double*)take(sizeof(double) * kNumQuant * kReduceBlocks);
   pl.scal = (double*)take(sizeof(double) * kScal);
   pl.hist = (double*)take(sizeof(double) * 8 * kMaxHist);
-  pl.tab = (double*)take(sizeof(double) * 2 * pl.nth);
-  pl.tabf = (float*)take(sizeof(float) * 2 * pl.nth);
+  void* tabs = take(table_bytes(pl.nth));
+  pl.tab = (double*)tabs;
+  pl.tabf = tabs ? (float*)((char*)tabs + 16 * (size_t)pl.nth) : nullptr;
+  pl.tabi = tabs ? (int32_t*)((char*)tabs + 24 * (size_t)pl.nth) : nullptr;
   return off;
 }
 
@@ -141,14 +143,27 @@ static void host_angles(int nth, std::vector<double>& cs_sn) {
   }
 }
 
-static int upload_tables(Plan& pl, cudaStream_t st) {
+// Fill the three angle tables at `base` (device, table_bytes(nth) bytes):
+// double cos/sin, their float roundings, and round(cos/sin * 2^30) as int32
+// for the fixed-point sample coordinates of the FP32 projection pair.
+static int upload_tables(Plan& pl, void* base, cudaStream_t st) {
   std::vector<double> t;
   host_angles(pl.nth, t);
-  std::vector<float> tf(t.size());
-  for (size_t i = 0; i < t.size(); ++i) tf[i] = (float)t[i];
-  CK(cudaMemcpyAsync(pl.tab, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(pl.tabf, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  // the host vectors die at return: make sure the copies have consumed them
+  const size_t m = t.size();
+  std::vector<unsigned char> buf(table_bytes(pl.nth));
+  double* d = (double*)buf.data();
+  float* f = (float*)(buf.data() + 8 * m);
+  int32_t* q = (int32_t*)(buf.data() + 12 * m);
+  for (size_t i = 0; i < m; ++i) {
+    d[i] = t[i];
+    f[i] = (float)t[i];
+    q[i] = (int32_t)llrint(t[i] * 1073741824.0);
+  }
+  pl.tab = (double*)base;
+  pl.tabf = (float*)((char*)base + 8 * m);
+  pl.tabi = (int32_t*)((char*)base + 12 * m);
+  CK(cudaMemcpyAsync(base, buf.data(), buf.size(), cudaMemcpyHostToDevice, st));
+  // the host buffer dies at return: make sure the copy has consumed it
   CK(cudaStreamSynchronize(st));
   return FFPAT_OK;
 }
@@ -181,7 +196,7 @@ static int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, siz
                  cudaStream_t st) {
   g_err[0] = 0;
   TRY(attach(pr, pl, ws, ws_bytes));
-  TRY(upload_tables(pl, st));
+  TRY(upload_tables(pl, pl.tab, st));
   TRY(setup_speed(pl, c, st));
   return FFPAT_OK;
 }
@@ -347,14 +362,12 @@ int ffpat_debug_samples(const ffpat_problem* problem, int32_t count, const int32
   if (count < 0 || (count > 0 && (!jkm || !ij || !f)))
     return fail(FFPAT_EINVAL, "bad sample list");
   cudaStream_t st = (cudaStream_t)stream;
-  double* tab = nullptr;
-  CK(cudaMallocAsync((void**)&tab, sizeof(double) * 2 * pl.nth, st));
-  pl.tab = tab;
-  std::vector<double> t;
-  host_angles(pl.nth, t);
-  CK(cudaMemcpyAsync(tab, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  TRY(launch_debug_samples(pl, count, jkm, ij, f, st));
-  CK(cudaFreeAsync(tab, st));
+  void* tabs = nullptr;
+  CK(cudaMallocAsync(&tabs, table_bytes(pl.nth), st));
+  int rc = upload_tables(pl, tabs, st);
+  if (rc == FFPAT_OK) rc = launch_debug_samples(pl, count, jkm, ij, f, st);
+  CK(cudaFreeAsync(tabs, st));
+  TRY(rc);
   CK(cudaStreamSynchronize(st));
   return FFPAT_OK;
 }
@@ -405,16 +418,11 @@ int ffpat_project(const ffpat_problem* problem, const void* p, void* g, void* st
   TRY(validate(problem, pl));
   if (!p || !g) return fail(FFPAT_EINVAL, "p or g is NULL");
   void* tabs = nullptr;
-  CK(cudaMallocAsync(&tabs, 24 * (size_t)pl.nth + 256, st));
-  pl.tab = (double*)tabs;
-  pl.tabf = (float*)((char*)tabs + 16 * (size_t)pl.nth);
-  std::vector<double> t;
-  host_angles(pl.nth, t);
-  std::vector<float> tf(t.begin(), t.end());
-  CK(cudaMemcpyAsync(pl.tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(pl.tabf, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, st));
-  TRY(launch_project(pl, p, g, nullptr, st));
+  CK(cudaMallocAsync(&tabs, table_bytes(pl.nth), st));
+  int rc = upload_tables(pl, tabs, st);
+  if (rc == FFPAT_OK) rc = launch_project(pl, p, g, nullptr, st);
   CK(cudaFreeAsync(tabs, st));
+  TRY(rc);
   CK(cudaStreamSynchronize(st));
   return FFPAT_OK;
 }
@@ -426,16 +434,11 @@ int ffpat_backproject(const ffpat_problem* problem, const void* g, void* h, void
   TRY(validate(problem, pl));
   if (!h || !g) return fail(FFPAT_EINVAL, "g or h is NULL");
   void* tabs = nullptr;
-  CK(cudaMallocAsync(&tabs, 24 * (size_t)pl.nth + 256, st));
-  pl.tab = (double*)tabs;
-  pl.tabf = (float*)((char*)tabs + 16 * (size_t)pl.nth);
-  std::vector<double> t;
-  host_angles(pl.nth, t);
-  std::vector<float> tf(t.begin(), t.end());
-  CK(cudaMemcpyAsync(pl.tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(pl.tabf, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, st));
-  TRY(launch_backproject(pl, g, h, nullptr, st));
+  CK(cudaMallocAsync(&tabs, table_bytes(pl.nth), st));
+  int rc = upload_tables(pl, tabs, st);
+  if (rc == FFPAT_OK) rc = launch_backproject(pl, g, h, nullptr, st);
   CK(cudaFreeAsync(tabs, st));
+  TRY(rc);
   CK(cudaStreamSynchronize(st));
   return FFPAT_OK;
 }

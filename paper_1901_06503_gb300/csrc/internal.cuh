@@ -29,9 +29,12 @@ struct Plan {
   double* partials = nullptr;  // kNumQuant * kReduceBlocks doubles
   double* scal = nullptr;      // small device scalars
   double* hist = nullptr;      // per-iteration FB statistics (8 doubles / iteration, up to kMaxHist)
-  double* tab = nullptr;       // cos[nth], sin[nth] (double)
-  float* tabf = nullptr;       // cos[nth], sin[nth] (float)
+  double* tab = nullptr;       // cos[nth], sin[nth] (double, host libm)
+  float* tabf = nullptr;       // cos[nth], sin[nth] rounded to float
+  int32_t* tabi = nullptr;     // cos[nth], sin[nth] in fixed point, round(. * 2^30)
 };
+// bytes of the three angle tables (double, float, fixed point) for nth angles
+inline size_t table_bytes(int nth) { return (size_t)nth * 2 * (8 + 4 + 4); }
 constexpr int kMaxHist = 4096;
 constexpr int kScal = 64;
 

@@ -88,8 +88,8 @@ __device__ __forceinline__ void ray_range(float cs, float sn, int k, int n, int 
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_project(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
-              const double* __restrict__ tab, const float* __restrict__ tabf, int n, int nth,
-              int ns) {
+              const double* __restrict__ tab, const float* __restrict__ tabf,
+              const int32_t* __restrict__ tabi, int n, int nth, int ns) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int l = blockIdx.y;
   const int j = blockIdx.z;
@@ -119,16 +119,22 @@ __global__ void __launch_bounds__(128)
       g[o] = out;
     }
   } else {
-    const float cN = 0.5f * (float)(n - 1);
-    const float u = (float)k + 0.5f - 0.5f * (float)n;
-    const float bx = fmaf(u, csf, cN), by = fmaf(u, snf, cN);
+    // fixed point, scale 2^31 grid units: the coordinates of the samples of one
+    // ray advance by exact integer steps, so fx, fy carry ~1e-9 absolute error
+    // at any grid size (a float coordinate near 384 would carry 3e-5)
+    const long long CS = tabi[j], SN = tabi[nth + j];
+    const long long u2 = 2LL * k + 1 - n, v2 = 2LL * mlo + 1 - ns;
+    const long long c2 = (long long)(n - 1) << 30;
+    long long GX = c2 + u2 * CS - v2 * SN;
+    long long GY = c2 + u2 * SN + v2 * CS;
+    const long long dGX = -2 * SN, dGY = 2 * CS;
+    constexpr float kInv = 4.656612873077392578125e-10f;  // 2^-31
     for (int m = mlo; m < mhi; ++m) {
-      const float v = (float)m + 0.5f - 0.5f * (float)ns;
-      const float gx = fmaf(-v, snf, bx);
-      const float gy = fmaf(v, csf, by);
-      const float flx = floorf(gx), fly = floorf(gy);
-      const int i0 = (int)flx, j0 = (int)fly;
-      const float fx = gx - flx, fy = gy - fly;
+      const int i0 = (int)(GX >> 31), j0 = (int)(GY >> 31);
+      const float fx = (float)(unsigned)(GX & 0x7fffffffLL) * kInv;
+      const float fy = (float)(unsigned)(GY & 0x7fffffffLL) * kInv;
+      GX += dGX;
+      GY += dGY;
       const float v00 = pix(sl, n, j0, i0), v10 = pix(sl, n, j0, i0 + 1);
       const float v01 = pix(sl, n, j0 + 1, i0), v11 = pix(sl, n, j0 + 1, i0 + 1);
       const float r0 = fmaf(fx, v10 - v00, v00);
@@ -153,43 +159,59 @@ __device__ __forceinline__ T hat(T a) {
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_backproject(const T* __restrict__ g, T* __restrict__ h, const T* __restrict__ scale,
-                  const double* __restrict__ tab, const float* __restrict__ tabf, int n, int nth,
-                  int ns) {
+                  const double* __restrict__ tab, const float* __restrict__ tabf,
+                  const int32_t* __restrict__ tabi, int n, int nth, int ns) {
   const int ix = blockIdx.x * 32 + threadIdx.x;
   const int iy = blockIdx.y * 8 + threadIdx.y;
   const int l = blockIdx.z;
   if (ix >= n || iy >= n) return;
-  const T cN = T(0.5) * T(n - 1);
-  const T X = T(ix) - cN, Y = T(iy) - cN;
-  const T koff = T(0.5) * T(n) - T(0.5);
-  const T moff = T(0.5) * T(ns) - T(0.5);
-  const T R = T(1.41521);  // sqrt(2) plus a margin; the hat weights vanish beyond it
+  constexpr float R = 1.41521f;  // sqrt(2) plus a margin; the hat weights vanish beyond it
   T acc = T(0);
-  for (int j = 0; j < nth; ++j) {
-    T cs, sn;
-    if constexpr (sizeof(T) == 8) {
-      cs = tab[j];
-      sn = tab[nth + j];
-    } else {
-      cs = tabf[j];
-      sn = tabf[nth + j];
-    }
-    const T u = X * cs + Y * sn;   // detector coordinate of the voxel (grid units)
-    const T v = Y * cs - X * sn;   // ray coordinate of the voxel
-    const T kk = u + koff, mm = v + moff;
-    const int klo = max(0, (int)ceil(kk - R)), khi = min(n - 1, (int)floor(kk + R));
-    const int mlo = max(0, (int)ceil(mm - R)), mhi = min(ns - 1, (int)floor(mm + R));
-    const T* __restrict__ row = g + ((size_t)j * n + l) * n;
-    for (int k = klo; k <= khi; ++k) {
-      const T du = T(k) - kk;
-      T wsum = T(0);
-      for (int m = mlo; m <= mhi; ++m) {
-        const T dv = T(m) - mm;
-        const T ax = du * cs - dv * sn;
-        const T ay = du * sn + dv * cs;
-        wsum += hat(ax) * hat(ay);
+  if constexpr (sizeof(T) == 8) {
+    const double cN = 0.5 * (n - 1);
+    const double X = ix - cN, Y = iy - cN;
+    const double koff = 0.5 * n - 0.5, moff = 0.5 * ns - 0.5;
+    for (int j = 0; j < nth; ++j) {
+      const double cs = tab[j], sn = tab[nth + j];
+      const double kk = X * cs + Y * sn + koff;  // detector index of the voxel
+      const double mm = Y * cs - X * sn + moff;  // ray sample index of the voxel
+      const int klo = max(0, (int)ceil(kk - R)), khi = min(n - 1, (int)floor(kk + R));
+      const int mlo = max(0, (int)ceil(mm - R)), mhi = min(ns - 1, (int)floor(mm + R));
+      const double* __restrict__ row = g + ((size_t)j * n + l) * n;
+      for (int k = klo; k <= khi; ++k) {
+        const double du = k - kk;
+        double wsum = 0.0;
+        for (int m = mlo; m <= mhi; ++m) {
+          const double dv = m - mm;
+          wsum += hat(du * cs - dv * sn) * hat(du * sn + dv * cs);
+        }
+        acc += wsum * __ldg(row + k);
       }
-      acc += wsum * __ldg(row + k);
+    }
+  } else {
+    // voxel position in the rotated frame in fixed point (scale 2^31) so
+    // that the offsets du, dv to the candidate samples are exact to ~1e-9
+    const long long X2 = 2LL * ix - (n - 1), Y2 = 2LL * iy - (n - 1);
+    const long long koff = (long long)(n - 1) << 30, moff = (long long)(ns - 1) << 30;
+    constexpr float kInv = 4.656612873077392578125e-10f;  // 2^-31
+    for (int j = 0; j < nth; ++j) {
+      const long long CS = tabi[j], SN = tabi[nth + j];
+      const float cs = tabf[j], sn = tabf[nth + j];
+      const long long KK = X2 * CS + Y2 * SN + koff;
+      const long long MM = Y2 * CS - X2 * SN + moff;
+      const float kkf = (float)KK * kInv, mmf = (float)MM * kInv;
+      const int klo = max(0, (int)ceilf(kkf - R)), khi = min(n - 1, (int)floorf(kkf + R));
+      const int mlo = max(0, (int)ceilf(mmf - R)), mhi = min(ns - 1, (int)floorf(mmf + R));
+      const float* __restrict__ row = g + ((size_t)j * n + l) * n;
+      for (int k = klo; k <= khi; ++k) {
+        const float du = (float)(((long long)k << 31) - KK) * kInv;
+        float wsum = 0.0f;
+        for (int m = mlo; m <= mhi; ++m) {
+          const float dv = (float)(((long long)m << 31) - MM) * kInv;
+          wsum += hat(du * cs - dv * sn) * hat(du * sn + dv * cs);
+        }
+        acc += wsum * __ldg(row + k);
+      }
     }
   }
   const size_t o = ((size_t)l * n + iy) * n + ix;
@@ -253,10 +275,10 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
   const dim3 grid((pl.n + 127) / 128, pl.n, pl.nth);
   if (pl.prec == FFPAT_FP64)
     k_project<double><<<grid, block, 0, st>>>((const double*)p, (double*)g, (const double*)sub,
-                                              pl.tab, pl.tabf, pl.n, pl.nth, pl.ns);
+                                              pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns);
   else
     k_project<float><<<grid, block, 0, st>>>((const float*)p, (float*)g, (const float*)sub, pl.tab,
-                                             pl.tabf, pl.n, pl.nth, pl.ns);
+                                             pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns);
   count_launch();
   return check_launch(__func__);
 }
@@ -266,11 +288,11 @@ int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale
   const dim3 grid((pl.n + 31) / 32, (pl.n + 7) / 8, pl.n);
   if (pl.prec == FFPAT_FP64)
     k_backproject<double><<<grid, block, 0, st>>>((const double*)g, (double*)h,
-                                                  (const double*)scale, pl.tab, pl.tabf, pl.n,
-                                                  pl.nth, pl.ns);
+                                                  (const double*)scale, pl.tab, pl.tabf,
+                                                  pl.tabi, pl.n, pl.nth, pl.ns);
   else
     k_backproject<float><<<grid, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
-                                                 pl.tab, pl.tabf, pl.n, pl.nth, pl.ns);
+                                                 pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns);
   count_launch();
   return check_launch(__func__);
 }

@@ -77,7 +77,7 @@ def test_project_fp32(n, nth, prec):
     p = random_volume(n, 200 + n)
     prob = F.problem(n, 1.0, nth, prec)
     g = host(F.project(prob, dev(p, prob)))
-    assert rel(g, o.project(as_input(p, prec), nth)) < 2e-6
+    assert rel(g, o.project(as_input(p, prec), nth)) < 5e-7
 
 
 @pytest.mark.parametrize("prec", [F.FP64, F.FP32])
@@ -87,7 +87,7 @@ def test_backproject(n, nth, prec):
     prob = F.problem(n, 1.0, nth, prec)
     h = host(F.backproject(prob, dev(g, prob)))
     want = o.backproject(as_input(g, prec), n)
-    assert rel(h, want) < (1e-12 if prec == F.FP64 else 2e-6)
+    assert rel(h, want) < (1e-12 if prec == F.FP64 else 5e-7)
 
 
 @pytest.mark.parametrize("prec", [F.FP64, F.FP32])
@@ -214,8 +214,8 @@ def test_fb_tolerance_and_warm_start():
     prob = F.problem(w.n, w.T, w.n_angles)
     h0 = np.maximum(w.h + 0.05 * random_volume(w.n, 33), 0)
     h_gpu, st, hist = F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, s, 50, h=dev(h0, prob),
-                                 tol=5e-3)
-    h_or, hist_or, k = o.fb(c, g, w.T, w.lam, s, 50, h0=h0, tol=5e-3)
+                                 tol=2e-2)
+    h_or, hist_or, k = o.fb(c, g, w.T, w.lam, s, 50, h0=h0, tol=2e-2)
     assert st["iters_done"] == k < 50
     assert rel(host(h_gpu), h_or) < 1e-10
 
@@ -275,10 +275,10 @@ def test_full_size_n384_fp32_spot_checks():
                     rng.integers(0, n, 3000)], axis=1)
     want = o.project_rays(h, nth, jlk)
     got = g[jlk[:, 0], jlk[:, 1], jlk[:, 2]]
-    assert rel(got, want) < 5e-6
+    assert rel(got, want) < 1e-6
     gt = dev(random_data(nth, n, 12), prob)
     bp = F.backproject(prob, gt)
     hd = dev(h, prob)
     lhs = float((F.project(prob, hd).double() * gt.double()).sum())
     rhs = float((hd.double() * bp.double()).sum())
-    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+    assert abs(lhs - rhs) < 1e-6 * abs(lhs)
