@@ -179,6 +179,18 @@ int ffpat_profile_read(ffpat_profile *out);
 /* Total kernels launched by this library since load (monotone counter). */
 int64_t ffpat_launch_count(void);
 
+/* Choice of leapfrog kernel (process-wide): 0 = automatic (the TMA-fed kernel
+ * when N % 4 == 0 for float or N % 2 == 0 for double and all arrays are
+ * 16-byte aligned, else the plain 2.5D kernel), 1 = always the plain kernel,
+ * 2 = always the TMA kernel (calls that cannot use it fail with FFPAT_EINVAL).
+ * Both compute the same steps; this exists for testing and measurement. */
+int ffpat_set_stencil_path(int32_t path);
+
+/* Device status word of the library's kernels: 0, or the negative status of
+ * the first device-side failure since the last clear (a bounded wait that ran
+ * out sets FFPAT_ETIMEDOUT).  Synchronises the device; clear != 0 resets it. */
+int ffpat_device_status(int32_t clear);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
 static std::atomic<long long> g_prof_launches{0};
 static std::atomic<int> g_prof_on{0};
+static std::atomic<int> g_stencil_path{0};  // 0 auto, 1 plain 2.5D kernel, 2 TMA kernel
 
 struct ProfRec {
   cudaEvent_t a, b;
@@ -205,6 +206,25 @@ static double bytes_per_point(const Plan& pl) {
   return pl.prec == FFPAT_FP64 ? 32.0 : (pl.prec == FFPAT_FP32 ? 16.0 : 28.0);
 }
 
+// One leapfrog launch, through the TMA kernel when the layout allows it.
+static int step3(const Plan& pl, bool tma, bool start, const void* p, const void* qin, void* qout,
+                 void* copy0, cudaStream_t st) {
+  if (tma) {
+    const void* q[2] = {start ? pl.kap : qin, pl.kap};
+    return launch_step_tma(pl, 0, start, p, q, qout, copy0, nullptr, st);
+  }
+  return launch_step3(pl, p, qin, qout, start, copy0, st);
+}
+
+static int step_inc(const Plan& pl, bool tma, bool start, const void* pin, void* pout, void* d,
+                    void* e, cudaStream_t st) {
+  if (tma) {
+    const void* q[3] = {start ? pl.kap : d, e, pl.kap};
+    return launch_step_tma(pl, 1, start, pin, q, pout, d, e, st);
+  }
+  return launch_step_inc(pl, pin, pout, d, e, start, st);
+}
+
 // W applied to `in` (N^3).  The result goes to `out` if non-null, else it
 // stays in a state buffer whose address is returned through *result.
 static int run_wave(const Plan& pl, const void* in, void* out, const void** result,
@@ -212,11 +232,17 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
   const int nt = pl.nt;
   ProfRec rec{};
   const bool prof = g_prof_on.load() && nt > 1;
+  const void* ptrs[8] = {in, out, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3], nullptr};
+  const int path = g_stencil_path.load();
+  const bool tma = path != 1 && tma_supported(pl, ptrs, 7);
+  if (path == 2 && !tma)
+    return fail(FFPAT_EINVAL, "TMA stencil requested but N = %d or an array alignment rules it out",
+                pl.n);
   if (pl.prec == FFPAT_FP32_KAHAN) {
     void* d = pl.s[2];
     void* e = pl.s[3];
     void* first = (nt == 1 && out) ? out : pl.s[0];
-    TRY(launch_step_inc(pl, in, first, d, e, true, st));
+    TRY(step_inc(pl, tma, true, in, first, d, e, st));
     const void* cur = first;
     if (prof) {
       CK(cudaEventCreate(&rec.a));
@@ -225,7 +251,7 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
     }
     for (int s = 1; s < nt; ++s) {
       void* nxt = (s == nt - 1 && out) ? out : (cur == pl.s[0] ? pl.s[1] : pl.s[0]);
-      TRY(launch_step_inc(pl, cur, nxt, d, e, false, st));
+      TRY(step_inc(pl, tma, false, cur, nxt, d, e, st));
       cur = nxt;
     }
     if (prof) CK(cudaEventRecord(rec.b, st));
@@ -235,10 +261,10 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
     void* B = pl.s[1];  // p^n
     if (nt == 1) {
       void* dst = out ? out : B;
-      TRY(launch_step3(pl, in, nullptr, dst, true, nullptr, st));
+      TRY(step3(pl, tma, true, in, nullptr, dst, nullptr, st));
       if (result) *result = dst;
     } else {
-      TRY(launch_step3(pl, in, nullptr, B, true, A, st));
+      TRY(step3(pl, tma, true, in, nullptr, B, A, st));
       if (prof) {
         CK(cudaEventCreate(&rec.a));
         CK(cudaEventCreate(&rec.b));
@@ -246,7 +272,7 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
       }
       for (int s = 1; s < nt; ++s) {
         void* dst = (s == nt - 1 && out) ? out : A;
-        TRY(launch_step3(pl, B, A, dst, false, nullptr, st));
+        TRY(step3(pl, tma, false, B, A, dst, nullptr, st));
         A = B;
         B = dst;
       }
@@ -560,5 +586,20 @@ int ffpat_profile_read(ffpat_profile* out) {
 }
 
 int64_t ffpat_launch_count(void) { return g_launches.load(); }
+
+int ffpat_set_stencil_path(int32_t path) {
+  g_err[0] = 0;
+  if (path < 0 || path > 2) return fail(FFPAT_EINVAL, "stencil path %d not in {0, 1, 2}", path);
+  g_stencil_path = path;
+  return FFPAT_OK;
+}
+
+int ffpat_device_status(int32_t clear) {
+  g_err[0] = 0;
+  unsigned v = 0;
+  TRY(read_device_status(&v, clear != 0));
+  if (v) fail(-(int)v, "a device-side wait timed out in an earlier launch");
+  return -(int)v;
+}
 
 }  // extern "C"

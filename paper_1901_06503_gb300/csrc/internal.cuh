@@ -51,6 +51,16 @@ int launch_step3(const Plan& pl, const void* p, const void* qin, void* qout, boo
 int launch_step_inc(const Plan& pl, const void* pin, void* pout, void* d, void* e, bool start,
                     cudaStream_t st);
 
+// stencil_tma.cu: the same steps fed by TMA (needs N % 4 == 0 for float, N % 2
+// == 0 for double, 16-byte aligned arrays).  form 0: three-term, q = {p^{n-1},
+// kap} (start: {kap}), o0 = p^{n+1}, o1 = copy of p^0 at start; form 1:
+// increment, q = {d, e, kap} (start: {kap}), o0 = p^{n+1}, o1 = d, o2 = e.
+bool tma_supported(const Plan& pl, const void* const* ptrs, int count);
+int launch_step_tma(const Plan& pl, int form, bool start, const void* p, const void* const* q,
+                    void* o0, void* o1, void* o2, cudaStream_t st);
+// device status word of the TMA kernels (0 = ok, else -FFPAT_* of the first error)
+int read_device_status(unsigned* out, bool clear);
+
 // xray.cu
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st);
 int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st);

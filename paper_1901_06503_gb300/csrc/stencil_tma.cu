@@ -1,0 +1,401 @@
+// stencil_tma.cu -- the leapfrog step of p_tt = c^2 Delta p (Sec. 2.1,
+// eq. (1)-(2)) as a TMA-fed, z-streaming persistent kernel for sm_103a.
+//
+// Same arithmetic as stencil.cu (see there for the two time-update forms);
+// what changes is how the data reach the SM:
+//   * every CTA owns a 64 x 8 (x, y) column tile and a z-range; a persistent
+//     grid walks the (tile, z-range) work items;
+//   * one thread issues cp.async.bulk.tensor (TMA) copies: the plane of p^n
+//     with its two-point x/y halo (a 72 x 12 float box starting 16-byte
+//     aligned at x0 - 4) into an 8-deep ring of shared-memory planes, and the
+//     halo-free tiles of the per-point streams (p^{n-1}, or d and e, and kap)
+//     into a 4-deep ring; an mbarrier per round counts the bytes in;
+//   * the ring runs three planes ahead of the plane being computed, so about
+//     30 KB per CTA are always in flight;
+//   * zero ghost values outside the box come for free: TMA fills boxes that
+//     cross the tensor bounds with zeros, including whole planes z < 0, z >= N;
+//   * the z-neighbours z +- 1, z +- 2 are read from the neighbouring ring
+//     planes, so each plane of p^n comes from HBM once per step.
+// Every mbarrier wait is bounded (about a second of clock64 time); on a
+// timeout the CTA records FFPAT_ETIMEDOUT in a device status word, waits a
+// bounded time for its own copies in flight, and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <unordered_map>
+
+#include "internal.cuh"
+
+namespace ffpat {
+
+__device__ unsigned int g_tma_status;  // 0 = ok, else the first error code (as unsigned)
+
+namespace {
+
+constexpr int TBX = 64, TBY = 8;   // output tile
+constexpr int NTX = 32, NTY = 8;   // threads: each computes x and x + 32
+constexpr int SP = 8;              // ring of p planes: z-2 .. z+5
+constexpr int SQ = 4;              // ring of per-point stream planes: z .. z+3
+constexpr long long kWaitCycles = 1LL << 31;
+
+template <typename T>
+struct Geo {
+  static constexpr int XH = 16 / (int)sizeof(T);  // x halo rounded up to 16 bytes
+  static constexpr int BXH = TBX + 2 * XH;
+  static constexpr int BYH = TBY + 4;
+  static constexpr int PBYTES = BXH * BYH * (int)sizeof(T);
+  static constexpr int QBYTES = TBX * TBY * (int)sizeof(T);
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false if the phase did not complete within `cycles`
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long cycles) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > cycles) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct Maps {
+  CUtensorMap p;     // p^n with the halo box
+  CUtensorMap q[3];  // halo-free per-point streams
+};
+
+// FORM 0: three-term (q = {p^{n-1}, kap} or, at START, {kap});
+// FORM 1: increment with Kahan carry (q = {d, e, kap} or, at START, {kap}).
+template <typename T, int FORM, bool START>
+struct Streams {
+  static constexpr int NQ = START ? 1 : (FORM == 0 ? 2 : 3);
+};
+
+__device__ __forceinline__ float lap12_diff(const float* P0, const float* Pm1, const float* Pp1,
+                                            const float* Pm2, const float* Pp2, int o, int row) {
+  const float c = P0[o];
+  float d1 = (P0[o - 1] - c) + (P0[o + 1] - c);
+  d1 += (P0[o - row] - c) + (P0[o + row] - c);
+  d1 += (Pm1[o] - c) + (Pp1[o] - c);
+  float d2 = (P0[o - 2] - c) + (P0[o + 2] - c);
+  d2 += (P0[o - 2 * row] - c) + (P0[o + 2 * row] - c);
+  d2 += (Pm2[o] - c) + (Pp2[o] - c);
+  return fmaf(16.0f, d1, -d2);
+}
+
+__device__ __forceinline__ double lap12_sum(const double* P0, const double* Pm1, const double* Pp1,
+                                            const double* Pm2, const double* Pp2, int o, int row) {
+  const double c = P0[o];
+  double s1 = P0[o - 1] + P0[o + 1];
+  s1 += P0[o - row];
+  s1 += P0[o + row];
+  s1 += Pm1[o];
+  s1 += Pp1[o];
+  double s2 = fma(90.0, c, P0[o - 2]);
+  s2 += P0[o + 2];
+  s2 += P0[o - 2 * row];
+  s2 += P0[o + 2 * row];
+  s2 += Pm2[o];
+  s2 += Pp2[o];
+  return fma(16.0, s1, -s2);
+}
+
+// Round R brings p plane R (needed while R <= z1 + 1) and the per-point
+// stream planes R - 2 (needed while z0 <= R - 2 < z1) of the item's tile.
+template <typename T, int NQ>
+__device__ __forceinline__ void issue_round(const Maps& maps, T* pst, T* qst, uint64_t* bar, int R,
+                                            int z0, int z1, int x0, int y0) {
+  using G = Geo<T>;
+  const bool wp = R <= z1 + 1;
+  const bool wq = (R - 2 >= z0) && (R - 2 < z1);
+  if (!wp && !wq) return;
+  uint64_t* b = &bar[R & (SP - 1)];
+  mbar_expect_tx(b, (wp ? G::PBYTES : 0) + (wq ? NQ * G::QBYTES : 0));
+  if (wp)
+    tma_load_3d(pst + (size_t)(R & (SP - 1)) * (G::PBYTES / sizeof(T)), &maps.p, x0 - G::XH,
+                y0 - 2, R, b);
+  if (wq) {
+    const int s = (R - 2) & (SQ - 1);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      tma_load_3d(qst + (size_t)(s * NQ + q) * (G::QBYTES / sizeof(T)), &maps.q[q], x0, y0, R - 2,
+                  b);
+  }
+}
+
+template <typename T, int FORM, bool START>
+__global__ void __launch_bounds__(NTX* NTY, 2)
+    k_step_tma(const __grid_constant__ Maps maps, T* __restrict__ o0, T* __restrict__ o1,
+               T* __restrict__ o2, int n, int zc, int tiles_x, int tiles_y, int nitems) {
+  using G = Geo<T>;
+  constexpr int NQ = Streams<T, FORM, START>::NQ;
+  extern __shared__ unsigned char smem_raw[];
+  // TMA destinations must be 128-byte aligned: align the dynamic window to 1 KB
+  unsigned char* smem =
+      smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  T* pst = reinterpret_cast<T*>(smem);                                   // SP planes
+  T* qst = reinterpret_cast<T*>(smem + SP * G::PBYTES);                  // SQ x NQ tiles
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SP * G::PBYTES + SQ * NQ * G::QBYTES);
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * NTX + tx;
+  if (tid == 0) {
+    for (int i = 0; i < SP; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned phase = 0;  // one parity bit per barrier slot
+  const size_t plane = (size_t)n * n;
+
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tix = item % tiles_x;
+    const int tiy = (item / tiles_x) % tiles_y;
+    const int z0 = (item / (tiles_x * tiles_y)) * zc;
+    const int z1 = min(n, z0 + zc);
+    const int x0 = tix * TBX, y0 = tiy * TBY;
+
+    if (tid == 0)
+      for (int R = z0 - 2; R <= z0 + SP - 3; ++R)
+        issue_round<T, NQ>(maps, pst, qst, bar, R, z0, z1, x0, y0);
+
+    bool timed_out = false;
+    int waited_upto = z0 - 3;  // last round this thread has waited for
+    for (int z = z0; z < z1; ++z) {
+      for (int R = waited_upto + 1; R <= z + 2; ++R) {
+        const int b = R & (SP - 1);
+        if (!mbar_wait(&bar[b], (phase >> b) & 1u, kWaitCycles)) timed_out = true;
+        phase ^= 1u << b;
+      }
+      waited_upto = z + 2;
+
+      const T* P0 = pst + (size_t)(z & (SP - 1)) * (G::PBYTES / sizeof(T));
+      const T* Pm1 = pst + (size_t)((z - 1) & (SP - 1)) * (G::PBYTES / sizeof(T));
+      const T* Pp1 = pst + (size_t)((z + 1) & (SP - 1)) * (G::PBYTES / sizeof(T));
+      const T* Pm2 = pst + (size_t)((z - 2) & (SP - 1)) * (G::PBYTES / sizeof(T));
+      const T* Pp2 = pst + (size_t)((z + 2) & (SP - 1)) * (G::PBYTES / sizeof(T));
+      const T* Q = qst + (size_t)((z & (SQ - 1)) * NQ) * (G::QBYTES / sizeof(T));
+      const int y = y0 + ty;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int xl = tx + 32 * h;
+        const int x = x0 + xl;
+        const int o = (ty + 2) * G::BXH + xl + G::XH;
+        const int qo = ty * TBX + xl;
+        T L;
+        if constexpr (sizeof(T) == 4)
+          L = lap12_diff(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
+        else
+          L = lap12_sum(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
+        const T c = P0[o];
+        const T k = Q[(NQ - 1) * (G::QBYTES / sizeof(T)) + qo];
+        if (x < n && y < n) {
+          const size_t gi = (size_t)z * plane + (size_t)y * n + x;
+          if constexpr (FORM == 0) {
+            if constexpr (START) {
+              o0[gi] = c + T(0.5) * k * L;
+              if (o1) o1[gi] = c;
+            } else {
+              const T pm = Q[qo];
+              if constexpr (sizeof(T) == 8)
+                o0[gi] = fma(k, L, fma(2.0, c, -pm));
+              else
+                o0[gi] = c + fmaf(k, L, c - pm);
+            }
+          } else {
+            float dn, eold;
+            if constexpr (START) {
+              dn = 0.5f * k * L;
+              eold = 0.0f;
+            } else {
+              dn = fmaf(k, L, Q[qo]);
+              eold = Q[(G::QBYTES / sizeof(T)) + qo];
+            }
+            const float yv = dn - eold;
+            const float tv = c + yv;
+            o0[gi] = tv;
+            o1[gi] = dn;
+            o2[gi] = (tv - c) - yv;
+          }
+        }
+      }
+      if (__syncthreads_or(timed_out)) {
+        if (tid == 0) {
+          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+          // bounded wait for this CTA's copies still in flight
+          for (int R = waited_upto + 1; R <= min(z1 + 1, z + SP - 3); ++R) {
+            const int b = R & (SP - 1);
+            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
+            phase ^= 1u << b;
+          }
+        }
+        return;
+      }
+      if (tid == 0) issue_round<T, NQ>(maps, pst, qst, bar, z + SP - 2, z0, z1, x0, y0);
+    }
+  }
+}
+
+// ------------------------------------------------------------- host side --
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+struct MapKey {
+  const void* ptr;
+  int n, esize, halo;
+  bool operator==(const MapKey& o) const {
+    return ptr == o.ptr && n == o.n && esize == o.esize && halo == o.halo;
+  }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    return std::hash<const void*>()(k.ptr) ^ ((size_t)k.n << 1) ^ ((size_t)k.esize << 13) ^
+           ((size_t)k.halo << 17);
+  }
+};
+
+int make_map(CUtensorMap* m, const void* base, int n, int esize, bool halo) {
+  static thread_local std::unordered_map<MapKey, CUtensorMap, MapKeyHash> cache;
+  const MapKey key{base, n, esize, halo ? 1 : 0};
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *m = it->second;
+    return FFPAT_OK;
+  }
+  std::call_once(g_encode_once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  if (!g_encode) return FFPAT_ECUDA;
+  const int xh = 16 / esize;
+  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[2] = {(cuuint64_t)n * esize, (cuuint64_t)n * n * esize};
+  cuuint32_t box[3] = {(cuuint32_t)(halo ? TBX + 2 * xh : TBX), (cuuint32_t)(halo ? TBY + 4 : TBY),
+                       1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = g_encode(
+      m, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return FFPAT_ECUDA;
+  if (cache.size() > 256) cache.clear();
+  cache.emplace(key, *m);
+  return FFPAT_OK;
+}
+
+template <typename T, int FORM, bool START>
+int launch_one(const Plan& pl, const Maps& maps, void* o0, void* o1, void* o2, cudaStream_t st) {
+  using G = Geo<T>;
+  constexpr int NQ = Streams<T, FORM, START>::NQ;
+  const size_t smem = (size_t)SP * G::PBYTES + (size_t)SQ * NQ * G::QBYTES + SP * 8 + 1024;
+  auto kern = k_step_tma<T, FORM, START>;
+  static int occ = 0;  // per instantiation
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTX * NTY, smem);
+    if (occ < 1) occ = 1;
+  });
+  const int n = pl.n;
+  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + TBY - 1) / TBY;
+  const int slots = kNumSMs * occ;
+  int zchunks = (4 * slots + tiles_x * tiles_y - 1) / (tiles_x * tiles_y);
+  const int zmax = n / 8 > 0 ? n / 8 : 1;
+  if (zchunks > zmax) zchunks = zmax;
+  if (zchunks < 1) zchunks = 1;
+  const int zc = (n + zchunks - 1) / zchunks;
+  zchunks = (n + zc - 1) / zc;
+  const int nitems = tiles_x * tiles_y * zchunks;
+  const int grid = nitems < slots ? nitems : slots;
+  kern<<<grid, dim3(NTX, NTY), smem, st>>>(maps, (T*)o0, (T*)o1, (T*)o2, n, zc, tiles_x, tiles_y,
+                                          nitems);
+  count_launch();
+  return check_launch("k_step_tma");
+}
+
+}  // namespace
+
+bool tma_supported(const Plan& pl, const void* const* ptrs, int count) {
+  if (pl.esize == 4 ? (pl.n % 4) : (pl.n % 2)) return false;
+  for (int i = 0; i < count; ++i)
+    if (ptrs[i] && ((uintptr_t)ptrs[i] & 15)) return false;
+  return true;
+}
+
+int launch_step_tma(const Plan& pl, int form, bool start, const void* p, const void* const* q,
+                    void* o0, void* o1, void* o2, cudaStream_t st) {
+  Maps maps;
+  const int es = (int)pl.esize;
+  if (make_map(&maps.p, p, pl.n, es, true) != FFPAT_OK) return check_launch("tensor map (p)");
+  const int nq = start ? 1 : (form == 0 ? 2 : 3);
+  for (int i = 0; i < 3; ++i) {
+    if (i < nq) {
+      if (make_map(&maps.q[i], q[i], pl.n, es, false) != FFPAT_OK)
+        return check_launch("tensor map (q)");
+    } else {
+      maps.q[i] = maps.p;
+    }
+  }
+  if (pl.prec == FFPAT_FP64) {
+    return start ? launch_one<double, 0, true>(pl, maps, o0, o1, o2, st)
+                 : launch_one<double, 0, false>(pl, maps, o0, o1, o2, st);
+  }
+  if (form == 0)
+    return start ? launch_one<float, 0, true>(pl, maps, o0, o1, o2, st)
+                 : launch_one<float, 0, false>(pl, maps, o0, o1, o2, st);
+  return start ? launch_one<float, 1, true>(pl, maps, o0, o1, o2, st)
+               : launch_one<float, 1, false>(pl, maps, o0, o1, o2, st);
+}
+
+int read_device_status(unsigned* out, bool clear) {
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tma_status, sizeof v);
+  if (e != cudaSuccess) return check_launch("read device status");
+  if (clear && v) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(g_tma_status, &z, sizeof z);
+  }
+  *out = v;
+  return FFPAT_OK;
+}
+
+}  // namespace ffpat

@@ -88,6 +88,8 @@ def _declare(L):
         "ffpat_profile_enable": (ctypes.c_int, [i32]),
         "ffpat_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile)]),
         "ffpat_launch_count": (i64, []),
+        "ffpat_set_stencil_path": (ctypes.c_int, [i32]),
+        "ffpat_device_status": (ctypes.c_int, [i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -298,6 +300,16 @@ def profile_read() -> dict:
 
 def launch_count() -> int:
     return int(lib().ffpat_launch_count())
+
+
+def set_stencil_path(path: int) -> None:
+    """0 automatic, 1 plain 2.5D leapfrog kernel, 2 TMA-fed kernel."""
+    _check(lib().ffpat_set_stencil_path(int(path)))
+
+
+def device_status(clear: bool = False) -> int:
+    """0, or the negative status of the first device-side failure."""
+    return int(lib().ffpat_device_status(1 if clear else 0))
 
 
 def version() -> str:

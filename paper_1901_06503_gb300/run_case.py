@@ -35,8 +35,10 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-kahan"], default="fp32-kahan")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--path", type=int, default=0, help="leapfrog kernel: 0 auto, 1 plain, 2 TMA")
     a = ap.parse_args(argv)
     build_lib.build()
+    F.set_stencil_path(a.path)
     prec = {"fp64": F.FP64, "fp32": F.FP32, "fp32-kahan": F.FP32_KAHAN}[a.precision]
     n = a.n
     cmax = 1.4
@@ -86,7 +88,7 @@ def main(argv=None):
         times.append(e0.elapsed_time(e1))
     prof = F.profile_read()
     F.profile_enable(False)
-    res = {"op": a.op, "n": n, "angles": a.angles, "nt": nt, "precision": a.precision,
+    res = {"op": a.op, "path": a.path, "n": n, "angles": a.angles, "nt": nt, "precision": a.precision,
            "ms": times, "ms_min": min(times)}
     if prof["step_launches"]:
         res["step_ms_avg"] = prof["step_ms"] / prof["step_launches"]

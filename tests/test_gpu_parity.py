@@ -282,3 +282,40 @@ def test_full_size_n384_fp32_spot_checks():
     lhs = float((F.project(prob, hd).double() * gt.double()).sum())
     rhs = float((hd.double() * bp.double()).sum())
     assert abs(lhs - rhs) < 1e-6 * abs(lhs)
+
+
+# ------------------------------------------------- the two stencil kernels --
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,T", [(36, 0.4), (64, 0.3), (96, 0.12)])
+def test_tma_stencil_matches_plain_and_oracle(n, T, prec):
+    """The TMA-fed kernel and the plain 2.5D kernel compute the same steps;
+    ragged tiles (36 = 64 - 28 in x, 36 = 4 x 8 + 4 in y) included."""
+    c = as_input(random_speed(n, 900 + n), prec)
+    h = as_input(random_volume(n, 901 + n), prec)
+    prob = F.problem(n, T, 4, prec)
+    outs = {}
+    try:
+        for path in (1, 2):
+            F.set_stencil_path(path)
+            outs[path] = (host(F.wave(prob, dev(c, prob), dev(h, prob))),
+                          host(F.wave(prob, dev(c, prob), dev(h, prob), transpose=True)))
+    finally:
+        F.set_stencil_path(0)
+    for a, b in zip(outs[1], outs[2]):
+        assert rel(a, b) < (1e-14 if prec == F.FP64 else 1e-6)
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    kap = o.kappa(n, dt, c)
+    assert rel(outs[2][0], o.wave(kap, h, nt)) < TOL[prec]
+    assert rel(outs[2][1], o.wave_adjoint(kap, h, nt)) < TOL[prec]
+    assert F.device_status() == 0
+
+
+def test_tma_path_rejects_unaligned_sizes():
+    prob = F.problem(33, 0.1, 4, F.FP32)
+    try:
+        F.set_stencil_path(2)
+        with pytest.raises(F.FFPATError):
+            F.wave(prob, dev(random_speed(33, 1), prob), dev(random_volume(33, 2), prob))
+    finally:
+        F.set_stencil_path(0)
