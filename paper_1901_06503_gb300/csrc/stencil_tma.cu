@@ -171,6 +171,9 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
   T* qst = reinterpret_cast<T*>(smem + SP * G::PBYTES);                  // SQ x NQ tiles
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SP * G::PBYTES + SQ * NQ * G::QBYTES);
 
+  // after a device-side failure, later launches return at once (the host
+  // reports the status word) instead of repeating bounded waits
+  if (*(volatile unsigned*)&g_tma_status != 0u) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * NTX + tx;
   if (tid == 0) {
