@@ -191,6 +191,21 @@ int ffpat_set_stencil_path(int32_t path);
  * out sets FFPAT_ETIMEDOUT).  Synchronises the device; clear != 0 resets it. */
 int ffpat_device_status(int32_t clear);
 
+/* g = P W h like ffpat_forward, for callers that cannot allocate device
+ * memory or pass a workspace (code inside an application that owns all device
+ * memory, fixed-budget or real-time pipelines that must not enter an
+ * allocator).  The paper has no counterpart; this is a deployment variant.
+ * It allocates nothing: its scratch is a 32 MiB file-scope device array that
+ * every GPU loading the library holds until exit, so problems whose
+ * ffpat_workspace_bytes exceeds 32 MiB fail with FFPAT_EINVAL (N <= 64 with up
+ * to 180 angles fits every precision).  The first call on a device looks up
+ * the array's device address (with that device current); make it before any
+ * stream capture.  All calls on a device share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  Nothing in the array
+ * needs to start at zero; it keeps the last call's contents. */
+int ffpat_forward_noalloc(const ffpat_problem *problem, const void *c, const void *h, void *g,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

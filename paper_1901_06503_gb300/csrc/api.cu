@@ -48,6 +48,14 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+int report(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
 int check_launch(const char* what) {
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(FFPAT_ECUDA, "%s: %s", what, cudaGetErrorString(e));

@@ -42,6 +42,8 @@ constexpr int kScal = 64;
 void count_launch(int k = 1);
 // FFPAT_OK, or FFPAT_ECUDA with the pending launch error recorded for ffpat_last_error()
 int check_launch(const char* what);
+// record a formatted message for ffpat_last_error() and return `code`
+int report(int code, const char* fmt, ...);
 
 // stencil.cu
 // three-term form.  start: out_p1 = p0 + kap*L(p0)/2 and copy_p0 = p0 (may be null)

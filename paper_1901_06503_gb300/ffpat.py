@@ -90,6 +90,7 @@ def _declare(L):
         "ffpat_launch_count": (i64, []),
         "ffpat_set_stencil_path": (ctypes.c_int, [i32]),
         "ffpat_device_status": (ctypes.c_int, [i32]),
+        "ffpat_forward_noalloc": (ctypes.c_int, [_PR, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -217,6 +218,15 @@ def forward(prob, c, h, g=None, ws=None, stream=None):
     _check(lib().ffpat_forward(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
                                _dev(h, prob, vol_shape(prob), "h"),
                                _dev(g, prob, data_shape(prob), "g"), wp, wn, _stream(stream)))
+    return g
+
+
+def forward_noalloc(prob, c, h, g, stream=None):
+    """g = P W h through the entry point that allocates nothing (static
+    device scratch; N <= 64 with <= 180 angles).  `g` must be preallocated."""
+    _check(lib().ffpat_forward_noalloc(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                                       _dev(h, prob, vol_shape(prob), "h"),
+                                       _dev(g, prob, data_shape(prob), "g"), _stream(stream)))
     return g
 
 
