@@ -15,6 +15,7 @@
 // sqrt(2) grid units of it in the rotated (xi, s) frame, i.e. at most 3 x 3
 // candidates; each contributes hat(dx) hat(dy) times its row value, which is
 // exactly the bilinear weight P gives that voxel.  Deterministic: fixed order.
+// P stages the plane in shared memory when it fits (N <= 220 in FP32).
 //
 // Lambda: one CTA per detector row, the row staged in shared memory, the odd
 // taps t_d = -1/(2 pi^2 d^2 dxi) and t_0 = 1/(8 dxi) applied as a linear
@@ -80,8 +81,8 @@ __device__ __forceinline__ void ray_range(float cs, float sn, int k, int n, int 
     return;
   }
   const float off = 0.5f * (float)ns - 0.5f;
-  mlo = max(0, (int)floorf(vlo + off) - 2);
-  mhi = min(ns, (int)ceilf(vhi + off) + 3);
+  mlo = max(0, (int)floorf(vlo + off) - 1);
+  mhi = min(ns, (int)ceilf(vhi + off) + 2);
   if (mhi < mlo) mhi = mlo;
 }
 
@@ -150,70 +151,178 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T hat(T a) {
-  const T v = T(1) - (a < T(0) ? -a : a);
-  return v > T(0) ? v : T(0);
-}
+// P with the whole plane staged in shared memory behind a zero border of
+// kPad points, so the bilinear corner loads need no bounds tests (used when
+// the padded plane fits; one CTA per (plane, group of angles), threads over
+// (angle, detector) pairs).  Same per-sample arithmetic as k_project.
+constexpr int kPad = 3;
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_backproject(const T* __restrict__ g, T* __restrict__ h, const T* __restrict__ scale,
-                  const double* __restrict__ tab, const float* __restrict__ tabf,
-                  const int32_t* __restrict__ tabi, int n, int nth, int ns) {
+    k_project_smem(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
+                   const double* __restrict__ tab, const float* __restrict__ tabf,
+                   const int32_t* __restrict__ tabi, int n, int nth, int ns, int group) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int W = n + 2 * kPad;
+  const int l = blockIdx.x;
+  const int ja = blockIdx.y * group, jb = min(nth, ja + group);
+  const T* __restrict__ sl = p + (size_t)l * n * n;
+  for (int yy = threadIdx.x / 32; yy < W; yy += blockDim.x / 32) {
+    const int y = yy - kPad;
+    for (int xx = threadIdx.x % 32; xx < W; xx += 32) {
+      const int x = xx - kPad;
+      s[yy * W + xx] = (x >= 0 && y >= 0 && x < n && y < n) ? __ldg(sl + (size_t)y * n + x) : T(0);
+    }
+  }
+  __syncthreads();
+  // corner (i0, j0) of the padded plane, clamped so that no load leaves it
+  auto at = [&](int j0, int i0) -> int {
+    const int jj = min(max(j0 + kPad, 0), W - 2), ii = min(max(i0 + kPad, 0), W - 2);
+    return jj * W + ii;
+  };
+  const int work = (jb - ja) * n;
+  for (int w = threadIdx.x; w < work; w += blockDim.x) {
+    const int j = ja + w / n, k = w % n;
+    int mlo, mhi;
+    ray_range(tabf[j], tabf[nth + j], k, n, ns, mlo, mhi);
+    T acc = T(0);
+    if constexpr (sizeof(T) == 8) {
+      const double cs = tab[j], sn = tab[nth + j];
+      const double dx = 2.0 / n, half = n / 2.0;
+      for (int m = mlo; m < mhi; ++m) {
+        int i0, j0;
+        double fx, fy;
+        sample64(cs, sn, k, m, ns, dx, half, i0, j0, fx, fy);
+        const int o = at(j0, i0);
+        const double ofx = __dsub_rn(1.0, fx), ofy = __dsub_rn(1.0, fy);
+        double b = __dmul_rn(__dmul_rn(ofx, ofy), s[o]);
+        b = __dadd_rn(b, __dmul_rn(__dmul_rn(fx, ofy), s[o + 1]));
+        b = __dadd_rn(b, __dmul_rn(__dmul_rn(ofx, fy), s[o + W]));
+        b = __dadd_rn(b, __dmul_rn(__dmul_rn(fx, fy), s[o + W + 1]));
+        acc = __dadd_rn(acc, b);
+      }
+      double out = __dmul_rn(dx, acc);
+      const size_t oo = ((size_t)j * n + l) * n + k;
+      if (sub) out = out - sub[oo];
+      g[oo] = out;
+    } else {
+      const long long CS = tabi[j], SN = tabi[nth + j];
+      const long long u2 = 2LL * k + 1 - n, v2 = 2LL * mlo + 1 - ns;
+      const long long c2 = (long long)(n - 1) << 30;
+      long long GX = c2 + u2 * CS - v2 * SN;
+      long long GY = c2 + u2 * SN + v2 * CS;
+      const long long dGX = -2 * SN, dGY = 2 * CS;
+      constexpr float kInv = 4.656612873077392578125e-10f;  // 2^-31
+      for (int m = mlo; m < mhi; ++m) {
+        const int i0 = (int)(GX >> 31), j0 = (int)(GY >> 31);
+        const float fx = (float)(unsigned)(GX & 0x7fffffffLL) * kInv;
+        const float fy = (float)(unsigned)(GY & 0x7fffffffLL) * kInv;
+        GX += dGX;
+        GY += dGY;
+        const int o = at(j0, i0);
+        const float v00 = s[o], v10 = s[o + 1], v01 = s[o + W], v11 = s[o + W + 1];
+        const float r0 = fmaf(fx, v10 - v00, v00);
+        const float r1 = fmaf(fx, v11 - v01, v01);
+        acc += fmaf(fy, r1 - r0, r0);
+      }
+      float out = (2.0f / (float)n) * acc;
+      const size_t oo = ((size_t)j * n + l) * n + k;
+      if (sub) out = out - sub[oo];
+      g[oo] = out;
+    }
+  }
+}
+
+// P^T, voxel-driven gather (deterministic, no atomics).  For each angle the
+// voxel's position in the rotated frame, kk (detector units) and mm (sample
+// units), is split into integer and fractional parts; the samples that can
+// reach the voxel are the 3 x 3 candidates k = kb .. kb + 2, m = mb .. mb + 2
+// around it (|k - kk|, |m - mm| < sqrt 2).  Each contributes hat(a) hat(b) of
+// its offset (a, b) in the grid frame, the bilinear weight P gives the voxel;
+// a and b step by (cos, sin) and (-sin, cos) between candidates.
+template <typename T>
+__device__ __forceinline__ T hat1(T a) {
+  const T v = T(1) - fabs(a);
+  return v > T(0) ? v : T(0);
+}
+
+constexpr int kAngleChunk = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_backproject2(const T* __restrict__ g, T* __restrict__ h, const T* __restrict__ scale,
+                   const double* __restrict__ tab, const float* __restrict__ tabf,
+                   const int32_t* __restrict__ tabi, int n, int nth, int ns) {
+  __shared__ T s_cs[kAngleChunk], s_sn[kAngleChunk];
+  __shared__ int s_CS[kAngleChunk], s_SN[kAngleChunk];
   const int ix = blockIdx.x * 32 + threadIdx.x;
   const int iy = blockIdx.y * 8 + threadIdx.y;
   const int l = blockIdx.z;
-  if (ix >= n || iy >= n) return;
-  constexpr float R = 1.41521f;  // sqrt(2) plus a margin; the hat weights vanish beyond it
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const bool in = ix < n && iy < n;
   T acc = T(0);
-  if constexpr (sizeof(T) == 8) {
-    const double cN = 0.5 * (n - 1);
-    const double X = ix - cN, Y = iy - cN;
-    const double koff = 0.5 * n - 0.5, moff = 0.5 * ns - 0.5;
-    for (int j = 0; j < nth; ++j) {
-      const double cs = tab[j], sn = tab[nth + j];
-      const double kk = X * cs + Y * sn + koff;  // detector index of the voxel
-      const double mm = Y * cs - X * sn + moff;  // ray sample index of the voxel
-      const int klo = max(0, (int)ceil(kk - R)), khi = min(n - 1, (int)floor(kk + R));
-      const int mlo = max(0, (int)ceil(mm - R)), mhi = min(ns - 1, (int)floor(mm + R));
-      const double* __restrict__ row = g + ((size_t)j * n + l) * n;
-      for (int k = klo; k <= khi; ++k) {
-        const double du = k - kk;
-        double wsum = 0.0;
-        for (int m = mlo; m <= mhi; ++m) {
-          const double dv = m - mm;
-          wsum += hat(du * cs - dv * sn) * hat(du * sn + dv * cs);
-        }
-        acc += wsum * __ldg(row + k);
+  for (int ja = 0; ja < nth; ja += kAngleChunk) {
+    const int jn = min(kAngleChunk, nth - ja);
+    __syncthreads();
+    for (int t = tid; t < jn; t += 256) {
+      if constexpr (sizeof(T) == 8) {
+        s_cs[t] = tab[ja + t];
+        s_sn[t] = tab[nth + ja + t];
+      } else {
+        s_cs[t] = tabf[ja + t];
+        s_sn[t] = tabf[nth + ja + t];
       }
+      s_CS[t] = tabi[ja + t];
+      s_SN[t] = tabi[nth + ja + t];
     }
-  } else {
-    // voxel position in the rotated frame in fixed point (scale 2^31) so
-    // that the offsets du, dv to the candidate samples are exact to ~1e-9
-    const long long X2 = 2LL * ix - (n - 1), Y2 = 2LL * iy - (n - 1);
-    const long long koff = (long long)(n - 1) << 30, moff = (long long)(ns - 1) << 30;
-    constexpr float kInv = 4.656612873077392578125e-10f;  // 2^-31
-    for (int j = 0; j < nth; ++j) {
-      const long long CS = tabi[j], SN = tabi[nth + j];
-      const float cs = tabf[j], sn = tabf[nth + j];
-      const long long KK = X2 * CS + Y2 * SN + koff;
-      const long long MM = Y2 * CS - X2 * SN + moff;
-      const float kkf = (float)KK * kInv, mmf = (float)MM * kInv;
-      const int klo = max(0, (int)ceilf(kkf - R)), khi = min(n - 1, (int)floorf(kkf + R));
-      const int mlo = max(0, (int)ceilf(mmf - R)), mhi = min(ns - 1, (int)floorf(mmf + R));
-      const float* __restrict__ row = g + ((size_t)j * n + l) * n;
-      for (int k = klo; k <= khi; ++k) {
-        const float du = (float)(((long long)k << 31) - KK) * kInv;
-        float wsum = 0.0f;
-        for (int m = mlo; m <= mhi; ++m) {
-          const float dv = (float)(((long long)m << 31) - MM) * kInv;
-          wsum += hat(du * cs - dv * sn) * hat(du * sn + dv * cs);
-        }
-        acc += wsum * __ldg(row + k);
+    __syncthreads();
+    if (!in) continue;
+    for (int t = 0; t < jn; ++t) {
+      const T cs = s_cs[t], sn = s_sn[t];
+      int KI, MI;
+      T fk, fm;
+      if constexpr (sizeof(T) == 8) {
+        const double X = ix - 0.5 * (n - 1), Y = iy - 0.5 * (n - 1);
+        const double kk = fma(X, cs, Y * sn) + 0.5 * (n - 1);
+        const double mm = fma(Y, cs, -X * sn) + 0.5 * (ns - 1);
+        const double fkk = floor(kk), fmm = floor(mm);
+        KI = (int)fkk;
+        MI = (int)fmm;
+        fk = kk - fkk;
+        fm = mm - fmm;
+      } else {
+        // fixed point, scale 2^31: exact integer parts, fractions to ~1e-9
+        const long long X2 = 2LL * ix - (n - 1), Y2 = 2LL * iy - (n - 1);
+        const long long KK = X2 * s_CS[t] + Y2 * s_SN[t] + ((long long)(n - 1) << 30);
+        const long long MM = Y2 * s_CS[t] - X2 * s_SN[t] + ((long long)(ns - 1) << 30);
+        constexpr float kInv = 4.656612873077392578125e-10f;
+        KI = (int)(KK >> 31);
+        MI = (int)(MM >> 31);
+        fk = (float)(unsigned)(KK & 0x7fffffffLL) * kInv;
+        fm = (float)(unsigned)(MM & 0x7fffffffLL) * kInv;
+      }
+      const int hk = fk >= T(0.5) ? 1 : 0, hm = fm >= T(0.5) ? 1 : 0;
+      const int kb = KI - 1 + hk, mb = MI - 1 + hm;
+      const T du0 = T(hk - 1) - fk, dv0 = T(hm - 1) - fm;  // offsets of candidate (kb, mb)
+      const T a0 = du0 * cs - dv0 * sn, b0 = du0 * sn + dv0 * cs;
+      const bool m0 = mb >= 0 && mb < ns, m1 = mb + 1 >= 0 && mb + 1 < ns,
+                 m2 = mb + 2 >= 0 && mb + 2 < ns;
+      const T* __restrict__ row = g + ((size_t)(ja + t) * n + l) * n;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int k = kb + i;
+        if (k < 0 || k >= n) continue;
+        const T ai = a0 + T(i) * cs, bi = b0 + T(i) * sn;
+        T w = T(0);
+        if (m0) w += hat1(ai) * hat1(bi);
+        if (m1) w += hat1(ai - sn) * hat1(bi + cs);
+        if (m2) w += hat1(ai - T(2) * sn) * hat1(bi + T(2) * cs);
+        acc += w * __ldg(row + k);
       }
     }
   }
+  if (!in) return;
   const size_t o = ((size_t)l * n + iy) * n + ix;
   T out = (T(2) / T(n)) * acc;
   if (scale) out *= scale[o];
@@ -271,6 +380,36 @@ __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int3
 }  // namespace
 
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st) {
+  const size_t W = (size_t)pl.n + 2 * kPad;
+  const size_t smem = W * W * pl.esize;
+  if (smem <= 200 * 1024) {
+    // one CTA per (plane, group of 8 angles); the padded plane is read once per CTA
+    const int group = 8;
+    const dim3 grid(pl.n, (pl.nth + group - 1) / group);
+    if (pl.prec == FFPAT_FP64) {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_project_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        attr = true;
+      }
+      k_project_smem<double><<<grid, 256, smem, st>>>((const double*)p, (double*)g,
+                                                      (const double*)sub, pl.tab, pl.tabf, pl.tabi,
+                                                      pl.n, pl.nth, pl.ns, group);
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_project_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        attr = true;
+      }
+      k_project_smem<float><<<grid, 256, smem, st>>>((const float*)p, (float*)g, (const float*)sub,
+                                                     pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns,
+                                                     group);
+    }
+    count_launch();
+    return check_launch(__func__);
+  }
   const dim3 block(128);
   const dim3 grid((pl.n + 127) / 128, pl.n, pl.nth);
   if (pl.prec == FFPAT_FP64)
@@ -287,11 +426,11 @@ int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale
   const dim3 block(32, 8);
   const dim3 grid((pl.n + 31) / 32, (pl.n + 7) / 8, pl.n);
   if (pl.prec == FFPAT_FP64)
-    k_backproject<double><<<grid, block, 0, st>>>((const double*)g, (double*)h,
+    k_backproject2<double><<<grid, block, 0, st>>>((const double*)g, (double*)h,
                                                   (const double*)scale, pl.tab, pl.tabf,
                                                   pl.tabi, pl.n, pl.nth, pl.ns);
   else
-    k_backproject<float><<<grid, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
+    k_backproject2<float><<<grid, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
                                                  pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns);
   count_launch();
   return check_launch(__func__);
