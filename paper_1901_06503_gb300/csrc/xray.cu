@@ -44,6 +44,14 @@ __device__ __forceinline__ void sample64(double cs, double sn, int k, int m, int
   fy = __dsub_rn(gy, fly);
 }
 
+// fraction (bits 0..30 of a scale-2^31 fixed-point value) as a float in
+// [0, 1): the top 23 fraction bits become the mantissa of a number in [1, 2)
+// (integer and logic ops only; no int-to-float conversion)
+__device__ __forceinline__ float frac31(long long v) {
+  const unsigned f = (unsigned)v & 0x7fffffffu;
+  return __uint_as_float(0x3f800000u | (f >> 8)) - 1.0f;
+}
+
 template <typename T>
 __device__ __forceinline__ T pix(const T* __restrict__ sl, int n, int iy, int ix) {
   return (ix >= 0 && iy >= 0 && ix < n && iy < n) ? __ldg(sl + (size_t)iy * n + ix) : T(0);
@@ -129,11 +137,9 @@ __global__ void __launch_bounds__(128)
     long long GX = c2 + u2 * CS - v2 * SN;
     long long GY = c2 + u2 * SN + v2 * CS;
     const long long dGX = -2 * SN, dGY = 2 * CS;
-    constexpr float kInv = 4.656612873077392578125e-10f;  // 2^-31
     for (int m = mlo; m < mhi; ++m) {
       const int i0 = (int)(GX >> 31), j0 = (int)(GY >> 31);
-      const float fx = (float)(unsigned)(GX & 0x7fffffffLL) * kInv;
-      const float fy = (float)(unsigned)(GY & 0x7fffffffLL) * kInv;
+      const float fx = frac31(GX), fy = frac31(GY);
       GX += dGX;
       GY += dGY;
       const float v00 = pix(sl, n, j0, i0), v10 = pix(sl, n, j0, i0 + 1);
@@ -213,11 +219,9 @@ __global__ void __launch_bounds__(256)
       long long GX = c2 + u2 * CS - v2 * SN;
       long long GY = c2 + u2 * SN + v2 * CS;
       const long long dGX = -2 * SN, dGY = 2 * CS;
-      constexpr float kInv = 4.656612873077392578125e-10f;  // 2^-31
       for (int m = mlo; m < mhi; ++m) {
         const int i0 = (int)(GX >> 31), j0 = (int)(GY >> 31);
-        const float fx = (float)(unsigned)(GX & 0x7fffffffLL) * kInv;
-        const float fy = (float)(unsigned)(GY & 0x7fffffffLL) * kInv;
+        const float fx = frac31(GX), fy = frac31(GY);
         GX += dGX;
         GY += dGY;
         const int o = at(j0, i0);
@@ -293,14 +297,14 @@ __global__ void __launch_bounds__(256)
         fm = mm - fmm;
       } else {
         // fixed point, scale 2^31: exact integer parts, fractions to ~1e-9
-        const long long X2 = 2LL * ix - (n - 1), Y2 = 2LL * iy - (n - 1);
-        const long long KK = X2 * s_CS[t] + Y2 * s_SN[t] + ((long long)(n - 1) << 30);
-        const long long MM = Y2 * s_CS[t] - X2 * s_SN[t] + ((long long)(ns - 1) << 30);
-        constexpr float kInv = 4.656612873077392578125e-10f;
+        const int X2 = 2 * ix - (n - 1), Y2 = 2 * iy - (n - 1);
+        const int CS = s_CS[t], SN = s_SN[t];
+        const long long KK = (long long)X2 * CS + (long long)Y2 * SN + ((long long)(n - 1) << 30);
+        const long long MM = (long long)Y2 * CS - (long long)X2 * SN + ((long long)(ns - 1) << 30);
         KI = (int)(KK >> 31);
         MI = (int)(MM >> 31);
-        fk = (float)(unsigned)(KK & 0x7fffffffLL) * kInv;
-        fm = (float)(unsigned)(MM & 0x7fffffffLL) * kInv;
+        fk = frac31(KK);
+        fm = frac31(MM);
       }
       const int hk = fk >= T(0.5) ? 1 : 0, hm = fm >= T(0.5) ? 1 : 0;
       const int kb = KI - 1 + hk, mb = MI - 1 + hm;
