@@ -57,6 +57,7 @@ typedef enum {
   FFPAT_ECUDA = -3,     /* a CUDA runtime call failed */
   FFPAT_EBUSY = -4,     /* server queue full */
   FFPAT_ETIMEDOUT = -5, /* a bounded wait ran out */
+  FFPAT_ECANCELED = -6, /* server request cancelled */
   FFPAT_PENDING = 1     /* server request not finished yet */
 } ffpat_status;
 
@@ -190,6 +191,55 @@ int ffpat_set_stencil_path(int32_t path);
  * the first device-side failure since the last clear (a bounded wait that ran
  * out sets FFPAT_ETIMEDOUT).  Synchronises the device; clear != 0 resets it. */
 int ffpat_device_status(int32_t clear);
+
+/* ---- Serving: many Algorithm-8 solves in flight on one GPU (continuous batching).
+ * A server owns a worker thread and a CUDA stream on the device that is
+ * current at creation.  Requests (FFPAT_FP32_KAHAN problems with N % 4 == 0;
+ * any N, angle count, T) wait in a FIFO queue and are admitted while a slot is
+ * free and their device memory fits the HBM budget; every launch of the
+ * leapfrog kernel advances all admitted requests that are inside a wave phase
+ * by one step, and requests that arrive while others run join at the next
+ * step.  Each request runs exactly the kernels of ffpat_fb_solve, so its
+ * result does not depend on the other requests.  The paper has no serving
+ * layer; this is the deployment side of Algorithm 8. */
+typedef struct ffpat_server ffpat_server;
+
+typedef struct {
+  int64_t completed, failed, cancelled;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* submit-to-completion latency */
+  double point_steps;                     /* leapfrog point-steps of completed requests */
+  int64_t ticks;                          /* batched leapfrog launches so far */
+  int32_t active, queued;
+  size_t hbm_in_use;                      /* bytes held by admitted requests */
+} ffpat_serving_stats;
+
+/* Create a server: hbm_budget_bytes bounds the device memory of admitted
+ * requests (each needs ffpat_workspace_bytes + 8 N^3 + 4 n_angles N^2 bytes);
+ * max_slots (1..28) bounds how many run at once. */
+int ffpat_server_create(size_t hbm_budget_bytes, int32_t max_slots, ffpat_server **out);
+
+/* Queue a reconstruction: c_host (N^3 float) and g_host (n_angles N^2 float)
+ * are HOST arrays, copied before the call returns; h_0 = 0; `iters` FB
+ * iterations with the given lambda; step <= 0 runs 20 power iterations first
+ * (as ffpat_fb_solve does).  Returns a ticket.  FFPAT_EBUSY if the queue holds
+ * 4096 requests; FFPAT_EINVAL if the request can never fit the budget. */
+int ffpat_submit(ffpat_server *server, const ffpat_problem *problem, const void *c_host,
+                 const void *g_host, double lambda, double step, int32_t iters, uint64_t *ticket);
+
+/* Non-blocking: FFPAT_PENDING while the request runs; FFPAT_OK once done (the
+ * iterate is copied to h_out_host, N^3 float, and *stats filled; the ticket is
+ * then released); FFPAT_ECANCELED or another error if it failed. */
+int ffpat_poll(ffpat_server *server, uint64_t ticket, void *h_out_host, ffpat_fb_stats *stats);
+
+/* Cancel a queued or running request (only that request is affected). */
+int ffpat_cancel(ffpat_server *server, uint64_t ticket);
+
+/* Latency percentiles and throughput counters; returns the worker's fatal
+ * error code (0 if none). */
+int ffpat_server_stats(ffpat_server *server, ffpat_serving_stats *out);
+
+/* Stop the worker (queued and running requests are cancelled) and free all. */
+int ffpat_server_destroy(ffpat_server *server);
 
 /* g = P W h like ffpat_forward, for callers that cannot allocate device
  * memory or pass a workspace (code inside an application that owns all device

@@ -132,7 +132,7 @@ static size_t carve(Plan& pl, void* ws) {
   return off;
 }
 
-static int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes) {
+int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes) {
   TRY(validate(pr, pl));
   const size_t need = carve(pl, nullptr);
   if (!ws) return fail(FFPAT_EINVAL, "workspace is NULL (%zu bytes needed)", need);
@@ -143,7 +143,7 @@ static int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes) 
   return FFPAT_OK;
 }
 
-static void host_angles(int nth, std::vector<double>& cs_sn) {
+void host_angles(int nth, std::vector<double>& cs_sn) {
   cs_sn.resize(2 * (size_t)nth);
   for (int j = 0; j < nth; ++j) {
     const double th = (M_PI * j) / nth;
@@ -155,19 +155,24 @@ static void host_angles(int nth, std::vector<double>& cs_sn) {
 // Fill the three angle tables at `base` (device, table_bytes(nth) bytes):
 // double cos/sin, their float roundings, and round(cos/sin * 2^30) as int32
 // for the fixed-point sample coordinates of the FP32 projection pair.
-static int upload_tables(Plan& pl, void* base, cudaStream_t st) {
+void fill_tables_host(int nth, unsigned char* buf) {
   std::vector<double> t;
-  host_angles(pl.nth, t);
+  host_angles(nth, t);
   const size_t m = t.size();
-  std::vector<unsigned char> buf(table_bytes(pl.nth));
-  double* d = (double*)buf.data();
-  float* f = (float*)(buf.data() + 8 * m);
-  int32_t* q = (int32_t*)(buf.data() + 12 * m);
+  double* d = (double*)buf;
+  float* f = (float*)(buf + 8 * m);
+  int32_t* q = (int32_t*)(buf + 12 * m);
   for (size_t i = 0; i < m; ++i) {
     d[i] = t[i];
     f[i] = (float)t[i];
     q[i] = (int32_t)llrint(t[i] * 1073741824.0);
   }
+}
+
+static int upload_tables(Plan& pl, void* base, cudaStream_t st) {
+  const size_t m = 2 * (size_t)pl.nth;
+  std::vector<unsigned char> buf(table_bytes(pl.nth));
+  fill_tables_host(pl.nth, buf.data());
   pl.tab = (double*)base;
   pl.tabf = (float*)((char*)base + 8 * m);
   pl.tabi = (int32_t*)((char*)base + 12 * m);
@@ -177,7 +182,7 @@ static int upload_tables(Plan& pl, void* base, cudaStream_t st) {
   return FFPAT_OK;
 }
 
-static int time_steps(const Plan& pl, double cmax, int* nt, double* dt) {
+int time_steps(const Plan& pl, double cmax, int* nt, double* dt) {
   const double x = pl.T * cmax / (pl.cfl * pl.dx);
   const double steps = ceil(x * (1.0 - 1e-12));
   if (!(steps < 2e9)) return fail(FFPAT_EINVAL, "T c_max / (cfl dx) = %g steps is too many", x);

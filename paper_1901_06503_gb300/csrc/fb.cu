@@ -148,8 +148,10 @@ __global__ void __launch_bounds__(kReduceThreads)
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads)
     k_fb_update(T* __restrict__ h, const T* __restrict__ w, const T* __restrict__ kap, size_t len,
-                double step, double lambda, double* __restrict__ partials) {
+                double step, const double* __restrict__ step_dev, double lambda,
+                double* __restrict__ partials) {
   double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
+  if (step_dev) step = *step_dev;
   const T s = (T)step, sl = (T)(step * lambda);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -174,6 +176,12 @@ __global__ void __launch_bounds__(kReduceThreads)
     partials[2 * kReduceBlocks + blockIdx.x] = dd;
     partials[3 * kReduceBlocks + blockIdx.x] = nn;
   }
+}
+
+// dst = 1 / sqrt(src): the step 1 / L from the last power-iteration norm,
+// the same arithmetic as the host's 1.0 / sqrt(.)
+__global__ void k_inv_sqrt(const double* __restrict__ src, double* __restrict__ dst) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) dst[0] = 1.0 / sqrt(src[0]);
 }
 
 // counter-based pseudo-random start vector (splitmix64 + Box-Muller)
@@ -257,15 +265,23 @@ int launch_dot(const Plan& pl, size_t len, const void* a, const void* b, double*
 }
 
 int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double lambda,
-                     double* dst, cudaStream_t st) {
+                     double* dst, cudaStream_t st, const double* step_dev) {
   if (pl.prec == FFPAT_FP64)
     k_fb_update<double><<<kReduceBlocks, kReduceThreads, 0, st>>>(
-        (double*)h, (const double*)w, (const double*)pl.kap, pl.n3, step, lambda, pl.partials);
+        (double*)h, (const double*)w, (const double*)pl.kap, pl.n3, step, step_dev, lambda,
+        pl.partials);
   else
     k_fb_update<float><<<kReduceBlocks, kReduceThreads, 0, st>>>(
-        (float*)h, (const float*)w, (const float*)pl.kap, pl.n3, step, lambda, pl.partials);
+        (float*)h, (const float*)w, (const float*)pl.kap, pl.n3, step, step_dev, lambda,
+        pl.partials);
   k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 4, dst);
   count_launch(2);
+  return check_launch(__func__);
+}
+
+int launch_inv_sqrt(const double* src, double* dst, cudaStream_t st) {
+  k_inv_sqrt<<<1, 32, 0, st>>>(src, dst);
+  count_launch();
   return check_launch(__func__);
 }
 

@@ -38,6 +38,11 @@ inline size_t table_bytes(int nth) { return (size_t)nth * 2 * (8 + 4 + 4); }
 constexpr int kMaxHist = 4096;
 constexpr int kScal = 64;
 
+// api.cu helpers shared with the server
+int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes);
+int time_steps(const Plan& pl, double cmax, int* nt, double* dt);
+void fill_tables_host(int nth, unsigned char* buf);  // table_bytes(nth) bytes
+
 // ---------------------------------------------------------------- launches --
 void count_launch(int k = 1);
 // FFPAT_OK, or FFPAT_ECUDA with the pending launch error recorded for ffpat_last_error()
@@ -60,6 +65,21 @@ int launch_step_inc(const Plan& pl, const void* pin, void* pout, void* d, void* 
 bool tma_supported(const Plan& pl, const void* const* ptrs, int count);
 int launch_step_tma(const Plan& pl, int form, bool start, const void* p, const void* const* q,
                     void* o0, void* o1, void* o2, cudaStream_t st);
+// One FP32-Kahan leapfrog step for each of `count` independent problems in a
+// single launch (same arithmetic as launch_step_tma form 1).  start: the step
+// p^1 = p^0 + d^1 with d, e written, else the regular step reading d, e.
+struct BatchStep {
+  const float* p;   // p^n (N^3, 16-byte aligned, N % 4 == 0)
+  float* pout;      // p^{n+1}
+  float* d;         // increment, updated in place
+  float* e;         // Kahan carry, updated in place
+  const float* kap; // kappa / 12
+  int n;
+  bool start;
+};
+int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st);
+constexpr int kMaxBatchRequests = 28;
+
 // device status word of the TMA kernels (0 = ok, else -FFPAT_* of the first error)
 int read_device_status(unsigned* out, bool clear);
 
@@ -82,8 +102,10 @@ int launch_scale_dev(const Plan& pl, size_t len, const void* a, void* out, const
 int launch_dot(const Plan& pl, size_t len, const void* a, const void* b, double* result,
                cudaStream_t st);
 // FB update + partial norms; results land in dst[0..3]
+// step_dev (optional): read the step from device memory instead of `step`
 int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double lambda,
-                     double* dst, cudaStream_t st);
+                     double* dst, cudaStream_t st, const double* step_dev = nullptr);
+int launch_inv_sqrt(const double* src, double* dst, cudaStream_t st);
 int launch_hash_fill(const Plan& pl, void* out, uint64_t seed, cudaStream_t st);
 
 }  // namespace ffpat

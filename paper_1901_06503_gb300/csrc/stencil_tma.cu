@@ -272,6 +272,136 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
   }
 }
 
+// ---------------------------------------------- batched step (serving) --
+// One launch advances several independent problems (different N) by one
+// FP32-Kahan leapfrog step each: the work items of all requests are
+// concatenated and the persistent grid walks them.  The per-point arithmetic
+// is the one of k_step_tma<float, 1, *>, so a request's result does not depend
+// on which other requests share its launches.  Start steps (which read only
+// kap besides p) and regular steps (d, e, kap) may share a launch.
+constexpr int kMaxBatch = 28;
+
+struct BatchReq {
+  CUtensorMap p;     // p^n with the halo box
+  CUtensorMap q[3];  // d, e, kap (halo-free)
+  float* o0;         // p^{n+1}
+  float* o1;         // d^{n+1}
+  float* o2;         // e^{n+1}
+  int n, zc, tiles_x, tiles_y, start;
+};
+
+struct BatchParams {
+  int count;
+  int item_end[kMaxBatch];  // exclusive prefix of the requests' item counts
+  BatchReq r[kMaxBatch];
+};
+
+__global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constant__ BatchParams bp) {
+  using G = Geo<float>;
+  constexpr int NQ = 3;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  float* pst = reinterpret_cast<float*>(smem);
+  float* qst = reinterpret_cast<float*>(smem + SP * G::PBYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SP * G::PBYTES + SQ * NQ * G::QBYTES);
+  if (*(volatile unsigned*)&g_tma_status != 0u) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * NTX + tx;
+  if (tid == 0) {
+    for (int i = 0; i < SP; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  const int nitems = bp.item_end[bp.count - 1];
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int r = 0;
+    while (item >= bp.item_end[r]) ++r;
+    const BatchReq& q = bp.r[r];
+    const int local = item - (r ? bp.item_end[r - 1] : 0);
+    const int n = q.n;
+    const int tix = local % q.tiles_x;
+    const int tiy = (local / q.tiles_x) % q.tiles_y;
+    const int z0 = (local / (q.tiles_x * q.tiles_y)) * q.zc;
+    const int z1 = min(n, z0 + q.zc);
+    const int x0 = tix * TBX, y0 = tiy * TBY;
+    const bool start = q.start != 0;
+    const size_t plane = (size_t)n * n;
+    // round R: p plane R and the stream planes R - 2 (kap only at a start step)
+    auto issue = [&](int R) {
+      const bool wp = R <= z1 + 1;
+      const bool wq = (R - 2 >= z0) && (R - 2 < z1);
+      if (!wp && !wq) return;
+      uint64_t* b = &bar[R & (SP - 1)];
+      mbar_expect_tx(b, (wp ? G::PBYTES : 0) + (wq ? (start ? 1 : NQ) * G::QBYTES : 0));
+      if (wp)
+        tma_load_3d(pst + (size_t)(R & (SP - 1)) * (G::PBYTES / 4), &q.p, x0 - G::XH, y0 - 2, R, b);
+      if (wq) {
+        const int sl = (R - 2) & (SQ - 1);
+        for (int k = start ? 2 : 0; k < NQ; ++k)
+          tma_load_3d(qst + (size_t)(sl * NQ + k) * (G::QBYTES / 4), &q.q[k], x0, y0, R - 2, b);
+      }
+    };
+    if (tid == 0)
+      for (int R = z0 - 2; R <= z0 + SP - 3; ++R) issue(R);
+    bool timed_out = false;
+    int waited_upto = z0 - 3;
+    for (int z = z0; z < z1; ++z) {
+      for (int R = waited_upto + 1; R <= z + 2; ++R) {
+        const int b = R & (SP - 1);
+        if (!mbar_wait(&bar[b], (phase >> b) & 1u, kWaitCycles)) timed_out = true;
+        phase ^= 1u << b;
+      }
+      waited_upto = z + 2;
+      const float* P0 = pst + (size_t)(z & (SP - 1)) * (G::PBYTES / 4);
+      const float* Pm1 = pst + (size_t)((z - 1) & (SP - 1)) * (G::PBYTES / 4);
+      const float* Pp1 = pst + (size_t)((z + 1) & (SP - 1)) * (G::PBYTES / 4);
+      const float* Pm2 = pst + (size_t)((z - 2) & (SP - 1)) * (G::PBYTES / 4);
+      const float* Pp2 = pst + (size_t)((z + 2) & (SP - 1)) * (G::PBYTES / 4);
+      const float* Qd = qst + (size_t)((z & (SQ - 1)) * NQ) * (G::QBYTES / 4);
+      const int y = y0 + ty;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int xl = tx + 32 * h;
+        const int x = x0 + xl;
+        const int o = (ty + 2) * G::BXH + xl + G::XH;
+        const int qo = ty * TBX + xl;
+        const float L = lap12_diff(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
+        const float c = P0[o];
+        const float k = Qd[2 * (G::QBYTES / 4) + qo];
+        if (x < n && y < n) {
+          const size_t gi = (size_t)z * plane + (size_t)y * n + x;
+          float dn, eold;
+          if (start) {
+            dn = 0.5f * k * L;
+            eold = 0.0f;
+          } else {
+            dn = fmaf(k, L, Qd[qo]);
+            eold = Qd[(G::QBYTES / 4) + qo];
+          }
+          const float yv = dn - eold;
+          const float tv = c + yv;
+          q.o0[gi] = tv;
+          q.o1[gi] = dn;
+          q.o2[gi] = (tv - c) - yv;
+        }
+      }
+      if (__syncthreads_or(timed_out)) {
+        if (tid == 0) {
+          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+          for (int R = waited_upto + 1; R <= min(z1 + 1, z + SP - 3); ++R) {
+            const int b = R & (SP - 1);
+            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
+            phase ^= 1u << b;
+          }
+        }
+        return;
+      }
+      if (tid == 0) issue(z + SP - 2);
+    }
+  }
+}
+
 // ------------------------------------------------------------- host side --
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -387,6 +517,61 @@ int launch_step_tma(const Plan& pl, int form, bool start, const void* p, const v
                  : launch_one<float, 0, false>(pl, maps, o0, o1, o2, st);
   return start ? launch_one<float, 1, true>(pl, maps, o0, o1, o2, st)
                : launch_one<float, 1, false>(pl, maps, o0, o1, o2, st);
+}
+
+int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
+  if (count < 1) return FFPAT_OK;
+  if (count > kMaxBatch) return report(FFPAT_EINVAL, "batched step: %d requests > %d", count, kMaxBatch);
+  using G = Geo<float>;
+  const size_t smem = (size_t)SP * G::PBYTES + (size_t)SQ * 3 * G::QBYTES + SP * 8 + 1024;
+  static int occ = 0;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute(k_step_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_batch, NTX * NTY, smem);
+    if (occ < 1) occ = 1;
+  });
+  static thread_local BatchParams bp;
+  int total = 0;
+  long long total_points = 0;
+  for (int i = 0; i < count; ++i) total_points += (long long)steps[i].n * steps[i].n * steps[i].n;
+  const int slots = kNumSMs * occ;
+  bp.count = count;
+  for (int i = 0; i < count; ++i) {
+    const BatchStep& b = steps[i];
+    BatchReq& r = bp.r[i];
+    if (make_map(&r.p, b.p, b.n, 4, true) != FFPAT_OK || make_map(&r.q[2], b.kap, b.n, 4, false) != FFPAT_OK)
+      return report(FFPAT_ECUDA, "batched step: tensor map");
+    if (!b.start) {
+      if (make_map(&r.q[0], b.d, b.n, 4, false) != FFPAT_OK ||
+          make_map(&r.q[1], b.e, b.n, 4, false) != FFPAT_OK)
+        return report(FFPAT_ECUDA, "batched step: tensor map");
+    } else {
+      r.q[0] = r.q[2];
+      r.q[1] = r.q[2];
+    }
+    r.o0 = b.pout;
+    r.o1 = b.d;
+    r.o2 = b.e;
+    r.n = b.n;
+    r.start = b.start ? 1 : 0;
+    r.tiles_x = (b.n + TBX - 1) / TBX;
+    r.tiles_y = (b.n + TBY - 1) / TBY;
+    // z-chunks in proportion to this request's share of the points
+    const double share = (double)b.n * b.n * b.n / (double)total_points;
+    int zchunks = (int)((4.0 * slots * share) / (r.tiles_x * r.tiles_y) + 1.0);
+    const int zmax = b.n / 8 > 0 ? b.n / 8 : 1;
+    if (zchunks > zmax) zchunks = zmax;
+    if (zchunks < 1) zchunks = 1;
+    r.zc = (b.n + zchunks - 1) / zchunks;
+    zchunks = (b.n + r.zc - 1) / r.zc;
+    total += r.tiles_x * r.tiles_y * zchunks;
+    bp.item_end[i] = total;
+  }
+  const int grid = total < slots ? total : slots;
+  k_step_batch<<<grid, dim3(NTX, NTY), smem, st>>>(bp);
+  count_launch();
+  return check_launch("k_step_batch");
 }
 
 int read_device_status(unsigned* out, bool clear) {

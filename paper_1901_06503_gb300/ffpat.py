@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ffpat.h")
 
 FP64, FP32, FP32_KAHAN = 0, 1, 2
 PRECOND_NONE, PRECOND_RAMP = 0, 1
-OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, PENDING = 0, -1, -2, -3, -4, -5, 1
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, ECANCELED, PENDING = 0, -1, -2, -3, -4, -5, -6, 1
 PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", FP32_KAHAN: "fp32-kahan"}
 
 
@@ -52,6 +52,15 @@ class FBStats(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_int64), ("step_ms", ctypes.c_double),
                 ("step_bytes", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class ServingStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("point_steps", ctypes.c_double),
+                ("ticks", ctypes.c_int64), ("active", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("hbm_in_use", ctypes.c_size_t)]
 
 
 class FFPATError(RuntimeError):
@@ -91,6 +100,13 @@ def _declare(L):
         "ffpat_set_stencil_path": (ctypes.c_int, [i32]),
         "ffpat_device_status": (ctypes.c_int, [i32]),
         "ffpat_forward_noalloc": (ctypes.c_int, [_PR, _P, _P, _P, _P]),
+        "ffpat_server_create": (ctypes.c_int, [sz, i32, ctypes.POINTER(ctypes.c_void_p)]),
+        "ffpat_submit": (ctypes.c_int, [_P, _PR, _P, _P, f64, f64, i32,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+        "ffpat_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(FBStats)]),
+        "ffpat_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+        "ffpat_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServingStats)]),
+        "ffpat_server_destroy": (ctypes.c_int, [_P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -324,3 +340,76 @@ def device_status(clear: bool = False) -> int:
 
 def version() -> str:
     return lib().ffpat_version().decode()
+
+
+class Server:
+    """Continuous-batching reconstruction server (ffpat_server_* / ffpat_submit /
+    ffpat_poll).  Requests carry HOST arrays (float32 c: N^3, g: n_angles N^2)
+    and run Algorithm 8 with the FP32-Kahan wave kernels on the device that is
+    current at creation; their leapfrog steps share batched launches."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 8):
+        h = ctypes.c_void_p()
+        _check(lib().ffpat_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, prob: Problem, c, g, lam: float, step: float, iters: int) -> int:
+        c = np.ascontiguousarray(c, dtype=np.float32)
+        g = np.ascontiguousarray(g, dtype=np.float32)
+        if c.shape != vol_shape(prob) or g.shape != data_shape(prob):
+            raise ValueError("c / g shapes do not match the problem")
+        t = ctypes.c_uint64()
+        _check(lib().ffpat_submit(self._h, ctypes.byref(prob), c.ctypes.data_as(_P),
+                                  g.ctypes.data_as(_P), float(lam), float(step), int(iters),
+                                  ctypes.byref(t)))
+        self._shapes[t.value] = vol_shape(prob)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (h, stats); raises FFPATError on failure."""
+        out = np.empty(self._shapes[ticket], dtype=np.float32)
+        st = FBStats()
+        rc = lib().ffpat_poll(self._h, ctypes.c_uint64(ticket), out.ctypes.data_as(_P),
+                              ctypes.byref(st))
+        if rc == PENDING:
+            return None
+        self._shapes.pop(ticket, None)
+        _check(rc)
+        return out, st.as_dict()
+
+    def wait(self, ticket: int, timeout: float = 600.0, interval: float = 1e-3):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout:
+                raise FFPATError(ETIMEDOUT, f"request {ticket} not done after {timeout} s")
+            time.sleep(interval)
+
+    def cancel(self, ticket: int) -> None:
+        _check(lib().ffpat_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def stats(self) -> dict:
+        st = ServingStats()
+        _check(lib().ffpat_server_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            lib().ffpat_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
