@@ -502,3 +502,60 @@ int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, c
   free(s.kappa);
   return k;
 }
+
+/* ------------------------------------------- gradient with respect to c -- */
+
+/* Gradient of the scalar <grad_g, A h> with respect to c (the differentiated
+ * forward operator, chain rule through kappa = (c dt / dx)^2 with dt held
+ * fixed): keep every p^n of W, run the transposed recurrence backwards
+ * (lambda^{Nt} = P^T grad_g, lambda^n = 2 lambda^{n+1} - lambda^{n+2}
+ * + L4(kappa lambda^{n+1}), lambda^0 = lambda^1 + 1/2 L4(kappa lambda^1)
+ * - lambda^2), and sum the kappa-derivatives of every step:
+ * d/dkappa = sum_{n>=1} lambda^{n+1} L4 p^n + 1/2 lambda^1 L4 p^0.
+ * grad_h (optional) receives lambda^0 = A^T grad_g. */
+int ffo_grad(int n, double T, double cfl, int nth, const double *c, const double *h,
+             const double *grad_g, double *grad_h, double *grad_c) {
+  ffo_setup_t s;
+  size_t n3 = (size_t)n * n * n;
+  setup(&s, n, T, cfl, nth, 0, c);
+  int nt = s.nt;
+  double *ps = malloc((size_t)(nt + 1) * n3 * sizeof(double)); /* p^0 .. p^nt */
+  double *lap = malloc(n3 * sizeof(double));
+  memcpy(ps, h, n3 * sizeof(double));
+  lap4(ps, n, lap);
+  for (size_t i = 0; i < n3; ++i) ps[n3 + i] = ps[i] + 0.5 * s.kappa[i] * lap[i];
+  for (int k = 1; k < nt; ++k) {
+    const double *cur = ps + (size_t)k * n3, *prev = ps + (size_t)(k - 1) * n3;
+    double *next = ps + (size_t)(k + 1) * n3;
+    lap4(cur, n, lap);
+    for (size_t i = 0; i < n3; ++i) next[i] = 2.0 * cur[i] - prev[i] + s.kappa[i] * lap[i];
+  }
+  double *later = calloc(n3, sizeof(double)); /* lambda^{n+2} */
+  double *cur = malloc(n3 * sizeof(double));  /* lambda^{n+1} */
+  double *kl = malloc(n3 * sizeof(double));
+  double *gk = calloc(n3, sizeof(double));    /* d/dkappa */
+  ffo_backproject(n, nth, grad_g, cur);       /* lambda^{nt} */
+  for (int k = nt - 1; k >= 0; --k) {         /* lambda^{k+1} in cur -> lambda^k */
+    lap4(ps + (size_t)k * n3, n, lap);
+    double w = k >= 1 ? 1.0 : 0.5;
+    for (size_t i = 0; i < n3; ++i) gk[i] += w * cur[i] * lap[i];
+    for (size_t i = 0; i < n3; ++i) kl[i] = s.kappa[i] * cur[i];
+    lap4(kl, n, lap);
+    for (size_t i = 0; i < n3; ++i) {
+      double earlier = k >= 1 ? 2.0 * cur[i] - later[i] + lap[i] : cur[i] + 0.5 * lap[i] - later[i];
+      later[i] = cur[i];
+      cur[i] = earlier;
+    }
+  }
+  if (grad_h) memcpy(grad_h, cur, n3 * sizeof(double));
+  if (grad_c)
+    for (size_t i = 0; i < n3; ++i) grad_c[i] = gk[i] * 2.0 * s.kappa[i] / c[i];
+  free(ps);
+  free(lap);
+  free(later);
+  free(cur);
+  free(kl);
+  free(gk);
+  free(s.kappa);
+  return nt;
+}

@@ -76,6 +76,9 @@ def lib():
             L.ffo_fb.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                  ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int, ctypes.c_double, _D, _D]
+            L.ffo_grad.restype = ctypes.c_int
+            L.ffo_grad.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   _D, _D, _D, _D, _D]
             L.ffo_num_threads.restype = ctypes.c_int
             L.ffo_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -217,3 +220,13 @@ def fb(c, g, T: float, lam: float, step: float, iters: int, h0=None, precond: in
     k = lib().ffo_fb(n, T, cfl, g.shape[0], precond, _p(c), _p(g), lam, step, iters, tol,
                      _p(h), _p(stats))
     return h, stats[:k], k
+
+
+def grad(c, h, grad_g, T: float, cfl: float = 0.3):
+    """(d/dh, d/dc) of <grad_g, A(c) h>, with dt held at its value for c."""
+    c, h, grad_g = _f64(c), _f64(h), _f64(grad_g)
+    n = c.shape[0]
+    gh = np.empty((n, n, n))
+    gc = np.empty((n, n, n))
+    lib().ffo_grad(n, T, cfl, grad_g.shape[0], _p(c), _p(h), _p(grad_g), _p(gh), _p(gc))
+    return gh, gc

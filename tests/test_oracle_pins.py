@@ -388,3 +388,43 @@ def test_fb_tolerance_stops_early():
     L = o.power(c, random_volume(n, 63), T, nth, iters=50)
     h, stats, k = o.fb(c, g, T, 1e-3, 1.0 / L, 500, tol=1e-3)
     assert 1 < k < 500 and stats[-1, 2] < 1e-3 and np.all(stats[:-1, 2] >= 1e-3)
+
+
+# ------------------------------------------------- gradient with respect to c --
+
+def test_grad_c_matches_central_differences():
+    """d/dc <w, A(c) h> against central differences of the oracle forward along
+    random directions (dt frozen at its value for c: the perturbation keeps
+    max c and hence Nt fixed)."""
+    n, nth, T = 10, 5, 0.5
+    rng = np.random.default_rng(71)
+    c = random_speed(n, 72, 0.9, 1.1)
+    c[0, 0, 0] = 1.2  # the maximum, never perturbed
+    h = random_volume(n, 73)
+    w = random_data(nth, n, 74)
+    gh, gc = o.grad(c, h, w, T)
+    assert np.allclose(gh, o.adjoint(c, w, T), rtol=0, atol=1e-12 * np.abs(gh).max())
+    eps = 1e-5
+    for _ in range(6):
+        d = rng.standard_normal((n, n, n))
+        d[0, 0, 0] = 0.0
+        fp = np.sum(w * o.forward(c + eps * d, h, T, nth))
+        fm = np.sum(w * o.forward(c - eps * d, h, T, nth))
+        fd = (fp - fm) / (2 * eps)
+        an = float(np.sum(gc * d))
+        assert abs(fd - an) < 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_grad_c_single_step_closed_form():
+    """Nt = 1: A h = P (h + kappa/2 L4 h), so d/dc_i = (P^T w)_i (L4 h)_i kappa_i / c_i."""
+    n, nth = 8, 4
+    c = random_speed(n, 81, 0.9, 1.1)
+    T = 0.3 * (2.0 / n) / c.max() * 0.99
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    assert nt == 1
+    h = random_volume(n, 82)
+    w = random_data(nth, n, 83)
+    kap = o.kappa(n, dt, c)
+    _, gc = o.grad(c, h, w, T)
+    want = o.backproject(w, n) * lap_from_wave(h) * kap / c
+    assert np.allclose(gc, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
