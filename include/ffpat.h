@@ -192,6 +192,33 @@ int ffpat_set_stencil_path(int32_t path);
  * out sets FFPAT_ETIMEDOUT).  Synchronises the device; clear != 0 resets it. */
 int ffpat_device_status(int32_t clear);
 
+/* ---- Differentiation of g = P W(c) h with respect to h and the sound speed c.
+ * The forward pass runs the three-term leapfrog (FFPAT_FP32_KAHAN problems
+ * take FP32 three-term steps on this path) and saves (p^{sk}, p^{sk+1}) every
+ * k = `every` steps into the caller's checkpoint buffer; the backward pass
+ * runs the transposed recurrence from P^T grad_g, recomputing each k-step
+ * segment from its checkpoint, and returns grad_h = A^T grad_g and
+ * grad_c = d<grad_g, A(c) h>/dc with dt held fixed (Nt is piecewise constant
+ * in c).  The paper differentiates only in h (Sec. 3.1); the c-gradient is the
+ * same discrete adjoint carried through kappa = (c dt / dx)^2. */
+
+/* Checkpoint buffer bytes for Nt steps (ffpat_problem_info) and interval
+ * `every`: (2 ceil(Nt / every) + every + 2) volumes; 0 if invalid. */
+size_t ffpat_ckpt_bytes(const ffpat_problem *problem, int32_t nt, int32_t every);
+
+/* g = P W h with checkpoints (device buffers as for ffpat_forward; ckpt is
+ * caller-owned device memory of ffpat_ckpt_bytes bytes, 256-byte aligned). */
+int ffpat_forward_ckpt(const ffpat_problem *problem, const void *c, const void *h, void *g,
+                       int32_t every, void *ckpt, size_t ckpt_bytes, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/* Backward pass after ffpat_forward_ckpt with the same problem, c, `every`
+ * and checkpoint buffer: grad_h (N^3, nullable) = A^T grad_g and grad_c (N^3,
+ * nullable) = d<grad_g, A(c) h>/dc. */
+int ffpat_backward(const ffpat_problem *problem, const void *c, const void *grad_g, void *grad_h,
+                   void *grad_c, int32_t every, void *ckpt, size_t ckpt_bytes, void *ws,
+                   size_t ws_bytes, void *stream);
+
 /* ---- Serving: many Algorithm-8 solves in flight on one GPU (continuous batching).
  * A server owns a worker thread and a CUDA stream on the device that is
  * current at creation.  Requests (FFPAT_FP32_KAHAN problems with N % 4 == 0;

@@ -206,8 +206,8 @@ static int setup_speed(Plan& pl, const void* c, cudaStream_t st) {
   return FFPAT_OK;
 }
 
-static int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_bytes,
-                 cudaStream_t st) {
+int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_bytes,
+          cudaStream_t st) {
   g_err[0] = 0;
   TRY(attach(pr, pl, ws, ws_bytes));
   TRY(upload_tables(pl, pl.tab, st));
@@ -220,8 +220,8 @@ static double bytes_per_point(const Plan& pl) {
 }
 
 // One leapfrog launch, through the TMA kernel when the layout allows it.
-static int step3(const Plan& pl, bool tma, bool start, const void* p, const void* qin, void* qout,
-                 void* copy0, cudaStream_t st) {
+int step3(const Plan& pl, bool tma, bool start, const void* p, const void* qin, void* qout,
+          void* copy0, cudaStream_t st) {
   if (tma) {
     const void* q[2] = {start ? pl.kap : qin, pl.kap};
     return launch_step_tma(pl, 0, start, p, q, qout, copy0, nullptr, st);

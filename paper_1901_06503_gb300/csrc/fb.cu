@@ -184,6 +184,24 @@ __global__ void k_inv_sqrt(const double* __restrict__ src, double* __restrict__ 
   if (threadIdx.x == 0 && blockIdx.x == 0) dst[0] = 1.0 / sqrt(src[0]);
 }
 
+// out = (a - b) / kap   (last step of the transposed recurrence, back from kap-scaled form)
+template <typename T>
+__global__ void k_sub_div(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ kap,
+                          T* __restrict__ out, size_t len) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (a[i] - b[i]) / kap[i];
+}
+
+// out = s * a / c
+template <typename T>
+__global__ void k_scale_div(const T* __restrict__ a, const T* __restrict__ c, T s,
+                            T* __restrict__ out, size_t len) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = s * a[i] / c[i];
+}
+
 // counter-based pseudo-random start vector (splitmix64 + Box-Muller)
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -276,6 +294,31 @@ int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double
         pl.partials);
   k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 4, dst);
   count_launch(2);
+  return check_launch(__func__);
+}
+
+int launch_sub_div(const Plan& pl, const void* a, const void* b, void* out, cudaStream_t st) {
+  const unsigned nb = ew_blocks(pl.n3);
+  if (pl.prec == FFPAT_FP64)
+    k_sub_div<double><<<nb, 256, 0, st>>>((const double*)a, (const double*)b,
+                                          (const double*)pl.kap, (double*)out, pl.n3);
+  else
+    k_sub_div<float><<<nb, 256, 0, st>>>((const float*)a, (const float*)b, (const float*)pl.kap,
+                                         (float*)out, pl.n3);
+  count_launch();
+  return check_launch(__func__);
+}
+
+int launch_scale_div(const Plan& pl, const void* a, const void* c, double s, void* out,
+                     cudaStream_t st) {
+  const unsigned nb = ew_blocks(pl.n3);
+  if (pl.prec == FFPAT_FP64)
+    k_scale_div<double><<<nb, 256, 0, st>>>((const double*)a, (const double*)c, s, (double*)out,
+                                            pl.n3);
+  else
+    k_scale_div<float><<<nb, 256, 0, st>>>((const float*)a, (const float*)c, (float)s,
+                                           (float*)out, pl.n3);
+  count_launch();
   return check_launch(__func__);
 }
 

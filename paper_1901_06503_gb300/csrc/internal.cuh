@@ -38,7 +38,12 @@ inline size_t table_bytes(int nth) { return (size_t)nth * 2 * (8 + 4 + 4); }
 constexpr int kMaxHist = 4096;
 constexpr int kScal = 64;
 
-// api.cu helpers shared with the server
+// api.cu helpers shared with the server and the gradient path
+int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_bytes,
+          cudaStream_t st);
+// one three-term leapfrog launch (TMA kernel when the layout allows)
+int step3(const Plan& pl, bool tma, bool start, const void* p, const void* qin, void* qout,
+          void* copy0, cudaStream_t st);
 int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes);
 int time_steps(const Plan& pl, double cmax, int* nt, double* dt);
 void fill_tables_host(int nth, unsigned char* buf);  // table_bytes(nth) bytes
@@ -106,6 +111,12 @@ int launch_dot(const Plan& pl, size_t len, const void* a, const void* b, double*
 int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double lambda,
                      double* dst, cudaStream_t st, const double* step_dev = nullptr);
 int launch_inv_sqrt(const double* src, double* dst, cudaStream_t st);
+int launch_sub_div(const Plan& pl, const void* a, const void* b, void* out, cudaStream_t st);
+int launch_scale_div(const Plan& pl, const void* a, const void* c, double s, void* out,
+                     cudaStream_t st);
+// stencil.cu: acc += w * u * L(p)
+int launch_lap_accum(const Plan& pl, void* acc, const void* u, const void* p, double w,
+                     cudaStream_t st);
 int launch_hash_fill(const Plan& pl, void* out, uint64_t seed, cudaStream_t st);
 
 }  // namespace ffpat

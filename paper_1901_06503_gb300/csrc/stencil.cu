@@ -189,6 +189,42 @@ __global__ void __launch_bounds__(BX* BY)
   }
 }
 
+// acc += w * u * L(p): the kappa-derivative terms of the differentiated
+// leapfrog (u holds kappa/12 times the adjoint state, so that, with L = 12 L4,
+// the sum over steps is the c-gradient up to the factor 2/c).
+template <typename T>
+__global__ void __launch_bounds__(BX* BY)
+    k_lap_accum(T* __restrict__ acc, const T* __restrict__ u, const T* __restrict__ p, T w, int n,
+                int zc) {
+  __shared__ Tile<T> t;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int x = x0 + tx, y = y0 + ty;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(n, z0 + zc);
+  const bool in = (x < n) && (y < n);
+  const size_t pl = (size_t)n * n;
+  const size_t col = in ? (size_t)y * n + x : 0;
+  T m2 = load_col(p, pl, col, z0 - 2, n, in);
+  T m1 = load_col(p, pl, col, z0 - 1, n, in);
+  T c0 = load_col(p, pl, col, z0, n, in);
+  T p1 = load_col(p, pl, col, z0 + 1, n, in);
+  T p2 = load_col(p, pl, col, z0 + 2, n, in);
+  for (int z = z0; z < z1; ++z) {
+    const size_t i = (size_t)z * pl + col;
+    const T p3 = load_col(p, pl, col, z + 3, n, in);
+    fill_plane(t, p, n, z, x0, y0, tx, ty, c0);
+    __syncthreads();
+    if (in) acc[i] += w * __ldg(u + i) * lap12(t, tx, ty, m2, m1, c0, p1, p2);
+    __syncthreads();
+    m2 = m1;
+    m1 = c0;
+    c0 = p1;
+    p1 = p2;
+    p2 = p3;
+  }
+}
+
 dim3 step_grid(int n, int* zc) {
   const int gx = (n + BX - 1) / BX, gy = (n + BY - 1) / BY;
   const int target = 8 * kNumSMs;  // 8 CTAs of 256 threads fill an SM
@@ -202,6 +238,21 @@ dim3 step_grid(int n, int* zc) {
 }
 
 }  // namespace
+
+int launch_lap_accum(const Plan& pl, void* acc, const void* u, const void* p, double w,
+                     cudaStream_t st) {
+  int zc;
+  const dim3 grid = step_grid(pl.n, &zc);
+  const dim3 block(BX, BY);
+  if (pl.prec == FFPAT_FP64)
+    k_lap_accum<double><<<grid, block, 0, st>>>((double*)acc, (const double*)u, (const double*)p, w,
+                                                pl.n, zc);
+  else
+    k_lap_accum<float><<<grid, block, 0, st>>>((float*)acc, (const float*)u, (const float*)p,
+                                               (float)w, pl.n, zc);
+  count_launch();
+  return check_launch(__func__);
+}
 
 int launch_step3(const Plan& pl, const void* p, const void* qin, void* qout, bool start,
                  void* copy_p0, cudaStream_t st) {

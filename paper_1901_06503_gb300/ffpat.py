@@ -100,6 +100,9 @@ def _declare(L):
         "ffpat_set_stencil_path": (ctypes.c_int, [i32]),
         "ffpat_device_status": (ctypes.c_int, [i32]),
         "ffpat_forward_noalloc": (ctypes.c_int, [_PR, _P, _P, _P, _P]),
+        "ffpat_ckpt_bytes": (sz, [_PR, i32, i32]),
+        "ffpat_forward_ckpt": (ctypes.c_int, [_PR, _P, _P, _P, i32, _P, sz, _P, sz, _P]),
+        "ffpat_backward": (ctypes.c_int, [_PR, _P, _P, _P, _P, i32, _P, sz, _P, sz, _P]),
         "ffpat_server_create": (ctypes.c_int, [sz, i32, ctypes.POINTER(ctypes.c_void_p)]),
         "ffpat_submit": (ctypes.c_int, [_P, _PR, _P, _P, f64, f64, i32,
                                         ctypes.POINTER(ctypes.c_uint64)]),
@@ -244,6 +247,39 @@ def forward_noalloc(prob, c, h, g, stream=None):
                                        _dev(h, prob, vol_shape(prob), "h"),
                                        _dev(g, prob, data_shape(prob), "g"), _stream(stream)))
     return g
+
+
+def ckpt_bytes(prob, nt: int, every: int) -> int:
+    b = lib().ffpat_ckpt_bytes(ctypes.byref(prob), int(nt), int(every))
+    if b == 0:
+        raise FFPATError(EINVAL, "invalid checkpoint request")
+    return int(b)
+
+
+def forward_ckpt(prob, c, h, every, ckpt, g=None, ws=None, stream=None):
+    """g = P W h, saving wavefield checkpoints every `every` steps into ckpt."""
+    g = _empty(prob, data_shape(prob), h) if g is None else g
+    ws, wp, wn = _ws(prob, ws, h.device)
+    _check(lib().ffpat_forward_ckpt(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                                    _dev(h, prob, vol_shape(prob), "h"),
+                                    _dev(g, prob, data_shape(prob), "g"), int(every),
+                                    ctypes.c_void_p(ckpt.data_ptr()), ctypes.c_size_t(ckpt.numel()),
+                                    wp, wn, _stream(stream)))
+    return g
+
+
+def backward(prob, c, grad_g, every, ckpt, want_h=True, want_c=True, ws=None, stream=None):
+    """(grad_h, grad_c) of <grad_g, A(c) h> after forward_ckpt."""
+    gh = _empty(prob, vol_shape(prob), grad_g) if want_h else None
+    gc = _empty(prob, vol_shape(prob), grad_g) if want_c else None
+    ws, wp, wn = _ws(prob, ws, grad_g.device)
+    _check(lib().ffpat_backward(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                                _dev(grad_g, prob, data_shape(prob), "grad_g"),
+                                _dev(gh, prob, vol_shape(prob), "grad_h") if want_h else None,
+                                _dev(gc, prob, vol_shape(prob), "grad_c") if want_c else None,
+                                int(every), ctypes.c_void_p(ckpt.data_ptr()),
+                                ctypes.c_size_t(ckpt.numel()), wp, wn, _stream(stream)))
+    return gh, gc
 
 
 def adjoint(prob, c, g, h=None, ws=None, stream=None):

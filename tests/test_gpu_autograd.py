@@ -1,0 +1,100 @@
+"""The differentiable operator: FFPATOp (torch.autograd.Function) with the
+checkpointed transposed solve, against the oracle gradient and central
+finite differences."""
+import numpy as np
+import pytest
+
+import oracle.oracle as o
+from paper_1901_06503_gb300 import build_lib
+from paper_1901_06503_gb300 import ffpat as F
+from paper_1901_06503_gb300.autograd import forward_op
+from paper_1901_06503_gb300.inputs import config, random_data, random_speed, random_volume
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib.build()
+    F.lib()
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.mark.parametrize("every", [1, 4, 16, 1000])
+@pytest.mark.parametrize("n,nth,T", [(24, 6, 0.5), (32, 8, 0.03)])
+def test_gradients_match_oracle_fp64(n, nth, T, every):
+    c = random_speed(n, 1000 + n)
+    h = random_volume(n, 1001 + n)
+    w = random_data(nth, n, 1002 + n)
+    prob = F.problem(n, T, nth, F.FP64)
+    ht = torch.tensor(h, device="cuda", requires_grad=True)
+    ct = torch.tensor(c, device="cuda", requires_grad=True)
+    g = forward_op(ht, ct, prob, every)
+    (g * torch.tensor(w, device="cuda")).sum().backward()
+    gh_or, gc_or = o.grad(c, h, w, T)
+    assert rel(g.detach().cpu().numpy(), o.forward(c, h, T, nth)) < 1e-10
+    assert rel(ht.grad.cpu().numpy(), gh_or) < 1e-10
+    assert rel(ct.grad.cpu().numpy(), gc_or) < 1e-10
+
+
+def test_grad_h_only_uses_adjoint():
+    n, nth, T = 32, 8, 0.4
+    c, h, w = random_speed(n, 1), random_volume(n, 2), random_data(nth, n, 3)
+    prob = F.problem(n, T, nth, F.FP64)
+    ht = torch.tensor(h, device="cuda", requires_grad=True)
+    g = forward_op(ht, torch.tensor(c, device="cuda"), prob)
+    (g * torch.tensor(w, device="cuda")).sum().backward()
+    assert rel(ht.grad.cpu().numpy(), o.adjoint(c, w, T)) < 1e-10
+
+
+def test_fp32_gradient_matches_oracle_at_48():
+    """The FP32 path at 48^3 (config-3 generator rescaled) against the FP64 oracle gradient."""
+    wl = config(3, n=48)
+    c = wl.c.astype(np.float32).astype(np.float64)
+    h = wl.h.astype(np.float32).astype(np.float64)
+    w = random_data(wl.n_angles, 48, 5).astype(np.float32).astype(np.float64)
+    prob = F.problem(48, wl.T, wl.n_angles, F.FP32)
+    ht = torch.tensor(h, device="cuda", dtype=torch.float32, requires_grad=True)
+    ct = torch.tensor(c, device="cuda", dtype=torch.float32, requires_grad=True)
+    g = forward_op(ht, ct, prob, 16)
+    (g * torch.tensor(w, device="cuda", dtype=torch.float32)).sum().backward()
+    gh_or, gc_or = o.grad(c, h, w, wl.T)
+    assert rel(ht.grad.double().cpu().numpy(), gh_or) < 2e-5
+    assert rel(ct.grad.double().cpu().numpy(), gc_or) < 1e-4
+
+
+def test_central_differences_fp64():
+    """Loss 1/2 ||A h - g||^2; directional derivatives in c and h against
+    central differences (eps = 1e-3 relative, 8 random directions; the
+    maximum of c is never perturbed so that Nt and dt stay fixed)."""
+    n, nth, T = 24, 6, 0.5
+    rng = np.random.default_rng(9)
+    c = random_speed(n, 11, 0.9, 1.1)
+    c[0, 0, 0] = 1.2
+    h = random_volume(n, 12)
+    gd = torch.tensor(random_data(nth, n, 13), device="cuda")
+    prob = F.problem(n, T, nth, F.FP64)
+
+    def loss(hh, cc):
+        return 0.5 * ((forward_op(hh, cc, prob, 4) - gd) ** 2).sum()
+
+    ht = torch.tensor(h, device="cuda", requires_grad=True)
+    ct = torch.tensor(c, device="cuda", requires_grad=True)
+    loss(ht, ct).backward()
+    eps = 1e-3
+    for _ in range(8):
+        dc = torch.tensor(rng.standard_normal((n, n, n)) * 0.05, device="cuda")
+        dc[0, 0, 0] = 0.0
+        dh = torch.tensor(rng.standard_normal((n, n, n)), device="cuda")
+        with torch.no_grad():
+            cc, hh = torch.tensor(c, device="cuda"), torch.tensor(h, device="cuda")
+            fd_c = (loss(hh, cc + eps * dc) - loss(hh, cc - eps * dc)) / (2 * eps)
+            fd_h = (loss(hh + eps * dh, cc) - loss(hh - eps * dh, cc)) / (2 * eps)
+        an_c = (ct.grad * dc).sum()
+        an_h = (ht.grad * dh).sum()
+        assert abs(float(fd_c - an_c)) < 1e-5 * max(abs(float(fd_c)), 1e-8)
+        assert abs(float(fd_h - an_h)) < 1e-8 * max(abs(float(fd_h)), 1e-8)
