@@ -320,6 +320,108 @@ def run_ours(args):
     return 0
 
 
+def run_serve(args):
+    """Serving mix (Poisson arrivals of requests of mixed size) through the
+    continuous-batching server; prints one JSON line with recons/s and p50/p99."""
+    import numpy as np
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    from paper_1901_06503_gb300.inputs import add_noise, config
+
+    build_lib.build()
+    F.lib()
+    dev = torch.device("cuda", 0)
+    pool = []
+    for s in range(1, args.pool + 1):
+        w = config(4, seed=1000 + s)
+        prob = F.problem(w.n, w.T, w.n_angles, F.FP32_KAHAN)
+        c = torch.as_tensor(w.c, device=dev).float()
+        g = F.forward(prob, c, torch.as_tensor(w.h, device=dev).float())
+        gd = add_noise(g.double().cpu().numpy(), w.noise, w.noise_rel).astype(np.float32)
+        step = 1.0 / F.opnorm(prob, c, torch.ones_like(c), iters=20)
+        nt, _, _ = F.problem_info(prob, float(w.c.astype(np.float32).max()))
+        pool.append((prob, w.c.astype(np.float32), gd, step, w.iters, nt, w.n))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=100000))
+    arrivals = arrivals[arrivals < args.window]
+    budget = int(args.budget_gb * (1 << 30))
+    tickets = []
+    with F.Server(budget, args.slots) as srv, Clocks(0) as clk:
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(arrivals) or any(t is not None for t in tickets):
+            now = time.perf_counter() - t0
+            while k < len(arrivals) and arrivals[k] <= now:
+                prob, c, gd, step, iters, nt, n = pool[k % len(pool)]
+                tickets.append(srv.submit(prob, c, gd, 1e-3, step, iters))
+                k += 1
+            for i, t in enumerate(tickets):
+                if t is not None and srv.poll(t) is not None:
+                    tickets[i] = None
+            time.sleep(0.001)
+        elapsed = time.perf_counter() - t0
+        st = srv.stats()
+    ps = st["point_steps"]
+    line = {"mode": "serve", "metric": "recons/s", "value": st["completed"] / elapsed,
+            "unit": "recons/s", "n_gpus": 1, "higher_is_better": True,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "max_ms": st["max_ms"], "completed": st["completed"], "failed": st["failed"],
+            "window_s": args.window, "elapsed_s": elapsed, "arrival_rate": args.rate,
+            "voxel_steps_per_s": ps / elapsed, "ticks": st["ticks"],
+            "config": {"workload": "serving mix: N in {64,96,128,192}, 45/90/180 angles, "
+                                   "T in [0.8,1.4], 20-60 FB iterations, FP32-Kahan",
+                       "pool": args.pool, "slots": args.slots, "budget_gb": args.budget_gb},
+            "clocks": clk.summary(), "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_precision(args):
+    """FP64 vs FP32 vs FP32-Kahan on the 128^3 single solve: time per FB
+    iteration and the relative L2 difference of the iterate from the FP64 GPU
+    iterate after the same number of iterations."""
+    import numpy as np
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    from paper_1901_06503_gb300.inputs import add_noise, config
+
+    build_lib.build()
+    dev = torch.device("cuda", 0)
+    w = config(2)
+    p64 = F.problem(w.n, w.T, w.n_angles, F.FP64)
+    c64 = torch.as_tensor(w.c, device=dev)
+    g64 = F.forward(p64, c64, torch.as_tensor(w.h, device=dev))
+    gd = torch.as_tensor(add_noise(g64.cpu().numpy(), w.noise, w.noise_rel), device=dev)
+    step = 1.0 / F.opnorm(p64, c64, torch.ones_like(c64), iters=20)
+    res = {}
+    for name, prec in (("fp64", F.FP64), ("fp32", F.FP32), ("fp32-kahan", F.FP32_KAHAN)):
+        prob = F.problem(w.n, w.T, w.n_angles, prec)
+        dt = F.torch_dtype(prob)
+        c, g = c64.to(dt), gd.to(dt)
+        F.fb_solve(prob, c, g, w.lam, step, 1, history=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h, st, _ = F.fb_solve(prob, c, g, w.lam, step, args.iters, history=False)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = (h.double(), e0.elapsed_time(e1) / args.iters)
+    ref = res["fp64"][0]
+    out = {"mode": "precision", "workload": "single solve N=128^3, 90 angles, T=1.2",
+           "iters": args.iters, "step": step}
+    for name, (h, ms) in res.items():
+        out[name] = {"ms_per_fb_iter": ms,
+                     "rel_l2_vs_fp64_gpu": float((h - ref).norm() / ref.norm()),
+                     "speedup_vs_fp64": res["fp64"][1] / ms}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,7 +432,20 @@ def main():
     ap.add_argument("--precision", choices=["fp32-kahan", "fp32", "fp64"], default="fp32-kahan")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["fb", "serve", "precision"], default="fb",
+                    help="fb: the default FB-iteration line; serve: the serving mix; "
+                         "precision: FP64 vs FP32 vs FP32-Kahan on the 128^3 solve")
+    ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window (s)")
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate (1/s)")
+    ap.add_argument("--pool", type=int, default=12, help="serve: distinct requests cycled")
+    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--iters", type=int, default=20, help="precision: FB iterations")
     args = ap.parse_args()
+    if args.mode == "serve":
+        return run_serve(args)
+    if args.mode == "precision":
+        return run_precision(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
