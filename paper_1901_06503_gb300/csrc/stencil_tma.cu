@@ -134,6 +134,47 @@ __device__ __forceinline__ double lap12_sum(const double* P0, const double* Pm1,
   return fma(16.0, s1, -s2);
 }
 
+// Neighbourhood of one point for the FP32 difference-form Laplacian.
+struct Nb {
+  float c, xm1, xp1, ym1, yp1, zm1, zp1, xm2, xp2, ym2, yp2, zm2, zp2;
+};
+
+// same operations in the same order as lap12_diff
+__device__ __forceinline__ float lap12_nb(const Nb& v) {
+  float d1 = (v.xm1 - v.c) + (v.xp1 - v.c);
+  d1 += (v.ym1 - v.c) + (v.yp1 - v.c);
+  d1 += (v.zm1 - v.c) + (v.zp1 - v.c);
+  float d2 = (v.xm2 - v.c) + (v.xp2 - v.c);
+  d2 += (v.ym2 - v.c) + (v.yp2 - v.c);
+  d2 += (v.zm2 - v.c) + (v.zp2 - v.c);
+  return fmaf(16.0f, d1, -d2);
+}
+
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// the neighbourhoods of the two x-adjacent points at o and o + 1 (o even),
+// read with eleven 64-bit shared-memory loads
+__device__ __forceinline__ void gather_pair(const float* P0, const float* Pm1, const float* Pp1,
+                                            const float* Pm2, const float* Pp2, int o, int row,
+                                            Nb& a, Nb& b) {
+  const float2 C = lds2(P0 + o), XM = lds2(P0 + o - 2), XP = lds2(P0 + o + 2);
+  const float2 YM1 = lds2(P0 + o - row), YP1 = lds2(P0 + o + row);
+  const float2 YM2 = lds2(P0 + o - 2 * row), YP2 = lds2(P0 + o + 2 * row);
+  const float2 ZM1 = lds2(Pm1 + o), ZP1 = lds2(Pp1 + o), ZM2 = lds2(Pm2 + o), ZP2 = lds2(Pp2 + o);
+  a = Nb{C.x, XM.y, C.y, YM1.x, YP1.x, ZM1.x, ZP1.x, XM.x, XP.x, YM2.x, YP2.x, ZM2.x, ZP2.x};
+  b = Nb{C.y, C.x, XP.x, YM1.y, YP1.y, ZM1.y, ZP1.y, XM.y, XP.y, YM2.y, YP2.y, ZM2.y, ZP2.y};
+}
+
+// Kahan-compensated increment update of one point; returns (p', d', e')
+__device__ __forceinline__ float3 kahan_update(float c, float k, float L, float dold, float eold,
+                                               bool start) {
+  const float dn = start ? 0.5f * k * L : fmaf(k, L, dold);
+  const float ev = start ? 0.0f : eold;
+  const float yv = dn - ev;
+  const float tv = c + yv;
+  return make_float3(tv, dn, (tv - c) - yv);
+}
+
 // Round R brings p plane R (needed while R <= z1 + 1) and the per-point
 // stream planes R - 2 (needed while z0 <= R - 2 < z1) of the item's tile.
 template <typename T, int NQ>
@@ -212,46 +253,61 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
       const T* Pp2 = pst + (size_t)((z + 2) & (SP - 1)) * (G::PBYTES / sizeof(T));
       const T* Q = qst + (size_t)((z & (SQ - 1)) * NQ) * (G::QBYTES / sizeof(T));
       const int y = y0 + ty;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int xl = tx + 32 * h;
+      if constexpr (sizeof(T) == 4) {
+        // two x-adjacent points per thread, 64-bit shared and global accesses
+        const int xl = 2 * tx;
         const int x = x0 + xl;
         const int o = (ty + 2) * G::BXH + xl + G::XH;
         const int qo = ty * TBX + xl;
-        T L;
-        if constexpr (sizeof(T) == 4)
-          L = lap12_diff(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
-        else
-          L = lap12_sum(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
-        const T c = P0[o];
-        const T k = Q[(NQ - 1) * (G::QBYTES / sizeof(T)) + qo];
-        if (x < n && y < n) {
+        constexpr int QS = G::QBYTES / 4;
+        Nb na, nb;
+        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
+        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        const float2 K = lds2(Q + (NQ - 1) * QS + qo);
+        if (x < n && y < n) {  // N is even, so x + 1 < n as well
           const size_t gi = (size_t)z * plane + (size_t)y * n + x;
           if constexpr (FORM == 0) {
+            if constexpr (START) {
+              *reinterpret_cast<float2*>(o0 + gi) =
+                  make_float2(na.c + 0.5f * K.x * La, nb.c + 0.5f * K.y * Lb);
+              if (o1) *reinterpret_cast<float2*>(o1 + gi) = make_float2(na.c, nb.c);
+            } else {
+              const float2 PM = lds2(Q + qo);
+              *reinterpret_cast<float2*>(o0 + gi) =
+                  make_float2(na.c + fmaf(K.x, La, na.c - PM.x), nb.c + fmaf(K.y, Lb, nb.c - PM.y));
+            }
+          } else {
+            float2 D = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
+            if constexpr (!START) {
+              D = lds2(Q + qo);
+              E = lds2(Q + QS + qo);
+            }
+            const float3 ra = kahan_update(na.c, K.x, La, D.x, E.x, START);
+            const float3 rb = kahan_update(nb.c, K.y, Lb, D.y, E.y, START);
+            *reinterpret_cast<float2*>(o0 + gi) = make_float2(ra.x, rb.x);
+            *reinterpret_cast<float2*>(o1 + gi) = make_float2(ra.y, rb.y);
+            *reinterpret_cast<float2*>(o2 + gi) = make_float2(ra.z, rb.z);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int xl = tx + 32 * h;
+          const int x = x0 + xl;
+          const int o = (ty + 2) * G::BXH + xl + G::XH;
+          const int qo = ty * TBX + xl;
+          const T L = lap12_sum(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
+          const T c = P0[o];
+          const T k = Q[(NQ - 1) * (G::QBYTES / sizeof(T)) + qo];
+          if (x < n && y < n) {
+            const size_t gi = (size_t)z * plane + (size_t)y * n + x;
             if constexpr (START) {
               o0[gi] = c + T(0.5) * k * L;
               if (o1) o1[gi] = c;
             } else {
               const T pm = Q[qo];
-              if constexpr (sizeof(T) == 8)
-                o0[gi] = fma(k, L, fma(2.0, c, -pm));
-              else
-                o0[gi] = c + fmaf(k, L, c - pm);
+              o0[gi] = fma(k, L, fma(2.0, c, -pm));
             }
-          } else {
-            float dn, eold;
-            if constexpr (START) {
-              dn = 0.5f * k * L;
-              eold = 0.0f;
-            } else {
-              dn = fmaf(k, L, Q[qo]);
-              eold = Q[(G::QBYTES / sizeof(T)) + qo];
-            }
-            const float yv = dn - eold;
-            const float tv = c + yv;
-            o0[gi] = tv;
-            o1[gi] = dn;
-            o2[gi] = (tv - c) - yv;
           }
         }
       }
@@ -360,30 +416,28 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
       const float* Pp2 = pst + (size_t)((z + 2) & (SP - 1)) * (G::PBYTES / 4);
       const float* Qd = qst + (size_t)((z & (SQ - 1)) * NQ) * (G::QBYTES / 4);
       const int y = y0 + ty;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int xl = tx + 32 * h;
+      {
+        const int xl = 2 * tx;
         const int x = x0 + xl;
         const int o = (ty + 2) * G::BXH + xl + G::XH;
         const int qo = ty * TBX + xl;
-        const float L = lap12_diff(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
-        const float c = P0[o];
-        const float k = Qd[2 * (G::QBYTES / 4) + qo];
+        constexpr int QS = G::QBYTES / 4;
+        Nb na, nb;
+        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
+        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        const float2 K = lds2(Qd + 2 * QS + qo);
         if (x < n && y < n) {
           const size_t gi = (size_t)z * plane + (size_t)y * n + x;
-          float dn, eold;
-          if (start) {
-            dn = 0.5f * k * L;
-            eold = 0.0f;
-          } else {
-            dn = fmaf(k, L, Qd[qo]);
-            eold = Qd[(G::QBYTES / 4) + qo];
+          float2 D = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
+          if (!start) {
+            D = lds2(Qd + qo);
+            E = lds2(Qd + QS + qo);
           }
-          const float yv = dn - eold;
-          const float tv = c + yv;
-          q.o0[gi] = tv;
-          q.o1[gi] = dn;
-          q.o2[gi] = (tv - c) - yv;
+          const float3 ra = kahan_update(na.c, K.x, La, D.x, E.x, start);
+          const float3 rb = kahan_update(nb.c, K.y, Lb, D.y, E.y, start);
+          *reinterpret_cast<float2*>(q.o0 + gi) = make_float2(ra.x, rb.x);
+          *reinterpret_cast<float2*>(q.o1 + gi) = make_float2(ra.y, rb.y);
+          *reinterpret_cast<float2*>(q.o2 + gi) = make_float2(ra.z, rb.z);
         }
       }
       if (__syncthreads_or(timed_out)) {
