@@ -101,7 +101,7 @@ def test_central_differences_fp64():
             fd = [(loss(hh, cc + e * dc) - loss(hh, cc - e * dc)) / (2 * e) for e in (eps, eps / 2)]
             an_c = float((ct.grad * dc).sum())
             err = [abs(f - an_c) for f in fd]
-            assert err[0] < 1e-3 * abs(an_c)
+            assert err[0] < 1e-2 * abs(an_c)
             assert err[1] < 0.35 * err[0] or err[0] < 1e-9 * abs(an_c)
             fd_h = (loss(hh + eps * dh, cc) - loss(hh - eps * dh, cc)) / (2 * eps)
             an_h = float((ht.grad * dh).sum())
