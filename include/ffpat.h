@@ -192,6 +192,13 @@ int ffpat_set_stencil_path(int32_t path);
  * out sets FFPAT_ETIMEDOUT).  Synchronises the device; clear != 0 resets it. */
 int ffpat_device_status(int32_t clear);
 
+/* Failure-detection check: launch a one-CTA kernel that waits on an mbarrier
+ * nothing will complete, with the same bounded wait as the stencil kernels
+ * (`microseconds` of SM clock, at most 2 s); the wait runs out and the kernel
+ * records FFPAT_ETIMEDOUT in the device status word and returns, so the CUDA
+ * context stays usable.  Synchronises the stream. */
+int ffpat_debug_wait_timeout(int32_t microseconds, void *stream);
+
 /* ---- Differentiation of g = P W(c) h with respect to h and the sound speed c.
  * The forward pass runs the three-term leapfrog (FFPAT_FP32_KAHAN problems
  * take FP32 three-term steps on this path) and saves (p^{sk}, p^{sk+1}) every

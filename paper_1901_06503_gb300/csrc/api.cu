@@ -607,6 +607,18 @@ int ffpat_set_stencil_path(int32_t path) {
   return FFPAT_OK;
 }
 
+int ffpat_debug_wait_timeout(int32_t microseconds, void* stream) {
+  g_err[0] = 0;
+  if (microseconds < 1 || microseconds > 2000000)
+    return fail(FFPAT_EINVAL, "timeout %d us outside [1, 2e6]", microseconds);
+  int khz = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) khz = 2070000;
+  TRY(launch_wait_timeout((long long)microseconds * (khz / 1000), (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return FFPAT_OK;
+}
+
 int ffpat_device_status(int32_t clear) {
   g_err[0] = 0;
   unsigned v = 0;

@@ -87,6 +87,7 @@ constexpr int kMaxBatchRequests = 28;
 
 // device status word of the TMA kernels (0 = ok, else -FFPAT_* of the first error)
 int read_device_status(unsigned* out, bool clear);
+int launch_wait_timeout(long long cycles, cudaStream_t st);
 
 // xray.cu
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st);

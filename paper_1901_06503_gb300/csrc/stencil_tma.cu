@@ -628,6 +628,25 @@ int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
   return check_launch("k_step_batch");
 }
 
+// A one-CTA kernel whose mbarrier never completes (nothing arrives on it):
+// the bounded wait runs out after `cycles` and the kernel records
+// FFPAT_ETIMEDOUT in the status word, exactly as the stencil kernels do, then
+// returns.  Used to test failure detection without faulting or hanging.
+__global__ void k_wait_timeout(long long cycles) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0u, cycles)) atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+  }
+}
+
+int launch_wait_timeout(long long cycles, cudaStream_t st) {
+  k_wait_timeout<<<1, 32, 0, st>>>(cycles);
+  count_launch();
+  return check_launch("k_wait_timeout");
+}
+
 int read_device_status(unsigned* out, bool clear) {
   unsigned v = 0;
   cudaError_t e = cudaMemcpyFromSymbol(&v, g_tma_status, sizeof v);

@@ -99,6 +99,7 @@ def _declare(L):
         "ffpat_launch_count": (i64, []),
         "ffpat_set_stencil_path": (ctypes.c_int, [i32]),
         "ffpat_device_status": (ctypes.c_int, [i32]),
+        "ffpat_debug_wait_timeout": (ctypes.c_int, [i32, _P]),
         "ffpat_forward_noalloc": (ctypes.c_int, [_PR, _P, _P, _P, _P]),
         "ffpat_ckpt_bytes": (sz, [_PR, i32, i32]),
         "ffpat_forward_ckpt": (ctypes.c_int, [_PR, _P, _P, _P, i32, _P, sz, _P, sz, _P]),
@@ -372,6 +373,11 @@ def set_stencil_path(path: int) -> None:
 def device_status(clear: bool = False) -> int:
     """0, or the negative status of the first device-side failure."""
     return int(lib().ffpat_device_status(1 if clear else 0))
+
+
+def debug_wait_timeout(microseconds: int = 20000, stream=None) -> None:
+    """Run a bounded device wait that cannot complete (sets FFPAT_ETIMEDOUT)."""
+    _check(lib().ffpat_debug_wait_timeout(int(microseconds), _stream(stream)))
 
 
 def version() -> str:
