@@ -304,9 +304,11 @@ def run_ours(args):
         "wall_s": wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                     "peak_source": f"{src} hbm_gbs", "kernel": "leapfrog step",
-                     "bytes_per_point_step": bpp, "launch_ms": launch_ms,
-                     "launches_timed": prof["step_launches"]},
+                     "peak_source": f"{src} hbm_gbs", "kernel": "leapfrog pass",
+                     "bytes_per_point_pass": bpp,
+                     "steps_per_pass": prof["steps"] / max(prof["step_launches"], 1),
+                     "launch_ms": launch_ms, "launches_timed": prof["step_launches"],
+                     "steps_timed": prof["steps"]},
         "cpu_baseline": cpu,
         "e2e": {"value": world * vs_per_iter / e2e_s, "unit": "voxel-steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

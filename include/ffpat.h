@@ -165,14 +165,17 @@ int ffpat_fb_solve(const ffpat_problem *problem, const void *c, const void *g, d
 
 /* Instrumentation.  While enabled, every wave time loop records CUDA events on
  * its stream around its leapfrog launches; ffpat_profile_read synchronises
- * those events and returns the number of leapfrog launches timed, their total
- * milliseconds, and the algorithmic HBM bytes they move (one pass per step:
- * 16 B FP32, 28 B FP32-Kahan, 32 B FP64 per grid point).  Reading resets. */
+ * those events and returns the leapfrog launches and steps timed, their total
+ * milliseconds, and the algorithmic HBM bytes they move: one pass of the state
+ * per launch (16 B FP32, 28 B FP32-Kahan, 32 B FP64 per grid point), where a
+ * two-step FP32-Kahan launch advances two steps in its one pass.  Reading
+ * resets. */
 typedef struct {
   int64_t step_launches;
   double step_ms;
   double step_bytes;
   int64_t kernel_launches; /* all kernels this library launched since the last reset */
+  int64_t steps;           /* leapfrog steps inside the timed launches */
 } ffpat_profile;
 int ffpat_profile_enable(int32_t on);
 int ffpat_profile_read(ffpat_profile *out);
@@ -180,11 +183,14 @@ int ffpat_profile_read(ffpat_profile *out);
 /* Total kernels launched by this library since load (monotone counter). */
 int64_t ffpat_launch_count(void);
 
-/* Choice of leapfrog kernel (process-wide): 0 = automatic (the TMA-fed kernel
+/* Choice of leapfrog kernel (process-wide): 0 = automatic (the TMA-fed kernels
  * when N % 4 == 0 for float or N % 2 == 0 for double and all arrays are
- * 16-byte aligned, else the plain 2.5D kernel), 1 = always the plain kernel,
- * 2 = always the TMA kernel (calls that cannot use it fail with FFPAT_EINVAL).
- * Both compute the same steps; this exists for testing and measurement. */
+ * 16-byte aligned -- two steps per pass for FP32-Kahan -- else the plain 2.5D
+ * kernel), 1 = always the plain kernel, 2 = the single-step TMA kernel, 3 =
+ * the two-step TMA kernel for FP32-Kahan (single steps otherwise); 2 and 3
+ * fail with FFPAT_EINVAL where TMA cannot be used.  All compute the same
+ * steps bit for bit (FP32-Kahan) or up to rounding order; this exists for
+ * testing and measurement. */
 int ffpat_set_stencil_path(int32_t path);
 
 /* Device status word of the library's kernels: 0, or the negative status of

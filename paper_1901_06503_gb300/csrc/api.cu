@@ -25,12 +25,14 @@ static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
 static std::atomic<long long> g_prof_launches{0};
 static std::atomic<int> g_prof_on{0};
-static std::atomic<int> g_stencil_path{0};  // 0 auto, 1 plain 2.5D kernel, 2 TMA kernel
+// 0 auto, 1 plain 2.5D kernel, 2 single-step TMA kernel, 3 two-step TMA kernel (FP32-Kahan)
+static std::atomic<int> g_stencil_path{0};
 
 struct ProfRec {
   cudaEvent_t a, b;
-  long long steps;
-  double bytes;
+  long long steps;     // leapfrog steps timed
+  long long launches;  // kernel launches (one HBM pass each) timed
+  double bytes;        // algorithmic bytes: one pass of the state per launch
 };
 static std::mutex g_prof_mu;
 static std::vector<ProfRec> g_prof;
@@ -104,7 +106,7 @@ static int validate(const ffpat_problem* pr, Plan& pl) {
   return FFPAT_OK;
 }
 
-static int nstate(const Plan& pl) { return pl.prec == FFPAT_FP32_KAHAN ? 4 : 2; }
+static int nstate(const Plan& pl) { return pl.prec == FFPAT_FP32_KAHAN ? 6 : 2; }
 
 // Carve the workspace (ws == nullptr: size only).
 static size_t carve(Plan& pl, void* ws) {
@@ -117,7 +119,7 @@ static size_t carve(Plan& pl, void* ws) {
   };
   const size_t vol = pl.n3 * pl.esize, dat = pl.nd * pl.esize;
   pl.kap = take(vol);
-  for (int i = 0; i < 4; ++i) pl.s[i] = i < nstate(pl) ? take(vol) : nullptr;
+  for (int i = 0; i < 6; ++i) pl.s[i] = i < nstate(pl) ? take(vol) : nullptr;
   pl.x = take(vol);
   pl.v = take(vol);
   pl.r = take(dat);
@@ -245,27 +247,44 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
   const int nt = pl.nt;
   ProfRec rec{};
   const bool prof = g_prof_on.load() && nt > 1;
-  const void* ptrs[8] = {in, out, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3], nullptr};
+  const void* ptrs[10] = {in, out, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3], pl.s[4], pl.s[5]};
   const int path = g_stencil_path.load();
-  const bool tma = path != 1 && tma_supported(pl, ptrs, 7);
-  if (path == 2 && !tma)
+  const bool tma = path != 1 && tma_supported(pl, ptrs, 9);
+  if (path >= 2 && !tma)
     return fail(FFPAT_EINVAL, "TMA stencil requested but N = %d or an array alignment rules it out",
                 pl.n);
+  long long launches = 0;
   if (pl.prec == FFPAT_FP32_KAHAN) {
-    void* d = pl.s[2];
-    void* e = pl.s[3];
-    void* first = (nt == 1 && out) ? out : pl.s[0];
-    TRY(step_inc(pl, tma, true, in, first, d, e, st));
+    const bool two = tma && (path == 0 || path == 3);
+    void* P[2] = {pl.s[0], pl.s[1]};
+    void* D[2] = {pl.s[2], pl.s[4]};
+    void* E[2] = {pl.s[3], pl.s[5]};
+    int c = 0;  // index of the buffers holding the current level
+    void* first = (nt == 1 && out) ? out : P[0];
+    TRY(step_inc(pl, tma, true, in, first, D[0], E[0], st));
     const void* cur = first;
     if (prof) {
       CK(cudaEventCreate(&rec.a));
       CK(cudaEventCreate(&rec.b));
       CK(cudaEventRecord(rec.a, st));
     }
-    for (int s = 1; s < nt; ++s) {
-      void* nxt = (s == nt - 1 && out) ? out : (cur == pl.s[0] ? pl.s[1] : pl.s[0]);
-      TRY(step_inc(pl, tma, false, cur, nxt, d, e, st));
-      cur = nxt;
+    int left = nt - 1;
+    while (left > 0) {
+      const int o = 1 - c;
+      if (two && left >= 2) {
+        void* dst = (left == 2 && out) ? out : (cur == P[0] ? P[1] : P[0]);
+        TRY(launch_step2_kahan(pl, cur, D[c], E[c], dst, D[o], E[o], st));
+        cur = dst;
+        c = o;
+        left -= 2;
+      } else {
+        // one step; d and e are read halo-free, so they update in place
+        void* dst = (left == 1 && out) ? out : (cur == P[0] ? P[1] : P[0]);
+        TRY(step_inc(pl, tma, false, cur, dst, D[c], E[c], st));
+        cur = dst;
+        left -= 1;
+      }
+      ++launches;
     }
     if (prof) CK(cudaEventRecord(rec.b, st));
     if (result) *result = cur;
@@ -288,6 +307,7 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
         TRY(step3(pl, tma, false, B, A, dst, nullptr, st));
         A = B;
         B = dst;
+        ++launches;
       }
       if (prof) CK(cudaEventRecord(rec.b, st));
       if (result) *result = B;
@@ -295,7 +315,8 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
   }
   if (prof) {
     rec.steps = nt - 1;
-    rec.bytes = (double)(nt - 1) * (double)pl.n3 * bytes_per_point(pl);
+    rec.launches = launches;
+    rec.bytes = (double)launches * (double)pl.n3 * bytes_per_point(pl);
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.push_back(rec);
   }
@@ -588,7 +609,8 @@ int ffpat_profile_read(ffpat_profile* out) {
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
       if (e != cudaSuccess) rc = fail(FFPAT_ECUDA, "profile events: %s", cudaGetErrorString(e));
     }
-    out->step_launches += r.steps;
+    out->step_launches += r.launches;
+    out->steps += r.steps;
     out->step_ms += ms;
     out->step_bytes += r.bytes;
     cudaEventDestroy(r.a);
@@ -602,7 +624,7 @@ int64_t ffpat_launch_count(void) { return g_launches.load(); }
 
 int ffpat_set_stencil_path(int32_t path) {
   g_err[0] = 0;
-  if (path < 0 || path > 2) return fail(FFPAT_EINVAL, "stencil path %d not in {0, 1, 2}", path);
+  if (path < 0 || path > 3) return fail(FFPAT_EINVAL, "stencil path %d not in {0, 1, 2, 3}", path);
   g_stencil_path = path;
   return FFPAT_OK;
 }

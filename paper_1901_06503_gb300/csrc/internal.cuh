@@ -21,7 +21,7 @@ struct Plan {
   size_t n3 = 0, nd = 0, esize = 0;
   // workspace carve (device)
   void* kap = nullptr;    // kappa / 12 for every grid point
-  void* s[4] = {};        // wavefield state (2 buffers three-term form, 4 increment form)
+  void* s[6] = {};        // wavefield state: three-term p^{n-1}, p^n; increment form p, p', d, e, d', e'
   void* x = nullptr;      // image-domain scratch (adjoint input / gradient)
   void* v = nullptr;      // image-domain scratch (power iteration vector)
   void* r = nullptr;      // data-domain scratch (residual)
@@ -84,6 +84,12 @@ struct BatchStep {
 };
 int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st);
 constexpr int kMaxBatchRequests = 28;
+
+// Two FP32-Kahan steps in one pass (temporal blocking): reads (p, d, e) at
+// level n with halos, writes level n + 2 to (po, dout, eout), which must not
+// alias the inputs.  TMA layout rules as launch_step_tma.
+int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void* e, void* po,
+                       void* dout, void* eout, cudaStream_t st);
 
 // device status word of the TMA kernels (0 = ok, else -FFPAT_* of the first error)
 int read_device_status(unsigned* out, bool clear);

@@ -456,6 +456,174 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
   }
 }
 
+// ------------------------------------- two FP32-Kahan steps per pass ----
+// Temporal blocking: one launch advances (p, d, e) from level n to n + 2.
+// Step A recomputes level n + 1 on the 64 x 8 tile plus a two-point x/y halo
+// (68 x 12 points) from a halo-4 box of p^n (72 x 16, starting 16-byte aligned
+// at x0 - 4) and halo-2 boxes of d^n, e^n, kap (72 x 12); step B then forms
+// level n + 2 on the tile from the level-(n+1) planes kept in shared memory.
+// Each point's arithmetic is that of the single-step kernel (same Laplacian
+// order, same Kahan update), so two passes of this kernel give bit-identical
+// results to four single steps.  HBM traffic is 28 B per point per TWO steps;
+// d and e are read with a halo, so they are double-buffered (no in place).
+// Points outside the grid read kap = d = e = p = 0 and therefore produce
+// p^{n+1} = 0 there: the zero ghost values of step B come out of step A.
+namespace tb2 {
+constexpr int PW = 72, PH = 16;  // p^n box (x0-4 .., y0-4 ..)
+constexpr int QW = 72, QH = 12;  // d, e, kap, and level-(n+1) p boxes (x0-4 .., y0-2 ..)
+constexpr int PB = PW * PH * 4, QB = QW * QH * 4, TB = TBX * TBY * 4;
+constexpr int RP = 7;  // p^n planes zA-2 .. zA+4
+constexpr int RK = 5;  // kap planes zA-2 .. zA+2 (step B reads kap two planes behind step A)
+constexpr int RD = 3;  // d^n, e^n planes zA .. zA+2
+constexpr int RA = 5;  // level-(n+1) p planes zA-4 .. zA
+constexpr int RAD = 3; // level-(n+1) d, e tile planes zA-2 .. zA
+constexpr size_t kSmem = (size_t)RP * PB + (size_t)RK * QB + (size_t)RD * 2 * QB +
+                         (size_t)RA * QB + (size_t)RAD * 2 * TB + RP * 8;
+__host__ __device__ constexpr int slot(int z, int m) { return (z + 64 * m) % m; }
+}  // namespace tb2
+
+struct Maps2 {
+  CUtensorMap p;  // p^n, 72 x 16 box
+  CUtensorMap d;  // d^n, 72 x 12
+  CUtensorMap e;  // e^n, 72 x 12
+  CUtensorMap k;  // kap, 72 x 12
+};
+
+__device__ __forceinline__ void tb2_issue(const Maps2& m, unsigned char* sm, uint64_t* bar, int R,
+                                          int z0, int z1, int x0, int y0) {
+  using namespace tb2;
+  const bool wp = R >= z0 - 4 && R <= z1 + 3;
+  const bool wq = R - 2 >= z0 - 2 && R - 2 <= z1 + 1;
+  if (!wp && !wq) return;
+  uint64_t* b = &bar[slot(R, RP)];
+  mbar_expect_tx(b, (wp ? PB : 0) + (wq ? 3 * QB : 0));
+  float* P = reinterpret_cast<float*>(sm);
+  float* K = reinterpret_cast<float*>(sm + RP * PB);
+  float* D = reinterpret_cast<float*>(sm + RP * PB + RK * QB);
+  if (wp) tma_load_3d(P + slot(R, RP) * (PB / 4), &m.p, x0 - 4, y0 - 4, R, b);
+  if (wq) {
+    const int z = R - 2;
+    tma_load_3d(K + slot(z, RK) * (QB / 4), &m.k, x0 - 4, y0 - 2, z, b);
+    tma_load_3d(D + slot(z, RD) * 2 * (QB / 4), &m.d, x0 - 4, y0 - 2, z, b);
+    tma_load_3d(D + (slot(z, RD) * 2 + 1) * (QB / 4), &m.e, x0 - 4, y0 - 2, z, b);
+  }
+}
+
+__global__ void __launch_bounds__(NTX* NTY, 1)
+    k_step2_kahan(const __grid_constant__ Maps2 maps, float* __restrict__ po,
+                  float* __restrict__ dout, float* __restrict__ eout, int n, int zc, int tiles_x,
+                  int tiles_y, int nitems) {
+  using namespace tb2;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const float* P = reinterpret_cast<const float*>(sm);
+  const float* K = reinterpret_cast<const float*>(sm + RP * PB);
+  const float* D = reinterpret_cast<const float*>(sm + RP * PB + RK * QB);
+  float* A = reinterpret_cast<float*>(sm + RP * PB + RK * QB + RD * 2 * QB);
+  float* AD = reinterpret_cast<float*>(sm + RP * PB + RK * QB + RD * 2 * QB + RA * QB);
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(sm + RP * PB + RK * QB + RD * 2 * QB + RA * QB + RAD * 2 * TB);
+  if (*(volatile unsigned*)&g_tma_status != 0u) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * NTX + tx;
+  if (tid == 0) {
+    for (int i = 0; i < RP; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  const size_t plane = (size_t)n * n;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tix = item % tiles_x;
+    const int tiy = (item / tiles_x) % tiles_y;
+    const int z0 = (item / (tiles_x * tiles_y)) * zc;
+    const int z1 = min(n, z0 + zc);
+    const int x0 = tix * TBX, y0 = tiy * TBY;
+    if (tid == 0)
+      for (int R = z0 - 4; R < z0 - 4 + RP; ++R) tb2_issue(maps, sm, bar, R, z0, z1, x0, y0);
+    bool timed_out = false;
+    int waited_upto = z0 - 5;
+    for (int zA = z0 - 2; zA <= z1 + 1; ++zA) {
+      for (int R = waited_upto + 1; R <= zA + 2; ++R) {
+        const int b = slot(R, RP);
+        if (!mbar_wait(&bar[b], (phase >> b) & 1u, kWaitCycles)) timed_out = true;
+        phase ^= 1u << b;
+      }
+      waited_upto = zA + 2;
+      // ---- step A: level n+1 at plane zA on the 68 x 12 extended tile
+      {
+        const float* P0 = P + slot(zA, RP) * (PB / 4);
+        const float* Pm1 = P + slot(zA - 1, RP) * (PB / 4);
+        const float* Pp1 = P + slot(zA + 1, RP) * (PB / 4);
+        const float* Pm2 = P + slot(zA - 2, RP) * (PB / 4);
+        const float* Pp2 = P + slot(zA + 2, RP) * (PB / 4);
+        const float* Kz = K + slot(zA, RK) * (QB / 4);
+        const float* Dz = D + slot(zA, RD) * 2 * (QB / 4);
+        const float* Ez = Dz + QB / 4;
+        float* Az = A + slot(zA, RA) * (QB / 4);
+        float* ADz = AD + slot(zA, RAD) * 2 * (TB / 4);
+        for (int q = tid; q < 34 * QH; q += NTX * NTY) {
+          const int qy = q / 34, qx = 2 + 2 * (q % 34);
+          const int po_ = (qy + 2) * PW + qx;  // same x origin, two more rows of halo
+          const int qo = qy * QW + qx;
+          Nb na, nb;
+          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, na, nb);
+          const float La = lap12_nb(na), Lb = lap12_nb(nb);
+          const float2 Kv = lds2(Kz + qo), Dv = lds2(Dz + qo), Ev = lds2(Ez + qo);
+          const float3 ra = kahan_update(na.c, Kv.x, La, Dv.x, Ev.x, false);
+          const float3 rb = kahan_update(nb.c, Kv.y, Lb, Dv.y, Ev.y, false);
+          *reinterpret_cast<float2*>(Az + qo) = make_float2(ra.x, rb.x);
+          if (qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TBY) {
+            const int to = (qy - 2) * TBX + (qx - 4);
+            *reinterpret_cast<float2*>(ADz + to) = make_float2(ra.y, rb.y);
+            *reinterpret_cast<float2*>(ADz + TB / 4 + to) = make_float2(ra.z, rb.z);
+          }
+        }
+      }
+      __syncthreads();
+      // ---- step B: level n+2 at plane zB = zA - 2 on the tile
+      const int zB = zA - 2;
+      if (zB >= z0) {
+        const float* A0 = A + slot(zB, RA) * (QB / 4);
+        const float* Am1 = A + slot(zB - 1, RA) * (QB / 4);
+        const float* Ap1 = A + slot(zB + 1, RA) * (QB / 4);
+        const float* Am2 = A + slot(zB - 2, RA) * (QB / 4);
+        const float* Ap2 = A + slot(zB + 2, RA) * (QB / 4);
+        const float* Kz = K + slot(zB, RK) * (QB / 4);
+        const float* ADz = AD + slot(zB, RAD) * 2 * (TB / 4);
+        const int xl = 2 * tx;
+        const int x = x0 + xl, y = y0 + ty;
+        const int qo = (ty + 2) * QW + xl + 4;
+        const int to = ty * TBX + xl;
+        Nb na, nb;
+        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, na, nb);
+        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        const float2 Kv = lds2(Kz + qo), Dv = lds2(ADz + to), Ev = lds2(ADz + TB / 4 + to);
+        if (x < n && y < n) {
+          const float3 ra = kahan_update(na.c, Kv.x, La, Dv.x, Ev.x, false);
+          const float3 rb = kahan_update(nb.c, Kv.y, Lb, Dv.y, Ev.y, false);
+          const size_t gi = (size_t)zB * plane + (size_t)y * n + x;
+          *reinterpret_cast<float2*>(po + gi) = make_float2(ra.x, rb.x);
+          *reinterpret_cast<float2*>(dout + gi) = make_float2(ra.y, rb.y);
+          *reinterpret_cast<float2*>(eout + gi) = make_float2(ra.z, rb.z);
+        }
+      }
+      if (__syncthreads_or(timed_out)) {
+        if (tid == 0) {
+          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+          for (int R = waited_upto + 1; R <= min(z1 + 3, zA + RP - 3); ++R) {
+            const int b = slot(R, RP);
+            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
+            phase ^= 1u << b;
+          }
+        }
+        return;
+      }
+      if (tid == 0) tb2_issue(maps, sm, bar, zA + RP - 2, z0, z1, x0, y0);
+    }
+  }
+}
+
 // ------------------------------------------------------------- host side --
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -463,21 +631,29 @@ std::once_flag g_encode_once;
 
 struct MapKey {
   const void* ptr;
-  int n, esize, halo;
+  int n, esize, bx, by;
   bool operator==(const MapKey& o) const {
-    return ptr == o.ptr && n == o.n && esize == o.esize && halo == o.halo;
+    return ptr == o.ptr && n == o.n && esize == o.esize && bx == o.bx && by == o.by;
   }
 };
 struct MapKeyHash {
   size_t operator()(const MapKey& k) const {
     return std::hash<const void*>()(k.ptr) ^ ((size_t)k.n << 1) ^ ((size_t)k.esize << 13) ^
-           ((size_t)k.halo << 17);
+           ((size_t)k.bx << 17) ^ ((size_t)k.by << 27);
   }
 };
 
+int make_map_box(CUtensorMap* m, const void* base, int n, int esize, int bx, int by);
+
+// the single-step kernels' boxes: p^n with the two-point halo, or the bare tile
 int make_map(CUtensorMap* m, const void* base, int n, int esize, bool halo) {
+  const int xh = 16 / esize;
+  return make_map_box(m, base, n, esize, halo ? TBX + 2 * xh : TBX, halo ? TBY + 4 : TBY);
+}
+
+int make_map_box(CUtensorMap* m, const void* base, int n, int esize, int bx, int by) {
   static thread_local std::unordered_map<MapKey, CUtensorMap, MapKeyHash> cache;
-  const MapKey key{base, n, esize, halo ? 1 : 0};
+  const MapKey key{base, n, esize, bx, by};
   auto it = cache.find(key);
   if (it != cache.end()) {
     *m = it->second;
@@ -492,11 +668,9 @@ int make_map(CUtensorMap* m, const void* base, int n, int esize, bool halo) {
       g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   });
   if (!g_encode) return FFPAT_ECUDA;
-  const int xh = 16 / esize;
   cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
   cuuint64_t strides[2] = {(cuuint64_t)n * esize, (cuuint64_t)n * n * esize};
-  cuuint32_t box[3] = {(cuuint32_t)(halo ? TBX + 2 * xh : TBX), (cuuint32_t)(halo ? TBY + 4 : TBY),
-                       1};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = g_encode(
       m, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
@@ -645,6 +819,41 @@ int launch_wait_timeout(long long cycles, cudaStream_t st) {
   k_wait_timeout<<<1, 32, 0, st>>>(cycles);
   count_launch();
   return check_launch("k_wait_timeout");
+}
+
+int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void* e, void* po,
+                       void* dout, void* eout, cudaStream_t st) {
+  Maps2 maps;
+  if (make_map_box(&maps.p, p, pl.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
+      make_map_box(&maps.d, d, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
+      make_map_box(&maps.e, e, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
+      make_map_box(&maps.k, pl.kap, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK)
+    return report(FFPAT_ECUDA, "two-step kernel: tensor map");
+  const size_t smem = tb2::kSmem + 1024;
+  static int occ = 0;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute(k_step2_kahan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step2_kahan, NTX * NTY, smem);
+    if (occ < 1) occ = 1;
+  });
+  const int n = pl.n;
+  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + TBY - 1) / TBY;
+  const int slots = kNumSMs * occ;
+  // z-ranges: step A repeats 4 planes per range, so keep ranges long where the
+  // grid allows and use enough of them to fill the GPU
+  int zchunks = (2 * slots + tiles_x * tiles_y - 1) / (tiles_x * tiles_y);
+  const int zmax = n / 16 > 0 ? n / 16 : 1;
+  if (zchunks > zmax) zchunks = zmax;
+  if (zchunks < 1) zchunks = 1;
+  const int zc = (n + zchunks - 1) / zchunks;
+  zchunks = (n + zc - 1) / zc;
+  const int nitems = tiles_x * tiles_y * zchunks;
+  const int grid = nitems < slots ? nitems : slots;
+  k_step2_kahan<<<grid, dim3(NTX, NTY), smem, st>>>(maps, (float*)po, (float*)dout, (float*)eout,
+                                                   n, zc, tiles_x, tiles_y, nitems);
+  count_launch();
+  return check_launch("k_step2_kahan");
 }
 
 int read_device_status(unsigned* out, bool clear) {

@@ -51,7 +51,8 @@ class FBStats(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_int64), ("step_ms", ctypes.c_double),
-                ("step_bytes", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("step_bytes", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("steps", ctypes.c_int64)]
 
 
 class ServingStats(ctypes.Structure):
@@ -366,7 +367,7 @@ def launch_count() -> int:
 
 
 def set_stencil_path(path: int) -> None:
-    """0 automatic, 1 plain 2.5D leapfrog kernel, 2 TMA-fed kernel."""
+    """0 automatic, 1 plain 2.5D kernel, 2 single-step TMA kernel, 3 two-step TMA kernel."""
     _check(lib().ffpat_set_stencil_path(int(path)))
 
 

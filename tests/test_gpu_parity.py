@@ -319,3 +319,27 @@ def test_tma_path_rejects_unaligned_sizes():
             F.wave(prob, dev(random_speed(33, 1), prob), dev(random_volume(33, 2), prob))
     finally:
         F.set_stencil_path(0)
+
+
+@pytest.mark.parametrize("n,T", [(36, 0.4), (36, 0.41), (64, 0.3), (96, 0.21), (128, 0.05)])
+def test_two_step_kahan_bit_identical(n, T):
+    """Two FP32-Kahan steps per pass (temporal blocking) against one step per
+    pass: the same per-point arithmetic, so W and W^T agree bit for bit, for
+    even and odd step counts and ragged tiles; and both match the oracle."""
+    prec = F.FP32_KAHAN
+    c = as_input(random_speed(n, 1100 + n), prec)
+    h = as_input(random_volume(n, 1101 + n), prec)
+    prob = F.problem(n, T, 4, prec)
+    outs = {}
+    try:
+        for path in (2, 3):
+            F.set_stencil_path(path)
+            outs[path] = (host(F.wave(prob, dev(c, prob), dev(h, prob))),
+                          host(F.wave(prob, dev(c, prob), dev(h, prob), transpose=True)))
+    finally:
+        F.set_stencil_path(0)
+    assert np.array_equal(outs[2][0], outs[3][0])
+    assert np.array_equal(outs[2][1], outs[3][1])
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    assert rel(outs[3][0], o.wave(o.kappa(n, dt, c), h, nt)) < TOL[prec]
+    assert F.device_status() == 0
