@@ -185,7 +185,7 @@ int64_t ffpat_launch_count(void);
 
 /* Choice of leapfrog kernel (process-wide): 0 = automatic (the TMA-fed kernels
  * when N % 4 == 0 for float or N % 2 == 0 for double and all arrays are
- * 16-byte aligned -- two steps per pass for FP32-Kahan -- else the plain 2.5D
+ * 16-byte aligned -- two steps per pass for FP32-Kahan at N >= 256 -- else the plain 2.5D
  * kernel), 1 = always the plain kernel, 2 = the single-step TMA kernel, 3 =
  * the two-step TMA kernel for FP32-Kahan (single steps otherwise); 2 and 3
  * fail with FFPAT_EINVAL where TMA cannot be used.  All compute the same

@@ -255,7 +255,10 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
                 pl.n);
   long long launches = 0;
   if (pl.prec == FFPAT_FP32_KAHAN) {
-    const bool two = tma && (path == 0 || path == 3);
+    // two steps per pass halve the HBM bytes; below ~256^3 the single-step
+    // kernel wins (the step working set sits in L2 and the two-step kernel has
+    // too few CTAs in flight), measured on GB300
+    const bool two = tma && (path == 3 || (path == 0 && pl.n >= 256));
     void* P[2] = {pl.s[0], pl.s[1]};
     void* D[2] = {pl.s[2], pl.s[4]};
     void* E[2] = {pl.s[3], pl.s[5]};
