@@ -27,6 +27,12 @@ sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM bytes per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_step_tma_fp32kahan_n128.md,
+# vectorised single-step kernel, cold caches).  Keyed by (workload, precision);
+# None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 33.574144e6}
+
 WORKLOADS = {
     "cfg2": dict(cfg=2, label="single solve N=128^3, 90 angles, T=1.2, 20 balls, GRF sound speed"),
     "cfg5": dict(cfg=5, label="large solve N=384^3, 180 angles, T=1.5, ramp-preconditioned"),
@@ -61,7 +67,7 @@ class Clocks:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -303,7 +309,9 @@ def run_ours(args):
         "fb_iters_per_s": world * args.steps / (dev_ms / 1e3),
         "wall_s": wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None,
+                     "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
+                     "traffic_source": "ncu capture of the same kernel at this size (cold caches)",
                      "peak_source": f"{src} hbm_gbs", "kernel": "leapfrog pass",
                      "bytes_per_point_pass": bpp,
                      "steps_per_pass": prof["steps"] / max(prof["step_launches"], 1),
@@ -427,8 +435,8 @@ def run_precision(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
     ap.add_argument("--precision", choices=["fp32-kahan", "fp32", "fp64"], default="fp32-kahan")

@@ -163,6 +163,14 @@ __global__ void __launch_bounds__(128)
 // (angle, detector) pairs).  Same per-sample arithmetic as k_project.
 constexpr int kPad = 3;
 
+// row pitch of the staged plane: at least n + 2 kPad, and 1 mod 32 so that the
+// 32 rays of a warp, which cross the plane along one direction, fall on
+// different shared-memory banks when they run along y
+__host__ __device__ inline int plane_pitch(int n) {
+  const int w = n + 2 * kPad;
+  return w + ((33 - w % 32) % 32);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_project_smem(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
@@ -170,11 +178,12 @@ __global__ void __launch_bounds__(256)
                    const int32_t* __restrict__ tabi, int n, int nth, int ns, int group) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
-  const int W = n + 2 * kPad;
+  const int W = plane_pitch(n);  // row pitch; rows = n + 2 kPad
   const int l = blockIdx.x;
   const int ja = blockIdx.y * group, jb = min(nth, ja + group);
   const T* __restrict__ sl = p + (size_t)l * n * n;
-  for (int yy = threadIdx.x / 32; yy < W; yy += blockDim.x / 32) {
+  const int H = n + 2 * kPad;
+  for (int yy = threadIdx.x / 32; yy < H; yy += blockDim.x / 32) {
     const int y = yy - kPad;
     for (int xx = threadIdx.x % 32; xx < W; xx += 32) {
       const int x = xx - kPad;
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   // corner (i0, j0) of the padded plane, clamped so that no load leaves it
   auto at = [&](int j0, int i0) -> int {
-    const int jj = min(max(j0 + kPad, 0), W - 2), ii = min(max(i0 + kPad, 0), W - 2);
+    const int jj = min(max(j0 + kPad, 0), H - 2), ii = min(max(i0 + kPad, 0), H - 2);
     return jj * W + ii;
   };
   const int work = (jb - ja) * n;
@@ -384,8 +393,7 @@ __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int3
 }  // namespace
 
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st) {
-  const size_t W = (size_t)pl.n + 2 * kPad;
-  const size_t smem = W * W * pl.esize;
+  const size_t smem = (size_t)plane_pitch(pl.n) * (pl.n + 2 * kPad) * pl.esize;
   if (smem <= 200 * 1024) {
     // one CTA per (plane, group of 8 angles); the padded plane is read once per CTA
     const int group = 8;
