@@ -22,6 +22,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <stdlib.h>
+
 #include <mutex>
 #include <unordered_map>
 
@@ -626,6 +628,16 @@ __global__ void __launch_bounds__(NTX* NTY, 1)
 
 // ------------------------------------------------------------- host side --
 
+// FFPAT_ZCHUNK=<planes> fixes the z-range of one work item of the TMA
+// stencil kernels (a tuning knob for measurements; 0 or unset = automatic)
+int zchunk_override() {
+  static int v = [] {
+    const char* e = getenv("FFPAT_ZCHUNK");
+    return e ? atoi(e) : 0;
+  }();
+  return v;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 
@@ -703,7 +715,8 @@ int launch_one(const Plan& pl, const Maps& maps, void* o0, void* o1, void* o2, c
   const int zmax = n / 8 > 0 ? n / 8 : 1;
   if (zchunks > zmax) zchunks = zmax;
   if (zchunks < 1) zchunks = 1;
-  const int zc = (n + zchunks - 1) / zchunks;
+  int zc = (n + zchunks - 1) / zchunks;
+  if (zchunk_override() > 0) zc = zchunk_override() < n ? zchunk_override() : n;
   zchunks = (n + zc - 1) / zc;
   const int nitems = tiles_x * tiles_y * zchunks;
   const int grid = nitems < slots ? nitems : slots;
@@ -846,7 +859,8 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
   const int zmax = n / 16 > 0 ? n / 16 : 1;
   if (zchunks > zmax) zchunks = zmax;
   if (zchunks < 1) zchunks = 1;
-  const int zc = (n + zchunks - 1) / zchunks;
+  int zc = (n + zchunks - 1) / zchunks;
+  if (zchunk_override() > 0) zc = zchunk_override() < n ? zchunk_override() : n;
   zchunks = (n + zc - 1) / zc;
   const int nitems = tiles_x * tiles_y * zchunks;
   const int grid = nitems < slots ? nitems : slots;
