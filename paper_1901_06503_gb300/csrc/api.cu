@@ -11,6 +11,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -240,13 +241,12 @@ static int step_inc(const Plan& pl, bool tma, bool start, const void* pin, void*
   return launch_step_inc(pl, pin, pout, d, e, start, st);
 }
 
-// W applied to `in` (N^3).  The result goes to `out` if non-null, else it
-// stays in a state buffer whose address is returned through *result.
-static int run_wave(const Plan& pl, const void* in, void* out, const void** result,
-                    cudaStream_t st) {
+// The launches of W applied to `in` (N^3): the result goes to `out` if
+// non-null, else it stays in a state buffer whose address is returned through
+// *result; *launches counts the leapfrog launches (one HBM pass each).
+static int wave_sequence(const Plan& pl, const void* in, void* out, const void** result,
+                         long long* nlaunch, cudaStream_t st) {
   const int nt = pl.nt;
-  ProfRec rec{};
-  const bool prof = g_prof_on.load() && nt > 1;
   const void* ptrs[10] = {in, out, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3], pl.s[4], pl.s[5]};
   const int path = g_stencil_path.load();
   const bool tma = path != 1 && tma_supported(pl, ptrs, 9);
@@ -265,12 +265,8 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
     int c = 0;  // index of the buffers holding the current level
     void* first = (nt == 1 && out) ? out : P[0];
     TRY(step_inc(pl, tma, true, in, first, D[0], E[0], st));
+    ++launches;
     const void* cur = first;
-    if (prof) {
-      CK(cudaEventCreate(&rec.a));
-      CK(cudaEventCreate(&rec.b));
-      CK(cudaEventRecord(rec.a, st));
-    }
     int left = nt - 1;
     while (left > 0) {
       const int o = 1 - c;
@@ -289,7 +285,6 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
       }
       ++launches;
     }
-    if (prof) CK(cudaEventRecord(rec.b, st));
     if (result) *result = cur;
   } else {
     void* A = pl.s[0];  // p^{n-1}
@@ -297,14 +292,11 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
     if (nt == 1) {
       void* dst = out ? out : B;
       TRY(step3(pl, tma, true, in, nullptr, dst, nullptr, st));
+      ++launches;
       if (result) *result = dst;
     } else {
       TRY(step3(pl, tma, true, in, nullptr, B, A, st));
-      if (prof) {
-        CK(cudaEventCreate(&rec.a));
-        CK(cudaEventCreate(&rec.b));
-        CK(cudaEventRecord(rec.a, st));
-      }
+      ++launches;
       for (int s = 1; s < nt; ++s) {
         void* dst = (s == nt - 1 && out) ? out : A;
         TRY(step3(pl, tma, false, B, A, dst, nullptr, st));
@@ -312,12 +304,107 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
         B = dst;
         ++launches;
       }
-      if (prof) CK(cudaEventRecord(rec.b, st));
       if (result) *result = B;
     }
   }
+  *nlaunch = launches;
+  return FFPAT_OK;
+}
+
+// ---- CUDA graphs of the time loop.  The second time the same W (same
+// buffers, step count, precision and kernel path) runs, its launch sequence is
+// captured on a private stream into a graph and from then on replayed with one
+// cudaGraphLaunch on the caller's stream: the host no longer issues one launch
+// per step, which bounds small grids (128^3 steps take ~10 us).  FFPAT_GRAPHS=0
+// turns this off; a caller that is itself capturing gets plain launches.
+struct GraphEntry {
+  std::vector<const void*> key;
+  cudaGraphExec_t exec = nullptr;
+  const void* result = nullptr;
+  long long launches = 0;
+  int device = -1;
+};
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;  // most recently used last
+constexpr size_t kMaxGraphs = 32;
+
+static bool graphs_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("FFPAT_GRAPHS");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+static int run_wave(const Plan& pl, const void* in, void* out, const void** result,
+                    cudaStream_t st) {
+  ProfRec rec{};
+  const bool prof = g_prof_on.load();
   if (prof) {
-    rec.steps = nt - 1;
+    CK(cudaEventCreate(&rec.a));
+    CK(cudaEventCreate(&rec.b));
+    CK(cudaEventRecord(rec.a, st));
+  }
+  long long launches = 0;
+  const void* res = nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  bool done = false, replay_only = false;
+  if (graphs_enabled() && cap == cudaStreamCaptureStatusNone && pl.nt >= 8) {
+    std::vector<const void*> key = {in, out, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3],
+                                    pl.s[4], pl.s[5], (const void*)(intptr_t)pl.nt,
+                                    (const void*)(intptr_t)pl.prec,
+                                    (const void*)(intptr_t)g_stencil_path.load(),
+                                    (const void*)(intptr_t)pl.n, (const void*)(intptr_t)dev};
+    std::unique_lock<std::mutex> lk(g_graph_mu);
+    int hit = -1;
+    for (int i = (int)g_graphs.size() - 1; i >= 0; --i)
+      if (g_graphs[i].key == key) {
+        hit = i;
+        break;
+      }
+    if (hit >= 0) {
+      GraphEntry e = g_graphs[hit];
+      g_graphs.erase(g_graphs.begin() + hit);
+      replay_only = e.exec != nullptr;
+      if (!e.exec) {
+        // second use: capture the sequence and keep the executable graph
+        static thread_local cudaStream_t cs = nullptr;
+        if (!cs) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const int rc = wave_sequence(pl, in, out, &e.result, &e.launches, cs);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+        if (rc != FFPAT_OK) return rc;
+        if (ec != cudaSuccess) return fail(FFPAT_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return fail(FFPAT_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        e.device = dev;
+      }
+      CK(cudaGraphLaunch(e.exec, st));
+      res = e.result;
+      launches = e.launches;
+      g_graphs.push_back(e);
+      done = true;
+    } else {
+      GraphEntry e;
+      e.key = key;
+      g_graphs.push_back(e);
+      if (g_graphs.size() > kMaxGraphs) {
+        if (g_graphs.front().exec) cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+      }
+    }
+  }
+  if (!done) TRY(wave_sequence(pl, in, out, &res, &launches, st));
+  if (replay_only) count_launch((int)launches);  // the graph's kernels run again
+  if (result) *result = res;
+  if (prof) {
+    CK(cudaEventRecord(rec.b, st));
+    rec.steps = pl.nt;
     rec.launches = launches;
     rec.bytes = (double)launches * (double)pl.n3 * bytes_per_point(pl);
     std::lock_guard<std::mutex> g(g_prof_mu);
@@ -325,6 +412,8 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
   }
   return FFPAT_OK;
 }
+
+
 
 // h = W^T P^T g  ->  x = K P^T g ; w = W x ; h = w / K
 static int apply_adjoint(const Plan& pl, const void* g, void* h, cudaStream_t st) {
