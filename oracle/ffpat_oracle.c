@@ -559,3 +559,65 @@ int ffo_grad(int n, double T, double cfl, int nth, const double *c, const double
   free(s.kappa);
   return nt;
 }
+
+/* ------------------------------------------------- two-step method (Alg. 9) -- */
+
+/* X^{-1} G = X^* Lambda G applied plane by plane (Sec. 3.1: filtered
+ * backprojection); the discrete form (2 pi / (n_angles dx)) P^T Lambda G,
+ * where 2 pi / n_angles is the angle weight of the backprojection over S^1
+ * and 1/dx undoes the sample length of P^T. */
+void ffo_fbp(int n, int nth, const double *G, double *out) {
+  size_t nd = (size_t)nth * n * n, n3 = (size_t)n * n * n;
+  double *lr = malloc(nd * sizeof(double));
+  ffo_ramp(n, nth, G, lr);
+  ffo_backproject(n, nth, lr, out);
+  double w = 2.0 * FFO_PI / (nth * (2.0 / n));
+  for (size_t i = 0; i < n3; ++i) out[i] *= w;
+  free(lr);
+}
+
+/* Algorithm 9: g = X^{-1} G, then h_{k+1} = prox_{s lambda R}(h_k - s W^T (W h_k - g))
+ * with R = ||h||_1 + indicator(h >= 0).  stats[4 k + 0..3]: objective
+ * 1/2 ||W h_k - g||^2 + lambda ||h_k||_1, ||W h_k - g||, relative change,
+ * ||h_{k+1}||. */
+int ffo_fb_two_step(int n, double T, double cfl, int nth, const double *c, const double *G,
+                    double lambda, double step, int iters, double tol, double *h, double *stats) {
+  ffo_setup_t s;
+  size_t n3 = (size_t)n * n * n;
+  setup(&s, n, T, cfl, nth, 0, c);
+  double *g = malloc(n3 * sizeof(double)), *r = malloc(n3 * sizeof(double));
+  double *grad = malloc(n3 * sizeof(double));
+  ffo_fbp(n, nth, G, g);
+  int k;
+  for (k = 0; k < iters; ++k) {
+    ffo_wave(n, s.nt, s.kappa, h, r);
+    for (size_t i = 0; i < n3; ++i) r[i] -= g[i];
+    ffo_wave_adjoint(n, s.nt, s.kappa, r, grad);
+    double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
+    for (size_t i = 0; i < n3; ++i) {
+      double f = h[i] - step * grad[i] - step * lambda;
+      double hn = f > 0.0 ? f : 0.0;
+      l1 += fabs(h[i]);
+      hh += h[i] * h[i];
+      dd += (hn - h[i]) * (hn - h[i]);
+      nn += hn * hn;
+      h[i] = hn;
+    }
+    double rel = sqrt(dd) / (sqrt(hh) > 1e-300 ? sqrt(hh) : 1e-300);
+    if (stats) {
+      stats[4 * k + 0] = 0.5 * dot(n3, r, r) + lambda * l1;
+      stats[4 * k + 1] = sqrt(dot(n3, r, r));
+      stats[4 * k + 2] = rel;
+      stats[4 * k + 3] = sqrt(nn);
+    }
+    if (tol > 0.0 && rel < tol) {
+      ++k;
+      break;
+    }
+  }
+  free(g);
+  free(r);
+  free(grad);
+  free(s.kappa);
+  return k;
+}

@@ -79,6 +79,11 @@ def lib():
             L.ffo_grad.restype = ctypes.c_int
             L.ffo_grad.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    _D, _D, _D, _D, _D]
+            L.ffo_fbp.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_fb_two_step.restype = ctypes.c_int
+            L.ffo_fb_two_step.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_double, _D, _D]
             L.ffo_num_threads.restype = ctypes.c_int
             L.ffo_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -230,3 +235,24 @@ def grad(c, h, grad_g, T: float, cfl: float = 0.3):
     gc = np.empty((n, n, n))
     lib().ffo_grad(n, T, cfl, grad_g.shape[0], _p(c), _p(h), _p(grad_g), _p(gh), _p(gc))
     return gh, gc
+
+
+def fbp(G) -> np.ndarray:
+    """X^{-1} G = (2 pi / (n_angles dx)) P^T Lambda G, plane by plane."""
+    G = _f64(G)
+    n = G.shape[1]
+    out = np.empty((n, n, n))
+    lib().ffo_fbp(n, G.shape[0], _p(G), _p(out))
+    return out
+
+
+def fb_two_step(c, G, T: float, lam: float, step: float, iters: int, h0=None, tol: float = 0.0,
+                cfl: float = 0.3):
+    """Algorithm 9 with R = l1 + positivity.  Returns (h, stats[k, 4], iters_done)."""
+    c, G = _f64(c), _f64(G)
+    n = c.shape[0]
+    h = np.zeros((n, n, n)) if h0 is None else _f64(h0).copy()
+    stats = np.zeros((max(iters, 1), 4))
+    k = lib().ffo_fb_two_step(n, T, cfl, G.shape[0], _p(c), _p(G), lam, step, iters, tol, _p(h),
+                              _p(stats))
+    return h, stats[:k], k

@@ -428,3 +428,41 @@ def test_grad_c_single_step_closed_form():
     _, gc = o.grad(c, h, w, T)
     want = o.backproject(w, n) * lap_from_wave(h) * kap / c
     assert np.allclose(gc, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+
+
+# ------------------------------------------------------ two-step method (Alg. 9) --
+
+def test_fbp_is_the_scaled_filtered_backprojection():
+    """fbp = (2 pi / (n_angles dx)) P^T Lambda (the discrete X* Lambda of Sec. 3.1,
+    whose accuracy the FBP identity pin checks)."""
+    n, nth = 12, 9
+    G = random_data(nth, n, 91)
+    want = (2 * np.pi / (nth * (2.0 / n))) * o.backproject(o.ramp(G), n)
+    assert np.allclose(o.fbp(G), want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+
+
+def test_two_step_first_iterate_and_kkt():
+    """Algorithm 9: from h_0 = 0 the first iterate is max(s W^T g - s lambda, 0)
+    with g = X^{-1} G; at the fixed point the KKT conditions of
+    1/2 ||W h - g||^2 + lambda (||h||_1 + i_{>=0}) hold (dense W at 6^3)."""
+    n, nth, T = 6, 8, 0.5
+    c = random_speed(n, 92)
+    G = random_data(nth, n, 93)
+    g = o.fbp(G)
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    kap = o.kappa(n, dt, c)
+    s, lam = 0.3, 0.05
+    h1, st, k = o.fb_two_step(c, G, T, lam, s, 1)
+    want = np.maximum(s * o.wave_adjoint(kap, g, nt) - s * lam, 0.0)
+    assert np.max(np.abs(h1 - want)) < 1e-13 * max(1.0, np.abs(want).max())
+    Wd = dense(lambda h: o.wave(kap, h, nt), n**3, (n, n, n))
+    H = Wd.T @ Wd
+    Lmax = np.linalg.eigvalsh(H).max()
+    lam = 0.02 * float(np.abs(Wd.T @ g.ravel()).max())
+    h, st, k = o.fb_two_step(c, G, T, lam, 1.0 / Lmax, 4000)
+    hr = h.ravel()
+    grad = H @ hr - Wd.T @ g.ravel()
+    pos = hr > 1e-9
+    assert pos.any() and (~pos).any()
+    assert np.max(np.abs(grad[pos] + lam)) < 1e-3 * lam
+    assert np.min(grad[~pos] + lam) > -1e-3 * lam
