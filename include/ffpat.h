@@ -163,6 +163,25 @@ int ffpat_fb_solve(const ffpat_problem *problem, const void *c, const void *g, d
                    ffpat_fb_stats *stats, double *history, void *ws, size_t ws_bytes,
                    void *stream);
 
+/* ---- The two-step method (Algorithm 9, Sec. 4.1), the paper's comparison:
+ * first g = X^{-1} G plane by plane, then FB on 1/2 ||W h - g||^2 + lambda R. */
+
+/* out (N^3) = X^{-1} G = X^* Lambda G (Sec. 3.1: filtered backprojection in
+ * every plane z = const), discretised as (2 pi / (n_angles dx)) P^T Lambda G:
+ * 2 pi / n_angles is the angle weight of the backprojection over S^1 (the data
+ * over [0, pi) count twice) and 1/dx undoes the sample length of P^T. */
+int ffpat_fbp(const ffpat_problem *problem, const void *G, void *out, void *ws, size_t ws_bytes,
+              void *stream);
+
+/* Algorithm 9 with R = ||h||_1 + indicator(h >= 0): g = X^{-1} G, then
+ * h_{k+1} = max(h_k - s W^T (W h_k - g) - s lambda, 0).  Arguments, step rule
+ * (power iteration on W^T W when step <= 0), tol and history as in
+ * ffpat_fb_solve; the objective is 1/2 ||W h_k - g||^2 + lambda ||h_k||_1. */
+int ffpat_fb_two_step(const ffpat_problem *problem, const void *c, const void *G, double lambda,
+                      double step, int32_t max_iters, double tol, void *h_inout,
+                      ffpat_fb_stats *stats, double *history, void *ws, size_t ws_bytes,
+                      void *stream);
+
 /* Instrumentation.  While enabled, every wave time loop records CUDA events on
  * its stream around its leapfrog launches; ffpat_profile_read synchronises
  * those events and returns the leapfrog launches and steps timed, their total

@@ -679,6 +679,105 @@ int ffpat_fb_solve(const ffpat_problem* problem, const void* c, const void* g, d
   return FFPAT_OK;
 }
 
+int ffpat_fbp(const ffpat_problem* problem, const void* G, void* out, void* ws, size_t ws_bytes,
+              void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  g_err[0] = 0;
+  TRY(attach(problem, pl, ws, ws_bytes));
+  if (!G || !out) return fail(FFPAT_EINVAL, "G or out is NULL");
+  TRY(upload_tables(pl, pl.tab, st));
+  TRY(launch_ramp(pl, G, pl.r2, st));
+  TRY(launch_backproject(pl, pl.r2, out, nullptr, st, 2.0 * M_PI / (pl.nth * pl.dx)));
+  return FFPAT_OK;
+}
+
+// power iteration on W^T W (vector in pl.v); W^T = K^-1 W K
+static int power_iteration_w(const Plan& pl, int iters, double* est, cudaStream_t st) {
+  double* sq = pl.scal + 8;
+  TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
+  TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
+  for (int it = 0; it < iters; ++it) {
+    const void* w = nullptr;
+    TRY(run_wave(pl, pl.v, nullptr, &w, st));
+    TRY(launch_kscale(pl, w, pl.x, true, st));
+    TRY(run_wave(pl, pl.x, nullptr, &w, st));
+    TRY(launch_kscale(pl, w, pl.v, false, st));
+    TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
+    TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
+  }
+  double h;
+  CK(cudaMemcpyAsync(&h, sq, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *est = sqrt(h);
+  return FFPAT_OK;
+}
+
+int ffpat_fb_two_step(const ffpat_problem* problem, const void* c, const void* G, double lambda,
+                      double step, int32_t max_iters, double tol, void* h_inout,
+                      ffpat_fb_stats* stats, double* history, void* ws, size_t ws_bytes,
+                      void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  TRY(setup(problem, pl, c, ws, ws_bytes, st));
+  if (!G || !h_inout) return fail(FFPAT_EINVAL, "G or h is NULL");
+  if (max_iters < 0 || max_iters > kMaxHist)
+    return fail(FFPAT_EINVAL, "max_iters = %d outside [0, %d]", max_iters, kMaxHist);
+  if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(FFPAT_EINVAL, "lambda must be >= 0");
+  if (!(tol >= 0.0)) return fail(FFPAT_EINVAL, "tol must be >= 0");
+  double opn = 0.0;
+  if (!(step > 0.0)) {
+    TRY(launch_hash_fill(pl, pl.v, 0x5eed1901ull, st));
+    TRY(power_iteration_w(pl, 20, &opn, st));
+    if (!(opn > 0.0) || !isfinite(opn)) return fail(FFPAT_EINVAL, "operator norm estimate %g", opn);
+    step = 1.0 / opn;
+  }
+  // g~ = X^{-1} G, kept in pl.v for the whole solve
+  TRY(launch_ramp(pl, G, pl.r2, st));
+  TRY(launch_backproject(pl, pl.r2, pl.v, nullptr, st, 2.0 * M_PI / (pl.nth * pl.dx)));
+  int k = 0;
+  for (; k < max_iters; ++k) {
+    double* hk = pl.hist + 8 * (size_t)k;
+    const void* w = nullptr;
+    TRY(run_wave(pl, h_inout, nullptr, &w, st));
+    TRY(launch_resid_kap(pl, w, pl.v, pl.x, hk, st));
+    TRY(run_wave(pl, pl.x, nullptr, &w, st));
+    TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st));
+    if (tol > 0.0) {
+      double q[4];
+      CK(cudaMemcpyAsync(q, hk + 2, sizeof q, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (sqrt(q[2]) / fmax(sqrt(q[1]), 1e-300) < tol) {
+        ++k;
+        break;
+      }
+    }
+  }
+  std::vector<double> hh(8 * (size_t)(k > 0 ? k : 1), 0.0);
+  if (k > 0) CK(cudaMemcpyAsync(hh.data(), pl.hist, 8 * sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < k && history; ++i) {
+    const double* q = &hh[8 * (size_t)i];
+    history[4 * i + 0] = 0.5 * q[0] + lambda * q[2];
+    history[4 * i + 1] = sqrt(q[1]);
+    history[4 * i + 2] = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
+    history[4 * i + 3] = sqrt(q[5]);
+  }
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->iters_done = k;
+    stats->step = step;
+    stats->opnorm_sq = opn;
+    if (k > 0) {
+      const double* q = &hh[8 * (size_t)(k - 1)];
+      stats->objective = 0.5 * q[0] + lambda * q[2];
+      stats->resid_norm = sqrt(q[1]);
+      stats->rel_change = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
+    }
+  }
+  return FFPAT_OK;
+}
+
 int ffpat_profile_enable(int32_t on) {
   g_prof_on = on ? 1 : 0;
   return FFPAT_OK;

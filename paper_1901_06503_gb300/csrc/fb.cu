@@ -184,6 +184,26 @@ __global__ void k_inv_sqrt(const double* __restrict__ src, double* __restrict__ 
   if (threadIdx.x == 0 && blockIdx.x == 0) dst[0] = 1.0 / sqrt(src[0]);
 }
 
+// Algorithm 9 residual: x = kap (w - g) (the input of W^T = K^-1 W K) and
+// the FP64 partial of sum (w - g)^2 (rows 0 and 1 both get it)
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_resid_kap(const T* __restrict__ w, const T* __restrict__ g, const T* __restrict__ kap,
+                T* __restrict__ x, size_t len, double* __restrict__ partials) {
+  double rr = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T r = w[i] - g[i];
+    x[i] = kap[i] * r;
+    rr = fma((double)r, (double)r, rr);
+  }
+  rr = block_sum(rr);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = rr;
+    partials[kReduceBlocks + blockIdx.x] = rr;
+  }
+}
+
 // out = (a - b) / kap   (last step of the transposed recurrence, back from kap-scaled form)
 template <typename T>
 __global__ void k_sub_div(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ kap,
@@ -293,6 +313,19 @@ int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double
         (float*)h, (const float*)w, (const float*)pl.kap, pl.n3, step, step_dev, lambda,
         pl.partials);
   k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 4, dst);
+  count_launch(2);
+  return check_launch(__func__);
+}
+
+int launch_resid_kap(const Plan& pl, const void* w, const void* g, void* x, double* dst,
+                     cudaStream_t st) {
+  if (pl.prec == FFPAT_FP64)
+    k_resid_kap<double><<<kReduceBlocks, kReduceThreads, 0, st>>>(
+        (const double*)w, (const double*)g, (const double*)pl.kap, (double*)x, pl.n3, pl.partials);
+  else
+    k_resid_kap<float><<<kReduceBlocks, kReduceThreads, 0, st>>>(
+        (const float*)w, (const float*)g, (const float*)pl.kap, (float*)x, pl.n3, pl.partials);
+  k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 2, dst);
   count_launch(2);
   return check_launch(__func__);
 }

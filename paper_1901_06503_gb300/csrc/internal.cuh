@@ -97,7 +97,9 @@ int launch_wait_timeout(long long cycles, cudaStream_t st);
 
 // xray.cu
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st);
-int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st);
+// h = mult * scale .* P^T g  (scale nullable)
+int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st,
+                       double mult = 1.0);
 int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st);
 int launch_debug_samples(const Plan& pl, int count, const int32_t* jkm, int32_t* ij, double* f,
                          cudaStream_t st);
@@ -119,6 +121,9 @@ int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double
                      double* dst, cudaStream_t st, const double* step_dev = nullptr);
 int launch_inv_sqrt(const double* src, double* dst, cudaStream_t st);
 int launch_sub_div(const Plan& pl, const void* a, const void* b, void* out, cudaStream_t st);
+// x = kap (w - g), dst[0] = dst[1] = sum (w - g)^2
+int launch_resid_kap(const Plan& pl, const void* w, const void* g, void* x, double* dst,
+                     cudaStream_t st);
 int launch_scale_div(const Plan& pl, const void* a, const void* c, double s, void* out,
                      cudaStream_t st);
 // stencil.cu: acc += w * u * L(p)

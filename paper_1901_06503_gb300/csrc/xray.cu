@@ -266,7 +266,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_backproject2(const T* __restrict__ g, T* __restrict__ h, const T* __restrict__ scale,
                    const double* __restrict__ tab, const float* __restrict__ tabf,
-                   const int32_t* __restrict__ tabi, int n, int nth, int ns) {
+                   const int32_t* __restrict__ tabi, int n, int nth, int ns, T mult) {
   __shared__ T s_cs[kAngleChunk], s_sn[kAngleChunk];
   __shared__ int s_CS[kAngleChunk], s_SN[kAngleChunk];
   const int ix = blockIdx.x * 32 + threadIdx.x;
@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(256)
   const size_t o = ((size_t)l * n + iy) * n + ix;
   T out = (T(2) / T(n)) * acc;
   if (scale) out *= scale[o];
+  if (mult != T(1)) out *= mult;
   h[o] = out;
 }
 
@@ -434,16 +435,18 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
   return check_launch(__func__);
 }
 
-int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st) {
+int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st,
+                       double mult) {
   const dim3 block(32, 8);
   const dim3 grid((pl.n + 31) / 32, (pl.n + 7) / 8, pl.n);
   if (pl.prec == FFPAT_FP64)
     k_backproject2<double><<<grid, block, 0, st>>>((const double*)g, (double*)h,
                                                   (const double*)scale, pl.tab, pl.tabf,
-                                                  pl.tabi, pl.n, pl.nth, pl.ns);
+                                                  pl.tabi, pl.n, pl.nth, pl.ns, mult);
   else
     k_backproject2<float><<<grid, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
-                                                 pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns);
+                                                 pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns,
+                                                 (float)mult);
   count_launch();
   return check_launch(__func__);
 }

@@ -95,6 +95,9 @@ def _declare(L):
         "ffpat_opnorm": (ctypes.c_int, [_PR, _P, _P, i32, ctypes.POINTER(f64), _P, sz, _P]),
         "ffpat_fb_solve": (ctypes.c_int, [_PR, _P, _P, f64, f64, i32, f64, _P,
                                           ctypes.POINTER(FBStats), _P, _P, sz, _P]),
+        "ffpat_fbp": (ctypes.c_int, [_PR, _P, _P, _P, sz, _P]),
+        "ffpat_fb_two_step": (ctypes.c_int, [_PR, _P, _P, f64, f64, i32, f64, _P,
+                                             ctypes.POINTER(FBStats), _P, _P, sz, _P]),
         "ffpat_profile_enable": (ctypes.c_int, [i32]),
         "ffpat_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile)]),
         "ffpat_launch_count": (i64, []),
@@ -348,6 +351,32 @@ def fb_solve(prob, c, g, lam, step, max_iters, h=None, tol=0.0, ws=None, stream=
                                 _dev(g, prob, data_shape(prob), "g"), float(lam), float(step),
                                 int(max_iters), float(tol), _dev(h, prob, vol_shape(prob), "h"),
                                 ctypes.byref(st), hp, wp, wn, _stream(stream)))
+    d = st.as_dict()
+    return h, d, (hist[: d["iters_done"]] if history else None)
+
+
+def fbp(prob, G, out=None, ws=None, stream=None):
+    """X^{-1} G plane by plane (filtered backprojection, N^3 result)."""
+    out = _empty(prob, vol_shape(prob), G) if out is None else out
+    ws, wp, wn = _ws(prob, ws, G.device)
+    _check(lib().ffpat_fbp(ctypes.byref(prob), _dev(G, prob, data_shape(prob), "G"),
+                           _dev(out, prob, vol_shape(prob), "out"), wp, wn, _stream(stream)))
+    return out
+
+
+def fb_two_step(prob, c, G, lam, step, max_iters, h=None, tol=0.0, ws=None, stream=None,
+                history=True):
+    """Algorithm 9; returns (h, stats dict, history array [k, 4] or None)."""
+    import torch
+    h = torch.zeros(vol_shape(prob), dtype=torch_dtype(prob), device=G.device) if h is None else h
+    ws, wp, wn = _ws(prob, ws, G.device)
+    st = FBStats()
+    hist = np.zeros((max(int(max_iters), 1), 4)) if history else None
+    hp = hist.ctypes.data_as(ctypes.c_void_p) if history else None
+    _check(lib().ffpat_fb_two_step(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                                   _dev(G, prob, data_shape(prob), "G"), float(lam), float(step),
+                                   int(max_iters), float(tol), _dev(h, prob, vol_shape(prob), "h"),
+                                   ctypes.byref(st), hp, wp, wn, _stream(stream)))
     d = st.as_dict()
     return h, d, (hist[: d["iters_done"]] if history else None)
 

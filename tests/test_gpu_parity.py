@@ -343,3 +343,29 @@ def test_two_step_kahan_bit_identical(n, T):
     nt, dt = o.time_steps(n, T, 0.3, c.max())
     assert rel(outs[3][0], o.wave(o.kappa(n, dt, c), h, nt)) < TOL[prec]
     assert F.device_status() == 0
+
+
+# ---------------------------------------------------- two-step method (Alg. 9) --
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fbp_and_two_step_fb(prec):
+    w = config(1)
+    c = as_input(w.c, prec)
+    G = as_input(add_noise(o.forward(c, w.h, w.T, w.n_angles), w.noise, w.noise_rel), prec)
+    prob = F.problem(w.n, w.T, w.n_angles, prec)
+    assert rel(host(F.fbp(prob, dev(G, prob))), o.fbp(G)) < (1e-10 if prec == F.FP64 else 2e-6)
+    h_gpu, st, hist = F.fb_two_step(prob, dev(c, prob), dev(G, prob), w.lam, 0.5, 6)
+    h_or, hist_or, k = o.fb_two_step(c, G, w.T, w.lam, 0.5, 6)
+    assert st["iters_done"] == k == 6
+    assert rel(host(h_gpu), h_or) < (1e-10 if prec == F.FP64 else 5e-5)
+    tol = 1e-9 if prec == F.FP64 else 1e-4
+    assert np.max(np.abs(hist[:, 0] - hist_or[:, 0]) / np.abs(hist_or[:, 0])) < tol
+
+
+def test_two_step_automatic_step():
+    w = config(1)
+    G = add_noise(o.forward(w.c, w.h, w.T, w.n_angles), w.noise, w.noise_rel)
+    prob = F.problem(w.n, w.T, w.n_angles)
+    _, st, _ = F.fb_two_step(prob, dev(w.c, prob), dev(G, prob), w.lam, 0.0, 1)
+    # W is a polynomial in K L4 bounded by one in the kappa^-1-weighted norm
+    assert 0.2 < st["opnorm_sq"] < 50 and abs(st["step"] * st["opnorm_sq"] - 1) < 1e-12
