@@ -94,14 +94,14 @@ __global__ void __launch_bounds__(kReduceThreads)
   }
 }
 
-// kap = (c dt / dx)^2 / 12, evaluated in FP64 as ((c dt) / dx)^2 / 12
+// kap = (c dt / dx)^2 / 12 in FP64, with dt / dx and 1/12 folded into one
+// factor q = (dt / dx)^2 / 12 computed on the host (multiplications only)
 template <typename T>
-__global__ void k_kappa(const T* __restrict__ c, T* __restrict__ kap, size_t len, double dt,
-                        double dx) {
+__global__ void k_kappa(const T* __restrict__ c, T* __restrict__ kap, size_t len, double q) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
        i += (size_t)gridDim.x * blockDim.x) {
-    const double r = (double)c[i] * dt / dx;
-    kap[i] = (T)(r * r / 12.0);
+    const double cv = (double)c[i];
+    kap[i] = (T)(cv * cv * q);
   }
 }
 
@@ -262,10 +262,12 @@ int launch_speed_stats(const Plan& pl, const void* c, double* out3, cudaStream_t
 
 int launch_kappa(const Plan& pl, const void* c, cudaStream_t st) {
   const unsigned nb = ew_blocks(pl.n3);
+  const double r = pl.dt / pl.dx;
+  const double q = r * r / 12.0;
   if (pl.prec == FFPAT_FP64)
-    k_kappa<double><<<nb, 256, 0, st>>>((const double*)c, (double*)pl.kap, pl.n3, pl.dt, pl.dx);
+    k_kappa<double><<<nb, 256, 0, st>>>((const double*)c, (double*)pl.kap, pl.n3, q);
   else
-    k_kappa<float><<<nb, 256, 0, st>>>((const float*)c, (float*)pl.kap, pl.n3, pl.dt, pl.dx);
+    k_kappa<float><<<nb, 256, 0, st>>>((const float*)c, (float*)pl.kap, pl.n3, q);
   count_launch();
   return check_launch(__func__);
 }
