@@ -410,20 +410,29 @@ static double dot(size_t len, const double *a, const double *b) {
   return acc;
 }
 
-/* grad = A^T Lambda (A h - g); r_out = A h - g; lr_out = Lambda r */
-static void data_gradient(const ffo_setup_t *s, const double *h, const double *g, double *r,
-                          double *lr, double *grad, double *work3) {
+/* grad = A^T chi Lambda chi (A h - g) with the data mask chi (Problem 1:
+ * chi_M, NULL = full data); r_out = chi (A h - g); lr_out = chi Lambda r */
+static void data_gradient_m(const ffo_setup_t *s, const double *h, const double *g,
+                            const double *mask, double *r, double *lr, double *grad,
+                            double *work3) {
   int n = s->n, nth = s->nth;
   size_t nd = (size_t)nth * n * n;
   ffo_wave(n, s->nt, s->kappa, h, work3);
   ffo_project(n, nth, work3, r);
-  for (size_t i = 0; i < nd; ++i) r[i] = r[i] - g[i];
+  for (size_t i = 0; i < nd; ++i) r[i] = (r[i] - g[i]) * (mask ? mask[i] : 1.0);
   if (s->precond)
     ffo_ramp(n, nth, r, lr);
   else
     memcpy(lr, r, nd * sizeof(double));
+  if (mask)
+    for (size_t i = 0; i < nd; ++i) lr[i] *= mask[i];
   ffo_backproject(n, nth, lr, work3);
   ffo_wave_adjoint(n, s->nt, s->kappa, work3, grad);
+}
+
+static void data_gradient(const ffo_setup_t *s, const double *h, const double *g, double *r,
+                          double *lr, double *grad, double *work3) {
+  data_gradient_m(s, h, g, NULL, r, lr, grad, work3);
 }
 
 /* Largest eigenvalue of A^T Lambda A by power iteration from v0 (the step
@@ -457,14 +466,19 @@ double ffo_power(int n, double T, double cfl, int nth, int precond, const double
 }
 
 /* Algorithm 8 (preconditioned proximal forward-backward, Sec. 3.2) with
- * R = ||h||_1 + indicator(h >= 0): r_k = A^T Lambda (A h_k - g) and
- * h_{k+1} = prox_{s lambda R}(h_k - s r_k) = max(h_k - s r_k - s lambda, 0).
+ * R = ||h||_1 + indicator(h >= 0), the data mask chi_M of Problem 1 (mask,
+ * NULL = full data) and the source support chi_V (support, NULL = the whole
+ * grid): r_k = A^T chi Lambda chi (A h_k - g) and
+ * h_{k+1} = chi_V max(h_k - s r_k - s lambda, 0) (the prox of
+ * s lambda (||.||_1 + i_{>=0}) + i_V).  With mask and support NULL this is
+ * the plain Algorithm 8.
  * stats[4 k + {0,1,2,3}] = objective 1/2 <Lambda r, r> + lambda ||h_k||_1,
- * ||A h_k - g||_2, ||h_{k+1} - h_k|| / max(||h_k||, 1e-300), ||h_{k+1}||_2.
+ * ||chi (A h_k - g)||_2, ||h_{k+1} - h_k|| / max(||h_k||, 1e-300), ||h_{k+1}||_2.
  * Returns the number of iterations run (stops early when tol > 0 and the
  * relative change drops below tol). */
-int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, const double *g,
-           double lambda, double step, int iters, double tol, double *h, double *stats) {
+int ffo_fb_ex(int n, double T, double cfl, int nth, int precond, const double *c, const double *g,
+              const double *mask, const double *support, double lambda, double step, int iters,
+              double tol, double *h, double *stats) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
   setup(&s, n, T, cfl, nth, precond, c);
@@ -472,11 +486,12 @@ int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, c
   double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
   int k;
   for (k = 0; k < iters; ++k) {
-    data_gradient(&s, h, g, r, lr, grad, work3);
+    data_gradient_m(&s, h, g, mask, r, lr, grad, work3);
     double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
     for (size_t i = 0; i < n3; ++i) {
       double f = h[i] - step * grad[i] - step * lambda;
       double hn = f > 0.0 ? f : 0.0;
+      if (support) hn *= support[i];
       l1 += fabs(h[i]);
       hh += h[i] * h[i];
       dd += (hn - h[i]) * (hn - h[i]);
@@ -501,6 +516,11 @@ int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, c
   free(lr);
   free(s.kappa);
   return k;
+}
+
+int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, const double *g,
+           double lambda, double step, int iters, double tol, double *h, double *stats) {
+  return ffo_fb_ex(n, T, cfl, nth, precond, c, g, NULL, NULL, lambda, step, iters, tol, h, stats);
 }
 
 /* ------------------------------------------- gradient with respect to c -- */

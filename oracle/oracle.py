@@ -84,6 +84,10 @@ def lib():
             L.ffo_fb_two_step.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_double, _D, _D]
+            L.ffo_fb_ex.restype = ctypes.c_int
+            L.ffo_fb_ex.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, _D, _D]
             L.ffo_num_threads.restype = ctypes.c_int
             L.ffo_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -255,4 +259,20 @@ def fb_two_step(c, G, T: float, lam: float, step: float, iters: int, h0=None, to
     stats = np.zeros((max(iters, 1), 4))
     k = lib().ffo_fb_two_step(n, T, cfl, G.shape[0], _p(c), _p(G), lam, step, iters, tol, _p(h),
                               _p(stats))
+    return h, stats[:k], k
+
+
+def fb_masked(c, g, T: float, lam: float, step: float, iters: int, mask=None, support=None,
+              h0=None, precond: int = 0, tol: float = 0.0, cfl: float = 0.3):
+    """Algorithm 8 with the data mask chi_M (Problem 1) and the source support
+    chi_V: r = A^T chi Lambda chi (A h - g), h+ = chi_V max(h - s r - s lambda, 0)."""
+    c, g = _f64(c), _f64(g)
+    n = c.shape[0]
+    h = np.zeros((n, n, n)) if h0 is None else _f64(h0).copy()
+    stats = np.zeros((max(iters, 1), 4))
+    m = _f64(mask) if mask is not None else None
+    sp = _f64(support) if support is not None else None
+    k = lib().ffo_fb_ex(n, T, cfl, g.shape[0], precond, _p(c), _p(g),
+                        _p(m) if m is not None else None, _p(sp) if sp is not None else None,
+                        lam, step, iters, tol, _p(h), _p(stats))
     return h, stats[:k], k

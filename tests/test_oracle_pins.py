@@ -466,3 +466,60 @@ def test_two_step_first_iterate_and_kkt():
     assert pos.any() and (~pos).any()
     assert np.max(np.abs(grad[pos] + lam)) < 1e-3 * lam
     assert np.min(grad[~pos] + lam) > -1e-3 * lam
+
+
+# ------------------------------------------ limited data chi_M, support chi_V --
+
+def _masks(n, nth, a=0.3, box=(2, -2)):
+    xi = axis(n)
+    mask = np.broadcast_to((np.abs(xi) > a).astype(float), (nth, n, n)).copy()
+    sup = np.zeros((n, n, n))
+    lo, hi = box
+    sup[lo:hi, lo:hi, lo:hi] = 1.0
+    return mask, sup
+
+
+def test_masked_fb_reduces_and_first_step():
+    """With all-ones masks the masked FB is Algorithm 8; from h_0 = 0 one masked
+    step is chi_V max(s A^T chi g - s lambda, 0) (Lambda = I)."""
+    n, nth, T = 10, 6, 0.5
+    c = random_speed(n, 95)
+    g = random_data(nth, n, 96)
+    h_a, st_a, _ = o.fb(c, g, T, 1e-3, 0.05, 3)
+    h_b, st_b, _ = o.fb_masked(c, g, T, 1e-3, 0.05, 3, mask=np.ones((nth, n, n)),
+                               support=np.ones((n, n, n)))
+    assert np.array_equal(h_a, h_b) and np.array_equal(st_a, st_b)
+    mask, sup = _masks(n, nth)
+    s, lam = 0.05, 0.2
+    h1, _, _ = o.fb_masked(c, g, T, lam, s, 1, mask=mask, support=sup)
+    want = sup * np.maximum(s * o.adjoint(c, mask * g, T) - s * lam, 0.0)
+    assert np.max(np.abs(h1 - want)) < 1e-13 * max(1.0, np.abs(want).max())
+
+
+def test_masked_fb_kkt():
+    """KKT of 1/2 <chi Lambda chi (Ah - g), Ah - g> + lambda (||h||_1 + i_{>=0} + i_V)
+    at the fixed point (dense A at 6^3, ramp preconditioner, |xi| > a data)."""
+    n, nth, T = 6, 8, 0.5
+    c = random_speed(n, 97)
+    rng = np.random.default_rng(98)
+    h_true = np.maximum(rng.standard_normal((n, n, n)), 0)
+    g = o.forward(c, h_true, T, nth)
+    mask, sup = _masks(n, nth, a=0.2, box=(1, -1))
+    A = dense_A(n, nth, c, T)
+    M = mask.ravel()
+    LA = dense(lambda h: mask * o.ramp(mask * o.forward(c, h, T, nth)), n**3, (n, n, n))
+    H = A.T @ LA
+    inside = sup.ravel() > 0
+    Hs = H[np.ix_(inside, inside)]
+    Lmax = np.linalg.eigvalsh(0.5 * (Hs + Hs.T)).max()
+    b = A.T @ (M * o.ramp(mask * g).ravel())
+    lam = 0.02 * float(np.abs(b[inside]).max())
+    h, st, k = o.fb_masked(c, g, T, lam, 1.0 / Lmax, 6000, mask=mask, support=sup, precond=1)
+    hr = h.ravel()
+    assert np.all(hr[~inside] == 0)
+    grad = H @ hr - b
+    pos = (hr > 1e-9) & inside
+    zero = (hr <= 1e-9) & inside
+    assert pos.any() and zero.any()
+    assert np.max(np.abs(grad[pos] + lam)) < 1e-3 * lam
+    assert np.min(grad[zero] + lam) > -1e-3 * lam
