@@ -182,6 +182,20 @@ int ffpat_fb_two_step(const ffpat_problem *problem, const void *c, const void *G
                       ffpat_fb_stats *stats, double *history, void *ws, size_t ws_bytes,
                       void *stream);
 
+/* Algorithm 8 for limited data and a bounded source (Problem 1 with
+ * M_theta != R^2; the source support V of the wave model, Sec. 2.1):
+ *   r_k = A^T chi_M Lambda chi_M (A h_k - g),
+ *   h_{k+1} = chi_V max(h_k - s r_k - s lambda, 0),
+ * i.e. FB on 1/2 <Lambda chi_M (A h - g), chi_M (A h - g)> + lambda (||h||_1
+ * + indicator(h >= 0) + indicator(supp h in V)).  mask (n_angles N^2) and
+ * support (N^3) are device arrays of 0/1 values of the problem's element
+ * type, or NULL for full data / the whole grid (then this is
+ * ffpat_fb_solve).  The power-iteration step uses the masked operator. */
+int ffpat_fb_solve_ex(const ffpat_problem *problem, const void *c, const void *g,
+                      const void *mask, const void *support, double lambda, double step,
+                      int32_t max_iters, double tol, void *h_inout, ffpat_fb_stats *stats,
+                      double *history, void *ws, size_t ws_bytes, void *stream);
+
 /* Instrumentation.  While enabled, every wave time loop records CUDA events on
  * its stream around its leapfrog launches; ffpat_profile_read synchronises
  * those events and returns the leapfrog launches and steps timed, their total

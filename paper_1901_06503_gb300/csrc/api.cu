@@ -424,16 +424,17 @@ static int apply_adjoint(const Plan& pl, const void* g, void* h, cudaStream_t st
   return FFPAT_OK;
 }
 
-// x-domain result of A^T Lambda (A v - g) without the final 1/kap: returns the
-// state buffer holding W K P^T Lambda r.  dots[0] = <Lambda r, r>, dots[1] = <r, r>.
+// x-domain result of A^T chi Lambda chi (A v - g) without the final 1/kap:
+// returns the state buffer holding W K P^T chi Lambda r, r = chi (A v - g)
+// (chi = the data mask, nullable).  dots[0] = <Lambda r, r>, dots[1] = <r, r>.
 static int data_gradient(const Plan& pl, const void* v, const void* g, const void** w,
-                         double* dots, cudaStream_t st) {
+                         double* dots, cudaStream_t st, const void* mask = nullptr) {
   const void* pN = nullptr;
   TRY(run_wave(pl, v, nullptr, &pN, st));
-  TRY(launch_project(pl, pN, pl.r, g, st));
+  TRY(launch_project(pl, pN, pl.r, g, st, mask));
   const void* lr = pl.r;
   if (pl.precond == FFPAT_PRECOND_RAMP) {
-    TRY(launch_ramp(pl, pl.r, pl.r2, st));
+    TRY(launch_ramp(pl, pl.r, pl.r2, st, mask));
     lr = pl.r2;
   }
   if (dots) TRY(launch_dot(pl, pl.nd, lr, pl.r, dots, st));
@@ -442,14 +443,15 @@ static int data_gradient(const Plan& pl, const void* v, const void* g, const voi
   return FFPAT_OK;
 }
 
-// power iteration on A^T Lambda A, vector in pl.v; returns the estimate
-static int power_iteration(const Plan& pl, int iters, double* est, cudaStream_t st) {
+// power iteration on A^T chi Lambda chi A, vector in pl.v; returns the estimate
+static int power_iteration(const Plan& pl, int iters, double* est, cudaStream_t st,
+                           const void* mask = nullptr) {
   double* sq = pl.scal + 8;
   TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
   TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
   for (int it = 0; it < iters; ++it) {
     const void* w = nullptr;
-    TRY(data_gradient(pl, pl.v, nullptr, &w, nullptr, st));
+    TRY(data_gradient(pl, pl.v, nullptr, &w, nullptr, st, mask));
     TRY(launch_kscale(pl, w, pl.v, false, st));
     TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
     TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
@@ -621,6 +623,14 @@ int ffpat_fb_solve(const ffpat_problem* problem, const void* c, const void* g, d
                    double step, int32_t max_iters, double tol, void* h_inout,
                    ffpat_fb_stats* stats, double* history, void* ws, size_t ws_bytes,
                    void* stream) {
+  return ffpat_fb_solve_ex(problem, c, g, nullptr, nullptr, lambda, step, max_iters, tol, h_inout,
+                           stats, history, ws, ws_bytes, stream);
+}
+
+int ffpat_fb_solve_ex(const ffpat_problem* problem, const void* c, const void* g,
+                      const void* mask, const void* support, double lambda, double step,
+                      int32_t max_iters, double tol, void* h_inout, ffpat_fb_stats* stats,
+                      double* history, void* ws, size_t ws_bytes, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
@@ -632,7 +642,7 @@ int ffpat_fb_solve(const ffpat_problem* problem, const void* c, const void* g, d
   double opn = 0.0;
   if (!(step > 0.0)) {
     TRY(launch_hash_fill(pl, pl.v, 0x5eed1901ull, st));
-    TRY(power_iteration(pl, 20, &opn, st));
+    TRY(power_iteration(pl, 20, &opn, st, mask));
     if (!(opn > 0.0) || !isfinite(opn)) return fail(FFPAT_EINVAL, "operator norm estimate %g", opn);
     step = 1.0 / opn;
   }
@@ -641,8 +651,8 @@ int ffpat_fb_solve(const ffpat_problem* problem, const void* c, const void* g, d
   for (; k < max_iters; ++k) {
     double* hk = pl.hist + 8 * (size_t)k;
     const void* w = nullptr;
-    TRY(data_gradient(pl, h_inout, g, &w, hk, st));
-    TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st));
+    TRY(data_gradient(pl, h_inout, g, &w, hk, st, mask));
+    TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st, nullptr, support));
     if (tol > 0.0) {
       double q[4];
       CK(cudaMemcpyAsync(q, hk + 2, sizeof q, cudaMemcpyDeviceToHost, st));

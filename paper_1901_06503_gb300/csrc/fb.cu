@@ -149,7 +149,7 @@ template <typename T>
 __global__ void __launch_bounds__(kReduceThreads)
     k_fb_update(T* __restrict__ h, const T* __restrict__ w, const T* __restrict__ kap, size_t len,
                 double step, const double* __restrict__ step_dev, double lambda,
-                double* __restrict__ partials) {
+                const T* __restrict__ support, double* __restrict__ partials) {
   double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
   if (step_dev) step = *step_dev;
   const T s = (T)step, sl = (T)(step * lambda);
@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(kReduceThreads)
     const T hv = h[i];
     const T grad = w[i] / kap[i];
     const T f = (hv - s * grad) - sl;
-    const T hn = f > T(0) ? f : T(0);
+    T hn = f > T(0) ? f : T(0);
+    if (support) hn = hn * support[i];
     h[i] = hn;
     const double hd = (double)hv, nd = (double)hn, df = nd - hd;
     l1 += fabs(hd);
@@ -305,15 +306,15 @@ int launch_dot(const Plan& pl, size_t len, const void* a, const void* b, double*
 }
 
 int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double lambda,
-                     double* dst, cudaStream_t st, const double* step_dev) {
+                     double* dst, cudaStream_t st, const double* step_dev, const void* support) {
   if (pl.prec == FFPAT_FP64)
     k_fb_update<double><<<kReduceBlocks, kReduceThreads, 0, st>>>(
         (double*)h, (const double*)w, (const double*)pl.kap, pl.n3, step, step_dev, lambda,
-        pl.partials);
+        (const double*)support, pl.partials);
   else
     k_fb_update<float><<<kReduceBlocks, kReduceThreads, 0, st>>>(
         (float*)h, (const float*)w, (const float*)pl.kap, pl.n3, step, step_dev, lambda,
-        pl.partials);
+        (const float*)support, pl.partials);
   k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 4, dst);
   count_launch(2);
   return check_launch(__func__);

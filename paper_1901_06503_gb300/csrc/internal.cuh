@@ -96,11 +96,15 @@ int read_device_status(unsigned* out, bool clear);
 int launch_wait_timeout(long long cycles, cudaStream_t st);
 
 // xray.cu
-int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st);
+// g = mask .* (P p - sub)  (sub, mask nullable)
+int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st,
+                   const void* mask = nullptr);
 // h = mult * scale .* P^T g  (scale nullable)
 int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st,
                        double mult = 1.0);
-int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st);
+// out = mask .* (Lambda r)  (mask nullable)
+int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st,
+                const void* mask = nullptr);
 int launch_debug_samples(const Plan& pl, int count, const int32_t* jkm, int32_t* ij, double* f,
                          cudaStream_t st);
 
@@ -117,8 +121,10 @@ int launch_dot(const Plan& pl, size_t len, const void* a, const void* b, double*
                cudaStream_t st);
 // FB update + partial norms; results land in dst[0..3]
 // step_dev (optional): read the step from device memory instead of `step`
+// support (nullable): the iterate is multiplied by it (projection onto the source support)
 int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double lambda,
-                     double* dst, cudaStream_t st, const double* step_dev = nullptr);
+                     double* dst, cudaStream_t st, const double* step_dev = nullptr,
+                     const void* support = nullptr);
 int launch_inv_sqrt(const double* src, double* dst, cudaStream_t st);
 int launch_sub_div(const Plan& pl, const void* a, const void* b, void* out, cudaStream_t st);
 // x = kap (w - g), dst[0] = dst[1] = sum (w - g)^2

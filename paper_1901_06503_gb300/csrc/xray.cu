@@ -97,8 +97,9 @@ __device__ __forceinline__ void ray_range(float cs, float sn, int k, int n, int 
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_project(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
-              const double* __restrict__ tab, const float* __restrict__ tabf,
-              const int32_t* __restrict__ tabi, int n, int nth, int ns) {
+              const T* __restrict__ mask, const double* __restrict__ tab,
+              const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n, int nth,
+              int ns) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int l = blockIdx.y;
   const int j = blockIdx.z;
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(128)
       double out = __dmul_rn(dx, acc);
       const size_t o = ((size_t)j * n + l) * n + k;
       if (sub) out = out - sub[o];
+      if (mask) out = out * mask[o];
       g[o] = out;
     }
   } else {
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(128)
       float out = (2.0f / (float)n) * acc;
       const size_t o = ((size_t)j * n + l) * n + k;
       if (sub) out = out - sub[o];
+      if (mask) out = out * mask[o];
       g[o] = out;
     }
   }
@@ -174,8 +177,9 @@ __host__ __device__ inline int plane_pitch(int n) {
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_project_smem(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
-                   const double* __restrict__ tab, const float* __restrict__ tabf,
-                   const int32_t* __restrict__ tabi, int n, int nth, int ns, int group) {
+                   const T* __restrict__ mask, const double* __restrict__ tab,
+                   const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n,
+                   int nth, int ns, int group) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   const int W = plane_pitch(n);  // row pitch; rows = n + 2 kPad
@@ -220,6 +224,7 @@ __global__ void __launch_bounds__(256)
       double out = __dmul_rn(dx, acc);
       const size_t oo = ((size_t)j * n + l) * n + k;
       if (sub) out = out - sub[oo];
+      if (mask) out = out * mask[oo];
       g[oo] = out;
     } else {
       const long long CS = tabi[j], SN = tabi[nth + j];
@@ -242,6 +247,7 @@ __global__ void __launch_bounds__(256)
       float out = (2.0f / (float)n) * acc;
       const size_t oo = ((size_t)j * n + l) * n + k;
       if (sub) out = out - sub[oo];
+      if (mask) out = out * mask[oo];
       g[oo] = out;
     }
   }
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(256)
 
 template <typename T>
 __global__ void __launch_bounds__(128)
-    k_ramp(const T* __restrict__ r, T* __restrict__ out, int n) {
+    k_ramp(const T* __restrict__ r, T* __restrict__ out, const T* __restrict__ mask, int n) {
   extern __shared__ unsigned char smem_raw[];
   T* row = reinterpret_cast<T*>(smem_raw);
   T* tap = row + n;  // tap[d] for d < n (odd d nonzero)
@@ -371,6 +377,7 @@ __global__ void __launch_bounds__(128)
       if (k + d < n) a += row[k + d];
       acc += tap[d] * a;
     }
+    if (mask) acc = acc * mask[base + k];
     out[base + k] = acc;
   }
 }
@@ -393,7 +400,8 @@ __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int3
 
 }  // namespace
 
-int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st) {
+int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st,
+                   const void* mask) {
   const size_t smem = (size_t)plane_pitch(pl.n) * (pl.n + 2 * kPad) * pl.esize;
   if (smem <= 200 * 1024) {
     // one CTA per (plane, group of 8 angles); the padded plane is read once per CTA
@@ -407,8 +415,9 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
         attr = true;
       }
       k_project_smem<double><<<grid, 256, smem, st>>>((const double*)p, (double*)g,
-                                                      (const double*)sub, pl.tab, pl.tabf, pl.tabi,
-                                                      pl.n, pl.nth, pl.ns, group);
+                                                      (const double*)sub, (const double*)mask,
+                                                      pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth,
+                                                      pl.ns, group);
     } else {
       static bool attr = false;
       if (!attr) {
@@ -417,8 +426,8 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
         attr = true;
       }
       k_project_smem<float><<<grid, 256, smem, st>>>((const float*)p, (float*)g, (const float*)sub,
-                                                     pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns,
-                                                     group);
+                                                     (const float*)mask, pl.tab, pl.tabf, pl.tabi,
+                                                     pl.n, pl.nth, pl.ns, group);
     }
     count_launch();
     return check_launch(__func__);
@@ -427,10 +436,12 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
   const dim3 grid((pl.n + 127) / 128, pl.n, pl.nth);
   if (pl.prec == FFPAT_FP64)
     k_project<double><<<grid, block, 0, st>>>((const double*)p, (double*)g, (const double*)sub,
-                                              pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns);
+                                              (const double*)mask, pl.tab, pl.tabf, pl.tabi, pl.n,
+                                              pl.nth, pl.ns);
   else
-    k_project<float><<<grid, block, 0, st>>>((const float*)p, (float*)g, (const float*)sub, pl.tab,
-                                             pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns);
+    k_project<float><<<grid, block, 0, st>>>((const float*)p, (float*)g, (const float*)sub,
+                                             (const float*)mask, pl.tab, pl.tabf, pl.tabi, pl.n,
+                                             pl.nth, pl.ns);
   count_launch();
   return check_launch(__func__);
 }
@@ -451,13 +462,14 @@ int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale
   return check_launch(__func__);
 }
 
-int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st) {
+int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st, const void* mask) {
   const unsigned rows = (unsigned)(pl.nth * pl.n);
   const size_t smem = 2 * (size_t)pl.n * pl.esize;
   if (pl.prec == FFPAT_FP64)
-    k_ramp<double><<<rows, 128, smem, st>>>((const double*)r, (double*)out, pl.n);
+    k_ramp<double><<<rows, 128, smem, st>>>((const double*)r, (double*)out, (const double*)mask,
+                                            pl.n);
   else
-    k_ramp<float><<<rows, 128, smem, st>>>((const float*)r, (float*)out, pl.n);
+    k_ramp<float><<<rows, 128, smem, st>>>((const float*)r, (float*)out, (const float*)mask, pl.n);
   count_launch();
   return check_launch(__func__);
 }

@@ -96,6 +96,8 @@ def _declare(L):
         "ffpat_fb_solve": (ctypes.c_int, [_PR, _P, _P, f64, f64, i32, f64, _P,
                                           ctypes.POINTER(FBStats), _P, _P, sz, _P]),
         "ffpat_fbp": (ctypes.c_int, [_PR, _P, _P, _P, sz, _P]),
+        "ffpat_fb_solve_ex": (ctypes.c_int, [_PR, _P, _P, _P, _P, f64, f64, i32, f64, _P,
+                                             ctypes.POINTER(FBStats), _P, _P, sz, _P]),
         "ffpat_fb_two_step": (ctypes.c_int, [_PR, _P, _P, f64, f64, i32, f64, _P,
                                              ctypes.POINTER(FBStats), _P, _P, sz, _P]),
         "ffpat_profile_enable": (ctypes.c_int, [i32]),
@@ -351,6 +353,27 @@ def fb_solve(prob, c, g, lam, step, max_iters, h=None, tol=0.0, ws=None, stream=
                                 _dev(g, prob, data_shape(prob), "g"), float(lam), float(step),
                                 int(max_iters), float(tol), _dev(h, prob, vol_shape(prob), "h"),
                                 ctypes.byref(st), hp, wp, wn, _stream(stream)))
+    d = st.as_dict()
+    return h, d, (hist[: d["iters_done"]] if history else None)
+
+
+def fb_solve_masked(prob, c, g, lam, step, max_iters, mask=None, support=None, h=None, tol=0.0,
+                    ws=None, stream=None, history=True):
+    """Algorithm 8 with the data mask chi_M (data-shaped 0/1) and the source
+    support chi_V (volume 0/1); None = full data / whole grid."""
+    import torch
+    h = torch.zeros(vol_shape(prob), dtype=torch_dtype(prob), device=g.device) if h is None else h
+    ws, wp, wn = _ws(prob, ws, g.device)
+    st = FBStats()
+    hist = np.zeros((max(int(max_iters), 1), 4)) if history else None
+    hp = hist.ctypes.data_as(ctypes.c_void_p) if history else None
+    mp = _dev(mask, prob, data_shape(prob), "mask") if mask is not None else None
+    sp = _dev(support, prob, vol_shape(prob), "support") if support is not None else None
+    _check(lib().ffpat_fb_solve_ex(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+                                   _dev(g, prob, data_shape(prob), "g"), mp, sp, float(lam),
+                                   float(step), int(max_iters), float(tol),
+                                   _dev(h, prob, vol_shape(prob), "h"), ctypes.byref(st), hp, wp,
+                                   wn, _stream(stream)))
     d = st.as_dict()
     return h, d, (hist[: d["iters_done"]] if history else None)
 

@@ -369,3 +369,28 @@ def test_two_step_automatic_step():
     _, st, _ = F.fb_two_step(prob, dev(w.c, prob), dev(G, prob), w.lam, 0.0, 1)
     # W is a polynomial in K L4 bounded by one in the kappa^-1-weighted norm
     assert 0.2 < st["opnorm_sq"] < 50 and abs(st["step"] * st["opnorm_sq"] - 1) < 1e-12
+
+
+# ------------------------------------------ limited data chi_M, support chi_V --
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("precond", [0, 1])
+def test_masked_fb(prec, precond):
+    from paper_1901_06503_gb300.inputs import axis
+    w, c, g, s = fb_case(prec, precond, n=20 if precond else None)
+    xi = axis(w.n)
+    mask = np.broadcast_to((np.abs(xi) > 0.25).astype(float), g.shape).copy()
+    sup = np.zeros(c.shape)
+    sup[3:-3, 3:-3, 3:-3] = 1.0
+    prob = F.problem(w.n, w.T, w.n_angles, prec, precond)
+    h_gpu, st, hist = F.fb_solve_masked(prob, dev(c, prob), dev(g, prob), w.lam, s, 6,
+                                        mask=dev(mask, prob), support=dev(sup, prob))
+    h_or, hist_or, k = o.fb_masked(c, g, w.T, w.lam, s, 6, mask=mask, support=sup,
+                                   precond=precond)
+    hg = host(h_gpu)
+    assert st["iters_done"] == k == 6
+    assert np.all(hg[sup == 0] == 0)
+    assert rel(hg, h_or) < (1e-10 if prec == F.FP64 else 5e-5)
+    tol = 1e-9 if prec == F.FP64 else 1e-4
+    for col in (0, 1, 3):
+        assert np.max(np.abs(hist[:, col] - hist_or[:, col]) / np.abs(hist_or[:, col])) < tol
