@@ -360,48 +360,133 @@ void ffo_ramp(int n, int nth, const double *r, double *out) {
 /* --------------------------------------------- forward operator A = P W -- */
 
 typedef struct {
-  int n, nth, nt, precond;
+  int n, pad, nw, nth, nt, precond;
   double dt, T, cfl;
-  double *kappa;
+  double *kappa; /* on the wave grid, nw^3 */
 } ffo_setup_t;
 
-static int setup(ffo_setup_t *s, int n, double T, double cfl, int nth, int precond, const double *c) {
-  size_t n3 = (size_t)n * n * n;
+/* The wave grid: the image box [-1,1]^3 (n cells per axis, dx = 2/n) enlarged
+ * by pad cells of the same size on every side, nw = n + 2 pad (the paper
+ * computes on a domain larger than the source region so that the waves leave
+ * it instead of reflecting, Sec. 5).  c is given on the wave grid; Nt follows
+ * from its maximum and dx.  pad = 0 is the image box itself. */
+static int setup(ffo_setup_t *s, int n, int pad, double T, double cfl, int nth, int precond,
+                 const double *c) {
   s->n = n;
+  s->pad = pad;
+  s->nw = n + 2 * pad;
+  size_t nw3 = (size_t)s->nw * s->nw * s->nw;
   s->nth = nth;
   s->T = T;
   s->cfl = cfl;
   s->precond = precond;
-  s->nt = ffo_time_steps(n, T, cfl, ffo_max(n3, c), &s->dt);
-  s->kappa = malloc(n3 * sizeof(double));
-  ffo_kappa(n, s->dt, c, s->kappa);
+  s->nt = ffo_time_steps(n, T, cfl, ffo_max(nw3, c), &s->dt);
+  s->kappa = malloc(nw3 * sizeof(double));
+  double dx = 2.0 / n;
+  for (size_t i = 0; i < nw3; ++i) {
+    double r = c[i] * s->dt / dx;
+    s->kappa[i] = r * r;
+  }
   return s->nt;
 }
 
-/* g = P W_T h (Problem 1 with full data, M = R^2) */
-int ffo_forward(int n, double T, double cfl, int nth, const double *c, const double *h, double *g) {
+/* zero-extension of an image-grid volume (n^3) to the wave grid (nw^3) */
+static void embed(int n, int pad, const double *in, double *out) {
+  int nw = n + 2 * pad;
+  memset(out, 0, (size_t)nw * nw * nw * sizeof(double));
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) out[at3(nw, z + pad, y + pad, x + pad)] = in[at3(n, z, y, x)];
+}
+
+/* restriction of a wave-grid volume to the image box (the transpose of embed) */
+static void restrict_box(int n, int pad, const double *in, double *out) {
+  int nw = n + 2 * pad;
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) out[at3(n, z, y, x)] = in[at3(nw, z + pad, y + pad, x + pad)];
+}
+
+/* R W_T E h on the image box: the source is zero outside the box, the wave
+ * runs on the wave grid and the result is read inside the box. */
+static void wave_img(const ffo_setup_t *s, const double *h, double *out) {
+  if (s->pad == 0) {
+    ffo_wave(s->n, s->nt, s->kappa, h, out);
+    return;
+  }
+  size_t nw3 = (size_t)s->nw * s->nw * s->nw;
+  double *a = malloc(nw3 * sizeof(double)), *b = malloc(nw3 * sizeof(double));
+  embed(s->n, s->pad, h, a);
+  ffo_wave(s->nw, s->nt, s->kappa, a, b);
+  restrict_box(s->n, s->pad, b, out);
+  free(a);
+  free(b);
+}
+
+/* its transpose E^T W_T^T R^T */
+static void wave_img_adjoint(const ffo_setup_t *s, const double *g, double *out) {
+  if (s->pad == 0) {
+    ffo_wave_adjoint(s->n, s->nt, s->kappa, g, out);
+    return;
+  }
+  size_t nw3 = (size_t)s->nw * s->nw * s->nw;
+  double *a = malloc(nw3 * sizeof(double)), *b = malloc(nw3 * sizeof(double));
+  embed(s->n, s->pad, g, a);
+  ffo_wave_adjoint(s->nw, s->nt, s->kappa, a, b);
+  restrict_box(s->n, s->pad, b, out);
+  free(a);
+  free(b);
+}
+
+/* W_T (transpose = 0) or W_T^T on the image box with pad cells of padding;
+ * returns Nt */
+int ffo_wave_img(int n, int pad, double T, double cfl, const double *c, const double *in,
+                 double *out, int transpose) {
+  ffo_setup_t s;
+  setup(&s, n, pad, T, cfl, 0, 0, c);
+  if (transpose)
+    wave_img_adjoint(&s, in, out);
+  else
+    wave_img(&s, in, out);
+  free(s.kappa);
+  return s.nt;
+}
+
+/* g = P W_T h (Problem 1 with full data, M = R^2), the wave on the grid
+ * padded by pad cells (c on that grid) */
+int ffo_forward_pad(int n, int pad, double T, double cfl, int nth, const double *c,
+                    const double *h, double *g) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n;
-  setup(&s, n, T, cfl, nth, 0, c);
+  setup(&s, n, pad, T, cfl, nth, 0, c);
   double *p = malloc(n3 * sizeof(double));
-  ffo_wave(n, s.nt, s.kappa, h, p);
+  wave_img(&s, h, p);
   ffo_project(n, nth, p, g);
   free(p);
   free(s.kappa);
   return s.nt;
 }
 
+int ffo_forward(int n, double T, double cfl, int nth, const double *c, const double *h, double *g) {
+  return ffo_forward_pad(n, 0, T, cfl, nth, c, h, g);
+}
+
 /* h = W_T^T P^T g */
-int ffo_adjoint(int n, double T, double cfl, int nth, const double *c, const double *g, double *h) {
+int ffo_adjoint_pad(int n, int pad, double T, double cfl, int nth, const double *c,
+                    const double *g, double *h) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n;
-  setup(&s, n, T, cfl, nth, 0, c);
+  setup(&s, n, pad, T, cfl, nth, 0, c);
   double *a = malloc(n3 * sizeof(double));
   ffo_backproject(n, nth, g, a);
-  ffo_wave_adjoint(n, s.nt, s.kappa, a, h);
+  wave_img_adjoint(&s, a, h);
   free(a);
   free(s.kappa);
   return s.nt;
+}
+
+int ffo_adjoint(int n, double T, double cfl, int nth, const double *c, const double *g, double *h) {
+  return ffo_adjoint_pad(n, 0, T, cfl, nth, c, g, h);
 }
 
 static double dot(size_t len, const double *a, const double *b) {
@@ -417,7 +502,7 @@ static void data_gradient_m(const ffo_setup_t *s, const double *h, const double 
                             double *work3) {
   int n = s->n, nth = s->nth;
   size_t nd = (size_t)nth * n * n;
-  ffo_wave(n, s->nt, s->kappa, h, work3);
+  wave_img(s, h, work3);
   ffo_project(n, nth, work3, r);
   for (size_t i = 0; i < nd; ++i) r[i] = (r[i] - g[i]) * (mask ? mask[i] : 1.0);
   if (s->precond)
@@ -427,21 +512,17 @@ static void data_gradient_m(const ffo_setup_t *s, const double *h, const double 
   if (mask)
     for (size_t i = 0; i < nd; ++i) lr[i] *= mask[i];
   ffo_backproject(n, nth, lr, work3);
-  ffo_wave_adjoint(n, s->nt, s->kappa, work3, grad);
+  wave_img_adjoint(s, work3, grad);
 }
 
-static void data_gradient(const ffo_setup_t *s, const double *h, const double *g, double *r,
-                          double *lr, double *grad, double *work3) {
-  data_gradient_m(s, h, g, NULL, r, lr, grad, work3);
-}
-
-/* Largest eigenvalue of A^T Lambda A by power iteration from v0 (the step
- * size bound 1/L; not in the paper, which fixes s = 0.2 for its own scaling). */
-double ffo_power(int n, double T, double cfl, int nth, int precond, const double *c,
-                 const double *v0, int iters) {
+/* Largest eigenvalue of A^T chi Lambda chi A (mask = chi_M, NULL = full data)
+ * by power iteration from v0 (the step size bound 1/L; not in the paper,
+ * which fixes s = 0.2 for its own scaling). */
+double ffo_power_ex(int n, int pad, double T, double cfl, int nth, int precond, const double *c,
+                    const double *mask, const double *v0, int iters) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
-  setup(&s, n, T, cfl, nth, precond, c);
+  setup(&s, n, pad, T, cfl, nth, precond, c);
   double *v = malloc(n3 * sizeof(double)), *w = malloc(n3 * sizeof(double));
   double *work3 = malloc(n3 * sizeof(double));
   double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
@@ -450,7 +531,7 @@ double ffo_power(int n, double T, double cfl, int nth, int precond, const double
   for (size_t i = 0; i < n3; ++i) v[i] = v0[i] / nv;
   double lam = 0.0;
   for (int it = 0; it < iters; ++it) {
-    data_gradient(&s, v, zero, r, lr, w, work3); /* w = A^T Lambda A v */
+    data_gradient_m(&s, v, zero, mask, r, lr, w, work3); /* w = A^T chi Lambda chi A v */
     double nw = sqrt(dot(n3, w, w));
     lam = nw;
     for (size_t i = 0; i < n3; ++i) v[i] = w[i] / nw;
@@ -465,6 +546,11 @@ double ffo_power(int n, double T, double cfl, int nth, int precond, const double
   return lam;
 }
 
+double ffo_power(int n, double T, double cfl, int nth, int precond, const double *c,
+                 const double *v0, int iters) {
+  return ffo_power_ex(n, 0, T, cfl, nth, precond, c, NULL, v0, iters);
+}
+
 /* Algorithm 8 (preconditioned proximal forward-backward, Sec. 3.2) with
  * R = ||h||_1 + indicator(h >= 0), the data mask chi_M of Problem 1 (mask,
  * NULL = full data) and the source support chi_V (support, NULL = the whole
@@ -476,12 +562,12 @@ double ffo_power(int n, double T, double cfl, int nth, int precond, const double
  * ||chi (A h_k - g)||_2, ||h_{k+1} - h_k|| / max(||h_k||, 1e-300), ||h_{k+1}||_2.
  * Returns the number of iterations run (stops early when tol > 0 and the
  * relative change drops below tol). */
-int ffo_fb_ex(int n, double T, double cfl, int nth, int precond, const double *c, const double *g,
-              const double *mask, const double *support, double lambda, double step, int iters,
-              double tol, double *h, double *stats) {
+int ffo_fb_ex(int n, int pad, double T, double cfl, int nth, int precond, const double *c,
+              const double *g, const double *mask, const double *support, double lambda,
+              double step, int iters, double tol, double *h, double *stats) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
-  setup(&s, n, T, cfl, nth, precond, c);
+  setup(&s, n, pad, T, cfl, nth, precond, c);
   double *grad = malloc(n3 * sizeof(double)), *work3 = malloc(n3 * sizeof(double));
   double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
   int k;
@@ -520,7 +606,8 @@ int ffo_fb_ex(int n, double T, double cfl, int nth, int precond, const double *c
 
 int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, const double *g,
            double lambda, double step, int iters, double tol, double *h, double *stats) {
-  return ffo_fb_ex(n, T, cfl, nth, precond, c, g, NULL, NULL, lambda, step, iters, tol, h, stats);
+  return ffo_fb_ex(n, 0, T, cfl, nth, precond, c, g, NULL, NULL, lambda, step, iters, tol, h,
+                   stats);
 }
 
 /* ------------------------------------------- gradient with respect to c -- */
@@ -537,7 +624,7 @@ int ffo_grad(int n, double T, double cfl, int nth, const double *c, const double
              const double *grad_g, double *grad_h, double *grad_c) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n;
-  setup(&s, n, T, cfl, nth, 0, c);
+  setup(&s, n, 0, T, cfl, nth, 0, c);
   int nt = s.nt;
   double *ps = malloc((size_t)(nt + 1) * n3 * sizeof(double)); /* p^0 .. p^nt */
   double *lap = malloc(n3 * sizeof(double));
@@ -600,19 +687,20 @@ void ffo_fbp(int n, int nth, const double *G, double *out) {
  * with R = ||h||_1 + indicator(h >= 0).  stats[4 k + 0..3]: objective
  * 1/2 ||W h_k - g||^2 + lambda ||h_k||_1, ||W h_k - g||, relative change,
  * ||h_{k+1}||. */
-int ffo_fb_two_step(int n, double T, double cfl, int nth, const double *c, const double *G,
-                    double lambda, double step, int iters, double tol, double *h, double *stats) {
+int ffo_fb_two_step(int n, int pad, double T, double cfl, int nth, const double *c,
+                    const double *G, double lambda, double step, int iters, double tol, double *h,
+                    double *stats) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n;
-  setup(&s, n, T, cfl, nth, 0, c);
+  setup(&s, n, pad, T, cfl, nth, 0, c);
   double *g = malloc(n3 * sizeof(double)), *r = malloc(n3 * sizeof(double));
   double *grad = malloc(n3 * sizeof(double));
   ffo_fbp(n, nth, G, g);
   int k;
   for (k = 0; k < iters; ++k) {
-    ffo_wave(n, s.nt, s.kappa, h, r);
+    wave_img(&s, h, r);
     for (size_t i = 0; i < n3; ++i) r[i] -= g[i];
-    ffo_wave_adjoint(n, s.nt, s.kappa, r, grad);
+    wave_img_adjoint(&s, r, grad);
     double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
     for (size_t i = 0; i < n3; ++i) {
       double f = h[i] - step * grad[i] - step * lambda;

@@ -69,6 +69,18 @@ def lib():
                                       _D, _D, _D]
             L.ffo_adjoint.restype = ctypes.c_int
             L.ffo_adjoint.argtypes = L.ffo_forward.argtypes
+            L.ffo_forward_pad.restype = ctypes.c_int
+            L.ffo_forward_pad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, _D, _D, _D]
+            L.ffo_adjoint_pad.restype = ctypes.c_int
+            L.ffo_adjoint_pad.argtypes = L.ffo_forward_pad.argtypes
+            L.ffo_wave_img.restype = ctypes.c_int
+            L.ffo_wave_img.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, _D, _D, _D, ctypes.c_int]
+            L.ffo_power_ex.restype = ctypes.c_double
+            L.ffo_power_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _D,
+                                       ctypes.c_int]
             L.ffo_power.restype = ctypes.c_double
             L.ffo_power.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, _D, _D, ctypes.c_int]
@@ -81,12 +93,12 @@ def lib():
                                    _D, _D, _D, _D, _D]
             L.ffo_fbp.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
             L.ffo_fb_two_step.restype = ctypes.c_int
-            L.ffo_fb_two_step.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                          ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double,
-                                          ctypes.c_int, ctypes.c_double, _D, _D]
+            L.ffo_fb_two_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, _D, _D, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_double, _D, _D]
             L.ffo_fb_ex.restype = ctypes.c_int
-            L.ffo_fb_ex.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                    ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
+            L.ffo_fb_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, _D, _D]
             L.ffo_num_threads.restype = ctypes.c_int
             L.ffo_set_num_threads.argtypes = [ctypes.c_int]
@@ -195,28 +207,49 @@ def ramp(r) -> np.ndarray:
     return out
 
 
-def forward(c, h, T: float, nth: int, cfl: float = 0.3) -> np.ndarray:
-    """g = P W_T h (Problem 1, full data)."""
+def _image_n(c, pad: int) -> int:
+    n = c.shape[0] - 2 * int(pad)
+    if n < 1 or pad < 0:
+        raise ValueError(f"c of side {c.shape[0]} cannot hold an image box padded by {pad}")
+    return n
+
+
+def forward(c, h, T: float, nth: int, cfl: float = 0.3, pad: int = 0) -> np.ndarray:
+    """g = P W_T h (Problem 1, full data).  pad > 0: the wave runs on the grid
+    enlarged by pad cells per side (c given on that grid, h on the image box)."""
     c, h = _f64(c), _f64(h)
     n = h.shape[0]
+    assert _image_n(c, pad) == n
     g = np.empty((nth, n, n))
-    lib().ffo_forward(n, T, cfl, nth, _p(c), _p(h), _p(g))
+    lib().ffo_forward_pad(n, pad, T, cfl, nth, _p(c), _p(h), _p(g))
     return g
 
 
-def adjoint(c, g, T: float, cfl: float = 0.3) -> np.ndarray:
+def adjoint(c, g, T: float, cfl: float = 0.3, pad: int = 0) -> np.ndarray:
     """h = W_T^T P^T g."""
     c, g = _f64(c), _f64(g)
-    n = c.shape[0]
+    n = _image_n(c, pad)
     h = np.empty((n, n, n))
-    lib().ffo_adjoint(n, T, cfl, g.shape[0], _p(c), _p(g), _p(h))
+    lib().ffo_adjoint_pad(n, pad, T, cfl, g.shape[0], _p(c), _p(g), _p(h))
     return h
 
 
-def power(c, v0, T: float, nth: int, precond: int = 0, iters: int = 20, cfl: float = 0.3) -> float:
-    """Largest eigenvalue of A^T Lambda A by power iteration from v0."""
+def wave_img(c, u, T: float, pad: int, transpose: bool = False, cfl: float = 0.3) -> np.ndarray:
+    """W_T (or W_T^T) restricted to the image box of the grid padded by pad cells."""
+    c, u = _f64(c), _f64(u)
+    n = _image_n(c, pad)
+    out = np.empty((n, n, n))
+    lib().ffo_wave_img(n, pad, T, cfl, _p(c), _p(u), _p(out), int(bool(transpose)))
+    return out
+
+
+def power(c, v0, T: float, nth: int, precond: int = 0, iters: int = 20, cfl: float = 0.3,
+          pad: int = 0, mask=None) -> float:
+    """Largest eigenvalue of A^T chi Lambda chi A by power iteration from v0."""
     c, v0 = _f64(c), _f64(v0)
-    return lib().ffo_power(c.shape[0], T, cfl, nth, precond, _p(c), _p(v0), iters)
+    m = _f64(mask) if mask is not None else None
+    return lib().ffo_power_ex(_image_n(c, pad), pad, T, cfl, nth, precond, _p(c),
+                              _p(m) if m is not None else None, _p(v0), iters)
 
 
 def fb(c, g, T: float, lam: float, step: float, iters: int, h0=None, precond: int = 0,
@@ -251,28 +284,29 @@ def fbp(G) -> np.ndarray:
 
 
 def fb_two_step(c, G, T: float, lam: float, step: float, iters: int, h0=None, tol: float = 0.0,
-                cfl: float = 0.3):
+                cfl: float = 0.3, pad: int = 0):
     """Algorithm 9 with R = l1 + positivity.  Returns (h, stats[k, 4], iters_done)."""
     c, G = _f64(c), _f64(G)
-    n = c.shape[0]
+    n = _image_n(c, pad)
     h = np.zeros((n, n, n)) if h0 is None else _f64(h0).copy()
     stats = np.zeros((max(iters, 1), 4))
-    k = lib().ffo_fb_two_step(n, T, cfl, G.shape[0], _p(c), _p(G), lam, step, iters, tol, _p(h),
-                              _p(stats))
+    k = lib().ffo_fb_two_step(n, pad, T, cfl, G.shape[0], _p(c), _p(G), lam, step, iters, tol,
+                              _p(h), _p(stats))
     return h, stats[:k], k
 
 
 def fb_masked(c, g, T: float, lam: float, step: float, iters: int, mask=None, support=None,
-              h0=None, precond: int = 0, tol: float = 0.0, cfl: float = 0.3):
+              h0=None, precond: int = 0, tol: float = 0.0, cfl: float = 0.3, pad: int = 0):
     """Algorithm 8 with the data mask chi_M (Problem 1) and the source support
-    chi_V: r = A^T chi Lambda chi (A h - g), h+ = chi_V max(h - s r - s lambda, 0)."""
+    chi_V: r = A^T chi Lambda chi (A h - g), h+ = chi_V max(h - s r - s lambda, 0).
+    pad > 0: the wave on the grid padded by pad cells (c on that grid)."""
     c, g = _f64(c), _f64(g)
-    n = c.shape[0]
+    n = _image_n(c, pad)
     h = np.zeros((n, n, n)) if h0 is None else _f64(h0).copy()
     stats = np.zeros((max(iters, 1), 4))
     m = _f64(mask) if mask is not None else None
     sp = _f64(support) if support is not None else None
-    k = lib().ffo_fb_ex(n, T, cfl, g.shape[0], precond, _p(c), _p(g),
+    k = lib().ffo_fb_ex(n, pad, T, cfl, g.shape[0], precond, _p(c), _p(g),
                         _p(m) if m is not None else None, _p(sp) if sp is not None else None,
                         lam, step, iters, tol, _p(h), _p(stats))
     return h, stats[:k], k

@@ -28,6 +28,19 @@ def axis(n: int) -> np.ndarray:
     return -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
 
 
+def padded_axis(n: int, pad: int) -> np.ndarray:
+    """Cell centres of the padded wave grid: the n cells of [-1, 1] plus pad
+    cells of the same size dx = 2/n on either side (the same values as axis(n)
+    on the image cells, bit for bit)."""
+    return -1.0 + (np.arange(n + 2 * pad) - pad + 0.5) * (2.0 / n)
+
+
+def extend_speed(c: np.ndarray, pad: int) -> np.ndarray:
+    """A sound speed on the image grid continued to the padded wave grid by
+    repeating its boundary values outwards."""
+    return np.pad(np.asarray(c, dtype=np.float64), int(pad), mode="edge")
+
+
 def _in_ball(rng: np.random.Generator, radius: float) -> np.ndarray:
     while True:
         p = rng.uniform(-radius, radius, size=3)
