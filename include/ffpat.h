@@ -22,6 +22,15 @@
  *            xi_k theta + s_m theta_perp, theta_perp = (-sin, cos);
  *   data     g[j][l][k] = dx sum_m B(p[l]; ...), layout [theta][z][xi],
  *            n_angles * N * N elements.
+ *   padding  pad > 0 runs the wave on a larger grid than the image box: Nw =
+ *            N + 2 pad points per axis with the same dx (the box
+ *            [-1,1]^3 plus pad cells on every side, the enlarged
+ *            computational domain of the paper's experiments, Sec. 5), so that
+ *            waves leave the box instead of reflecting at its faces.  The
+ *            source h, the image-domain results and the support are N^3 on
+ *            the box; W h means: zero-extend h to the wave grid, step there,
+ *            read the box.  The sound speed c is given on the wave grid,
+ *            Nw^3 elements (Nw = N when pad = 0), and Nt uses its maximum.
  * The adjoint entry points apply the exact matrix transposes of these
  * discrete operators, so <A h, g> = <h, A^T g> up to rounding.
  *
@@ -80,6 +89,7 @@ typedef struct {
   int32_t n_angles;  /* number of projection directions, >= 1 */
   int32_t precision; /* ffpat_precision */
   int32_t precond;   /* ffpat_precond (used by ffpat_fb_solve and ffpat_opnorm) */
+  int32_t pad;       /* cells of padding on every side of the wave grid (0..2048; see below) */
 } ffpat_problem;
 
 /* Per-solve summary of Algorithm 8.  objective = 1/2 <Lambda r, r> + lambda ||h_k||_1
@@ -120,7 +130,7 @@ int ffpat_debug_tables(const ffpat_problem *problem, double *cos_sin);
 int ffpat_debug_samples(const ffpat_problem *problem, int32_t count, const int32_t *jkm,
                         int32_t *ij, double *f, void *stream);
 
-/* g = P W h  (eq. (4) composed with W of eq. (3)).  c, h: N^3; g: n_angles N^2. */
+/* g = P W h  (eq. (4) composed with W of eq. (3)).  c: Nw^3, h: N^3; g: n_angles N^2. */
 int ffpat_forward(const ffpat_problem *problem, const void *c, const void *h, void *g, void *ws,
                   size_t ws_bytes, void *stream);
 
@@ -129,7 +139,8 @@ int ffpat_forward(const ffpat_problem *problem, const void *c, const void *h, vo
 int ffpat_adjoint(const ffpat_problem *problem, const void *c, const void *g, void *h, void *ws,
                   size_t ws_bytes, void *stream);
 
-/* out = W in (transpose = 0) or W^T in (transpose = 1); N^3 each (eq. (3)). */
+/* out = W in (transpose = 0) or W^T in (transpose = 1); N^3 each on the image
+ * box (eq. (3)); with padding, the box restriction of W on the wave grid. */
 int ffpat_wave(const ffpat_problem *problem, const void *c, const void *in, void *out,
                int32_t transpose, void *ws, size_t ws_bytes, void *stream);
 
@@ -248,6 +259,8 @@ int ffpat_debug_wait_timeout(int32_t microseconds, void *stream);
  * in c).  The paper differentiates only in h (Sec. 3.1); the c-gradient is the
  * same discrete adjoint carried through kappa = (c dt / dx)^2. */
 
+/* The differentiated operator needs pad = 0 (the box is the wave grid). */
+
 /* Checkpoint buffer bytes for Nt steps (ffpat_problem_info) and interval
  * `every`: (2 ceil(Nt / every) + every + 2) volumes; 0 if invalid. */
 size_t ffpat_ckpt_bytes(const ffpat_problem *problem, int32_t nt, int32_t every);
@@ -267,8 +280,8 @@ int ffpat_backward(const ffpat_problem *problem, const void *c, const void *grad
 
 /* ---- Serving: many Algorithm-8 solves in flight on one GPU (continuous batching).
  * A server owns a worker thread and a CUDA stream on the device that is
- * current at creation.  Requests (FFPAT_FP32_KAHAN problems with N % 4 == 0;
- * any N, angle count, T) wait in a FIFO queue and are admitted while a slot is
+ * current at creation.  Requests (FFPAT_FP32_KAHAN problems with N % 4 == 0
+ * and pad = 0; any N, angle count, T) wait in a FIFO queue and are admitted while a slot is
  * free and their device memory fits the HBM budget; every launch of the
  * leapfrog kernel advances all admitted requests that are inside a wave phase
  * by one step, and requests that arrive while others run join at the next

@@ -93,6 +93,8 @@ static int validate(const ffpat_problem* pr, Plan& pl) {
     return fail(FFPAT_EINVAL, "unknown precision %d", pr->precision);
   if (pr->precond < FFPAT_PRECOND_NONE || pr->precond > FFPAT_PRECOND_RAMP)
     return fail(FFPAT_EINVAL, "unknown preconditioner %d", pr->precond);
+  if (pr->pad < 0 || pr->pad > 2048 || pr->n + 2 * pr->pad > 4096)
+    return fail(FFPAT_EINVAL, "pad = %d outside [0, 2048] or N + 2 pad > 4096", pr->pad);
   pl.n = pr->n;
   pl.nth = pr->n_angles;
   pl.ns = 2 * (int)ceil((double)pr->n / sqrt(2.0));
@@ -102,6 +104,9 @@ static int validate(const ffpat_problem* pr, Plan& pl) {
   pl.cfl = pr->cfl;
   pl.dx = 2.0 / pr->n;
   pl.n3 = (size_t)pl.n * pl.n * pl.n;
+  pl.pad = pr->pad;
+  pl.nw = pr->n + 2 * pr->pad;
+  pl.nw3 = (size_t)pl.nw * pl.nw * pl.nw;
   pl.nd = (size_t)pl.nth * pl.n * pl.n;
   pl.esize = pl.prec == FFPAT_FP64 ? 8 : 4;
   return FFPAT_OK;
@@ -118,11 +123,14 @@ static size_t carve(Plan& pl, void* ws) {
     off += up256(bytes);
     return p;
   };
-  const size_t vol = pl.n3 * pl.esize, dat = pl.nd * pl.esize;
+  const size_t vol = pl.n3 * pl.esize, dat = pl.nd * pl.esize, wvol = pl.nw3 * pl.esize;
   pl.kap = take(vol);
-  for (int i = 0; i < 6; ++i) pl.s[i] = i < nstate(pl) ? take(vol) : nullptr;
+  pl.kapw = pl.pad ? take(wvol) : pl.kap;
+  for (int i = 0; i < 6; ++i) pl.s[i] = i < nstate(pl) ? take(wvol) : nullptr;
   pl.x = take(vol);
   pl.v = take(vol);
+  pl.xw = pl.pad ? take(wvol) : nullptr;
+  pl.xo = pl.pad ? take(vol) : nullptr;
   pl.r = take(dat);
   pl.r2 = take(dat);
   pl.partials = (double*)take(sizeof(double) * kNumQuant * kReduceBlocks);
@@ -195,9 +203,10 @@ int time_steps(const Plan& pl, double cmax, int* nt, double* dt) {
 }
 
 // c statistics -> Nt, dt, kappa (one device-to-host read of three doubles).
+// c and kapw live on the wave grid; kap is kapw's restriction to the box.
 static int setup_speed(Plan& pl, const void* c, cudaStream_t st) {
   if (!c) return fail(FFPAT_EINVAL, "c is NULL");
-  TRY(launch_speed_stats(pl, c, pl.scal, st));
+  TRY(launch_speed_stats(wave_plan(pl), c, pl.scal, st));
   double h3[3];
   CK(cudaMemcpyAsync(h3, pl.scal, sizeof h3, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -205,7 +214,12 @@ static int setup_speed(Plan& pl, const void* c, cudaStream_t st) {
     return fail(FFPAT_EINVAL, "sound speed has %.0f entries that are not finite and > 0", h3[2]);
   pl.cmax = h3[0];
   TRY(time_steps(pl, pl.cmax, &pl.nt, &pl.dt));
-  TRY(launch_kappa(pl, c, st));
+  TRY(launch_kappa(wave_plan(pl), c, st));
+  if (pl.pad) {
+    TRY(launch_restrict(pl, pl.kapw, pl.kap, st));
+    // the padded W's input buffer: only its box cells are ever written
+    CK(cudaMemsetAsync(pl.xw, 0, pl.nw3 * pl.esize, st));
+  }
   return FFPAT_OK;
 }
 
@@ -414,12 +428,26 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
 }
 
 
+// W on the image box.  Without padding this is run_wave; with padding the
+// input is zero-extended to the wave grid, the time loop runs there and the
+// box cells of the result are copied out (to `out`, else to pl.xo).
+static int run_wave_box(const Plan& pl, const void* in, void* out, const void** result,
+                        cudaStream_t st) {
+  if (pl.pad == 0) return run_wave(pl, in, out, result, st);
+  TRY(launch_embed(pl, in, pl.xw, st));
+  const void* w = nullptr;
+  TRY(run_wave(wave_plan(pl), pl.xw, nullptr, &w, st));
+  void* dst = out ? out : pl.xo;
+  TRY(launch_restrict(pl, w, dst, st));
+  if (result) *result = dst;
+  return FFPAT_OK;
+}
 
 // h = W^T P^T g  ->  x = K P^T g ; w = W x ; h = w / K
 static int apply_adjoint(const Plan& pl, const void* g, void* h, cudaStream_t st) {
   TRY(launch_backproject(pl, g, pl.x, pl.kap, st));
   const void* w = nullptr;
-  TRY(run_wave(pl, pl.x, nullptr, &w, st));
+  TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
   TRY(launch_kscale(pl, w, h, false, st));
   return FFPAT_OK;
 }
@@ -430,7 +458,7 @@ static int apply_adjoint(const Plan& pl, const void* g, void* h, cudaStream_t st
 static int data_gradient(const Plan& pl, const void* v, const void* g, const void** w,
                          double* dots, cudaStream_t st, const void* mask = nullptr) {
   const void* pN = nullptr;
-  TRY(run_wave(pl, v, nullptr, &pN, st));
+  TRY(run_wave_box(pl, v, nullptr, &pN, st));
   TRY(launch_project(pl, pN, pl.r, g, st, mask));
   const void* lr = pl.r;
   if (pl.precond == FFPAT_PRECOND_RAMP) {
@@ -439,7 +467,7 @@ static int data_gradient(const Plan& pl, const void* v, const void* g, const voi
   }
   if (dots) TRY(launch_dot(pl, pl.nd, lr, pl.r, dots, st));
   TRY(launch_backproject(pl, lr, pl.x, pl.kap, st));
-  TRY(run_wave(pl, pl.x, nullptr, w, st));
+  TRY(run_wave_box(pl, pl.x, nullptr, w, st));
   return FFPAT_OK;
 }
 
@@ -533,7 +561,7 @@ int ffpat_forward(const ffpat_problem* problem, const void* c, const void* h, vo
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
   if (!h || !g) return fail(FFPAT_EINVAL, "h or g is NULL");
   const void* pN = nullptr;
-  TRY(run_wave(pl, h, nullptr, &pN, st));
+  TRY(run_wave_box(pl, h, nullptr, &pN, st));
   TRY(launch_project(pl, pN, g, nullptr, st));
   return FFPAT_OK;
 }
@@ -555,11 +583,11 @@ int ffpat_wave(const ffpat_problem* problem, const void* c, const void* in, void
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
   if (!in || !out) return fail(FFPAT_EINVAL, "in or out is NULL");
   if (!transpose) {
-    TRY(run_wave(pl, in, out, nullptr, st));
+    TRY(run_wave_box(pl, in, out, nullptr, st));
   } else {
     TRY(launch_kscale(pl, in, pl.x, true, st));
     const void* w = nullptr;
-    TRY(run_wave(pl, pl.x, nullptr, &w, st));
+    TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
     TRY(launch_kscale(pl, w, out, false, st));
   }
   return FFPAT_OK;
@@ -709,9 +737,9 @@ static int power_iteration_w(const Plan& pl, int iters, double* est, cudaStream_
   TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
   for (int it = 0; it < iters; ++it) {
     const void* w = nullptr;
-    TRY(run_wave(pl, pl.v, nullptr, &w, st));
+    TRY(run_wave_box(pl, pl.v, nullptr, &w, st));
     TRY(launch_kscale(pl, w, pl.x, true, st));
-    TRY(run_wave(pl, pl.x, nullptr, &w, st));
+    TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
     TRY(launch_kscale(pl, w, pl.v, false, st));
     TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
     TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
@@ -749,9 +777,9 @@ int ffpat_fb_two_step(const ffpat_problem* problem, const void* c, const void* G
   for (; k < max_iters; ++k) {
     double* hk = pl.hist + 8 * (size_t)k;
     const void* w = nullptr;
-    TRY(run_wave(pl, h_inout, nullptr, &w, st));
+    TRY(run_wave_box(pl, h_inout, nullptr, &w, st));
     TRY(launch_resid_kap(pl, w, pl.v, pl.x, hk, st));
-    TRY(run_wave(pl, pl.x, nullptr, &w, st));
+    TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
     TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st));
     if (tol > 0.0) {
       double q[4];

@@ -113,6 +113,26 @@ __global__ void k_kscale(const T* __restrict__ a, T* __restrict__ out, const T* 
     out[i] = mul ? a[i] * kap[i] : a[i] / kap[i];
 }
 
+// copy between the image box (n^3) and its cells inside the wave grid (nw^3,
+// pad cells on every side)
+template <typename T>
+__global__ void k_box_copy(const T* __restrict__ src, T* __restrict__ dst, int n, int nw, int pad,
+                           bool to_wave) {
+  const size_t n3 = (size_t)n * n * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % n);
+    const size_t t = i / n;
+    const int y = (int)(t % n);
+    const int z = (int)(t / n);
+    const size_t w = ((size_t)(z + pad) * nw + (y + pad)) * nw + (x + pad);
+    if (to_wave)
+      dst[w] = src[i];
+    else
+      dst[i] = src[w];
+  }
+}
+
 template <typename T>
 __global__ void k_scale_dev(const T* __restrict__ a, T* __restrict__ out, size_t len,
                             const double* __restrict__ sq) {
@@ -281,6 +301,26 @@ int launch_kscale(const Plan& pl, const void* a, void* out, bool mul, cudaStream
     k_kscale<float><<<nb, 256, 0, st>>>((const float*)a, (float*)out, (const float*)pl.kap, pl.n3, mul);
   count_launch();
   return check_launch(__func__);
+}
+
+static int box_copy(const Plan& pl, const void* src, void* dst, bool to_wave, cudaStream_t st) {
+  const unsigned nb = ew_blocks(pl.n3);
+  if (pl.prec == FFPAT_FP64)
+    k_box_copy<double><<<nb, 256, 0, st>>>((const double*)src, (double*)dst, pl.n, pl.nw, pl.pad,
+                                           to_wave);
+  else
+    k_box_copy<float><<<nb, 256, 0, st>>>((const float*)src, (float*)dst, pl.n, pl.nw, pl.pad,
+                                          to_wave);
+  count_launch();
+  return check_launch(__func__);
+}
+
+int launch_embed(const Plan& pl, const void* box, void* wave, cudaStream_t st) {
+  return box_copy(pl, box, wave, true, st);
+}
+
+int launch_restrict(const Plan& pl, const void* wave, void* box, cudaStream_t st) {
+  return box_copy(pl, wave, box, false, st);
 }
 
 int launch_scale_dev(const Plan& pl, size_t len, const void* a, void* out, const double* s,

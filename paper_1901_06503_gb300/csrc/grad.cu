@@ -30,6 +30,7 @@ struct Ckpt {
 };
 
 int ckpt_layout(const Plan& pl, int nt, int every, void* base, Ckpt* ck) {
+  if (pl.pad != 0) return report(FFPAT_EINVAL, "the differentiated operator needs pad = 0");
   if (every < 1 || every > 4096) return report(FFPAT_EINVAL, "checkpoint interval %d", every);
   ck->vol = up256(pl.n3 * pl.esize);
   ck->every = every;

@@ -15,13 +15,19 @@ constexpr int kReduceThreads = 256;
 constexpr int kNumQuant = 8;           // quantities one reduction pass can carry
 
 // Derived, validated problem plus the carve of the caller's workspace.
+// Grid fields (n, n3, kap) describe the image box; with padding the wave runs
+// on a grid of nw = n + 2 pad points per axis whose view wave_plan() gives.
 struct Plan {
   int n = 0, nth = 0, ns = 0, nt = 0, prec = 0, precond = 0;
+  int pad = 0, nw = 0;    // cells of padding per side; wave grid points per axis
   double T = 0, cfl = 0, dx = 0, dt = 0, cmax = 0;
-  size_t n3 = 0, nd = 0, esize = 0;
+  size_t n3 = 0, nd = 0, esize = 0, nw3 = 0;
   // workspace carve (device)
-  void* kap = nullptr;    // kappa / 12 for every grid point
-  void* s[6] = {};        // wavefield state: three-term p^{n-1}, p^n; increment form p, p', d, e, d', e'
+  void* kap = nullptr;    // kappa / 12 on the image box
+  void* kapw = nullptr;   // kappa / 12 on the wave grid (== kap without padding)
+  void* s[6] = {};        // wavefield state (wave grid): three-term p^{n-1}, p^n; increment form p, p', d, e, d', e'
+  void* xw = nullptr;     // wave-grid input of a padded W (zero outside the box)
+  void* xo = nullptr;     // image-box result of a padded W
   void* x = nullptr;      // image-domain scratch (adjoint input / gradient)
   void* v = nullptr;      // image-domain scratch (power iteration vector)
   void* r = nullptr;      // data-domain scratch (residual)
@@ -33,6 +39,14 @@ struct Plan {
   float* tabf = nullptr;       // cos[nth], sin[nth] rounded to float
   int32_t* tabi = nullptr;     // cos[nth], sin[nth] in fixed point, round(. * 2^30)
 };
+// The plan as the wave kernels see it: the wave grid and its kappa.
+inline Plan wave_plan(const Plan& pl) {
+  Plan w = pl;
+  w.n = pl.nw;
+  w.n3 = pl.nw3;
+  w.kap = pl.kapw;
+  return w;
+}
 // bytes of the three angle tables (double, float, fixed point) for nth angles
 inline size_t table_bytes(int nth) { return (size_t)nth * 2 * (8 + 4 + 4); }
 constexpr int kMaxHist = 4096;
@@ -112,6 +126,10 @@ int launch_debug_samples(const Plan& pl, int count, const int32_t* jkm, int32_t*
 int launch_speed_stats(const Plan& pl, const void* c, double* out3, cudaStream_t st);
 int launch_kappa(const Plan& pl, const void* c, cudaStream_t st);
 // out[i] = a[i] * kap[i] (mul = true) or a[i] / kap[i]
+// padding: box (n^3) -> interior of the wave grid (the rest of `wave` is left
+// as it is: zero by construction), and wave grid -> box
+int launch_embed(const Plan& pl, const void* box, void* wave, cudaStream_t st);
+int launch_restrict(const Plan& pl, const void* wave, void* box, cudaStream_t st);
 int launch_kscale(const Plan& pl, const void* a, void* out, bool mul, cudaStream_t st);
 // out[i] = a[i] * s  (s a device double)
 int launch_scale_dev(const Plan& pl, size_t len, const void* a, void* out, const double* s,

@@ -377,8 +377,8 @@ int ffpat_submit(ffpat_server* S, const ffpat_problem* problem, const void* c_ho
   r->prob = *problem;
   const size_t ws = ffpat_workspace_bytes(problem);
   if (ws == 0) return FFPAT_EINVAL;
-  if (problem->precision != FFPAT_FP32_KAHAN || problem->n % 4 != 0)
-    return report(FFPAT_EINVAL, "served problems are FFPAT_FP32_KAHAN with N %% 4 == 0");
+  if (problem->precision != FFPAT_FP32_KAHAN || problem->n % 4 != 0 || problem->pad != 0)
+    return report(FFPAT_EINVAL, "served problems are FFPAT_FP32_KAHAN with N %% 4 == 0 and pad = 0");
   if (iters < 1 || iters > kMaxHist) return report(FFPAT_EINVAL, "iters = %d", iters);
   if (!(lambda >= 0.0) || !isfinite(lambda) || !isfinite(step))
     return report(FFPAT_EINVAL, "lambda / step not finite");

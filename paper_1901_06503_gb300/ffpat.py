@@ -32,12 +32,12 @@ PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", FP32_KAHAN: "fp32-kahan"}
 class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("T", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("n_angles", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("precond", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"Problem(n={self.n}, T={self.T}, cfl={self.cfl}, n_angles={self.n_angles}, "
                 f"precision={PRECISION_NAMES.get(self.precision, self.precision)}, "
-                f"precond={self.precond})")
+                f"precond={self.precond}, pad={self.pad})")
 
 
 class FBStats(ctypes.Structure):
@@ -152,8 +152,11 @@ def _check(rc):
 
 
 def problem(n: int, T: float, n_angles: int, precision: int = FP64, precond: int = 0,
-            cfl: float = 0.3) -> Problem:
-    return Problem(int(n), float(T), float(cfl), int(n_angles), int(precision), int(precond))
+            cfl: float = 0.3, pad: int = 0) -> Problem:
+    """pad > 0: the wave runs on the grid of n + 2 pad points per axis (c is
+    given there); sources, images and data stay on the n^3 box."""
+    return Problem(int(n), float(T), float(cfl), int(n_angles), int(precision), int(precond),
+                   int(pad))
 
 
 def torch_dtype(prob: Problem):
@@ -185,6 +188,12 @@ def _dev(t, prob, shape, name):
 
 def vol_shape(prob):
     return (prob.n, prob.n, prob.n)
+
+
+def wave_shape(prob):
+    """Shape of the sound speed: the wave grid, n + 2 pad points per axis."""
+    nw = prob.n + 2 * prob.pad
+    return (nw, nw, nw)
 
 
 def data_shape(prob):
@@ -241,7 +250,7 @@ def forward(prob, c, h, g=None, ws=None, stream=None):
     """g = P W h."""
     g = _empty(prob, data_shape(prob), h) if g is None else g
     ws, wp, wn = _ws(prob, ws, h.device)
-    _check(lib().ffpat_forward(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_forward(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                _dev(h, prob, vol_shape(prob), "h"),
                                _dev(g, prob, data_shape(prob), "g"), wp, wn, _stream(stream)))
     return g
@@ -250,7 +259,7 @@ def forward(prob, c, h, g=None, ws=None, stream=None):
 def forward_noalloc(prob, c, h, g, stream=None):
     """g = P W h through the entry point that allocates nothing (static
     device scratch; N <= 64 with <= 180 angles).  `g` must be preallocated."""
-    _check(lib().ffpat_forward_noalloc(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_forward_noalloc(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                        _dev(h, prob, vol_shape(prob), "h"),
                                        _dev(g, prob, data_shape(prob), "g"), _stream(stream)))
     return g
@@ -267,7 +276,7 @@ def forward_ckpt(prob, c, h, every, ckpt, g=None, ws=None, stream=None):
     """g = P W h, saving wavefield checkpoints every `every` steps into ckpt."""
     g = _empty(prob, data_shape(prob), h) if g is None else g
     ws, wp, wn = _ws(prob, ws, h.device)
-    _check(lib().ffpat_forward_ckpt(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_forward_ckpt(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                     _dev(h, prob, vol_shape(prob), "h"),
                                     _dev(g, prob, data_shape(prob), "g"), int(every),
                                     ctypes.c_void_p(ckpt.data_ptr()), ctypes.c_size_t(ckpt.numel()),
@@ -280,7 +289,7 @@ def backward(prob, c, grad_g, every, ckpt, want_h=True, want_c=True, ws=None, st
     gh = _empty(prob, vol_shape(prob), grad_g) if want_h else None
     gc = _empty(prob, vol_shape(prob), grad_g) if want_c else None
     ws, wp, wn = _ws(prob, ws, grad_g.device)
-    _check(lib().ffpat_backward(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_backward(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                 _dev(grad_g, prob, data_shape(prob), "grad_g"),
                                 _dev(gh, prob, vol_shape(prob), "grad_h") if want_h else None,
                                 _dev(gc, prob, vol_shape(prob), "grad_c") if want_c else None,
@@ -293,7 +302,7 @@ def adjoint(prob, c, g, h=None, ws=None, stream=None):
     """h = W^T P^T g."""
     h = _empty(prob, vol_shape(prob), g) if h is None else h
     ws, wp, wn = _ws(prob, ws, g.device)
-    _check(lib().ffpat_adjoint(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_adjoint(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                _dev(g, prob, data_shape(prob), "g"),
                                _dev(h, prob, vol_shape(prob), "h"), wp, wn, _stream(stream)))
     return h
@@ -303,7 +312,7 @@ def wave(prob, c, x, out=None, transpose=False, ws=None, stream=None):
     """W x (or W^T x)."""
     out = _empty(prob, vol_shape(prob), x) if out is None else out
     ws, wp, wn = _ws(prob, ws, x.device)
-    _check(lib().ffpat_wave(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_wave(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                             _dev(x, prob, vol_shape(prob), "in"),
                             _dev(out, prob, vol_shape(prob), "out"), int(bool(transpose)), wp, wn,
                             _stream(stream)))
@@ -334,7 +343,7 @@ def ramp(prob, r, out=None, stream=None):
 def opnorm(prob, c, v0, iters=20, ws=None, stream=None) -> float:
     ws, wp, wn = _ws(prob, ws, v0.device)
     est = ctypes.c_double()
-    _check(lib().ffpat_opnorm(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_opnorm(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                               _dev(v0, prob, vol_shape(prob), "v0"), int(iters),
                               ctypes.byref(est), wp, wn, _stream(stream)))
     return est.value
@@ -349,7 +358,7 @@ def fb_solve(prob, c, g, lam, step, max_iters, h=None, tol=0.0, ws=None, stream=
     st = FBStats()
     hist = np.zeros((max(int(max_iters), 1), 4)) if history else None
     hp = hist.ctypes.data_as(ctypes.c_void_p) if history else None
-    _check(lib().ffpat_fb_solve(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_fb_solve(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                 _dev(g, prob, data_shape(prob), "g"), float(lam), float(step),
                                 int(max_iters), float(tol), _dev(h, prob, vol_shape(prob), "h"),
                                 ctypes.byref(st), hp, wp, wn, _stream(stream)))
@@ -369,7 +378,7 @@ def fb_solve_masked(prob, c, g, lam, step, max_iters, mask=None, support=None, h
     hp = hist.ctypes.data_as(ctypes.c_void_p) if history else None
     mp = _dev(mask, prob, data_shape(prob), "mask") if mask is not None else None
     sp = _dev(support, prob, vol_shape(prob), "support") if support is not None else None
-    _check(lib().ffpat_fb_solve_ex(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_fb_solve_ex(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                    _dev(g, prob, data_shape(prob), "g"), mp, sp, float(lam),
                                    float(step), int(max_iters), float(tol),
                                    _dev(h, prob, vol_shape(prob), "h"), ctypes.byref(st), hp, wp,
@@ -396,7 +405,7 @@ def fb_two_step(prob, c, G, lam, step, max_iters, h=None, tol=0.0, ws=None, stre
     st = FBStats()
     hist = np.zeros((max(int(max_iters), 1), 4)) if history else None
     hp = hist.ctypes.data_as(ctypes.c_void_p) if history else None
-    _check(lib().ffpat_fb_two_step(ctypes.byref(prob), _dev(c, prob, vol_shape(prob), "c"),
+    _check(lib().ffpat_fb_two_step(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                    _dev(G, prob, data_shape(prob), "G"), float(lam), float(step),
                                    int(max_iters), float(tol), _dev(h, prob, vol_shape(prob), "h"),
                                    ctypes.byref(st), hp, wp, wn, _stream(stream)))

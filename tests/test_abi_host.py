@@ -49,15 +49,26 @@ def test_workspace_grows_with_problem(L):
     assert big > small > 0 and kahan > fp32
     # FP64 stores 8-byte values: at least kappa + 2 states + 2 scratch volumes
     assert big >= 5 * 64**3 * 8
+    # padding: kappa, two states and the input on the wave grid on top
+    padded = F.workspace_bytes(F.problem(64, 1.0, 24, pad=32))
+    assert padded >= big + 4 * (128**3 - 64**3) * 8
+
+
+def test_padding_rejected_where_unsupported(L):
+    prob = F.problem(16, 1.0, 4, F.FP32_KAHAN, pad=4)
+    assert L.ffpat_ckpt_bytes(ctypes.byref(prob), 10, 4) == 0
+    assert b"pad" in L.ffpat_last_error()
 
 
 @pytest.mark.parametrize("bad", [
     dict(n=0), dict(n=5000), dict(T=0.0), dict(T=float("nan")), dict(cfl=0.51), dict(cfl=0.0),
-    dict(n_angles=0), dict(precision=7), dict(precond=3)])
+    dict(n_angles=0), dict(precision=7), dict(precond=3), dict(pad=-1), dict(pad=2049),
+    dict(n=2048, pad=1025)])
 def test_invalid_problems_rejected(L, bad):
-    kw = dict(n=16, T=1.0, n_angles=4, precision=0, precond=0, cfl=0.3)
+    kw = dict(n=16, T=1.0, n_angles=4, precision=0, precond=0, cfl=0.3, pad=0)
     kw.update(bad)
-    prob = F.Problem(kw["n"], kw["T"], kw["cfl"], kw["n_angles"], kw["precision"], kw["precond"])
+    prob = F.Problem(kw["n"], kw["T"], kw["cfl"], kw["n_angles"], kw["precision"], kw["precond"],
+                     kw["pad"])
     assert L.ffpat_workspace_bytes(ctypes.byref(prob)) == 0
     assert L.ffpat_last_error()
     # entry points reject the problem before touching the GPU
