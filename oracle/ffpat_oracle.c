@@ -357,6 +357,73 @@ void ffo_ramp(int n, int nth, const double *r, double *out) {
   }
 }
 
+/* ------------------------------- gradient regulariser R = 1/2 |grad h|^2 -- */
+
+/* The discrete R of the paper's experiments (Sec. 5): forward differences
+ * between neighbouring cells of the box, none across its faces (h lives on the
+ * box V only), scaled by 1/dx:  R(h) = 1/2 sum_axes sum (h[i+1] - h[i])^2 / dx^2
+ * = 1/2 <D h, D h> / dx^2.  This returns <D h, D h> (no 1/dx^2). */
+double ffo_grad_energy(int n, const double *h) {
+  double acc = 0.0;
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        double u = h[at3(n, z, y, x)];
+        if (x + 1 < n) acc += (h[at3(n, z, y, x + 1)] - u) * (h[at3(n, z, y, x + 1)] - u);
+        if (y + 1 < n) acc += (h[at3(n, z, y + 1, x)] - u) * (h[at3(n, z, y + 1, x)] - u);
+        if (z + 1 < n) acc += (h[at3(n, z + 1, y, x)] - u) * (h[at3(n, z + 1, y, x)] - u);
+      }
+  return acc;
+}
+
+/* prox of a R with a = s lambda / dx^2 (the proximal map of Sec. 3.2):
+ * argmin 1/2 ||h - f||^2 + a/2 <D h, D h>, i.e. the solution of
+ * (I + a D^T D) h = f.  D^T D is the cell-centred Laplacian with zero-flux
+ * (Neumann) faces, which the orthonormal DCT-II diagonalises axis by axis:
+ * C[k][i] = w_k cos(pi k (2 i + 1) / (2 n)), w_0 = sqrt(1/n), w_k = sqrt(2/n),
+ * eigenvalue 4 sin^2(pi k / (2 n)) per axis.  So h = C^T diag(1 / (1 + a mu)) C f
+ * with the transforms taken along x, y and z. */
+static void dct_axis(int n, const double *C, int transpose, int axis, const double *in,
+                     double *out) {
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        int k = axis == 0 ? x : (axis == 1 ? y : z);
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) {
+          double m = transpose ? C[(size_t)i * n + k] : C[(size_t)k * n + i];
+          size_t src = axis == 0 ? at3(n, z, y, i) : (axis == 1 ? at3(n, z, i, x) : at3(n, i, y, x));
+          acc += m * in[src];
+        }
+        out[at3(n, z, y, x)] = acc;
+      }
+}
+
+void ffo_prox_grad(int n, double a, const double *f, double *out) {
+  size_t n3 = (size_t)n * n * n;
+  double *C = malloc((size_t)n * n * sizeof(double)), *mu = malloc((size_t)n * sizeof(double));
+  double *t1 = malloc(n3 * sizeof(double)), *t2 = malloc(n3 * sizeof(double));
+  for (int k = 0; k < n; ++k) {
+    double w = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+    for (int i = 0; i < n; ++i) C[(size_t)k * n + i] = w * cos(FFO_PI * k * (2.0 * i + 1.0) / (2.0 * n));
+    double sn = sin(FFO_PI * k / (2.0 * n));
+    mu[k] = 4.0 * sn * sn;
+  }
+  dct_axis(n, C, 0, 0, f, t1);
+  dct_axis(n, C, 0, 1, t1, t2);
+  dct_axis(n, C, 0, 2, t2, t1);
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) t1[at3(n, z, y, x)] /= 1.0 + a * (mu[x] + mu[y] + mu[z]);
+  dct_axis(n, C, 1, 2, t1, t2);
+  dct_axis(n, C, 1, 1, t2, t1);
+  dct_axis(n, C, 1, 0, t1, out);
+  free(C);
+  free(mu);
+  free(t1);
+  free(t2);
+}
+
 /* --------------------------------------------- forward operator A = P W -- */
 
 typedef struct {
@@ -557,28 +624,44 @@ double ffo_power(int n, double T, double cfl, int nth, int precond, const double
  * grid): r_k = A^T chi Lambda chi (A h_k - g) and
  * h_{k+1} = chi_V max(h_k - s r_k - s lambda, 0) (the prox of
  * s lambda (||.||_1 + i_{>=0}) + i_V).  With mask and support NULL this is
- * the plain Algorithm 8.
+ * the plain Algorithm 8.  reg = 1 takes the paper's experimental regulariser
+ * R = 1/2 |grad h|^2 instead (ffo_prox_grad; support must be NULL): then
+ * h_{k+1} = prox_{s lambda R}(h_k - s r_k) and the objective carries
+ * lambda R(h_k).
  * stats[4 k + {0,1,2,3}] = objective 1/2 <Lambda r, r> + lambda ||h_k||_1,
  * ||chi (A h_k - g)||_2, ||h_{k+1} - h_k|| / max(||h_k||, 1e-300), ||h_{k+1}||_2.
  * Returns the number of iterations run (stops early when tol > 0 and the
  * relative change drops below tol). */
 int ffo_fb_ex(int n, int pad, double T, double cfl, int nth, int precond, const double *c,
-              const double *g, const double *mask, const double *support, double lambda,
-              double step, int iters, double tol, double *h, double *stats) {
+              const double *g, const double *mask, const double *support, int reg,
+              double lambda, double step, int iters, double tol, double *h, double *stats) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
+  if (reg == 1 && support) return -1; /* the smoothing prox is defined on the whole box */
   setup(&s, n, pad, T, cfl, nth, precond, c);
   double *grad = malloc(n3 * sizeof(double)), *work3 = malloc(n3 * sizeof(double));
   double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
+  double dx = 2.0 / n;
   int k;
   for (k = 0; k < iters; ++k) {
     data_gradient_m(&s, h, g, mask, r, lr, grad, work3);
     double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
+    if (reg == 1) {
+      /* h_{k+1} = prox_{s lambda R}(h_k - s r_k), R = 1/2 |grad h|^2 */
+      l1 = 0.5 * ffo_grad_energy(n, h) / (dx * dx);
+      for (size_t i = 0; i < n3; ++i) grad[i] = h[i] - step * grad[i];
+      ffo_prox_grad(n, step * lambda / (dx * dx), grad, work3);
+    }
     for (size_t i = 0; i < n3; ++i) {
-      double f = h[i] - step * grad[i] - step * lambda;
-      double hn = f > 0.0 ? f : 0.0;
-      if (support) hn *= support[i];
-      l1 += fabs(h[i]);
+      double hn;
+      if (reg == 1) {
+        hn = work3[i];
+      } else {
+        double f = h[i] - step * grad[i] - step * lambda;
+        hn = f > 0.0 ? f : 0.0;
+        if (support) hn *= support[i];
+        l1 += fabs(h[i]);
+      }
       hh += h[i] * h[i];
       dd += (hn - h[i]) * (hn - h[i]);
       nn += hn * hn;
@@ -606,7 +689,7 @@ int ffo_fb_ex(int n, int pad, double T, double cfl, int nth, int precond, const 
 
 int ffo_fb(int n, double T, double cfl, int nth, int precond, const double *c, const double *g,
            double lambda, double step, int iters, double tol, double *h, double *stats) {
-  return ffo_fb_ex(n, 0, T, cfl, nth, precond, c, g, NULL, NULL, lambda, step, iters, tol, h,
+  return ffo_fb_ex(n, 0, T, cfl, nth, precond, c, g, NULL, NULL, 0, lambda, step, iters, tol, h,
                    stats);
 }
 
@@ -684,17 +767,18 @@ void ffo_fbp(int n, int nth, const double *G, double *out) {
 }
 
 /* Algorithm 9: g = X^{-1} G, then h_{k+1} = prox_{s lambda R}(h_k - s W^T (W h_k - g))
- * with R = ||h||_1 + indicator(h >= 0).  stats[4 k + 0..3]: objective
+ * with R = ||h||_1 + indicator(h >= 0) (reg = 0) or R = 1/2 |grad h|^2 (reg = 1).  stats[4 k + 0..3]: objective
  * 1/2 ||W h_k - g||^2 + lambda ||h_k||_1, ||W h_k - g||, relative change,
  * ||h_{k+1}||. */
 int ffo_fb_two_step(int n, int pad, double T, double cfl, int nth, const double *c,
-                    const double *G, double lambda, double step, int iters, double tol, double *h,
-                    double *stats) {
+                    const double *G, int reg, double lambda, double step, int iters, double tol,
+                    double *h, double *stats) {
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n;
   setup(&s, n, pad, T, cfl, nth, 0, c);
   double *g = malloc(n3 * sizeof(double)), *r = malloc(n3 * sizeof(double));
-  double *grad = malloc(n3 * sizeof(double));
+  double *grad = malloc(n3 * sizeof(double)), *prox = malloc(n3 * sizeof(double));
+  double dx = 2.0 / n;
   ffo_fbp(n, nth, G, g);
   int k;
   for (k = 0; k < iters; ++k) {
@@ -702,10 +786,20 @@ int ffo_fb_two_step(int n, int pad, double T, double cfl, int nth, const double 
     for (size_t i = 0; i < n3; ++i) r[i] -= g[i];
     wave_img_adjoint(&s, r, grad);
     double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
+    if (reg == 1) {
+      l1 = 0.5 * ffo_grad_energy(n, h) / (dx * dx);
+      for (size_t i = 0; i < n3; ++i) grad[i] = h[i] - step * grad[i];
+      ffo_prox_grad(n, step * lambda / (dx * dx), grad, prox);
+    }
     for (size_t i = 0; i < n3; ++i) {
-      double f = h[i] - step * grad[i] - step * lambda;
-      double hn = f > 0.0 ? f : 0.0;
-      l1 += fabs(h[i]);
+      double hn;
+      if (reg == 1) {
+        hn = prox[i];
+      } else {
+        double f = h[i] - step * grad[i] - step * lambda;
+        hn = f > 0.0 ? f : 0.0;
+        l1 += fabs(h[i]);
+      }
       hh += h[i] * h[i];
       dd += (hn - h[i]) * (hn - h[i]);
       nn += hn * hn;
@@ -726,6 +820,7 @@ int ffo_fb_two_step(int n, int pad, double T, double cfl, int nth, const double 
   free(g);
   free(r);
   free(grad);
+  free(prox);
   free(s.kappa);
   return k;
 }

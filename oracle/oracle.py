@@ -94,11 +94,16 @@ def lib():
             L.ffo_fbp.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
             L.ffo_fb_two_step.restype = ctypes.c_int
             L.ffo_fb_two_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                          ctypes.c_double, ctypes.c_int, _D, _D, ctypes.c_double,
-                                          ctypes.c_double, ctypes.c_int, ctypes.c_double, _D, _D]
+                                          ctypes.c_double, ctypes.c_int, _D, _D, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_double, _D, _D]
+            L.ffo_grad_energy.restype = ctypes.c_double
+            L.ffo_grad_energy.argtypes = [ctypes.c_int, _D]
+            L.ffo_prox_grad.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D]
             L.ffo_fb_ex.restype = ctypes.c_int
             L.ffo_fb_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_int,
+                                    ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, _D, _D]
             L.ffo_num_threads.restype = ctypes.c_int
             L.ffo_set_num_threads.argtypes = [ctypes.c_int]
@@ -284,22 +289,25 @@ def fbp(G) -> np.ndarray:
 
 
 def fb_two_step(c, G, T: float, lam: float, step: float, iters: int, h0=None, tol: float = 0.0,
-                cfl: float = 0.3, pad: int = 0):
-    """Algorithm 9 with R = l1 + positivity.  Returns (h, stats[k, 4], iters_done)."""
+                cfl: float = 0.3, pad: int = 0, reg: int = 0):
+    """Algorithm 9 with R = l1 + positivity (reg 0) or 1/2 |grad h|^2 (reg 1).
+    Returns (h, stats[k, 4], iters_done)."""
     c, G = _f64(c), _f64(G)
     n = _image_n(c, pad)
     h = np.zeros((n, n, n)) if h0 is None else _f64(h0).copy()
     stats = np.zeros((max(iters, 1), 4))
-    k = lib().ffo_fb_two_step(n, pad, T, cfl, G.shape[0], _p(c), _p(G), lam, step, iters, tol,
-                              _p(h), _p(stats))
+    k = lib().ffo_fb_two_step(n, pad, T, cfl, G.shape[0], _p(c), _p(G), int(reg), lam, step,
+                              iters, tol, _p(h), _p(stats))
     return h, stats[:k], k
 
 
 def fb_masked(c, g, T: float, lam: float, step: float, iters: int, mask=None, support=None,
-              h0=None, precond: int = 0, tol: float = 0.0, cfl: float = 0.3, pad: int = 0):
+              h0=None, precond: int = 0, tol: float = 0.0, cfl: float = 0.3, pad: int = 0,
+              reg: int = 0):
     """Algorithm 8 with the data mask chi_M (Problem 1) and the source support
     chi_V: r = A^T chi Lambda chi (A h - g), h+ = chi_V max(h - s r - s lambda, 0).
-    pad > 0: the wave on the grid padded by pad cells (c on that grid)."""
+    pad > 0: the wave on the grid padded by pad cells (c on that grid).
+    reg = 1: R = 1/2 |grad h|^2 (prox_grad) instead of l1 + positivity."""
     c, g = _f64(c), _f64(g)
     n = _image_n(c, pad)
     h = np.zeros((n, n, n)) if h0 is None else _f64(h0).copy()
@@ -308,5 +316,21 @@ def fb_masked(c, g, T: float, lam: float, step: float, iters: int, mask=None, su
     sp = _f64(support) if support is not None else None
     k = lib().ffo_fb_ex(n, pad, T, cfl, g.shape[0], precond, _p(c), _p(g),
                         _p(m) if m is not None else None, _p(sp) if sp is not None else None,
-                        lam, step, iters, tol, _p(h), _p(stats))
+                        int(reg), lam, step, iters, tol, _p(h), _p(stats))
+    if k < 0:
+        raise ValueError("the gradient regulariser takes no support mask")
     return h, stats[:k], k
+
+
+def grad_energy(h) -> float:
+    """<D h, D h>: squared forward differences between neighbouring box cells."""
+    h = _f64(h)
+    return lib().ffo_grad_energy(h.shape[0], _p(h))
+
+
+def prox_grad(f, a: float) -> np.ndarray:
+    """(I + a D^T D)^{-1} f: the prox of s lambda R, R = 1/2 |grad h|^2, a = s lambda / dx^2."""
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().ffo_prox_grad(f.shape[0], float(a), _p(f), _p(out))
+    return out

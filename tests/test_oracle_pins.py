@@ -608,3 +608,93 @@ def test_padded_fb_kkt():
     assert pos.any() and zero.any()
     assert np.max(np.abs(grad[pos] + lam)) < 1e-3 * lam
     assert np.min(grad[zero] + lam) > -1e-3 * lam
+
+
+# ------------------------- gradient regulariser R = 1/2 |grad h|^2 (Sec. 5) --
+
+def neumann_dtd(h):
+    """D^T D h, D = forward differences between neighbouring box cells along
+    each axis (none across the faces), written with np.diff."""
+    out = np.zeros_like(h)
+    for ax in range(3):
+        d = np.diff(h, axis=ax)
+        z = np.zeros_like(np.take(h, [0], axis=ax))
+        out += np.concatenate([z, d], axis=ax) - np.concatenate([d, z], axis=ax)
+    return out
+
+
+def test_grad_energy_is_the_sum_of_squared_differences():
+    h = random_volume(9, 151)
+    want = sum(float((np.diff(h, axis=ax) ** 2).sum()) for ax in range(3))
+    assert abs(o.grad_energy(h) - want) < 1e-12 * want
+    assert abs(float((h * neumann_dtd(h)).sum()) - want) < 1e-12 * want
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_prox_grad_is_the_dense_solve(n):
+    """(I + a D^T D)^{-1} f solved densely (D^T D assembled column by column
+    from the difference definition) against the DCT-diagonalised oracle."""
+    M = dense(neumann_dtd, n**3, (n, n, n))
+    f = random_volume(n, 152 + n)
+    for a in (0.0, 0.3, 17.0):
+        want = np.linalg.solve(np.eye(n**3) + a * M, f.ravel()).reshape(f.shape)
+        got = o.prox_grad(f, a)
+        assert np.max(np.abs(got - want)) < 1e-12 * np.abs(f).max()
+
+
+def test_prox_grad_optimality_and_kernel():
+    """The prox satisfies h - f + a D^T D h = 0 (first-order optimality of
+    1/2 ||h - f||^2 + a/2 ||D h||^2) on a ragged grid, and leaves constants,
+    the kernel of D, unchanged."""
+    n, a = 13, 3.7
+    f = random_volume(n, 155)
+    h = o.prox_grad(f, a)
+    assert np.linalg.norm(h - f + a * neumann_dtd(h)) < 1e-12 * np.linalg.norm(f)
+    const = np.full((n, n, n), 2.5)
+    assert np.max(np.abs(o.prox_grad(const, a) - const)) < 1e-13
+    assert np.max(np.abs(o.prox_grad(f, 0.0) - f)) < 1e-13
+
+
+def test_fb_gradient_regulariser_first_step_and_objective():
+    """From h_0 = 0 one step with R = 1/2 |grad h|^2 is prox(s A^T g) with
+    a = s lambda / dx^2; the first objective is 1/2 ||g||^2 (R(0) = 0) and the
+    second carries lambda R(h_1) = lambda/2 ||D h_1||^2 / dx^2."""
+    n, nth, T, s, lam = 10, 6, 0.5, 0.05, 0.3
+    c = random_speed(n, 157)
+    g = random_data(nth, n, 158)
+    dx = 2.0 / n
+    h1, st1, _ = o.fb_masked(c, g, T, lam, s, 1, reg=1)
+    want = o.prox_grad(s * o.adjoint(c, g, T), s * lam / dx**2)
+    assert np.max(np.abs(h1 - want)) < 1e-13 * np.abs(want).max()
+    assert abs(st1[0, 0] - 0.5 * float((g * g).sum())) < 1e-12 * st1[0, 0]
+    h2, st2, _ = o.fb_masked(c, g, T, lam, s, 2, reg=1)
+    r = o.forward(c, h1, T, nth) - g
+    obj = 0.5 * float((r * r).sum()) + lam * 0.5 * o.grad_energy(h1) / dx**2
+    assert abs(st2[1, 0] - obj) < 1e-12 * obj
+    with pytest.raises(ValueError):
+        o.fb_masked(c, g, T, lam, s, 1, reg=1, support=np.ones((n, n, n)))
+
+
+def test_fb_gradient_regulariser_stationary_point():
+    """At the fixed point of FB with R = 1/2 |grad h|^2 the gradient of the
+    smooth functional vanishes: A^T (A h - g) + lambda D^T D h / dx^2 = 0."""
+    n, nth, T, lam = 6, 6, 0.5, 0.02
+    c = random_speed(n, 159)
+    g = random_data(nth, n, 160)
+    dx = 2.0 / n
+    L = o.power(c, random_volume(n, 161), T, nth, iters=200)
+    h, st, k = o.fb_masked(c, g, T, lam, 1.0 / L, 3000, reg=1)
+    grad = o.adjoint(c, o.forward(c, h, T, nth) - g, T) + lam * neumann_dtd(h) / dx**2
+    assert np.linalg.norm(grad) < 1e-8 * np.linalg.norm(o.adjoint(c, g, T))
+    assert np.all(np.diff(st[:, 0]) <= 1e-12 * st[0, 0])  # monotone objective (s = 1/L)
+
+
+def test_two_step_gradient_regulariser_first_iterate():
+    """Algorithm 9 with R = 1/2 |grad h|^2: h_1 = prox(s W^T X^{-1} G)."""
+    n, nth, T, s, lam = 10, 8, 0.5, 0.4, 0.2
+    c = random_speed(n, 163)
+    G = random_data(nth, n, 164)
+    dx = 2.0 / n
+    h1, _, _ = o.fb_two_step(c, G, T, lam, s, 1, reg=1)
+    want = o.prox_grad(s * o.wave_img(c, o.fbp(G), T, 0, transpose=True), s * lam / dx**2)
+    assert np.max(np.abs(h1 - want)) < 1e-13 * np.abs(want).max()
