@@ -81,6 +81,11 @@ typedef enum {
   FFPAT_PRECOND_RAMP = 1  /* Lambda: F Lambda Phi = |omega| / (4 pi) F Phi along xi (Sec. 3.1) */
 } ffpat_precond;
 
+typedef enum {
+  FFPAT_REG_L1_POS = 0, /* R = ||h||_1 + indicator(h >= 0): h+ = max(f - s lambda, 0) */
+  FFPAT_REG_GRAD2 = 1   /* R = 1/2 |grad h|^2 (the paper's experiments, Sec. 5): see ffpat_prox_grad */
+} ffpat_regulariser;
+
 /* Problem statement (Problem 1 of Sec. 2.1 with full data). */
 typedef struct {
   int32_t n;         /* grid points per axis N (1..2048); N^3 volume, N detectors, N planes */
@@ -154,6 +159,16 @@ int ffpat_backproject(const ffpat_problem *problem, const void *g, void *h, void
  * t_0 = 1/(8 dxi), t_d = -1/(2 pi^2 d^2 dxi) for odd d, 0 for even d != 0. */
 int ffpat_ramp(const ffpat_problem *problem, const void *r, void *out, void *stream);
 
+/* out = prox of the gradient regulariser, (I + a D^T D)^{-1} f with
+ * a = s lambda / dx^2 (N^3 each; in place allowed): the minimiser of
+ * 1/2 ||h - f||^2 + s lambda R(h), R(h) = 1/2 <D h, D h> / dx^2, where D takes
+ * the forward differences between neighbouring cells of the box along each
+ * axis and none across its faces (h lives on the box: zero-flux faces).
+ * Solved exactly by the orthonormal DCT-II along x, y, z (eigenvalues
+ * 4 sin^2(pi k / 2N) per axis).  a >= 0.  Uses the workspace. */
+int ffpat_prox_grad(const ffpat_problem *problem, double a, const void *f, void *out, void *ws,
+                    size_t ws_bytes, void *stream);
+
 /* Power iteration v <- A^T Lambda A v / ||.|| from v0 (device, N^3) for `iters`
  * steps; *opnorm_sq = the estimate of the largest eigenvalue of A^T Lambda A.
  * Synchronises the stream. */
@@ -201,11 +216,25 @@ int ffpat_fb_two_step(const ffpat_problem *problem, const void *c, const void *G
  * + indicator(h >= 0) + indicator(supp h in V)).  mask (n_angles N^2) and
  * support (N^3) are device arrays of 0/1 values of the problem's element
  * type, or NULL for full data / the whole grid (then this is
- * ffpat_fb_solve).  The power-iteration step uses the masked operator. */
+ * ffpat_fb_solve).  The power-iteration step uses the masked operator.
+ * regulariser (ffpat_regulariser): FFPAT_REG_GRAD2 replaces the shrinkage by
+ * h_{k+1} = prox_{s lambda R}(h_k - s r_k) with R = 1/2 |grad h|^2
+ * (ffpat_prox_grad), the objective then carrying lambda R(h_k); it takes no
+ * support (EINVAL). */
 int ffpat_fb_solve_ex(const ffpat_problem *problem, const void *c, const void *g,
-                      const void *mask, const void *support, double lambda, double step,
-                      int32_t max_iters, double tol, void *h_inout, ffpat_fb_stats *stats,
-                      double *history, void *ws, size_t ws_bytes, void *stream);
+                      const void *mask, const void *support, int32_t regulariser, double lambda,
+                      double step, int32_t max_iters, double tol, void *h_inout,
+                      ffpat_fb_stats *stats, double *history, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/* Algorithm 9 with the choice of regulariser (ffpat_fb_two_step is
+ * FFPAT_REG_L1_POS): with FFPAT_REG_GRAD2,
+ * h_{k+1} = prox_{s lambda R}(h_k - s W^T (W h_k - g)), R = 1/2 |grad h|^2,
+ * the method of the paper's experiments (lambda = 0.5, s = 0.2 there). */
+int ffpat_fb_two_step_ex(const ffpat_problem *problem, const void *c, const void *G,
+                         int32_t regulariser, double lambda, double step, int32_t max_iters,
+                         double tol, void *h_inout, ffpat_fb_stats *stats, double *history,
+                         void *ws, size_t ws_bytes, void *stream);
 
 /* Instrumentation.  While enabled, every wave time loop records CUDA events on
  * its stream around its leapfrog launches; ffpat_profile_read synchronises

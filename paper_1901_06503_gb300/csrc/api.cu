@@ -140,6 +140,8 @@ static size_t carve(Plan& pl, void* ws) {
   pl.tab = (double*)tabs;
   pl.tabf = tabs ? (float*)((char*)tabs + 16 * (size_t)pl.nth) : nullptr;
   pl.tabi = tabs ? (int32_t*)((char*)tabs + 24 * (size_t)pl.nth) : nullptr;
+  pl.dct = take(dct_bytes(pl.n, pl.esize));
+  pl.dct_mu = pl.dct ? (const double*)((char*)pl.dct + 2 * (size_t)pl.n * pl.n * pl.esize) : nullptr;
   return off;
 }
 
@@ -491,6 +493,27 @@ static int power_iteration(const Plan& pl, int iters, double* est, cudaStream_t 
   return FFPAT_OK;
 }
 
+// validate the regulariser choice; the gradient one needs the DCT tables
+static int check_regulariser(const Plan& pl, int32_t reg, const void* support, cudaStream_t st) {
+  if (reg != FFPAT_REG_L1_POS && reg != FFPAT_REG_GRAD2)
+    return fail(FFPAT_EINVAL, "unknown regulariser %d", reg);
+  if (reg == FFPAT_REG_GRAD2) {
+    if (support) return fail(FFPAT_EINVAL, "the gradient regulariser takes no support mask");
+    TRY(upload_dct(pl, st));
+  }
+  return FFPAT_OK;
+}
+
+// h <- prox_{s lambda R}(h - s w / kap), R = 1/2 |grad h|^2, with the
+// statistics rows at dst (R(h), ||h||^2, ||h+ - h||^2, ||h+||^2)
+static int prox_grad_step(const Plan& pl, void* h, const void* w, double step, double lambda,
+                          double* dst, cudaStream_t st) {
+  TRY(launch_prox_prep(pl, h, w, step, pl.x, st));
+  TRY(launch_prox_grad(pl, step * lambda / (pl.dx * pl.dx), pl.x, pl.x, pl.s[0], pl.s[1], st));
+  TRY(launch_prox_finish(pl, h, pl.x, dst, st));
+  return FFPAT_OK;
+}
+
 }  // namespace ffpat
 
 using namespace ffpat;
@@ -636,6 +659,19 @@ int ffpat_ramp(const ffpat_problem* problem, const void* r, void* out, void* str
   return FFPAT_OK;
 }
 
+int ffpat_prox_grad(const ffpat_problem* problem, double a, const void* f, void* out, void* ws,
+                    size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl;
+  g_err[0] = 0;
+  TRY(attach(problem, pl, ws, ws_bytes));
+  if (!f || !out) return fail(FFPAT_EINVAL, "f or out is NULL");
+  if (!(a >= 0.0) || !isfinite(a)) return fail(FFPAT_EINVAL, "a = %g must be finite and >= 0", a);
+  TRY(upload_dct(pl, st));
+  TRY(launch_prox_grad(pl, a, f, out, pl.s[0], pl.s[1], st));
+  return FFPAT_OK;
+}
+
 int ffpat_opnorm(const ffpat_problem* problem, const void* c, const void* v0, int32_t iters,
                  double* opnorm_sq, void* ws, size_t ws_bytes, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -651,18 +687,20 @@ int ffpat_fb_solve(const ffpat_problem* problem, const void* c, const void* g, d
                    double step, int32_t max_iters, double tol, void* h_inout,
                    ffpat_fb_stats* stats, double* history, void* ws, size_t ws_bytes,
                    void* stream) {
-  return ffpat_fb_solve_ex(problem, c, g, nullptr, nullptr, lambda, step, max_iters, tol, h_inout,
-                           stats, history, ws, ws_bytes, stream);
+  return ffpat_fb_solve_ex(problem, c, g, nullptr, nullptr, FFPAT_REG_L1_POS, lambda, step,
+                           max_iters, tol, h_inout, stats, history, ws, ws_bytes, stream);
 }
 
 int ffpat_fb_solve_ex(const ffpat_problem* problem, const void* c, const void* g,
-                      const void* mask, const void* support, double lambda, double step,
-                      int32_t max_iters, double tol, void* h_inout, ffpat_fb_stats* stats,
-                      double* history, void* ws, size_t ws_bytes, void* stream) {
+                      const void* mask, const void* support, int32_t regulariser, double lambda,
+                      double step, int32_t max_iters, double tol, void* h_inout,
+                      ffpat_fb_stats* stats, double* history, void* ws, size_t ws_bytes,
+                      void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
   if (!g || !h_inout) return fail(FFPAT_EINVAL, "g or h is NULL");
+  TRY(check_regulariser(pl, regulariser, support, st));
   if (max_iters < 0 || max_iters > kMaxHist)
     return fail(FFPAT_EINVAL, "max_iters = %d outside [0, %d]", max_iters, kMaxHist);
   if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(FFPAT_EINVAL, "lambda must be >= 0");
@@ -680,7 +718,10 @@ int ffpat_fb_solve_ex(const ffpat_problem* problem, const void* c, const void* g
     double* hk = pl.hist + 8 * (size_t)k;
     const void* w = nullptr;
     TRY(data_gradient(pl, h_inout, g, &w, hk, st, mask));
-    TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st, nullptr, support));
+    if (regulariser == FFPAT_REG_GRAD2)
+      TRY(prox_grad_step(pl, h_inout, w, step, lambda, hk + 2, st));
+    else
+      TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st, nullptr, support));
     if (tol > 0.0) {
       double q[4];
       CK(cudaMemcpyAsync(q, hk + 2, sizeof q, cudaMemcpyDeviceToHost, st));
@@ -755,10 +796,19 @@ int ffpat_fb_two_step(const ffpat_problem* problem, const void* c, const void* G
                       double step, int32_t max_iters, double tol, void* h_inout,
                       ffpat_fb_stats* stats, double* history, void* ws, size_t ws_bytes,
                       void* stream) {
+  return ffpat_fb_two_step_ex(problem, c, G, FFPAT_REG_L1_POS, lambda, step, max_iters, tol,
+                              h_inout, stats, history, ws, ws_bytes, stream);
+}
+
+int ffpat_fb_two_step_ex(const ffpat_problem* problem, const void* c, const void* G,
+                         int32_t regulariser, double lambda, double step, int32_t max_iters,
+                         double tol, void* h_inout, ffpat_fb_stats* stats, double* history,
+                         void* ws, size_t ws_bytes, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
   if (!G || !h_inout) return fail(FFPAT_EINVAL, "G or h is NULL");
+  TRY(check_regulariser(pl, regulariser, nullptr, st));
   if (max_iters < 0 || max_iters > kMaxHist)
     return fail(FFPAT_EINVAL, "max_iters = %d outside [0, %d]", max_iters, kMaxHist);
   if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(FFPAT_EINVAL, "lambda must be >= 0");
@@ -780,7 +830,10 @@ int ffpat_fb_two_step(const ffpat_problem* problem, const void* c, const void* G
     TRY(run_wave_box(pl, h_inout, nullptr, &w, st));
     TRY(launch_resid_kap(pl, w, pl.v, pl.x, hk, st));
     TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
-    TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st));
+    if (regulariser == FFPAT_REG_GRAD2)
+      TRY(prox_grad_step(pl, h_inout, w, step, lambda, hk + 2, st));
+    else
+      TRY(launch_fb_update(pl, h_inout, w, step, lambda, hk + 2, st));
     if (tol > 0.0) {
       double q[4];
       CK(cudaMemcpyAsync(q, hk + 2, sizeof q, cudaMemcpyDeviceToHost, st));

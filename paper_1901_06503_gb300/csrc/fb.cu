@@ -199,6 +199,51 @@ __global__ void __launch_bounds__(kReduceThreads)
   }
 }
 
+// gradient-regulariser FB step, part 1: x = h - s w / kap (the argument of
+// the prox; the same arithmetic as k_fb_update before its shrinkage)
+template <typename T>
+__global__ void k_prox_prep(const T* __restrict__ h, const T* __restrict__ w,
+                            const T* __restrict__ kap, T* __restrict__ x, size_t len, double step,
+                            const double* __restrict__ step_dev) {
+  if (step_dev) step = *step_dev;
+  const T s = (T)step;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x)
+    x[i] = h[i] - s * (w[i] / kap[i]);
+}
+
+// part 2, after the prox wrote hn: the FP64 partials of R(h) = 1/2 <D h, D h>
+// / dx^2 (forward differences inside the box), ||h||^2, ||hn - h||^2, ||hn||^2
+// in the rows k_fb_update uses for |h|_1, ||h||^2, ...
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_prox_finish(const T* __restrict__ h, const T* __restrict__ hn, int n, double half_inv_dx2,
+                  double* __restrict__ partials) {
+  const size_t nn = (size_t)n * n, len = nn * n;
+  double rr = 0.0, hh = 0.0, dd = 0.0, qq = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / nn);
+    const double u = (double)h[i], v = (double)hn[i], df = v - u;
+    if (x + 1 < n) { const double e = (double)h[i + 1] - u; rr = fma(e, e, rr); }
+    if (y + 1 < n) { const double e = (double)h[i + n] - u; rr = fma(e, e, rr); }
+    if (z + 1 < n) { const double e = (double)h[i + nn] - u; rr = fma(e, e, rr); }
+    hh = fma(u, u, hh);
+    dd = fma(df, df, dd);
+    qq = fma(v, v, qq);
+  }
+  rr = block_sum(rr);
+  hh = block_sum(hh);
+  dd = block_sum(dd);
+  qq = block_sum(qq);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = rr * half_inv_dx2;
+    partials[kReduceBlocks + blockIdx.x] = hh;
+    partials[2 * kReduceBlocks + blockIdx.x] = dd;
+    partials[3 * kReduceBlocks + blockIdx.x] = qq;
+  }
+}
+
 // dst = 1 / sqrt(src): the step 1 / L from the last power-iteration norm,
 // the same arithmetic as the host's 1.0 / sqrt(.)
 __global__ void k_inv_sqrt(const double* __restrict__ src, double* __restrict__ dst) {
@@ -358,6 +403,35 @@ int launch_fb_update(const Plan& pl, void* h, const void* w, double step, double
   k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 4, dst);
   count_launch(2);
   return check_launch(__func__);
+}
+
+int launch_prox_prep(const Plan& pl, const void* h, const void* w, double step, void* x,
+                     cudaStream_t st, const double* step_dev) {
+  const unsigned nb = ew_blocks(pl.n3);
+  if (pl.prec == FFPAT_FP64)
+    k_prox_prep<double><<<nb, 256, 0, st>>>((const double*)h, (const double*)w,
+                                            (const double*)pl.kap, (double*)x, pl.n3, step, step_dev);
+  else
+    k_prox_prep<float><<<nb, 256, 0, st>>>((const float*)h, (const float*)w, (const float*)pl.kap,
+                                           (float*)x, pl.n3, step, step_dev);
+  count_launch();
+  return check_launch(__func__);
+}
+
+int launch_prox_finish(const Plan& pl, void* h, const void* hn, double* dst, cudaStream_t st) {
+  const double q = 0.5 / (pl.dx * pl.dx);
+  if (pl.prec == FFPAT_FP64)
+    k_prox_finish<double><<<kReduceBlocks, kReduceThreads, 0, st>>>(
+        (const double*)h, (const double*)hn, pl.n, q, pl.partials);
+  else
+    k_prox_finish<float><<<kReduceBlocks, kReduceThreads, 0, st>>>(
+        (const float*)h, (const float*)hn, pl.n, q, pl.partials);
+  k_finalize<<<1, kReduceThreads, 0, st>>>(pl.partials, 4, dst);
+  count_launch(2);
+  if (check_launch(__func__) != FFPAT_OK) return FFPAT_ECUDA;
+  if (cudaMemcpyAsync(h, hn, pl.n3 * pl.esize, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return check_launch("prox: copy of the iterate");
+  return FFPAT_OK;
 }
 
 int launch_resid_kap(const Plan& pl, const void* w, const void* g, void* x, double* dst,

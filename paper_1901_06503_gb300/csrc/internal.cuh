@@ -38,6 +38,8 @@ struct Plan {
   double* tab = nullptr;       // cos[nth], sin[nth] (double, host libm)
   float* tabf = nullptr;       // cos[nth], sin[nth] rounded to float
   int32_t* tabi = nullptr;     // cos[nth], sin[nth] in fixed point, round(. * 2^30)
+  void* dct = nullptr;         // DCT-II matrix C and C^T (n^2 each, element type), then mu[n] (double)
+  const double* dct_mu = nullptr;
 };
 // The plan as the wave kernels see it: the wave grid and its kappa.
 inline Plan wave_plan(const Plan& pl) {
@@ -126,6 +128,17 @@ int launch_debug_samples(const Plan& pl, int count, const int32_t* jkm, int32_t*
 int launch_speed_stats(const Plan& pl, const void* c, double* out3, cudaStream_t st);
 int launch_kappa(const Plan& pl, const void* c, cudaStream_t st);
 // out[i] = a[i] * kap[i] (mul = true) or a[i] / kap[i]
+// prox.cu: prox of the gradient regulariser, (I + a D^T D)^{-1} in -> out
+// through the scratch volumes s0, s1 (in, out != s0, s1; in == out allowed).
+size_t dct_bytes(int n, size_t esize);
+int upload_dct(const Plan& pl, cudaStream_t st);  // fills pl.dct (synchronises)
+int launch_prox_grad(const Plan& pl, double a, const void* in, void* out, void* s0, void* s1,
+                     cudaStream_t st);
+// FB step with that prox: x = h - s w / kap; then, after the prox wrote hn,
+// the statistics rows (R(h), ||h||^2, ||hn - h||^2, ||hn||^2) and h = hn.
+int launch_prox_prep(const Plan& pl, const void* h, const void* w, double step, void* x,
+                     cudaStream_t st, const double* step_dev = nullptr);
+int launch_prox_finish(const Plan& pl, void* h, const void* hn, double* dst, cudaStream_t st);
 // padding: box (n^3) -> interior of the wave grid (the rest of `wave` is left
 // as it is: zero by construction), and wave grid -> box
 int launch_embed(const Plan& pl, const void* box, void* wave, cudaStream_t st);

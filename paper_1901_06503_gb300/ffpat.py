@@ -25,6 +25,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ffpat.h")
 
 FP64, FP32, FP32_KAHAN = 0, 1, 2
 PRECOND_NONE, PRECOND_RAMP = 0, 1
+REG_L1_POS, REG_GRAD2 = 0, 1
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, ECANCELED, PENDING = 0, -1, -2, -3, -4, -5, -6, 1
 PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", FP32_KAHAN: "fp32-kahan"}
 
@@ -96,8 +97,11 @@ def _declare(L):
         "ffpat_fb_solve": (ctypes.c_int, [_PR, _P, _P, f64, f64, i32, f64, _P,
                                           ctypes.POINTER(FBStats), _P, _P, sz, _P]),
         "ffpat_fbp": (ctypes.c_int, [_PR, _P, _P, _P, sz, _P]),
-        "ffpat_fb_solve_ex": (ctypes.c_int, [_PR, _P, _P, _P, _P, f64, f64, i32, f64, _P,
+        "ffpat_fb_solve_ex": (ctypes.c_int, [_PR, _P, _P, _P, _P, i32, f64, f64, i32, f64, _P,
                                              ctypes.POINTER(FBStats), _P, _P, sz, _P]),
+        "ffpat_fb_two_step_ex": (ctypes.c_int, [_PR, _P, _P, i32, f64, f64, i32, f64, _P,
+                                                ctypes.POINTER(FBStats), _P, _P, sz, _P]),
+        "ffpat_prox_grad": (ctypes.c_int, [_PR, f64, _P, _P, _P, sz, _P]),
         "ffpat_fb_two_step": (ctypes.c_int, [_PR, _P, _P, f64, f64, i32, f64, _P,
                                              ctypes.POINTER(FBStats), _P, _P, sz, _P]),
         "ffpat_profile_enable": (ctypes.c_int, [i32]),
@@ -367,9 +371,10 @@ def fb_solve(prob, c, g, lam, step, max_iters, h=None, tol=0.0, ws=None, stream=
 
 
 def fb_solve_masked(prob, c, g, lam, step, max_iters, mask=None, support=None, h=None, tol=0.0,
-                    ws=None, stream=None, history=True):
+                    ws=None, stream=None, history=True, reg=0):
     """Algorithm 8 with the data mask chi_M (data-shaped 0/1) and the source
-    support chi_V (volume 0/1); None = full data / whole grid."""
+    support chi_V (volume 0/1); None = full data / whole grid.  reg = REG_GRAD2
+    uses R = 1/2 |grad h|^2 instead of l1 + positivity."""
     import torch
     h = torch.zeros(vol_shape(prob), dtype=torch_dtype(prob), device=g.device) if h is None else h
     ws, wp, wn = _ws(prob, ws, g.device)
@@ -379,12 +384,22 @@ def fb_solve_masked(prob, c, g, lam, step, max_iters, mask=None, support=None, h
     mp = _dev(mask, prob, data_shape(prob), "mask") if mask is not None else None
     sp = _dev(support, prob, vol_shape(prob), "support") if support is not None else None
     _check(lib().ffpat_fb_solve_ex(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
-                                   _dev(g, prob, data_shape(prob), "g"), mp, sp, float(lam),
+                                   _dev(g, prob, data_shape(prob), "g"), mp, sp, int(reg),
+                                   float(lam),
                                    float(step), int(max_iters), float(tol),
                                    _dev(h, prob, vol_shape(prob), "h"), ctypes.byref(st), hp, wp,
                                    wn, _stream(stream)))
     d = st.as_dict()
     return h, d, (hist[: d["iters_done"]] if history else None)
+
+
+def prox_grad(prob, f, a, out=None, ws=None, stream=None):
+    """(I + a D^T D)^{-1} f: the prox of s lambda R, R = 1/2 |grad h|^2, a = s lambda / dx^2."""
+    out = _empty(prob, vol_shape(prob), f) if out is None else out
+    ws, wp, wn = _ws(prob, ws, f.device)
+    _check(lib().ffpat_prox_grad(ctypes.byref(prob), float(a), _dev(f, prob, vol_shape(prob), "f"),
+                                 _dev(out, prob, vol_shape(prob), "out"), wp, wn, _stream(stream)))
+    return out
 
 
 def fbp(prob, G, out=None, ws=None, stream=None):
@@ -397,18 +412,20 @@ def fbp(prob, G, out=None, ws=None, stream=None):
 
 
 def fb_two_step(prob, c, G, lam, step, max_iters, h=None, tol=0.0, ws=None, stream=None,
-                history=True):
-    """Algorithm 9; returns (h, stats dict, history array [k, 4] or None)."""
+                history=True, reg=0):
+    """Algorithm 9; returns (h, stats dict, history array [k, 4] or None).
+    reg = REG_GRAD2: R = 1/2 |grad h|^2 (the paper's experiments)."""
     import torch
     h = torch.zeros(vol_shape(prob), dtype=torch_dtype(prob), device=G.device) if h is None else h
     ws, wp, wn = _ws(prob, ws, G.device)
     st = FBStats()
     hist = np.zeros((max(int(max_iters), 1), 4)) if history else None
     hp = hist.ctypes.data_as(ctypes.c_void_p) if history else None
-    _check(lib().ffpat_fb_two_step(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
-                                   _dev(G, prob, data_shape(prob), "G"), float(lam), float(step),
-                                   int(max_iters), float(tol), _dev(h, prob, vol_shape(prob), "h"),
-                                   ctypes.byref(st), hp, wp, wn, _stream(stream)))
+    _check(lib().ffpat_fb_two_step_ex(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
+                                      _dev(G, prob, data_shape(prob), "G"), int(reg), float(lam),
+                                      float(step), int(max_iters), float(tol),
+                                      _dev(h, prob, vol_shape(prob), "h"), ctypes.byref(st), hp,
+                                      wp, wn, _stream(stream)))
     d = st.as_dict()
     return h, d, (hist[: d["iters_done"]] if history else None)
 

@@ -151,7 +151,7 @@ def gaussian_random_field(n, corr_len, rng) -> np.ndarray:
     s = corr_len / math.sqrt(2.0)
     filt = np.exp(-0.5 * s * s * (k[:, None, None] ** 2 + k[None, :, None] ** 2
                                   + kr[None, None, :] ** 2))
-    f = np.fft.irfftn(np.fft.rfftn(w) * filt, s=(n, n, n))
+    f = np.fft.irfftn(np.fft.rfftn(w) * filt, s=(n, n, n), axes=(0, 1, 2))
     f -= f.mean()
     f /= f.std()
     return f
