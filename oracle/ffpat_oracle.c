@@ -191,22 +191,31 @@ void ffo_angles(int nth, double *cs, double *sn) {
 int ffo_ray_samples(int n) { return 2 * (int)ceil((double)n / sqrt(2.0)); }
 
 /* bilinear interpolation weights of the sample point (xi_k theta + s_m theta_perp)
- * in slice coordinates; returns the lower-left corner through i0/j0 */
-static void sample_point(int n, double cs, double sn, int k, int m, int ns, int *i0, int *j0,
-                         double *fx, double *fy) {
-  double dx = 2.0 / n;
-  double xi = -1.0 + (k + 0.5) * dx;           /* detector centre xi_k */
+ * in slice coordinates; returns the lower-left corner through i0/j0.  The
+ * slice has ng cells per axis of physical size dx = 2 / nimg, so it spans
+ * [-L, L] with L = ng / nimg (ng = nimg: the box [-1, 1]); detectors and ray
+ * samples are spaced dx. */
+static void sample_point_g(int ng, int nimg, double cs, double sn, int k, int m, int ns, int *i0,
+                           int *j0, double *fx, double *fy) {
+  double dx = 2.0 / nimg;
+  double L = (double)ng / nimg;
+  double xi = -L + (k + 0.5) * dx;             /* detector centre xi_k */
   double s = (m + 0.5 - ns / 2) * dx;          /* ray sample s_m */
   double x = xi * cs - s * sn;                 /* xi theta + s theta_perp, theta_perp = (-sin, cos) */
   double y = xi * sn + s * cs;
-  double half = n / 2.0;
-  double gx = (x + 1.0) * half - 0.5;          /* continuous grid index of x */
-  double gy = (y + 1.0) * half - 0.5;
+  double half = nimg / 2.0;
+  double gx = (x + L) * half - 0.5;            /* continuous grid index of x */
+  double gy = (y + L) * half - 0.5;
   double fl_x = floor(gx), fl_y = floor(gy);
   *i0 = (int)fl_x;
   *j0 = (int)fl_y;
   *fx = gx - fl_x;
   *fy = gy - fl_y;
+}
+
+static void sample_point(int n, double cs, double sn, int k, int m, int ns, int *i0, int *j0,
+                         double *fx, double *fy) {
+  sample_point_g(n, n, cs, sn, k, m, ns, i0, j0, fx, fy);
 }
 
 /* exposes the sample arithmetic for the bit-exact index-table check */
@@ -235,11 +244,14 @@ static double slice_at(const double *slice, int n, int iy, int ix) {
 
 /* P: g[j][l][k] = ds sum_m B(p[l]; xi_k theta_j + s_m theta_j^perp), eq. (4)
  * applied in each horizontal plane z_l (the X-ray transform is the 2D Radon
- * transform per plane), with zero-extended bilinear interpolation B. */
-void ffo_project(int n, int nth, const double *p, double *g) {
+ * transform per plane), with zero-extended bilinear interpolation B.  The
+ * planes have ng cells per axis of size ds = 2 / nimg (see sample_point_g);
+ * ng detectors, Ns = 2 ceil(ng / sqrt 2) samples per ray. */
+void ffo_project_g(int ng, int nimg, int nth, const double *p, double *g) {
+  int n = ng;
   double *cs = malloc(nth * sizeof(double)), *sn = malloc(nth * sizeof(double));
   int ns = ffo_ray_samples(n);
-  double ds = 2.0 / n;
+  double ds = 2.0 / nimg;
   ffo_angles(nth, cs, sn);
   int jl;
 #pragma omp parallel for schedule(static)
@@ -251,7 +263,7 @@ void ffo_project(int n, int nth, const double *p, double *g) {
       for (int m = 0; m < ns; ++m) {
         int i0, j0;
         double fx, fy;
-        sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+        sample_point_g(n, nimg, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
         double b = (1.0 - fx) * (1.0 - fy) * slice_at(slice, n, j0, i0) +
                    fx * (1.0 - fy) * slice_at(slice, n, j0, i0 + 1) +
                    (1.0 - fx) * fy * slice_at(slice, n, j0 + 1, i0) +
@@ -264,6 +276,8 @@ void ffo_project(int n, int nth, const double *p, double *g) {
   free(cs);
   free(sn);
 }
+
+void ffo_project(int n, int nth, const double *p, double *g) { ffo_project_g(n, n, nth, p, g); }
 
 /* selected rays of ffo_project: out[t] = g[j][l][k] for jlk[3t..3t+2] = (j, l, k);
  * the same loop as ffo_project, restricted, for spot checks on large grids */
@@ -300,10 +314,11 @@ static void scatter(double *slice, int n, int iy, int ix, double v) {
 /* P^T: the matrix transpose of ffo_project (the discrete counterpart of the
  * backprojection X* of Sec. 3.1): every sample spreads ds g[j][l][k] onto its
  * four bilinear corners with the same weights. */
-void ffo_backproject(int n, int nth, const double *g, double *out) {
+void ffo_backproject_g(int ng, int nimg, int nth, const double *g, double *out) {
+  int n = ng;
   double *cs = malloc(nth * sizeof(double)), *sn = malloc(nth * sizeof(double));
   int ns = ffo_ray_samples(n);
-  double ds = 2.0 / n;
+  double ds = 2.0 / nimg;
   ffo_angles(nth, cs, sn);
   memset(out, 0, (size_t)n * n * n * sizeof(double));
   int l;
@@ -316,7 +331,7 @@ void ffo_backproject(int n, int nth, const double *g, double *out) {
         for (int m = 0; m < ns; ++m) {
           int i0, j0;
           double fx, fy;
-          sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+          sample_point_g(n, nimg, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
           scatter(slice, n, j0, i0, (1.0 - fx) * (1.0 - fy) * w);
           scatter(slice, n, j0, i0 + 1, fx * (1.0 - fy) * w);
           scatter(slice, n, j0 + 1, i0, (1.0 - fx) * fy * w);
@@ -328,21 +343,27 @@ void ffo_backproject(int n, int nth, const double *g, double *out) {
   free(sn);
 }
 
+void ffo_backproject(int n, int nth, const double *g, double *out) {
+  ffo_backproject_g(n, n, nth, g, out);
+}
+
 /* ------------------------------------------------ preconditioner Lambda -- */
 
 /* Filter tap t_d of Lambda (Sec. 3.1, F Lambda Phi = |omega|/(4 pi) F Phi in
  * the detector variable): half the band-limited ramp filter on the detector
- * spacing dxi, times the quadrature weight dxi. */
-double ffo_ramp_tap(int n, int d) {
-  double dxi = 2.0 / n;
+ * spacing dxi = 2 / nimg, times the quadrature weight dxi. */
+double ffo_ramp_tap(int nimg, int d) {
+  double dxi = 2.0 / nimg;
   if (d < 0) d = -d;
   if (d == 0) return 1.0 / (8.0 * dxi);
   if (d % 2 == 0) return 0.0;
   return -1.0 / (2.0 * FFO_PI * FFO_PI * (double)d * (double)d * dxi);
 }
 
-/* (Lambda r)[j][l][k] = sum_{k'} t_{k-k'} r[j][l][k'] along each detector row */
-void ffo_ramp(int n, int nth, const double *r, double *out) {
+/* (Lambda r)[j][l][k] = sum_{k'} t_{k-k'} r[j][l][k'] along each detector row
+ * of ng detectors (nth ng rows) */
+void ffo_ramp_g(int ng, int nimg, int nth, const double *r, double *out) {
+  int n = ng;
   int row;
   int rows = nth * n;
 #pragma omp parallel for schedule(static)
@@ -351,11 +372,13 @@ void ffo_ramp(int n, int nth, const double *r, double *out) {
     double *oo = out + (size_t)row * n;
     for (int k = 0; k < n; ++k) {
       double acc = 0.0;
-      for (int kk = 0; kk < n; ++kk) acc += ffo_ramp_tap(n, k - kk) * rr[kk];
+      for (int kk = 0; kk < n; ++kk) acc += ffo_ramp_tap(nimg, k - kk) * rr[kk];
       oo[k] = acc;
     }
   }
 }
+
+void ffo_ramp(int n, int nth, const double *r, double *out) { ffo_ramp_g(n, n, nth, r, out); }
 
 /* ------------------------------- gradient regulariser R = 1/2 |grad h|^2 -- */
 
@@ -433,10 +456,13 @@ typedef struct {
 } ffo_setup_t;
 
 /* The wave grid: the image box [-1,1]^3 (n cells per axis, dx = 2/n) enlarged
- * by pad cells of the same size on every side, nw = n + 2 pad (the paper
- * computes on a domain larger than the source region so that the waves leave
- * it instead of reflecting, Sec. 5).  c is given on the wave grid; Nt follows
- * from its maximum and dx.  pad = 0 is the image box itself. */
+ * by pad cells of the same size on every side, nw = n + 2 pad.  This is the
+ * V_T of the wave model (Sec. 2.1: W_T maps sources supported in V to fields
+ * supported in a larger V_T, and the X-ray transform acts on V_T); the
+ * paper's experiments compute on such an enlarged domain (Sec. 5).  c is
+ * given on the wave grid and Nt follows from its maximum and dx; the data
+ * are the projections of the whole wave grid: nw planes of nw detectors of
+ * spacing dx.  pad = 0 is the box itself. */
 static int setup(ffo_setup_t *s, int n, int pad, double T, double cfl, int nth, int precond,
                  const double *c) {
   s->n = n;
@@ -457,7 +483,10 @@ static int setup(ffo_setup_t *s, int n, int pad, double T, double cfl, int nth, 
   return s->nt;
 }
 
-/* zero-extension of an image-grid volume (n^3) to the wave grid (nw^3) */
+static size_t wave_len(const ffo_setup_t *s) { return (size_t)s->nw * s->nw * s->nw; }
+static size_t data_len(const ffo_setup_t *s) { return (size_t)s->nth * s->nw * s->nw; }
+
+/* zero-extension E of an image-grid volume (n^3) to the wave grid (nw^3) */
 static void embed(int n, int pad, const double *in, double *out) {
   int nw = n + 2 * pad;
   memset(out, 0, (size_t)nw * nw * nw * sizeof(double));
@@ -466,7 +495,7 @@ static void embed(int n, int pad, const double *in, double *out) {
       for (int x = 0; x < n; ++x) out[at3(nw, z + pad, y + pad, x + pad)] = in[at3(n, z, y, x)];
 }
 
-/* restriction of a wave-grid volume to the image box (the transpose of embed) */
+/* its transpose E^T: the box cells of a wave-grid volume */
 static void restrict_box(int n, int pad, const double *in, double *out) {
   int nw = n + 2 * pad;
   for (int z = 0; z < n; ++z)
@@ -474,61 +503,52 @@ static void restrict_box(int n, int pad, const double *in, double *out) {
       for (int x = 0; x < n; ++x) out[at3(n, z, y, x)] = in[at3(nw, z + pad, y + pad, x + pad)];
 }
 
-/* R W_T E h on the image box: the source is zero outside the box, the wave
- * runs on the wave grid and the result is read inside the box. */
-static void wave_img(const ffo_setup_t *s, const double *h, double *out) {
+/* W_T E h: the field on the wave grid (nw^3) at time T of the source h on the box */
+static void wave_out(const ffo_setup_t *s, const double *h, double *out) {
   if (s->pad == 0) {
     ffo_wave(s->n, s->nt, s->kappa, h, out);
     return;
   }
-  size_t nw3 = (size_t)s->nw * s->nw * s->nw;
-  double *a = malloc(nw3 * sizeof(double)), *b = malloc(nw3 * sizeof(double));
+  double *a = malloc(wave_len(s) * sizeof(double));
   embed(s->n, s->pad, h, a);
-  ffo_wave(s->nw, s->nt, s->kappa, a, b);
-  restrict_box(s->n, s->pad, b, out);
+  ffo_wave(s->nw, s->nt, s->kappa, a, out);
   free(a);
-  free(b);
 }
 
-/* its transpose E^T W_T^T R^T */
-static void wave_img_adjoint(const ffo_setup_t *s, const double *g, double *out) {
+/* its transpose E^T W_T^T: a wave-grid volume to the box */
+static void wave_back(const ffo_setup_t *s, const double *g, double *out) {
   if (s->pad == 0) {
     ffo_wave_adjoint(s->n, s->nt, s->kappa, g, out);
     return;
   }
-  size_t nw3 = (size_t)s->nw * s->nw * s->nw;
-  double *a = malloc(nw3 * sizeof(double)), *b = malloc(nw3 * sizeof(double));
-  embed(s->n, s->pad, g, a);
-  ffo_wave_adjoint(s->nw, s->nt, s->kappa, a, b);
+  double *b = malloc(wave_len(s) * sizeof(double));
+  ffo_wave_adjoint(s->nw, s->nt, s->kappa, g, b);
   restrict_box(s->n, s->pad, b, out);
-  free(a);
   free(b);
 }
 
-/* W_T (transpose = 0) or W_T^T on the image box with pad cells of padding;
- * returns Nt */
-int ffo_wave_img(int n, int pad, double T, double cfl, const double *c, const double *in,
+/* transpose = 0: out (nw^3) = W_T E in (in: n^3); transpose = 1: out (n^3)
+ * = E^T W_T^T in (in: nw^3).  Returns Nt. */
+int ffo_wave_pad(int n, int pad, double T, double cfl, const double *c, const double *in,
                  double *out, int transpose) {
   ffo_setup_t s;
   setup(&s, n, pad, T, cfl, 0, 0, c);
   if (transpose)
-    wave_img_adjoint(&s, in, out);
+    wave_back(&s, in, out);
   else
-    wave_img(&s, in, out);
+    wave_out(&s, in, out);
   free(s.kappa);
   return s.nt;
 }
 
-/* g = P W_T h (Problem 1 with full data, M = R^2), the wave on the grid
- * padded by pad cells (c on that grid) */
+/* g = P W_T E h (Problem 1 with full data, M = R^2): g is n_angles x nw x nw */
 int ffo_forward_pad(int n, int pad, double T, double cfl, int nth, const double *c,
                     const double *h, double *g) {
   ffo_setup_t s;
-  size_t n3 = (size_t)n * n * n;
   setup(&s, n, pad, T, cfl, nth, 0, c);
-  double *p = malloc(n3 * sizeof(double));
-  wave_img(&s, h, p);
-  ffo_project(n, nth, p, g);
+  double *p = malloc(wave_len(&s) * sizeof(double));
+  wave_out(&s, h, p);
+  ffo_project_g(s.nw, n, nth, p, g);
   free(p);
   free(s.kappa);
   return s.nt;
@@ -538,15 +558,14 @@ int ffo_forward(int n, double T, double cfl, int nth, const double *c, const dou
   return ffo_forward_pad(n, 0, T, cfl, nth, c, h, g);
 }
 
-/* h = W_T^T P^T g */
+/* h = E^T W_T^T P^T g */
 int ffo_adjoint_pad(int n, int pad, double T, double cfl, int nth, const double *c,
                     const double *g, double *h) {
   ffo_setup_t s;
-  size_t n3 = (size_t)n * n * n;
   setup(&s, n, pad, T, cfl, nth, 0, c);
-  double *a = malloc(n3 * sizeof(double));
-  ffo_backproject(n, nth, g, a);
-  wave_img_adjoint(&s, a, h);
+  double *a = malloc(wave_len(&s) * sizeof(double));
+  ffo_backproject_g(s.nw, n, nth, g, a);
+  wave_back(&s, a, h);
   free(a);
   free(s.kappa);
   return s.nt;
@@ -563,23 +582,24 @@ static double dot(size_t len, const double *a, const double *b) {
 }
 
 /* grad = A^T chi Lambda chi (A h - g) with the data mask chi (Problem 1:
- * chi_M, NULL = full data); r_out = chi (A h - g); lr_out = chi Lambda r */
+ * chi_M, NULL = full data); r_out = chi (A h - g); lr_out = chi Lambda r.
+ * work: a wave-grid volume. */
 static void data_gradient_m(const ffo_setup_t *s, const double *h, const double *g,
                             const double *mask, double *r, double *lr, double *grad,
-                            double *work3) {
-  int n = s->n, nth = s->nth;
-  size_t nd = (size_t)nth * n * n;
-  wave_img(s, h, work3);
-  ffo_project(n, nth, work3, r);
+                            double *work) {
+  int n = s->n, nw = s->nw, nth = s->nth;
+  size_t nd = data_len(s);
+  wave_out(s, h, work);
+  ffo_project_g(nw, n, nth, work, r);
   for (size_t i = 0; i < nd; ++i) r[i] = (r[i] - g[i]) * (mask ? mask[i] : 1.0);
   if (s->precond)
-    ffo_ramp(n, nth, r, lr);
+    ffo_ramp_g(nw, n, nth, r, lr);
   else
     memcpy(lr, r, nd * sizeof(double));
   if (mask)
     for (size_t i = 0; i < nd; ++i) lr[i] *= mask[i];
-  ffo_backproject(n, nth, lr, work3);
-  wave_img_adjoint(s, work3, grad);
+  ffo_backproject_g(nw, n, nth, lr, work);
+  wave_back(s, work, grad);
 }
 
 /* Largest eigenvalue of A^T chi Lambda chi A (mask = chi_M, NULL = full data)
@@ -588,10 +608,11 @@ static void data_gradient_m(const ffo_setup_t *s, const double *h, const double 
 double ffo_power_ex(int n, int pad, double T, double cfl, int nth, int precond, const double *c,
                     const double *mask, const double *v0, int iters) {
   ffo_setup_t s;
-  size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
+  size_t n3 = (size_t)n * n * n;
   setup(&s, n, pad, T, cfl, nth, precond, c);
+  size_t nd = data_len(&s);
   double *v = malloc(n3 * sizeof(double)), *w = malloc(n3 * sizeof(double));
-  double *work3 = malloc(n3 * sizeof(double));
+  double *work3 = malloc(wave_len(&s) * sizeof(double));
   double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
   double *zero = calloc(nd, sizeof(double));
   double nv = sqrt(dot(n3, v0, v0));
@@ -636,10 +657,11 @@ int ffo_fb_ex(int n, int pad, double T, double cfl, int nth, int precond, const 
               const double *g, const double *mask, const double *support, int reg,
               double lambda, double step, int iters, double tol, double *h, double *stats) {
   ffo_setup_t s;
-  size_t n3 = (size_t)n * n * n, nd = (size_t)nth * n * n;
+  size_t n3 = (size_t)n * n * n;
   if (reg == 1 && support) return -1; /* the smoothing prox is defined on the whole box */
   setup(&s, n, pad, T, cfl, nth, precond, c);
-  double *grad = malloc(n3 * sizeof(double)), *work3 = malloc(n3 * sizeof(double));
+  size_t nd = data_len(&s);
+  double *grad = malloc(n3 * sizeof(double)), *work3 = malloc(wave_len(&s) * sizeof(double));
   double *r = malloc(nd * sizeof(double)), *lr = malloc(nd * sizeof(double));
   double dx = 2.0 / n;
   int k;
@@ -756,19 +778,23 @@ int ffo_grad(int n, double T, double cfl, int nth, const double *c, const double
  * backprojection); the discrete form (2 pi / (n_angles dx)) P^T Lambda G,
  * where 2 pi / n_angles is the angle weight of the backprojection over S^1
  * and 1/dx undoes the sample length of P^T. */
-void ffo_fbp(int n, int nth, const double *G, double *out) {
-  size_t nd = (size_t)nth * n * n, n3 = (size_t)n * n * n;
+void ffo_fbp_g(int ng, int nimg, int nth, const double *G, double *out) {
+  size_t nd = (size_t)nth * ng * ng, n3 = (size_t)ng * ng * ng;
   double *lr = malloc(nd * sizeof(double));
-  ffo_ramp(n, nth, G, lr);
-  ffo_backproject(n, nth, lr, out);
-  double w = 2.0 * FFO_PI / (nth * (2.0 / n));
+  ffo_ramp_g(ng, nimg, nth, G, lr);
+  ffo_backproject_g(ng, nimg, nth, lr, out);
+  double w = 2.0 * FFO_PI / (nth * (2.0 / nimg));
   for (size_t i = 0; i < n3; ++i) out[i] *= w;
   free(lr);
 }
 
-/* Algorithm 9: g = X^{-1} G, then h_{k+1} = prox_{s lambda R}(h_k - s W^T (W h_k - g))
- * with R = ||h||_1 + indicator(h >= 0) (reg = 0) or R = 1/2 |grad h|^2 (reg = 1).  stats[4 k + 0..3]: objective
- * 1/2 ||W h_k - g||^2 + lambda ||h_k||_1, ||W h_k - g||, relative change,
+void ffo_fbp(int n, int nth, const double *G, double *out) { ffo_fbp_g(n, n, nth, G, out); }
+
+/* Algorithm 9: g = X^{-1} G (on the wave grid), then
+ * h_{k+1} = prox_{s lambda R}(h_k - s W^T (W h_k - g)) with W = W_T E (box to
+ * wave grid) and R = ||h||_1 + indicator(h >= 0) (reg = 0) or
+ * R = 1/2 |grad h|^2 (reg = 1).  stats[4 k + 0..3]: objective
+ * 1/2 ||W h_k - g||^2 + lambda R(h_k), ||W h_k - g||, relative change,
  * ||h_{k+1}||. */
 int ffo_fb_two_step(int n, int pad, double T, double cfl, int nth, const double *c,
                     const double *G, int reg, double lambda, double step, int iters, double tol,
@@ -776,15 +802,16 @@ int ffo_fb_two_step(int n, int pad, double T, double cfl, int nth, const double 
   ffo_setup_t s;
   size_t n3 = (size_t)n * n * n;
   setup(&s, n, pad, T, cfl, nth, 0, c);
-  double *g = malloc(n3 * sizeof(double)), *r = malloc(n3 * sizeof(double));
+  size_t nw3 = wave_len(&s);
+  double *g = malloc(nw3 * sizeof(double)), *r = malloc(nw3 * sizeof(double));
   double *grad = malloc(n3 * sizeof(double)), *prox = malloc(n3 * sizeof(double));
   double dx = 2.0 / n;
-  ffo_fbp(n, nth, G, g);
+  ffo_fbp_g(s.nw, n, nth, G, g);
   int k;
   for (k = 0; k < iters; ++k) {
-    wave_img(&s, h, r);
-    for (size_t i = 0; i < n3; ++i) r[i] -= g[i];
-    wave_img_adjoint(&s, r, grad);
+    wave_out(&s, h, r);
+    for (size_t i = 0; i < nw3; ++i) r[i] -= g[i];
+    wave_back(&s, r, grad);
     double l1 = 0.0, hh = 0.0, dd = 0.0, nn = 0.0;
     if (reg == 1) {
       l1 = 0.5 * ffo_grad_energy(n, h) / (dx * dx);
@@ -807,8 +834,8 @@ int ffo_fb_two_step(int n, int pad, double T, double cfl, int nth, const double 
     }
     double rel = sqrt(dd) / (sqrt(hh) > 1e-300 ? sqrt(hh) : 1e-300);
     if (stats) {
-      stats[4 * k + 0] = 0.5 * dot(n3, r, r) + lambda * l1;
-      stats[4 * k + 1] = sqrt(dot(n3, r, r));
+      stats[4 * k + 0] = 0.5 * dot(nw3, r, r) + lambda * l1;
+      stats[4 * k + 1] = sqrt(dot(nw3, r, r));
       stats[4 * k + 2] = rel;
       stats[4 * k + 3] = sqrt(nn);
     }

@@ -74,9 +74,13 @@ def lib():
                                           ctypes.c_double, ctypes.c_int, _D, _D, _D]
             L.ffo_adjoint_pad.restype = ctypes.c_int
             L.ffo_adjoint_pad.argtypes = L.ffo_forward_pad.argtypes
-            L.ffo_wave_img.restype = ctypes.c_int
-            L.ffo_wave_img.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+            L.ffo_wave_pad.restype = ctypes.c_int
+            L.ffo_wave_pad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, _D, _D, _D, ctypes.c_int]
+            L.ffo_project_g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_backproject_g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_ramp_g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+            L.ffo_fbp_g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
             L.ffo_power_ex.restype = ctypes.c_double
             L.ffo_power_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _D,
@@ -177,11 +181,13 @@ def sample_points(n: int, nth: int, jkm) -> tuple[np.ndarray, np.ndarray]:
     return ij, f
 
 
-def project(p, nth: int) -> np.ndarray:
+def project(p, nth: int, nimg: int | None = None) -> np.ndarray:
+    """P of the planes of p (ng^3); the cells have size 2 / nimg (default ng:
+    the box [-1, 1]^3; nimg < ng: a wave grid padded around the box)."""
     p = _f64(p)
     n = p.shape[0]
     g = np.empty((nth, n, n))
-    lib().ffo_project(n, nth, _p(p), _p(g))
+    lib().ffo_project_g(n, nimg or n, nth, _p(p), _p(g))
     return g
 
 
@@ -194,10 +200,10 @@ def project_rays(p, nth: int, jlk) -> np.ndarray:
     return out
 
 
-def backproject(g, n: int) -> np.ndarray:
+def backproject(g, n: int, nimg: int | None = None) -> np.ndarray:
     g = _f64(g)
     out = np.empty((n, n, n))
-    lib().ffo_backproject(n, g.shape[0], _p(g), _p(out))
+    lib().ffo_backproject_g(n, nimg or n, g.shape[0], _p(g), _p(out))
     return out
 
 
@@ -205,10 +211,10 @@ def ramp_tap(n: int, d: int) -> float:
     return lib().ffo_ramp_tap(n, d)
 
 
-def ramp(r) -> np.ndarray:
+def ramp(r, nimg: int | None = None) -> np.ndarray:
     r = _f64(r)
     out = np.empty_like(r)
-    lib().ffo_ramp(r.shape[1], r.shape[0], _p(r), _p(out))
+    lib().ffo_ramp_g(r.shape[1], nimg or r.shape[1], r.shape[0], _p(r), _p(out))
     return out
 
 
@@ -221,11 +227,13 @@ def _image_n(c, pad: int) -> int:
 
 def forward(c, h, T: float, nth: int, cfl: float = 0.3, pad: int = 0) -> np.ndarray:
     """g = P W_T h (Problem 1, full data).  pad > 0: the wave runs on the grid
-    enlarged by pad cells per side (c given on that grid, h on the image box)."""
+    enlarged by pad cells per side (c given on that grid, h on the image box)
+    and g holds the projections of that whole grid, n_angles x nw x nw."""
     c, h = _f64(c), _f64(h)
     n = h.shape[0]
     assert _image_n(c, pad) == n
-    g = np.empty((nth, n, n))
+    nw = n + 2 * pad
+    g = np.empty((nth, nw, nw))
     lib().ffo_forward_pad(n, pad, T, cfl, nth, _p(c), _p(h), _p(g))
     return g
 
@@ -239,12 +247,14 @@ def adjoint(c, g, T: float, cfl: float = 0.3, pad: int = 0) -> np.ndarray:
     return h
 
 
-def wave_img(c, u, T: float, pad: int, transpose: bool = False, cfl: float = 0.3) -> np.ndarray:
-    """W_T (or W_T^T) restricted to the image box of the grid padded by pad cells."""
+def wave_pad(c, u, T: float, pad: int, transpose: bool = False, cfl: float = 0.3) -> np.ndarray:
+    """W_T E (box source u -> field on the wave grid padded by pad cells), or
+    its transpose E^T W_T^T (wave-grid volume u -> box)."""
     c, u = _f64(c), _f64(u)
     n = _image_n(c, pad)
-    out = np.empty((n, n, n))
-    lib().ffo_wave_img(n, pad, T, cfl, _p(c), _p(u), _p(out), int(bool(transpose)))
+    m = n if transpose else n + 2 * pad
+    out = np.empty((m, m, m))
+    lib().ffo_wave_pad(n, pad, T, cfl, _p(c), _p(u), _p(out), int(bool(transpose)))
     return out
 
 
@@ -279,12 +289,13 @@ def grad(c, h, grad_g, T: float, cfl: float = 0.3):
     return gh, gc
 
 
-def fbp(G) -> np.ndarray:
-    """X^{-1} G = (2 pi / (n_angles dx)) P^T Lambda G, plane by plane."""
+def fbp(G, nimg: int | None = None) -> np.ndarray:
+    """X^{-1} G = (2 pi / (n_angles dx)) P^T Lambda G, plane by plane (cells
+    of size dx = 2 / nimg, default the grid size of G)."""
     G = _f64(G)
     n = G.shape[1]
     out = np.empty((n, n, n))
-    lib().ffo_fbp(n, G.shape[0], _p(G), _p(out))
+    lib().ffo_fbp_g(n, nimg or n, G.shape[0], _p(G), _p(out))
     return out
 
 

@@ -529,48 +529,97 @@ def test_masked_fb_kkt():
 # ------------------------------------------ padded wave grid (Sec. 5 setup) --
 
 def test_padded_wave_matches_free_space_solution():
-    """With the wave grid padded, the outgoing spherical wave of an off-centre
-    Gaussian leaves the image box instead of reflecting at its faces: on the
-    box the padded W_T follows the free-space radial solution (c = 1) with the
-    leapfrog's accuracy, while the box-sized operator (Dirichlet walls at
-    the faces) carries the reflected wave."""
+    """With the wave grid padded (V_T larger than the box V) the outgoing
+    spherical wave of an off-centre Gaussian travels past the box faces: on the
+    whole wave grid W_T E follows the free-space radial solution (c = 1), while
+    the box-sized operator (Dirichlet walls at the faces) carries the wave
+    reflected back into the box."""
     x0, sigma, T = 0.45, 0.08, 0.75
     errs = []
     for n in (32, 64):
         pad = n // 2
+        f = lambda s: np.exp(-s * s / (2 * sigma * sigma))  # noqa: E731
         x = axis(n)
         r = np.sqrt((x[None, None, :] - x0) ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2)
-        f = lambda s: np.exp(-s * s / (2 * sigma * sigma))  # noqa: E731
-        want = spherical_solution(r, f, T)
-        got = o.wave_img(np.ones((n + 2 * pad,) * 3), f(r), T, pad)
-        errs.append(rel(got, want))
+        xw = padded_axis(n, pad)
+        rw = np.sqrt((xw[None, None, :] - x0) ** 2 + xw[None, :, None] ** 2
+                     + xw[:, None, None] ** 2)
+        got = o.wave_pad(np.ones((n + 2 * pad,) * 3), f(r), T, pad)
+        assert got.shape == (n + 2 * pad,) * 3
+        errs.append(rel(got, spherical_solution(rw, f, T)))
         if n == 64:
-            walls = rel(o.wave_img(np.ones((n,) * 3), f(r), T, 0), want)
-    # N = 32 is coarse for sigma = 0.08 (pre-asymptotic, order ~2.6 between
-    # the two grids): ask for at least second-order-like decay
+            walls = rel(o.wave_pad(np.ones((n,) * 3), f(r), T, 0), spherical_solution(r, f, T))
+            inbox = rel(got[pad:-pad, pad:-pad, pad:-pad], spherical_solution(r, f, T))
+    # N = 32 is coarse for sigma = 0.08 (pre-asymptotic): ask for at least
+    # second-order-like decay
     assert errs[1] < 2e-2 and errs[0] / errs[1] > 3.5, errs
-    assert walls > 10 * errs[1], (walls, errs)
+    assert walls > 10 * inbox, (walls, inbox)
+
+
+def test_padded_dalembert_past_the_box():
+    """The 1D reduction of Sec. 2.2 on the padded grid: the plane integrals
+    sum_l dz g[j, l, k] of the data of the whole wave grid follow
+    1/2 (Rh(xi - T) + Rh(xi + T)) with xi on the padded detector line, also
+    once the waves have left the box (T = 0.8 here, c = 1)."""
+    x0, sigma, amp, T, nth = (0.3, -0.2, 0.1), 0.08, 0.9, 0.8, 5
+    errs = []
+    for n in (32, 64):
+        pad = n // 2
+        x = axis(n)
+        gz = np.exp(-((x - x0[2]) ** 2) / (2 * sigma**2))
+        gy = np.exp(-((x - x0[1]) ** 2) / (2 * sigma**2))
+        gx = np.exp(-((x - x0[0]) ** 2) / (2 * sigma**2))
+        h = amp * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+        g = o.forward(np.ones((n + 2 * pad,) * 3), h, T, nth, pad=pad)
+        assert g.shape == (nth, n + 2 * pad, n + 2 * pad)
+        got = g.sum(axis=1) * (2.0 / n)
+        th = np.pi * np.arange(nth) / nth
+        pr = x0[0] * np.cos(th) + x0[1] * np.sin(th)
+        Rh = lambda s: amp * 2 * np.pi * sigma**2 * np.exp(-((s - pr[:, None]) ** 2) / (2 * sigma**2))  # noqa
+        xi = padded_axis(n, pad)
+        errs.append(rel(got, 0.5 * (Rh(xi[None, :] - T) + Rh(xi[None, :] + T))))
+    assert errs[1] < 1.5e-2 and 3.0 < errs[0] / errs[1] < 5.0, errs
 
 
 def test_padded_operator_transpose_dense():
-    """The padded A (zero-extend, W_T on the wave grid, restrict, P) and its
-    transpose, as dense matrices (5^3 box, 2 cells of padding, variable c)."""
+    """The padded A (zero-extend, W_T on the wave grid, P of the wave grid)
+    and its transpose, as dense matrices (5^3 box, 2 cells of padding, variable
+    c); likewise W_T E and E^T W_T^T."""
     n, pad, nth, T = 5, 2, 4, 0.5
-    c = random_speed(n + 2 * pad, 131)
+    nw = n + 2 * pad
+    c = random_speed(nw, 131)
     A = dense(lambda h: o.forward(c, h, T, nth, pad=pad), n**3, (n, n, n))
-    At = dense(lambda g: o.adjoint(c, g, T, pad=pad), nth * n * n, (nth, n, n))
+    At = dense(lambda g: o.adjoint(c, g, T, pad=pad), nth * nw * nw, (nth, nw, nw))
+    assert A.shape == (nth * nw * nw, n**3)
     assert np.max(np.abs(At - A.T)) <= 1e-13 * np.abs(A).max()
-    W = dense(lambda h: o.wave_img(c, h, T, pad), n**3, (n, n, n))
-    Wt = dense(lambda h: o.wave_img(c, h, T, pad, transpose=True), n**3, (n, n, n))
+    W = dense(lambda h: o.wave_pad(c, h, T, pad), n**3, (n, n, n))
+    Wt = dense(lambda u: o.wave_pad(c, u, T, pad, transpose=True), nw**3, (nw, nw, nw))
     assert np.max(np.abs(Wt - W.T)) <= 1e-13 * np.abs(W).max()
+
+
+def test_padded_projection_is_the_scaled_grid_projection():
+    """P on a grid of cells of size 2 / nimg is the same index geometry as on
+    the unit box, with samples of length 2 / nimg: P_nimg = (ng / nimg) P_ng;
+    likewise Lambda_nimg = (nimg / ng) Lambda_ng (taps ~ 1 / dxi); the
+    filtered backprojection scales by nimg / ng, so that as an inverse of P it
+    is unchanged: FBP_nimg P_nimg = FBP_ng P_ng."""
+    ng, nimg, nth = 14, 10, 6
+    p = random_volume(ng, 141)
+    assert np.max(np.abs(o.project(p, nth, nimg) - (ng / nimg) * o.project(p, nth))) < 1e-13
+    r = random_data(nth, ng, 142)
+    assert np.max(np.abs(o.ramp(r, nimg) - (nimg / ng) * o.ramp(r))) < 1e-12
+    assert np.max(np.abs(o.backproject(r, ng, nimg) - (ng / nimg) * o.backproject(r, ng))) < 1e-13
+    assert np.max(np.abs(o.fbp(r, nimg) - (nimg / ng) * o.fbp(r))) < 1e-12
+    a, b = o.fbp(o.project(p, nth, nimg), nimg), o.fbp(o.project(p, nth))
+    assert np.max(np.abs(a - b)) < 1e-12 * np.abs(b).max()
 
 
 def test_padding_past_the_domain_of_dependence():
     """The stencil reaches two cells per step, so once the padding has at least
-    Nt cells the walls cannot reach the box within Nt steps: the data are then
-    the same, bit for bit, for any larger padding (c a smooth function of
-    position, the same on the shared cells); thin padding changes them."""
-    n, nth, T = 8, 5, 0.25
+    Nt cells the walls cannot reach the box within Nt steps: the box part of
+    W_T E h is then the same, bit for bit, for any larger padding (c a smooth
+    function of position, the same on the shared cells); thin padding changes it."""
+    n, T = 8, 0.25
     h = random_volume(n, 133)
 
     def speed(pad):
@@ -578,12 +627,15 @@ def test_padding_past_the_domain_of_dependence():
         r2 = x[None, None, :] ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2
         return 1.0 + 0.2 * np.exp(-r2 / 0.09)
 
+    def box(u, pad):
+        return u[pad:pad + n, pad:pad + n, pad:pad + n]
+
     nt, _ = o.time_steps(n, T, 0.3, float(speed(0).max()))
     assert nt >= 3
-    g1 = o.forward(speed(nt), h, T, nth, pad=nt)
-    g2 = o.forward(speed(nt + 3), h, T, nth, pad=nt + 3)
-    assert np.array_equal(g1, g2)
-    assert not np.array_equal(o.forward(speed(1), h, T, nth, pad=1), g1)
+    w1 = box(o.wave_pad(speed(nt), h, T, nt), nt)
+    w2 = box(o.wave_pad(speed(nt + 3), h, T, nt + 3), nt + 3)
+    assert np.array_equal(w1, w2)
+    assert not np.array_equal(box(o.wave_pad(speed(1), h, T, 1), 1), w1)
     assert np.array_equal(padded_axis(n, 0), axis(n))
     assert np.array_equal(padded_axis(n, 3)[3:-3], axis(n))
 
@@ -696,5 +748,5 @@ def test_two_step_gradient_regulariser_first_iterate():
     G = random_data(nth, n, 164)
     dx = 2.0 / n
     h1, _, _ = o.fb_two_step(c, G, T, lam, s, 1, reg=1)
-    want = o.prox_grad(s * o.wave_img(c, o.fbp(G), T, 0, transpose=True), s * lam / dx**2)
+    want = o.prox_grad(s * o.wave_pad(c, o.fbp(G), T, 0, transpose=True), s * lam / dx**2)
     assert np.max(np.abs(h1 - want)) < 1e-13 * np.abs(want).max()
