@@ -22,15 +22,18 @@
  *            xi_k theta + s_m theta_perp, theta_perp = (-sin, cos);
  *   data     g[j][l][k] = dx sum_m B(p[l]; ...), layout [theta][z][xi],
  *            n_angles * N * N elements.
- *   padding  pad > 0 runs the wave on a larger grid than the image box: Nw =
- *            N + 2 pad points per axis with the same dx (the box
- *            [-1,1]^3 plus pad cells on every side, the enlarged
+ *   padding  pad > 0 runs the wave on a larger grid than the source box: Nw =
+ *            N + 2 pad points per axis with the same dx, spanning [-L, L]^3,
+ *            L = Nw / N (the V_T of the wave model, Sec. 2.1, and the enlarged
  *            computational domain of the paper's experiments, Sec. 5), so that
- *            waves leave the box instead of reflecting at its faces.  The
- *            source h, the image-domain results and the support are N^3 on
- *            the box; W h means: zero-extend h to the wave grid, step there,
- *            read the box.  The sound speed c is given on the wave grid,
- *            Nw^3 elements (Nw = N when pad = 0), and Nt uses its maximum.
+ *            waves travel past the box instead of reflecting at its faces.
+ *            The source h, the image-domain results and the support are N^3
+ *            on the box; W zero-extends h to the wave grid and steps there;
+ *            P projects the whole wave grid: Nw planes of Nw detectors
+ *            xi_k = -L + (k + 1/2) dx, Ns = 2 ceil(Nw / sqrt 2) samples, so
+ *            the data are n_angles Nw^2 values.  The sound speed c is given
+ *            on the wave grid, Nw^3 elements, and Nt uses its maximum.  With
+ *            pad = 0, Nw = N and L = 1 throughout.
  * The adjoint entry points apply the exact matrix transposes of these
  * discrete operators, so <A h, g> = <h, A^T g> up to rounding.
  *
@@ -88,7 +91,7 @@ typedef enum {
 
 /* Problem statement (Problem 1 of Sec. 2.1 with full data). */
 typedef struct {
-  int32_t n;         /* grid points per axis N (1..2048); N^3 volume, N detectors, N planes */
+  int32_t n;         /* grid points per axis N (1..2048) of the source box; N^3 volume */
   double T;          /* final time T > 0 */
   double cfl;        /* dt <= cfl dx / c_max; 0 < cfl <= 0.5 (stability of L4 leapfrog) */
   int32_t n_angles;  /* number of projection directions, >= 1 */
@@ -135,7 +138,7 @@ int ffpat_debug_tables(const ffpat_problem *problem, double *cos_sin);
 int ffpat_debug_samples(const ffpat_problem *problem, int32_t count, const int32_t *jkm,
                         int32_t *ij, double *f, void *stream);
 
-/* g = P W h  (eq. (4) composed with W of eq. (3)).  c: Nw^3, h: N^3; g: n_angles N^2. */
+/* g = P W h  (eq. (4) composed with W of eq. (3)).  c: Nw^3, h: N^3; g: n_angles Nw^2. */
 int ffpat_forward(const ffpat_problem *problem, const void *c, const void *h, void *g, void *ws,
                   size_t ws_bytes, void *stream);
 
@@ -144,12 +147,12 @@ int ffpat_forward(const ffpat_problem *problem, const void *c, const void *h, vo
 int ffpat_adjoint(const ffpat_problem *problem, const void *c, const void *g, void *h, void *ws,
                   size_t ws_bytes, void *stream);
 
-/* out = W in (transpose = 0) or W^T in (transpose = 1); N^3 each on the image
- * box (eq. (3)); with padding, the box restriction of W on the wave grid. */
+/* out = W in (transpose = 0; in: N^3 box source, out: Nw^3 field) or
+ * out = W^T in (transpose = 1; in: Nw^3, out: N^3), eq. (3). */
 int ffpat_wave(const ffpat_problem *problem, const void *c, const void *in, void *out,
                int32_t transpose, void *ws, size_t ws_bytes, void *stream);
 
-/* g = P p (eq. (4)); p: N^3, g: n_angles N^2.  No workspace. */
+/* g = P p (eq. (4)) on the data grid; p: Nw^3, g: n_angles Nw^2.  No workspace. */
 int ffpat_project(const ffpat_problem *problem, const void *p, void *g, void *stream);
 
 /* h = P^T g, the exact transpose of ffpat_project (backprojection X^* of Sec. 3.1). */
@@ -192,7 +195,7 @@ int ffpat_fb_solve(const ffpat_problem *problem, const void *c, const void *g, d
 /* ---- The two-step method (Algorithm 9, Sec. 4.1), the paper's comparison:
  * first g = X^{-1} G plane by plane, then FB on 1/2 ||W h - g||^2 + lambda R. */
 
-/* out (N^3) = X^{-1} G = X^* Lambda G (Sec. 3.1: filtered backprojection in
+/* out (Nw^3) = X^{-1} G = X^* Lambda G (Sec. 3.1: filtered backprojection in
  * every plane z = const), discretised as (2 pi / (n_angles dx)) P^T Lambda G:
  * 2 pi / n_angles is the angle weight of the backprojection over S^1 (the data
  * over [0, pi) count twice) and 1/dx undoes the sample length of P^T. */
@@ -213,7 +216,7 @@ int ffpat_fb_two_step(const ffpat_problem *problem, const void *c, const void *G
  *   r_k = A^T chi_M Lambda chi_M (A h_k - g),
  *   h_{k+1} = chi_V max(h_k - s r_k - s lambda, 0),
  * i.e. FB on 1/2 <Lambda chi_M (A h - g), chi_M (A h - g)> + lambda (||h||_1
- * + indicator(h >= 0) + indicator(supp h in V)).  mask (n_angles N^2) and
+ * + indicator(h >= 0) + indicator(supp h in V)).  mask (n_angles Nw^2) and
  * support (N^3) are device arrays of 0/1 values of the problem's element
  * type, or NULL for full data / the whole grid (then this is
  * ffpat_fb_solve).  The power-iteration step uses the masked operator.

@@ -213,13 +213,9 @@ static void sample_point_g(int ng, int nimg, double cs, double sn, int k, int m,
   *fy = gy - fl_y;
 }
 
-static void sample_point(int n, double cs, double sn, int k, int m, int ns, int *i0, int *j0,
-                         double *fx, double *fy) {
-  sample_point_g(n, n, cs, sn, k, m, ns, i0, j0, fx, fy);
-}
-
 /* exposes the sample arithmetic for the bit-exact index-table check */
-void ffo_sample_points(int n, int nth, int count, const int32_t *jkm, int32_t *ij, double *f) {
+void ffo_sample_points_g(int n, int nimg, int nth, int count, const int32_t *jkm, int32_t *ij,
+                         double *f) {
   double *cs = malloc(nth * sizeof(double)), *sn = malloc(nth * sizeof(double));
   int ns = ffo_ray_samples(n);
   ffo_angles(nth, cs, sn);
@@ -227,7 +223,7 @@ void ffo_sample_points(int n, int nth, int count, const int32_t *jkm, int32_t *i
     int j = jkm[3 * t], k = jkm[3 * t + 1], m = jkm[3 * t + 2];
     int i0, j0;
     double fx, fy;
-    sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+    sample_point_g(n, nimg, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
     ij[2 * t] = i0;
     ij[2 * t + 1] = j0;
     f[2 * t] = fx;
@@ -235,6 +231,10 @@ void ffo_sample_points(int n, int nth, int count, const int32_t *jkm, int32_t *i
   }
   free(cs);
   free(sn);
+}
+
+void ffo_sample_points(int n, int nth, int count, const int32_t *jkm, int32_t *ij, double *f) {
+  ffo_sample_points_g(n, n, nth, count, jkm, ij, f);
 }
 
 static double slice_at(const double *slice, int n, int iy, int ix) {
@@ -293,7 +293,7 @@ void ffo_project_rays(int n, int nth, const double *p, int count, const int32_t 
     for (int m = 0; m < ns; ++m) {
       int i0, j0;
       double fx, fy;
-      sample_point(n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
+      sample_point_g(n, n, cs[j], sn[j], k, m, ns, &i0, &j0, &fx, &fy);
       double b = (1.0 - fx) * (1.0 - fy) * slice_at(slice, n, j0, i0) +
                  fx * (1.0 - fy) * slice_at(slice, n, j0, i0 + 1) +
                  (1.0 - fx) * fy * slice_at(slice, n, j0 + 1, i0) +

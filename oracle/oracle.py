@@ -58,6 +58,8 @@ def lib():
             L.ffo_ray_samples.restype = ctypes.c_int
             L.ffo_ray_samples.argtypes = [ctypes.c_int]
             L.ffo_sample_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _I32, _I32, _D]
+            L.ffo_sample_points_g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, _I32, _I32, _D]
             L.ffo_project.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
             L.ffo_project_rays.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _I32, _D]
             L.ffo_backproject.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
@@ -171,13 +173,14 @@ def ray_samples(n: int) -> int:
     return lib().ffo_ray_samples(n)
 
 
-def sample_points(n: int, nth: int, jkm) -> tuple[np.ndarray, np.ndarray]:
-    """(i0, j0) corners and (fx, fy) fractions of the ray samples (j, k, m)."""
+def sample_points(n: int, nth: int, jkm, nimg: int | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """(i0, j0) corners and (fx, fy) fractions of the ray samples (j, k, m) on
+    a data grid of n cells of size 2 / nimg (default n)."""
     jkm = np.ascontiguousarray(jkm, dtype=np.int32).reshape(-1, 3)
     ij = np.empty((jkm.shape[0], 2), dtype=np.int32)
     f = np.empty((jkm.shape[0], 2), dtype=np.float64)
-    lib().ffo_sample_points(n, nth, jkm.shape[0], jkm.ctypes.data_as(_I32),
-                            ij.ctypes.data_as(_I32), _p(f))
+    lib().ffo_sample_points_g(n, nimg or n, nth, jkm.shape[0], jkm.ctypes.data_as(_I32),
+                              ij.ctypes.data_as(_I32), _p(f))
     return ij, f
 
 

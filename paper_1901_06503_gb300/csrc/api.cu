@@ -96,8 +96,9 @@ static int validate(const ffpat_problem* pr, Plan& pl) {
   if (pr->pad < 0 || pr->pad > 2048 || pr->n + 2 * pr->pad > 4096)
     return fail(FFPAT_EINVAL, "pad = %d outside [0, 2048] or N + 2 pad > 4096", pr->pad);
   pl.n = pr->n;
+  pl.nimg = pr->n;
   pl.nth = pr->n_angles;
-  pl.ns = 2 * (int)ceil((double)pr->n / sqrt(2.0));
+  pl.ns = 2 * (int)ceil((double)(pr->n + 2 * pr->pad) / sqrt(2.0));
   pl.prec = pr->precision;
   pl.precond = pr->precond;
   pl.T = pr->T;
@@ -107,7 +108,7 @@ static int validate(const ffpat_problem* pr, Plan& pl) {
   pl.pad = pr->pad;
   pl.nw = pr->n + 2 * pr->pad;
   pl.nw3 = (size_t)pl.nw * pl.nw * pl.nw;
-  pl.nd = (size_t)pl.nth * pl.n * pl.n;
+  pl.nd = (size_t)pl.nth * pl.nw * pl.nw;
   pl.esize = pl.prec == FFPAT_FP64 ? 8 : 4;
   return FFPAT_OK;
 }
@@ -131,6 +132,7 @@ static size_t carve(Plan& pl, void* ws) {
   pl.v = take(vol);
   pl.xw = pl.pad ? take(wvol) : nullptr;
   pl.xo = pl.pad ? take(vol) : nullptr;
+  pl.xg = pl.pad ? take(wvol) : nullptr;
   pl.r = take(dat);
   pl.r2 = take(dat);
   pl.partials = (double*)take(sizeof(double) * kNumQuant * kReduceBlocks);
@@ -217,11 +219,7 @@ static int setup_speed(Plan& pl, const void* c, cudaStream_t st) {
   pl.cmax = h3[0];
   TRY(time_steps(pl, pl.cmax, &pl.nt, &pl.dt));
   TRY(launch_kappa(wave_plan(pl), c, st));
-  if (pl.pad) {
-    TRY(launch_restrict(pl, pl.kapw, pl.kap, st));
-    // the padded W's input buffer: only its box cells are ever written
-    CK(cudaMemsetAsync(pl.xw, 0, pl.nw3 * pl.esize, st));
-  }
+  if (pl.pad) TRY(launch_restrict(pl, pl.kapw, pl.kap, st));
   return FFPAT_OK;
 }
 
@@ -430,46 +428,55 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
 }
 
 
-// W on the image box.  Without padding this is run_wave; with padding the
-// input is zero-extended to the wave grid, the time loop runs there and the
-// box cells of the result are copied out (to `out`, else to pl.xo).
-static int run_wave_box(const Plan& pl, const void* in, void* out, const void** result,
-                        cudaStream_t st) {
-  if (pl.pad == 0) return run_wave(pl, in, out, result, st);
-  TRY(launch_embed(pl, in, pl.xw, st));
-  const void* w = nullptr;
-  TRY(run_wave(wave_plan(pl), pl.xw, nullptr, &w, st));
-  void* dst = out ? out : pl.xo;
-  TRY(launch_restrict(pl, w, dst, st));
-  if (result) *result = dst;
+// W E v: the wave-grid field at T of the box source v, left in a state
+// buffer returned through *pN (pad = 0: W v).
+static int wave_fwd(const Plan& pl, const void* v, const void** pN, cudaStream_t st) {
+  if (pl.pad == 0) return run_wave(pl, v, nullptr, pN, st);
+  TRY(launch_embed(pl, v, pl.xw, st));
+  return run_wave(wave_plan(pl), pl.xw, nullptr, pN, st);
+}
+
+// The wave-grid input buffer of wave_back (pl.x without padding).
+static void* wave_in(const Plan& pl) { return pl.pad ? pl.xw : pl.x; }
+
+// E^T W x for a wave-grid x (already scaled by kappa: W^T = K^-1 W K), the
+// box result returned through *w (a state buffer, or pl.xo when padded).
+static int wave_back(const Plan& pl, const void* x, const void** w, cudaStream_t st) {
+  if (pl.pad == 0) return run_wave(pl, x, nullptr, w, st);
+  const void* r = nullptr;
+  TRY(run_wave(wave_plan(pl), x, nullptr, &r, st));
+  TRY(launch_restrict(pl, r, pl.xo, st));
+  *w = pl.xo;
   return FFPAT_OK;
 }
 
-// h = W^T P^T g  ->  x = K P^T g ; w = W x ; h = w / K
+// h = E^T W^T P^T g  ->  x = K P^T g ; w = E^T W x ; h = w / K
 static int apply_adjoint(const Plan& pl, const void* g, void* h, cudaStream_t st) {
-  TRY(launch_backproject(pl, g, pl.x, pl.kap, st));
+  const Plan wp = wave_plan(pl);
+  TRY(launch_backproject(wp, g, wave_in(pl), wp.kap, st));
   const void* w = nullptr;
-  TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
+  TRY(wave_back(pl, wave_in(pl), &w, st));
   TRY(launch_kscale(pl, w, h, false, st));
   return FFPAT_OK;
 }
 
 // x-domain result of A^T chi Lambda chi (A v - g) without the final 1/kap:
-// returns the state buffer holding W K P^T chi Lambda r, r = chi (A v - g)
+// returns the buffer holding E^T W K P^T chi Lambda r, r = chi (A v - g)
 // (chi = the data mask, nullable).  dots[0] = <Lambda r, r>, dots[1] = <r, r>.
 static int data_gradient(const Plan& pl, const void* v, const void* g, const void** w,
                          double* dots, cudaStream_t st, const void* mask = nullptr) {
+  const Plan wp = wave_plan(pl);
   const void* pN = nullptr;
-  TRY(run_wave_box(pl, v, nullptr, &pN, st));
-  TRY(launch_project(pl, pN, pl.r, g, st, mask));
+  TRY(wave_fwd(pl, v, &pN, st));
+  TRY(launch_project(wp, pN, pl.r, g, st, mask));
   const void* lr = pl.r;
   if (pl.precond == FFPAT_PRECOND_RAMP) {
-    TRY(launch_ramp(pl, pl.r, pl.r2, st, mask));
+    TRY(launch_ramp(wp, pl.r, pl.r2, st, mask));
     lr = pl.r2;
   }
   if (dots) TRY(launch_dot(pl, pl.nd, lr, pl.r, dots, st));
-  TRY(launch_backproject(pl, lr, pl.x, pl.kap, st));
-  TRY(run_wave_box(pl, pl.x, nullptr, w, st));
+  TRY(launch_backproject(wp, lr, wave_in(pl), wp.kap, st));
+  TRY(wave_back(pl, wave_in(pl), w, st));
   return FFPAT_OK;
 }
 
@@ -570,7 +577,7 @@ int ffpat_debug_samples(const ffpat_problem* problem, int32_t count, const int32
   void* tabs = nullptr;
   CK(cudaMallocAsync(&tabs, table_bytes(pl.nth), st));
   int rc = upload_tables(pl, tabs, st);
-  if (rc == FFPAT_OK) rc = launch_debug_samples(pl, count, jkm, ij, f, st);
+  if (rc == FFPAT_OK) rc = launch_debug_samples(wave_plan(pl), count, jkm, ij, f, st);
   CK(cudaFreeAsync(tabs, st));
   TRY(rc);
   CK(cudaStreamSynchronize(st));
@@ -584,8 +591,8 @@ int ffpat_forward(const ffpat_problem* problem, const void* c, const void* h, vo
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
   if (!h || !g) return fail(FFPAT_EINVAL, "h or g is NULL");
   const void* pN = nullptr;
-  TRY(run_wave_box(pl, h, nullptr, &pN, st));
-  TRY(launch_project(pl, pN, g, nullptr, st));
+  TRY(wave_fwd(pl, h, &pN, st));
+  TRY(launch_project(wave_plan(pl), pN, g, nullptr, st));
   return FFPAT_OK;
 }
 
@@ -606,11 +613,16 @@ int ffpat_wave(const ffpat_problem* problem, const void* c, const void* in, void
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
   if (!in || !out) return fail(FFPAT_EINVAL, "in or out is NULL");
   if (!transpose) {
-    TRY(run_wave_box(pl, in, out, nullptr, st));
+    if (pl.pad == 0) {
+      TRY(run_wave(pl, in, out, nullptr, st));
+    } else {
+      TRY(launch_embed(pl, in, pl.xw, st));
+      TRY(run_wave(wave_plan(pl), pl.xw, out, nullptr, st));
+    }
   } else {
-    TRY(launch_kscale(pl, in, pl.x, true, st));
+    TRY(launch_kscale(wave_plan(pl), in, wave_in(pl), true, st));
     const void* w = nullptr;
-    TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
+    TRY(wave_back(pl, wave_in(pl), &w, st));
     TRY(launch_kscale(pl, w, out, false, st));
   }
   return FFPAT_OK;
@@ -625,7 +637,7 @@ int ffpat_project(const ffpat_problem* problem, const void* p, void* g, void* st
   void* tabs = nullptr;
   CK(cudaMallocAsync(&tabs, table_bytes(pl.nth), st));
   int rc = upload_tables(pl, tabs, st);
-  if (rc == FFPAT_OK) rc = launch_project(pl, p, g, nullptr, st);
+  if (rc == FFPAT_OK) rc = launch_project(wave_plan(pl), p, g, nullptr, st);
   CK(cudaFreeAsync(tabs, st));
   TRY(rc);
   CK(cudaStreamSynchronize(st));
@@ -641,7 +653,7 @@ int ffpat_backproject(const ffpat_problem* problem, const void* g, void* h, void
   void* tabs = nullptr;
   CK(cudaMallocAsync(&tabs, table_bytes(pl.nth), st));
   int rc = upload_tables(pl, tabs, st);
-  if (rc == FFPAT_OK) rc = launch_backproject(pl, g, h, nullptr, st);
+  if (rc == FFPAT_OK) rc = launch_backproject(wave_plan(pl), g, h, nullptr, st);
   CK(cudaFreeAsync(tabs, st));
   TRY(rc);
   CK(cudaStreamSynchronize(st));
@@ -655,7 +667,7 @@ int ffpat_ramp(const ffpat_problem* problem, const void* r, void* out, void* str
   TRY(validate(problem, pl));
   if (!r || !out) return fail(FFPAT_EINVAL, "r or out is NULL");
   if (r == out) return fail(FFPAT_EINVAL, "ramp cannot run in place");
-  TRY(launch_ramp(pl, r, out, st));
+  TRY(launch_ramp(wave_plan(pl), r, out, st));
   return FFPAT_OK;
 }
 
@@ -766,8 +778,9 @@ int ffpat_fbp(const ffpat_problem* problem, const void* G, void* out, void* ws, 
   TRY(attach(problem, pl, ws, ws_bytes));
   if (!G || !out) return fail(FFPAT_EINVAL, "G or out is NULL");
   TRY(upload_tables(pl, pl.tab, st));
-  TRY(launch_ramp(pl, G, pl.r2, st));
-  TRY(launch_backproject(pl, pl.r2, out, nullptr, st, 2.0 * M_PI / (pl.nth * pl.dx)));
+  const Plan wp = wave_plan(pl);
+  TRY(launch_ramp(wp, G, pl.r2, st));
+  TRY(launch_backproject(wp, pl.r2, out, nullptr, st, 2.0 * M_PI / (pl.nth * pl.dx)));
   return FFPAT_OK;
 }
 
@@ -778,9 +791,9 @@ static int power_iteration_w(const Plan& pl, int iters, double* est, cudaStream_
   TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
   for (int it = 0; it < iters; ++it) {
     const void* w = nullptr;
-    TRY(run_wave_box(pl, pl.v, nullptr, &w, st));
-    TRY(launch_kscale(pl, w, pl.x, true, st));
-    TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
+    TRY(wave_fwd(pl, pl.v, &w, st));
+    TRY(launch_kscale(wave_plan(pl), w, wave_in(pl), true, st));
+    TRY(wave_back(pl, wave_in(pl), &w, st));
     TRY(launch_kscale(pl, w, pl.v, false, st));
     TRY(launch_dot(pl, pl.n3, pl.v, pl.v, sq, st));
     TRY(launch_scale_dev(pl, pl.n3, pl.v, pl.v, sq, st));
@@ -820,16 +833,19 @@ int ffpat_fb_two_step_ex(const ffpat_problem* problem, const void* c, const void
     if (!(opn > 0.0) || !isfinite(opn)) return fail(FFPAT_EINVAL, "operator norm estimate %g", opn);
     step = 1.0 / opn;
   }
-  // g~ = X^{-1} G, kept in pl.v for the whole solve
-  TRY(launch_ramp(pl, G, pl.r2, st));
-  TRY(launch_backproject(pl, pl.r2, pl.v, nullptr, st, 2.0 * M_PI / (pl.nth * pl.dx)));
+  // g~ = X^{-1} G on the wave grid, kept for the whole solve (pl.v, or pl.xg
+  // when padded)
+  const Plan wp = wave_plan(pl);
+  void* gt = pl.pad ? pl.xg : pl.v;
+  TRY(launch_ramp(wp, G, pl.r2, st));
+  TRY(launch_backproject(wp, pl.r2, gt, nullptr, st, 2.0 * M_PI / (pl.nth * pl.dx)));
   int k = 0;
   for (; k < max_iters; ++k) {
     double* hk = pl.hist + 8 * (size_t)k;
     const void* w = nullptr;
-    TRY(run_wave_box(pl, h_inout, nullptr, &w, st));
-    TRY(launch_resid_kap(pl, w, pl.v, pl.x, hk, st));
-    TRY(run_wave_box(pl, pl.x, nullptr, &w, st));
+    TRY(wave_fwd(pl, h_inout, &w, st));
+    TRY(launch_resid_kap(wp, w, gt, wave_in(pl), hk, st));
+    TRY(wave_back(pl, wave_in(pl), &w, st));
     if (regulariser == FFPAT_REG_GRAD2)
       TRY(prox_grad_step(pl, h_inout, w, step, lambda, hk + 2, st));
     else

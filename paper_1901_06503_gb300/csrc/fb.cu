@@ -113,23 +113,26 @@ __global__ void k_kscale(const T* __restrict__ a, T* __restrict__ out, const T* 
     out[i] = mul ? a[i] * kap[i] : a[i] / kap[i];
 }
 
-// copy between the image box (n^3) and its cells inside the wave grid (nw^3,
-// pad cells on every side)
+// to_wave: the wave grid (nw^3) gets the box (n^3) in its central cells and
+// zero elsewhere; else the box gets the central cells of the wave grid
 template <typename T>
 __global__ void k_box_copy(const T* __restrict__ src, T* __restrict__ dst, int n, int nw, int pad,
                            bool to_wave) {
-  const size_t n3 = (size_t)n * n * n;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
+  const int m = to_wave ? nw : n;
+  const size_t len = (size_t)m * m * m;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
        i += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % n);
-    const size_t t = i / n;
-    const int y = (int)(t % n);
-    const int z = (int)(t / n);
-    const size_t w = ((size_t)(z + pad) * nw + (y + pad)) * nw + (x + pad);
-    if (to_wave)
-      dst[w] = src[i];
-    else
-      dst[i] = src[w];
+    const int x = (int)(i % m);
+    const size_t t = i / m;
+    const int y = (int)(t % m);
+    const int z = (int)(t / m);
+    if (to_wave) {
+      const int bx = x - pad, by = y - pad, bz = z - pad;
+      const bool in = bx >= 0 && by >= 0 && bz >= 0 && bx < n && by < n && bz < n;
+      dst[i] = in ? src[((size_t)bz * n + by) * n + bx] : T(0);
+    } else {
+      dst[i] = src[((size_t)(z + pad) * nw + (y + pad)) * nw + (x + pad)];
+    }
   }
 }
 
@@ -349,7 +352,7 @@ int launch_kscale(const Plan& pl, const void* a, void* out, bool mul, cudaStream
 }
 
 static int box_copy(const Plan& pl, const void* src, void* dst, bool to_wave, cudaStream_t st) {
-  const unsigned nb = ew_blocks(pl.n3);
+  const unsigned nb = ew_blocks(to_wave ? pl.nw3 : pl.n3);
   if (pl.prec == FFPAT_FP64)
     k_box_copy<double><<<nb, 256, 0, st>>>((const double*)src, (double*)dst, pl.n, pl.nw, pl.pad,
                                            to_wave);

@@ -15,19 +15,23 @@ constexpr int kReduceThreads = 256;
 constexpr int kNumQuant = 8;           // quantities one reduction pass can carry
 
 // Derived, validated problem plus the carve of the caller's workspace.
-// Grid fields (n, n3, kap) describe the image box; with padding the wave runs
-// on a grid of nw = n + 2 pad points per axis whose view wave_plan() gives.
+// Grid fields (n, n3, kap) describe the image box (the source domain V);
+// with padding the wave runs on a grid of nw = n + 2 pad points per axis (the
+// V_T of the wave model) whose view wave_plan() gives.  The data are always
+// the projections of the wave grid: nd = nth nw^2 values, ns samples per ray.
 struct Plan {
   int n = 0, nth = 0, ns = 0, nt = 0, prec = 0, precond = 0;
   int pad = 0, nw = 0;    // cells of padding per side; wave grid points per axis
+  int nimg = 0;           // box points per axis in every view (cell size 2 / nimg)
   double T = 0, cfl = 0, dx = 0, dt = 0, cmax = 0;
   size_t n3 = 0, nd = 0, esize = 0, nw3 = 0;
   // workspace carve (device)
   void* kap = nullptr;    // kappa / 12 on the image box
   void* kapw = nullptr;   // kappa / 12 on the wave grid (== kap without padding)
   void* s[6] = {};        // wavefield state (wave grid): three-term p^{n-1}, p^n; increment form p, p', d, e, d', e'
-  void* xw = nullptr;     // wave-grid input of a padded W (zero outside the box)
-  void* xo = nullptr;     // image-box result of a padded W
+  void* xw = nullptr;     // wave-grid input of a padded W or W^T
+  void* xo = nullptr;     // image-box result of a padded W^T
+  void* xg = nullptr;     // wave-grid scratch (the FBP of Algorithm 9 when padded)
   void* x = nullptr;      // image-domain scratch (adjoint input / gradient)
   void* v = nullptr;      // image-domain scratch (power iteration vector)
   void* r = nullptr;      // data-domain scratch (residual)
@@ -139,8 +143,7 @@ int launch_prox_grad(const Plan& pl, double a, const void* in, void* out, void* 
 int launch_prox_prep(const Plan& pl, const void* h, const void* w, double step, void* x,
                      cudaStream_t st, const double* step_dev = nullptr);
 int launch_prox_finish(const Plan& pl, void* h, const void* hn, double* dst, cudaStream_t st);
-// padding: box (n^3) -> interior of the wave grid (the rest of `wave` is left
-// as it is: zero by construction), and wave grid -> box
+// padding: box (n^3) -> wave grid (zero outside the box), and wave grid -> box
 int launch_embed(const Plan& pl, const void* box, void* wave, cudaStream_t st);
 int launch_restrict(const Plan& pl, const void* wave, void* box, cudaStream_t st);
 int launch_kscale(const Plan& pl, const void* a, void* out, bool mul, cudaStream_t st);

@@ -2,6 +2,12 @@
 // exact transpose P^T (the discrete backprojection X^* of Sec. 3.1) and the
 // ramp preconditioner Lambda of Sec. 3.1.
 //
+// Geometry: the planes have n cells per axis of physical size dx = 2 / nimg
+// (nimg = n on the box [-1, 1]^3; n = nimg + 2 pad on a padded wave grid,
+// which then spans [-L, L], L = n / nimg); n detectors and Ns = 2 ceil(n /
+// sqrt 2) ray samples, both spaced dx.  The index geometry depends on n only;
+// dx enters as the sample length and the detector spacing of Lambda.
+//
 // P (ray-driven, no atomics): one thread per detector xi_k of one (theta_j,
 // z_l) row; it walks the ray samples s_m that can touch the grid and
 // accumulates the zero-extended bilinear samples in order, reading the plane
@@ -28,15 +34,18 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 
 // FP64 ray sample (theta, k, m): lower-left corner and fractions.  Same
-// operations, same order as the plain definition; no fused multiply-add.
+// operations, same order as the plain definition; no fused multiply-add.  The
+// plane spans [-L, L] in cells of size dx = 2 / nimg (L = n / nimg: 1 on the
+// box, larger on a padded wave grid); half = nimg / 2.
 __device__ __forceinline__ void sample64(double cs, double sn, int k, int m, int ns, double dx,
-                                         double half, int& i0, int& j0, double& fx, double& fy) {
-  const double xi = __dadd_rn(-1.0, __dmul_rn((double)k + 0.5, dx));
+                                         double half, double L, int& i0, int& j0, double& fx,
+                                         double& fy) {
+  const double xi = __dadd_rn(-L, __dmul_rn((double)k + 0.5, dx));
   const double s = __dmul_rn(((double)m + 0.5) - (double)(ns / 2), dx);
   const double x = __dsub_rn(__dmul_rn(xi, cs), __dmul_rn(s, sn));
   const double y = __dadd_rn(__dmul_rn(xi, sn), __dmul_rn(s, cs));
-  const double gx = __dsub_rn(__dmul_rn(__dadd_rn(x, 1.0), half), 0.5);
-  const double gy = __dsub_rn(__dmul_rn(__dadd_rn(y, 1.0), half), 0.5);
+  const double gx = __dsub_rn(__dmul_rn(__dadd_rn(x, L), half), 0.5);
+  const double gy = __dsub_rn(__dmul_rn(__dadd_rn(y, L), half), 0.5);
   const double flx = floor(gx), fly = floor(gy);
   i0 = (int)flx;
   j0 = (int)fly;
@@ -99,7 +108,7 @@ __global__ void __launch_bounds__(128)
     k_project(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
               const T* __restrict__ mask, const double* __restrict__ tab,
               const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n, int nth,
-              int ns) {
+              int ns, int nimg) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int l = blockIdx.y;
   const int j = blockIdx.z;
@@ -110,11 +119,11 @@ __global__ void __launch_bounds__(128)
   T acc = T(0);
   if constexpr (sizeof(T) == 8) {
     const double cs = tab[j], sn = tab[nth + j];
-    const double dx = 2.0 / n, half = n / 2.0;
+    const double dx = 2.0 / nimg, half = nimg / 2.0, L = (double)n / nimg;
     for (int m = mlo; m < mhi; ++m) {
       int i0, j0;
       double fx, fy;
-      sample64(cs, sn, k, m, ns, dx, half, i0, j0, fx, fy);
+      sample64(cs, sn, k, m, ns, dx, half, L, i0, j0, fx, fy);
       const double ofx = __dsub_rn(1.0, fx), ofy = __dsub_rn(1.0, fy);
       double b = __dmul_rn(__dmul_rn(ofx, ofy), pix(sl, n, j0, i0));
       b = __dadd_rn(b, __dmul_rn(__dmul_rn(fx, ofy), pix(sl, n, j0, i0 + 1)));
@@ -151,7 +160,7 @@ __global__ void __launch_bounds__(128)
       acc += fmaf(fy, r1 - r0, r0);
     }
     if (k < n) {
-      float out = (2.0f / (float)n) * acc;
+      float out = (2.0f / (float)nimg) * acc;
       const size_t o = ((size_t)j * n + l) * n + k;
       if (sub) out = out - sub[o];
       if (mask) out = out * mask[o];
@@ -179,7 +188,7 @@ __global__ void __launch_bounds__(256)
     k_project_smem(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
                    const T* __restrict__ mask, const double* __restrict__ tab,
                    const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n,
-                   int nth, int ns, int group) {
+                   int nth, int ns, int nimg, int group) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   const int W = plane_pitch(n);  // row pitch; rows = n + 2 kPad
@@ -208,11 +217,11 @@ __global__ void __launch_bounds__(256)
     T acc = T(0);
     if constexpr (sizeof(T) == 8) {
       const double cs = tab[j], sn = tab[nth + j];
-      const double dx = 2.0 / n, half = n / 2.0;
+      const double dx = 2.0 / nimg, half = nimg / 2.0, L = (double)n / nimg;
       for (int m = mlo; m < mhi; ++m) {
         int i0, j0;
         double fx, fy;
-        sample64(cs, sn, k, m, ns, dx, half, i0, j0, fx, fy);
+        sample64(cs, sn, k, m, ns, dx, half, L, i0, j0, fx, fy);
         const int o = at(j0, i0);
         const double ofx = __dsub_rn(1.0, fx), ofy = __dsub_rn(1.0, fy);
         double b = __dmul_rn(__dmul_rn(ofx, ofy), s[o]);
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(256)
         const float r1 = fmaf(fx, v11 - v01, v01);
         acc += fmaf(fy, r1 - r0, r0);
       }
-      float out = (2.0f / (float)n) * acc;
+      float out = (2.0f / (float)nimg) * acc;
       const size_t oo = ((size_t)j * n + l) * n + k;
       if (sub) out = out - sub[oo];
       if (mask) out = out * mask[oo];
@@ -272,7 +281,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_backproject2(const T* __restrict__ g, T* __restrict__ h, const T* __restrict__ scale,
                    const double* __restrict__ tab, const float* __restrict__ tabf,
-                   const int32_t* __restrict__ tabi, int n, int nth, int ns, T mult) {
+                   const int32_t* __restrict__ tabi, int n, int nth, int ns, int nimg, T mult) {
   __shared__ T s_cs[kAngleChunk], s_sn[kAngleChunk];
   __shared__ int s_CS[kAngleChunk], s_SN[kAngleChunk];
   const int ix = blockIdx.x * 32 + threadIdx.x;
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(256)
   }
   if (!in) return;
   const size_t o = ((size_t)l * n + iy) * n + ix;
-  T out = (T(2) / T(n)) * acc;
+  T out = (T(2) / T(nimg)) * acc;
   if (scale) out *= scale[o];
   if (mult != T(1)) out *= mult;
   h[o] = out;
@@ -351,12 +360,13 @@ __global__ void __launch_bounds__(256)
 
 template <typename T>
 __global__ void __launch_bounds__(128)
-    k_ramp(const T* __restrict__ r, T* __restrict__ out, const T* __restrict__ mask, int n) {
+    k_ramp(const T* __restrict__ r, T* __restrict__ out, const T* __restrict__ mask, int n,
+           int nimg) {
   extern __shared__ unsigned char smem_raw[];
   T* row = reinterpret_cast<T*>(smem_raw);
   T* tap = row + n;  // tap[d] for d < n (odd d nonzero)
   const size_t base = (size_t)blockIdx.x * n;
-  const double dxi = 2.0 / n;
+  const double dxi = 2.0 / nimg;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     row[i] = r[base + i];
     double t;
@@ -384,14 +394,15 @@ __global__ void __launch_bounds__(128)
 
 __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int32_t* __restrict__ ij,
                                 double* __restrict__ f, const double* __restrict__ tab, int n,
-                                int nth, int ns) {
+                                int nth, int ns, int nimg) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const int j = jkm[3 * t], k = jkm[3 * t + 1], m = jkm[3 * t + 2];
   if (j < 0 || j >= nth) return;
   int i0, j0;
   double fx, fy;
-  sample64(tab[j], tab[nth + j], k, m, ns, 2.0 / n, n / 2.0, i0, j0, fx, fy);
+  sample64(tab[j], tab[nth + j], k, m, ns, 2.0 / nimg, nimg / 2.0, (double)n / nimg, i0, j0, fx,
+           fy);
   ij[2 * t] = i0;
   ij[2 * t + 1] = j0;
   f[2 * t] = fx;
@@ -417,7 +428,7 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
       k_project_smem<double><<<grid, 256, smem, st>>>((const double*)p, (double*)g,
                                                       (const double*)sub, (const double*)mask,
                                                       pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth,
-                                                      pl.ns, group);
+                                                      pl.ns, pl.nimg, group);
     } else {
       static bool attr = false;
       if (!attr) {
@@ -427,7 +438,7 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
       }
       k_project_smem<float><<<grid, 256, smem, st>>>((const float*)p, (float*)g, (const float*)sub,
                                                      (const float*)mask, pl.tab, pl.tabf, pl.tabi,
-                                                     pl.n, pl.nth, pl.ns, group);
+                                                     pl.n, pl.nth, pl.ns, pl.nimg, group);
     }
     count_launch();
     return check_launch(__func__);
@@ -437,11 +448,11 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
   if (pl.prec == FFPAT_FP64)
     k_project<double><<<grid, block, 0, st>>>((const double*)p, (double*)g, (const double*)sub,
                                               (const double*)mask, pl.tab, pl.tabf, pl.tabi, pl.n,
-                                              pl.nth, pl.ns);
+                                              pl.nth, pl.ns, pl.nimg);
   else
     k_project<float><<<grid, block, 0, st>>>((const float*)p, (float*)g, (const float*)sub,
                                              (const float*)mask, pl.tab, pl.tabf, pl.tabi, pl.n,
-                                             pl.nth, pl.ns);
+                                             pl.nth, pl.ns, pl.nimg);
   count_launch();
   return check_launch(__func__);
 }
@@ -453,11 +464,11 @@ int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale
   if (pl.prec == FFPAT_FP64)
     k_backproject2<double><<<grid, block, 0, st>>>((const double*)g, (double*)h,
                                                   (const double*)scale, pl.tab, pl.tabf,
-                                                  pl.tabi, pl.n, pl.nth, pl.ns, mult);
+                                                  pl.tabi, pl.n, pl.nth, pl.ns, pl.nimg, mult);
   else
     k_backproject2<float><<<grid, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
                                                  pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns,
-                                                 (float)mult);
+                                                 pl.nimg, (float)mult);
   count_launch();
   return check_launch(__func__);
 }
@@ -467,9 +478,10 @@ int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st, const
   const size_t smem = 2 * (size_t)pl.n * pl.esize;
   if (pl.prec == FFPAT_FP64)
     k_ramp<double><<<rows, 128, smem, st>>>((const double*)r, (double*)out, (const double*)mask,
-                                            pl.n);
+                                            pl.n, pl.nimg);
   else
-    k_ramp<float><<<rows, 128, smem, st>>>((const float*)r, (float*)out, (const float*)mask, pl.n);
+    k_ramp<float><<<rows, 128, smem, st>>>((const float*)r, (float*)out, (const float*)mask, pl.n,
+                                           pl.nimg);
   count_launch();
   return check_launch(__func__);
 }
@@ -478,7 +490,7 @@ int launch_debug_samples(const Plan& pl, int count, const int32_t* jkm, int32_t*
                          cudaStream_t st) {
   if (count <= 0) return FFPAT_OK;
   k_debug_samples<<<(count + 127) / 128, 128, 0, st>>>(count, jkm, ij, f, pl.tab, pl.n, pl.nth,
-                                                      pl.ns);
+                                                      pl.ns, pl.nimg);
   count_launch();
   return check_launch(__func__);
 }

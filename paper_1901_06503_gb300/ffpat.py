@@ -201,7 +201,9 @@ def wave_shape(prob):
 
 
 def data_shape(prob):
-    return (prob.n_angles, prob.n, prob.n)
+    """Projections of the wave grid: n_angles x nw x nw."""
+    nw = prob.n + 2 * prob.pad
+    return (prob.n_angles, nw, nw)
 
 
 def workspace_bytes(prob: Problem) -> int:
@@ -313,27 +315,29 @@ def adjoint(prob, c, g, h=None, ws=None, stream=None):
 
 
 def wave(prob, c, x, out=None, transpose=False, ws=None, stream=None):
-    """W x (or W^T x)."""
-    out = _empty(prob, vol_shape(prob), x) if out is None else out
+    """W x (box source -> wave grid) or W^T x (wave grid -> box)."""
+    ins, outs = (wave_shape(prob), vol_shape(prob)) if transpose else (vol_shape(prob),
+                                                                        wave_shape(prob))
+    out = _empty(prob, outs, x) if out is None else out
     ws, wp, wn = _ws(prob, ws, x.device)
     _check(lib().ffpat_wave(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
-                            _dev(x, prob, vol_shape(prob), "in"),
-                            _dev(out, prob, vol_shape(prob), "out"), int(bool(transpose)), wp, wn,
-                            _stream(stream)))
+                            _dev(x, prob, ins, "in"), _dev(out, prob, outs, "out"),
+                            int(bool(transpose)), wp, wn, _stream(stream)))
     return out
 
 
 def project(prob, p, g=None, stream=None):
+    """P of the wave grid (the box when pad = 0)."""
     g = _empty(prob, data_shape(prob), p) if g is None else g
-    _check(lib().ffpat_project(ctypes.byref(prob), _dev(p, prob, vol_shape(prob), "p"),
+    _check(lib().ffpat_project(ctypes.byref(prob), _dev(p, prob, wave_shape(prob), "p"),
                                _dev(g, prob, data_shape(prob), "g"), _stream(stream)))
     return g
 
 
 def backproject(prob, g, h=None, stream=None):
-    h = _empty(prob, vol_shape(prob), g) if h is None else h
+    h = _empty(prob, wave_shape(prob), g) if h is None else h
     _check(lib().ffpat_backproject(ctypes.byref(prob), _dev(g, prob, data_shape(prob), "g"),
-                                   _dev(h, prob, vol_shape(prob), "h"), _stream(stream)))
+                                   _dev(h, prob, wave_shape(prob), "h"), _stream(stream)))
     return h
 
 
@@ -403,11 +407,11 @@ def prox_grad(prob, f, a, out=None, ws=None, stream=None):
 
 
 def fbp(prob, G, out=None, ws=None, stream=None):
-    """X^{-1} G plane by plane (filtered backprojection, N^3 result)."""
-    out = _empty(prob, vol_shape(prob), G) if out is None else out
+    """X^{-1} G plane by plane (filtered backprojection onto the wave grid)."""
+    out = _empty(prob, wave_shape(prob), G) if out is None else out
     ws, wp, wn = _ws(prob, ws, G.device)
     _check(lib().ffpat_fbp(ctypes.byref(prob), _dev(G, prob, data_shape(prob), "G"),
-                           _dev(out, prob, vol_shape(prob), "out"), wp, wn, _stream(stream)))
+                           _dev(out, prob, wave_shape(prob), "out"), wp, wn, _stream(stream)))
     return out
 
 

@@ -1,7 +1,8 @@
-"""GPU parity on the padded wave grid (the enlarged computational domain of
-the paper's experiments, Sec. 5): the wave runs on N + 2 pad points per axis,
-sources, images and data stay on the N^3 box.  Each case is compared with the
-oracle's padded operators element by element."""
+"""GPU parity on the padded wave grid (V_T of the wave model, the enlarged
+computational domain of the paper's experiments, Sec. 5): the wave runs on
+Nw = N + 2 pad points per axis, sources and images stay on the N^3 box, and
+the data are the projections of the whole wave grid (n_angles x Nw x Nw).
+Each case is compared with the oracle's padded operators element by element."""
 from __future__ import annotations
 
 import numpy as np
@@ -10,8 +11,8 @@ import pytest
 import oracle.oracle as o
 from paper_1901_06503_gb300 import build_lib
 from paper_1901_06503_gb300 import ffpat as F
-from paper_1901_06503_gb300.inputs import (add_noise, axis, config, extend_speed, random_data,
-                                           random_volume)
+from paper_1901_06503_gb300.inputs import (add_noise, config, extend_speed, padded_axis,
+                                           random_data, random_volume)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,11 +60,32 @@ def test_padded_forward_adjoint(prec, n, pad):
     g_gpu = host(F.forward(prob, dev(c, prob), dev(h, prob)))
     g_or = o.forward(c, h, w.T, w.n_angles, pad=pad)
     assert rel(g_gpu, g_or) < TOL[prec]
-    gd = as_input(add_noise(g_or, random_data(w.n_angles, n, 7), 0.01), prec)
+    gd = as_input(add_noise(g_or, random_data(w.n_angles, n + 2 * pad, 7), 0.01), prec)
     a_gpu = host(F.adjoint(prob, dev(c, prob), dev(gd, prob)))
     assert rel(a_gpu, o.adjoint(c, gd, w.T, pad=pad)) < TOL[prec]
-    # the padding matters here: the box-sized operator differs
-    assert rel(g_or, o.forward(w.c, w.h, w.T, w.n_angles)) > 100 * TOL[prec]
+    # the padding matters here: the box-sized operator differs on the box's rays
+    box = g_or[:, pad:-pad, pad:-pad]
+    assert rel(box, o.forward(w.c, w.h, w.T, w.n_angles)) > 100 * TOL[prec]
+
+
+@pytest.mark.parametrize("n,pad", [(32, 8), (20, 3)])
+def test_padded_projection_fp64_bit_exact(n, pad):
+    """P of the wave grid in FP64 reproduces the oracle bit for bit (same
+    sample arithmetic with L = Nw / N), and the sample tables agree."""
+    nw, nth = n + 2 * pad, 7
+    p = random_volume(nw, 9)
+    prob = F.problem(n, 1.0, nth, pad=pad)
+    g = host(F.project(prob, dev(p, prob)))
+    assert np.array_equal(g, o.project(p, nth, nimg=n))
+    rng = np.random.default_rng(10)
+    ns = 2 * int(np.ceil(nw / np.sqrt(2.0)))
+    jkm = np.stack([rng.integers(0, nth, 500), rng.integers(0, nw, 500),
+                    rng.integers(0, ns, 500)], axis=1)
+    ij, f = F.debug_samples(prob, jkm)
+    ij_or, f_or = o.sample_points(nw, nth, jkm, nimg=n)
+    assert np.array_equal(ij, ij_or) and np.array_equal(f, f_or)
+    h = host(F.backproject(prob, dev(g, prob)))
+    assert rel(h, o.backproject(g, nw, nimg=n)) < 1e-12
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -72,9 +94,10 @@ def test_padded_wave_and_transpose(prec):
     w, c, _ = case(n, pad, prec, seed=11)
     x = as_input(random_volume(n, 12), prec)
     prob = F.problem(n, T, 4, prec, pad=pad)
-    assert rel(host(F.wave(prob, dev(c, prob), dev(x, prob))), o.wave_img(c, x, T, pad)) < TOL[prec]
-    wt = host(F.wave(prob, dev(c, prob), dev(x, prob), transpose=True))
-    assert rel(wt, o.wave_img(c, x, T, pad, transpose=True)) < TOL[prec]
+    assert rel(host(F.wave(prob, dev(c, prob), dev(x, prob))), o.wave_pad(c, x, T, pad)) < TOL[prec]
+    u = as_input(random_volume(n + 2 * pad, 13), prec)
+    wt = host(F.wave(prob, dev(c, prob), dev(u, prob), transpose=True))
+    assert rel(wt, o.wave_pad(c, u, T, pad, transpose=True)) < TOL[prec]
 
 
 def test_padded_opnorm_fp64():
@@ -90,12 +113,13 @@ def test_padded_opnorm_fp64():
 @pytest.mark.parametrize("precond", [0, 1])
 def test_padded_limited_view_fb(prec, precond):
     """The paper's experimental setting: padded wave grid, data only for
-    |xi| > a (chi_M) and a source support chi_V inside the box."""
+    |xi| > a = 1 (chi_M: the rays that miss the source box) and a source
+    support chi_V inside the box."""
     n, pad = 24, 8
     w, c, h = case(n, pad, prec, seed=15)
     g = as_input(add_noise(o.forward(c, h, w.T, w.n_angles, pad=pad),
-                           random_data(w.n_angles, n, 16), 0.01), prec)
-    mask = np.broadcast_to((np.abs(axis(n)) > 0.3).astype(float), g.shape).copy()
+                           random_data(w.n_angles, n + 2 * pad, 16), 0.01), prec)
+    mask = np.broadcast_to((np.abs(padded_axis(n, pad)) > 1.0).astype(float), g.shape).copy()
     sup = np.zeros((n, n, n))
     sup[2:-2, 2:-2, 2:-2] = 1.0
     L = o.power(c, random_volume(n, 17), w.T, w.n_angles, precond=precond, iters=20, pad=pad,

@@ -9,8 +9,8 @@ import pytest
 import oracle.oracle as o
 from paper_1901_06503_gb300 import build_lib
 from paper_1901_06503_gb300 import ffpat as F
-from paper_1901_06503_gb300.inputs import (add_noise, axis, config, extend_speed, random_data,
-                                           random_volume)
+from paper_1901_06503_gb300.inputs import (add_noise, axis, config, extend_speed, padded_axis,
+                                           random_data, random_volume)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -82,12 +82,12 @@ def test_fb_gradient_regulariser(prec, precond):
 @pytest.mark.parametrize("prec", PRECS)
 def test_two_step_gradient_regulariser_padded(prec):
     """Algorithm 9 as in the paper's experiments: padded wave grid, data for
-    |xi| > a only, R = 1/2 |grad h|^2."""
+    |xi| > a = 1 only (outside the source box), R = 1/2 |grad h|^2."""
     n, pad = 24, 8
     w = config(1, n=n, seed=23)
     c, h = as_input(extend_speed(w.c, pad), prec), as_input(w.h, prec)
     G = o.forward(c, h, w.T, w.n_angles, pad=pad)
-    G = as_input(G * (np.abs(axis(n)) > 0.3), prec)
+    G = as_input(G * (np.abs(padded_axis(n, pad)) > 1.0), prec)
     prob = F.problem(n, w.T, w.n_angles, prec, pad=pad)
     h_gpu, st, hist = F.fb_two_step(prob, dev(c, prob), dev(G, prob), 0.5 * 0.3, 0.3, 5,
                                     reg=F.REG_GRAD2)
