@@ -432,6 +432,110 @@ def run_precision(args):
     return 0
 
 
+# FP32 FFMA peak of the GB300 for the dense DCT passes of the gradient prox:
+# 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz (maximum SM clock)
+FP32_FFMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_paper(args):
+    """The paper's experimental setting (Sec. 5) in 3D: the source box N^3 on
+    [-1, 1]^3, the wave grid padded to [-3, 3]^3 (pad = N, the paper's 3x
+    domain), T = 2, data only where |xi| > 1 (the rays that miss the source
+    box), 10 % relative noise, R = 1/2 |grad h|^2 with s lambda / dx^2 = 1 and
+    s = 1/L; the one-step method (Algorithm 8, ramp-preconditioned) against the two-step method
+    (Algorithm 9): time per iteration, voxel-steps/s on the wave grid, the
+    gradient prox's own rate, and the relative L2 error of both reconstructions
+    after the same number of iterations.  The phantom and sound speed are the
+    synthetic 20-ball / Gaussian-random-field pair (the paper's are not
+    published), so the errors are context, not a reproduction."""
+    import numpy as np
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    from paper_1901_06503_gb300.inputs import add_noise, config, extend_speed, padded_axis
+
+    build_lib.build()
+    dev = torch.device("cuda", 0)
+    n, pad, T, nth = args.paper_n, args.paper_n, 2.0, args.paper_angles
+    nw = n + 2 * pad
+    w = config(2, n=n)
+    c_np = extend_speed(w.c, pad)
+    prec = {"fp32-kahan": F.FP32_KAHAN, "fp32": F.FP32, "fp64": F.FP64}[args.precision]
+    # Algorithm 8 is the preconditioned one-step method: Lambda = ramp filter
+    prob = F.problem(n, T, nth, prec, F.PRECOND_RAMP, pad=pad)
+    dt = F.torch_dtype(prob)
+    p64 = F.problem(n, T, nth, F.FP64, pad=pad)
+    g64 = F.forward(p64, torch.as_tensor(c_np, device=dev), torch.as_tensor(w.h, device=dev))
+    rng = np.random.default_rng(1901)
+    mask_np = np.broadcast_to((np.abs(padded_axis(n, pad)) > 1.0).astype(np.float64),
+                              (nth, nw, nw)).copy()
+    g_np = mask_np * add_noise(g64.cpu().numpy(), rng.standard_normal((nth, nw, nw)), 0.10)
+    del g64
+    c = torch.as_tensor(c_np, device=dev).to(dt)
+    g = torch.as_tensor(g_np, device=dev).to(dt)
+    mask = torch.as_tensor(mask_np, device=dev).to(dt)
+    h_true = torch.as_tensor(w.h, device=dev)
+    ws = F.workspace(prob, dev)
+    dx = 2.0 / n
+    nt, _, _ = F.problem_info(prob, float(c.double().max()))
+    iters = args.iters
+
+    def err(h):
+        return float((h.double() - h_true).norm() / h_true.norm())
+
+    out = {"mode": "paper",
+           "workload": f"source box {n}^3 on [-1,1]^3, wave grid {nw}^3 on [-3,3]^3, T = 2, "
+                       f"{nth} angles, data for |xi| > 1, 10% noise, R = 1/2|grad h|^2",
+           "precision": F.PRECISION_NAMES[prec], "nt": nt, "iters": iters}
+    # one-step: step 1/L of the masked A^T A, then lambda with s lambda / dx^2 = 1
+    _, st0, _ = F.fb_solve_masked(prob, c, g, 0.0, 0.0, 0, mask=mask, ws=ws, reg=F.REG_GRAD2)
+    s1 = st0["step"]
+    lam1 = dx * dx / s1
+    F.fb_solve_masked(prob, c, g, lam1, s1, 1, mask=mask, ws=ws, reg=F.REG_GRAD2, history=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    h1, st1, _ = F.fb_solve_masked(prob, c, g, lam1, s1, iters, mask=mask, ws=ws,
+                                   reg=F.REG_GRAD2, history=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / iters
+    vs = 2.0 * nt * float(nw) ** 3
+    out["one_step"] = {"ms_per_iter": ms1, "voxel_steps_per_s": vs / (ms1 / 1e3),
+                       "rel_l2_error": err(h1), "step": s1, "lambda": lam1,
+                       "objective": st1["objective"]}
+    # two-step: X^{-1} of the masked data, then FB on 1/2 ||W h - g~||^2
+    _, st0, _ = F.fb_two_step(prob, c, g, 0.0, 0.0, 0, ws=ws, reg=F.REG_GRAD2)
+    s2 = st0["step"]
+    lam2 = dx * dx / s2
+    torch.cuda.synchronize()
+    e0.record()
+    h2, st2, _ = F.fb_two_step(prob, c, g, lam2, s2, iters, ws=ws, reg=F.REG_GRAD2, history=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms2 = e0.elapsed_time(e1) / iters
+    out["two_step"] = {"ms_per_iter": ms2, "voxel_steps_per_s": vs / (ms2 / 1e3),
+                       "rel_l2_error": err(h2), "step": s2, "lambda": lam2}
+    # the gradient prox alone (six DCT passes on the box, 2 n^4 FLOP each)
+    f = torch.randn((n, n, n), device=dev, dtype=torch.float64).to(dt)
+    F.prox_grad(prob, f, 1.0, ws=ws)
+    torch.cuda.synchronize()
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        F.prox_grad(prob, f, 1.0, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1) / reps
+    flop = 6 * 2.0 * float(n) ** 4
+    out["prox"] = {"ms": pms, "tflops": flop / (pms / 1e3) / 1e12, "bound": "alu",
+                   "peak_tflops": FP32_FFMA_TFLOPS if prec != F.FP64 else None,
+                   "share_of_one_step_iter": pms / ms1}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,20 +546,25 @@ def main():
     ap.add_argument("--precision", choices=["fp32-kahan", "fp32", "fp64"], default="fp32-kahan")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["fb", "serve", "precision"], default="fb",
+    ap.add_argument("--mode", choices=["fb", "serve", "precision", "paper"], default="fb",
                     help="fb: the default FB-iteration line; serve: the serving mix; "
-                         "precision: FP64 vs FP32 vs FP32-Kahan on the 128^3 solve")
+                         "precision: FP64 vs FP32 vs FP32-Kahan on the 128^3 solve; "
+                         "paper: the paper's experimental setting in 3D (one- vs two-step)")
+    ap.add_argument("--paper-n", type=int, default=64, help="paper: source box points per axis")
+    ap.add_argument("--paper-angles", type=int, default=180, help="paper: projection angles")
     ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window (s)")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate (1/s)")
     ap.add_argument("--pool", type=int, default=12, help="serve: distinct requests cycled")
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--budget-gb", type=float, default=64.0)
-    ap.add_argument("--iters", type=int, default=20, help="precision: FB iterations")
+    ap.add_argument("--iters", type=int, default=20, help="precision / paper: FB iterations")
     args = ap.parse_args()
     if args.mode == "serve":
         return run_serve(args)
     if args.mode == "precision":
         return run_precision(args)
+    if args.mode == "paper":
+        return run_paper(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -93,7 +93,8 @@ def main(argv=None):
     if prof["step_launches"]:
         res["step_ms_avg"] = prof["step_ms"] / prof["step_launches"]
         res["step_gbs"] = prof["step_bytes"] / (prof["step_ms"] / 1e3) / 1e9
-        res["voxel_steps_per_s"] = prof["step_launches"] * n**3 / (prof["step_ms"] / 1e3)
+        res["voxel_steps_per_s"] = prof["steps"] * n**3 / (prof["step_ms"] / 1e3)
+        res["step_ms_per_step"] = prof["step_ms"] / max(prof["steps"], 1)
     assert np.isfinite(out_v.double().sum().item()) or a.op in ("forward", "project", "ramp")
     print(json.dumps(res))
 
