@@ -54,6 +54,14 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
+// Let the dependent grid launch, then wait until the grid this one depends on
+// (programmatic stream serialization) has completed with its memory visible.
+// Without a programmatic dependency both return at once.
+__device__ __forceinline__ void grid_dependency_sync() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -214,15 +222,19 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
   T* qst = reinterpret_cast<T*>(smem + SP * G::PBYTES);                  // SQ x NQ tiles
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SP * G::PBYTES + SQ * NQ * G::QBYTES);
 
-  // after a device-side failure, later launches return at once (the host
-  // reports the status word) instead of repeating bounded waits
-  if (*(volatile unsigned*)&g_tma_status != 0u) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * NTX + tx;
   if (tid == 0) {
     for (int i = 0; i < SP; ++i) mbar_init(&bar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // programmatic dependent launch: the next step's grid may be scheduled as
+  // this one's CTAs retire and run the prologue above; no global memory is
+  // touched before the previous grid has completed and its writes are visible
+  grid_dependency_sync();
+  // after a device-side failure, later launches return at once (the host
+  // reports the status word) instead of repeating bounded waits
+  if (*(volatile unsigned*)&g_tma_status != 0u) return;
   __syncthreads();
   unsigned phase = 0;  // one parity bit per barrier slot
   const size_t plane = (size_t)n * n;
@@ -474,11 +486,16 @@ namespace tb2 {
 constexpr int PW = 72, PH = 16;  // p^n box (x0-4 .., y0-4 ..)
 constexpr int QW = 72, QH = 12;  // d, e, kap, and level-(n+1) p boxes (x0-4 .., y0-2 ..)
 constexpr int PB = PW * PH * 4, QB = QW * QH * 4, TB = TBX * TBY * 4;
-constexpr int RP = 7;  // p^n planes zA-2 .. zA+4
-constexpr int RK = 5;  // kap planes zA-2 .. zA+2 (step B reads kap two planes behind step A)
-constexpr int RD = 3;  // d^n, e^n planes zA .. zA+2
-constexpr int RA = 5;  // level-(n+1) p planes zA-4 .. zA
-constexpr int RAD = 3; // level-(n+1) d, e tile planes zA-2 .. zA
+// Rings.  One block barrier per plane (after step A): a ring slot may be
+// refilled or rewritten only when its last reader ran before the latest
+// barrier, which sets the depths.
+constexpr int RP = 7;   // p^n planes zA-2 .. zA+4 (plane zA+5 is loaded into zA-2's slot)
+constexpr int RK = 6;   // kap planes zA-5 .. zA (zA+3 is loaded into zA-3's slot)
+constexpr int RD = 3;   // d^n, e^n planes zA .. zA+2
+constexpr int RA = 6;   // level-(n+1) p planes zA-5 .. zA
+constexpr int RAD = 4;  // level-(n+1) d, e tile planes zA-3 .. zA
+constexpr int NTY2 = 13;  // 13 warps: step A's 34 x 12 point pairs take one round
+constexpr int NT2 = NTX * NTY2;
 constexpr size_t kSmem = (size_t)RP * PB + (size_t)RK * QB + (size_t)RD * 2 * QB +
                          (size_t)RA * QB + (size_t)RAD * 2 * TB + RP * 8;
 __host__ __device__ constexpr int slot(int z, int m) { return (z + 64 * m) % m; }
@@ -511,7 +528,7 @@ __device__ __forceinline__ void tb2_issue(const Maps2& m, unsigned char* sm, uin
   }
 }
 
-__global__ void __launch_bounds__(NTX* NTY, 1)
+__global__ void __launch_bounds__(tb2::NT2, 2)
     k_step2_kahan(const __grid_constant__ Maps2 maps, float* __restrict__ po,
                   float* __restrict__ dout, float* __restrict__ eout, int n, int zc, int tiles_x,
                   int tiles_y, int nitems) {
@@ -525,13 +542,14 @@ __global__ void __launch_bounds__(NTX* NTY, 1)
   float* AD = reinterpret_cast<float*>(sm + RP * PB + RK * QB + RD * 2 * QB + RA * QB);
   uint64_t* bar =
       reinterpret_cast<uint64_t*>(sm + RP * PB + RK * QB + RD * 2 * QB + RA * QB + RAD * 2 * TB);
-  if (*(volatile unsigned*)&g_tma_status != 0u) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * NTX + tx;
   if (tid == 0) {
     for (int i = 0; i < RP; ++i) mbar_init(&bar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  grid_dependency_sync();
+  if (*(volatile unsigned*)&g_tma_status != 0u) return;
   __syncthreads();
   unsigned phase = 0;
   const size_t plane = (size_t)n * n;
@@ -564,7 +582,7 @@ __global__ void __launch_bounds__(NTX* NTY, 1)
         const float* Ez = Dz + QB / 4;
         float* Az = A + slot(zA, RA) * (QB / 4);
         float* ADz = AD + slot(zA, RAD) * 2 * (TB / 4);
-        for (int q = tid; q < 34 * QH; q += NTX * NTY) {
+        for (int q = tid; q < 34 * QH; q += NT2) {
           const int qy = q / 34, qx = 2 + 2 * (q % 34);
           const int po_ = (qy + 2) * PW + qx;  // same x origin, two more rows of halo
           const int qo = qy * QW + qx;
@@ -582,10 +600,28 @@ __global__ void __launch_bounds__(NTX* NTY, 1)
           }
         }
       }
-      __syncthreads();
-      // ---- step B: level n+2 at plane zB = zA - 2 on the tile
+      // the plane's only block barrier, also the vote on a timed-out wait
+      if (__syncthreads_or(timed_out)) {
+        if (tid == 0) {
+          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+          for (int R = waited_upto + 1; R <= min(z1 + 3, zA + RP - 3); ++R) {
+            const int b = slot(R, RP);
+            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
+            phase ^= 1u << b;
+          }
+        }
+        return;
+      }
+      // refill: p plane zA+5 into zA-2's slot (last read by step A above),
+      // kap zA+3 into zA-3's (last read by step B of the previous plane),
+      // d, e zA+3 into zA's (last read by step A above)
+      if (tid == 0) tb2_issue(maps, sm, bar, zA + RP - 2, z0, z1, x0, y0);
+      // ---- step B: level n+2 at plane zB = zA - 2 on the tile.  It reads
+      // level-(n+1) planes zA-4 .. zA and tiles zA-2; step A of plane zA+1
+      // writes zA+1's slots, last read by step B of plane zA-1 (before the
+      // barrier above)
       const int zB = zA - 2;
-      if (zB >= z0) {
+      if (zB >= z0 && ty < TBY) {
         const float* A0 = A + slot(zB, RA) * (QB / 4);
         const float* Am1 = A + slot(zB - 1, RA) * (QB / 4);
         const float* Ap1 = A + slot(zB + 1, RA) * (QB / 4);
@@ -610,19 +646,9 @@ __global__ void __launch_bounds__(NTX* NTY, 1)
           *reinterpret_cast<float2*>(eout + gi) = make_float2(ra.z, rb.z);
         }
       }
-      if (__syncthreads_or(timed_out)) {
-        if (tid == 0) {
-          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
-          for (int R = waited_upto + 1; R <= min(z1 + 3, zA + RP - 3); ++R) {
-            const int b = slot(R, RP);
-            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
-            phase ^= 1u << b;
-          }
-        }
-        return;
-      }
-      if (tid == 0) tb2_issue(maps, sm, bar, zA + RP - 2, z0, z1, x0, y0);
     }
+    // the next work item refills every ring from its first plane on
+    __syncthreads();
   }
 }
 
@@ -695,6 +721,51 @@ int make_map_box(CUtensorMap* m, const void* base, int n, int esize, int bx, int
   return FFPAT_OK;
 }
 
+// Launch with programmatic stream serialization, so that consecutive leapfrog
+// launches overlap one's tail with the next one's prologue (the kernels wait
+// in grid_dependency_sync before touching global memory).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// z-range of one work item of the single-step kernel: every work item costs
+// its zc planes plus the ring's 4 halo planes, and the grid runs
+// ceil(items / slots) rounds of items; pick the zc (>= 6) of least
+// rounds x (zc + 4) among those that keep at least 90 % of the CTA slots
+// busy.  Grids too small for that keep ranges of N / 8.. planes as before.
+int choose_zchunk(int n, int tiles, int slots) {
+  int best = 0;
+  long long best_cost = 0;
+  for (int zc = 6; zc <= n; ++zc) {
+    const long long items = (long long)tiles * ((n + zc - 1) / zc);
+    if (items * 10 < (long long)slots * 9) break;  // items only shrink as zc grows
+    const long long rounds = (items + slots - 1) / slots;
+    const long long cost = rounds * (zc + 4);
+    if (best == 0 || cost < best_cost) {
+      best = zc;
+      best_cost = cost;
+    }
+  }
+  if (best > 0) return best;
+  int zchunks = (4 * slots + tiles - 1) / tiles;
+  const int zmax = n / 8 > 0 ? n / 8 : 1;
+  if (zchunks > zmax) zchunks = zmax;
+  if (zchunks < 1) zchunks = 1;
+  return (n + zchunks - 1) / zchunks;
+}
+
 template <typename T, int FORM, bool START>
 int launch_one(const Plan& pl, const Maps& maps, void* o0, void* o1, void* o2, cudaStream_t st) {
   using G = Geo<T>;
@@ -711,18 +782,19 @@ int launch_one(const Plan& pl, const Maps& maps, void* o0, void* o1, void* o2, c
   const int n = pl.n;
   const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + TBY - 1) / TBY;
   const int slots = kNumSMs * occ;
-  int zchunks = (4 * slots + tiles_x * tiles_y - 1) / (tiles_x * tiles_y);
-  const int zmax = n / 8 > 0 ? n / 8 : 1;
-  if (zchunks > zmax) zchunks = zmax;
-  if (zchunks < 1) zchunks = 1;
-  int zc = (n + zchunks - 1) / zchunks;
+  int zc = choose_zchunk(n, tiles_x * tiles_y, slots);
   if (zchunk_override() > 0) zc = zchunk_override() < n ? zchunk_override() : n;
-  zchunks = (n + zc - 1) / zc;
+  const int zchunks = (n + zc - 1) / zc;
   const int nitems = tiles_x * tiles_y * zchunks;
   const int grid = nitems < slots ? nitems : slots;
-  kern<<<grid, dim3(NTX, NTY), smem, st>>>(maps, (T*)o0, (T*)o1, (T*)o2, n, zc, tiles_x, tiles_y,
-                                          nitems);
+  const cudaError_t e =
+      launch_pdl(kern, dim3(grid), dim3(NTX, NTY), smem, st, maps, (T*)o0, (T*)o1, (T*)o2, n, zc,
+                 tiles_x, tiles_y, nitems);
   count_launch();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "k_step_tma launch: %s", cudaGetErrorString(e));
+  }
   return check_launch("k_step_tma");
 }
 
@@ -847,7 +919,7 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
   static std::once_flag once;
   std::call_once(once, [&] {
     cudaFuncSetAttribute(k_step2_kahan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step2_kahan, NTX * NTY, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step2_kahan, tb2::NT2, smem);
     if (occ < 1) occ = 1;
   });
   const int n = pl.n;
@@ -864,9 +936,14 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
   zchunks = (n + zc - 1) / zc;
   const int nitems = tiles_x * tiles_y * zchunks;
   const int grid = nitems < slots ? nitems : slots;
-  k_step2_kahan<<<grid, dim3(NTX, NTY), smem, st>>>(maps, (float*)po, (float*)dout, (float*)eout,
-                                                   n, zc, tiles_x, tiles_y, nitems);
+  const cudaError_t le = launch_pdl(k_step2_kahan, dim3(grid), dim3(NTX, tb2::NTY2), smem, st, maps,
+                                    (float*)po, (float*)dout, (float*)eout, n, zc, tiles_x,
+                                    tiles_y, nitems);
   count_launch();
+  if (le != cudaSuccess) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "k_step2_kahan launch: %s", cudaGetErrorString(le));
+  }
   return check_launch("k_step2_kahan");
 }
 
