@@ -389,6 +389,79 @@ def run_serve(args):
     return 0
 
 
+def run_serve_vs_fp64(args):
+    """The served FP32 path against the plain FP64 GPU path on the same
+    requests: a burst of the serving pool through the continuous-batching
+    server (FP32-Kahan, all submitted at once: saturated throughput) and the
+    same reconstructions one after another through ffpat_fb_solve in FP64,
+    with the same step and iteration count.  Prints recons/s of both, their
+    ratio and the largest relative L2 difference of a served image from its
+    FP64 reconstruction."""
+    import numpy as np
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    from paper_1901_06503_gb300.inputs import add_noise, config
+
+    build_lib.build()
+    F.lib()
+    dev = torch.device("cuda", 0)
+    pool = []
+    for s in range(1, args.pool + 1):
+        w = config(4, seed=1000 + s)
+        p32 = F.problem(w.n, w.T, w.n_angles, F.FP32_KAHAN)
+        p64 = F.problem(w.n, w.T, w.n_angles, F.FP64)
+        c64 = torch.as_tensor(w.c, device=dev)
+        g64 = F.forward(p64, c64, torch.as_tensor(w.h, device=dev))
+        gd = add_noise(g64.cpu().numpy(), w.noise, w.noise_rel)
+        step = 1.0 / F.opnorm(p64, c64, torch.ones_like(c64), iters=20)
+        pool.append((p32, p64, w.c, gd, step, w.iters, w.n))
+    torch.cuda.synchronize()
+    budget = int(args.budget_gb * (1 << 30))
+    served = {}
+    with F.Server(budget, args.slots) as srv:
+        # warm-up: one request through the server
+        p32, _, c, gd, step, iters, _ = pool[0]
+        srv.wait(srv.submit(p32, c.astype(np.float32), gd.astype(np.float32), 1e-3, step, 1))
+        t0 = time.perf_counter()
+        tickets = [(i, srv.submit(p32, c.astype(np.float32), gd.astype(np.float32), 1e-3, step,
+                                  iters))
+                   for i, (p32, _, c, gd, step, iters, _) in enumerate(pool)]
+        for i, t in tickets:
+            served[i] = srv.wait(t)[0]
+        t_served = time.perf_counter() - t0
+    # FP64, one reconstruction after another (device-resident inputs)
+    t64 = 0.0
+    errs = []
+    for i, (_, p64, c, gd, step, iters, _) in enumerate(pool):
+        c_d = torch.as_tensor(c, device=dev)
+        g_d = torch.as_tensor(gd, device=dev)
+        ws = F.workspace(p64, dev)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        h64, _, _ = F.fb_solve(p64, c_d, g_d, 1e-3, step, iters, ws=ws, history=False)
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - a
+        h64 = h64.cpu().numpy()
+        h32 = np.asarray(served[i], dtype=np.float64)
+        errs.append(float(np.linalg.norm(h32 - h64) / np.linalg.norm(h64)))
+        del ws
+    r_served = len(pool) / t_served
+    r64 = len(pool) / t64
+    line = {"mode": "serve_vs_fp64", "metric": "recons/s", "unit": "recons/s",
+            "served_fp32_kahan": r_served, "plain_fp64_gpu": r64, "ratio": r_served / r64,
+            "max_rel_l2_vs_fp64": max(errs), "rel_l2_vs_fp64": errs,
+            "requests": [{"n": n, "iters": it} for (_, _, _, _, _, it, n) in pool],
+            "config": {"workload": "serving pool: N in {64,96,128,192}, 45/90/180 angles, "
+                                   "T in [0.8,1.4], 20-60 FB iterations; FP32-Kahan served as "
+                                   "one burst vs FP64 ffpat_fb_solve one after another",
+                       "pool": args.pool, "slots": args.slots},
+            "dtype": "f32 vs f64", "data": "synthetic"}
+    print(json.dumps(line))
+    return 0
+
+
 def run_precision(args):
     """FP64 vs FP32 vs FP32-Kahan on the 128^3 single solve: time per FB
     iteration and the relative L2 difference of the iterate from the FP64 GPU
@@ -546,10 +619,12 @@ def main():
     ap.add_argument("--precision", choices=["fp32-kahan", "fp32", "fp64"], default="fp32-kahan")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["fb", "serve", "precision", "paper"], default="fb",
+    ap.add_argument("--mode", choices=["fb", "serve", "serve_vs_fp64", "precision", "paper"],
+                    default="fb",
                     help="fb: the default FB-iteration line; serve: the serving mix; "
                          "precision: FP64 vs FP32 vs FP32-Kahan on the 128^3 solve; "
-                         "paper: the paper's experimental setting in 3D (one- vs two-step)")
+                         "paper: the paper's experimental setting in 3D (one- vs two-step); "
+                         "serve_vs_fp64: served FP32 burst vs plain FP64 GPU solves")
     ap.add_argument("--paper-n", type=int, default=64, help="paper: source box points per axis")
     ap.add_argument("--paper-angles", type=int, default=180, help="paper: projection angles")
     ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window (s)")
@@ -563,6 +638,8 @@ def main():
         return run_serve(args)
     if args.mode == "precision":
         return run_precision(args)
+    if args.mode == "serve_vs_fp64":
+        return run_serve_vs_fp64(args)
     if args.mode == "paper":
         return run_paper(args)
     if args.impl == "reference":
