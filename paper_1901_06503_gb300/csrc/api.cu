@@ -468,7 +468,7 @@ static int data_gradient(const Plan& pl, const void* v, const void* g, const voi
   const Plan wp = wave_plan(pl);
   const void* pN = nullptr;
   TRY(wave_fwd(pl, v, &pN, st));
-  TRY(launch_project(wp, pN, pl.r, g, st, mask));
+  TRY(launch_project(wp, pN, pl.r, g, st, mask, wave_in(pl)));
   const void* lr = pl.r;
   if (pl.precond == FFPAT_PRECOND_RAMP) {
     TRY(launch_ramp(wp, pl.r, pl.r2, st, mask));
@@ -592,7 +592,7 @@ int ffpat_forward(const ffpat_problem* problem, const void* c, const void* h, vo
   if (!h || !g) return fail(FFPAT_EINVAL, "h or g is NULL");
   const void* pN = nullptr;
   TRY(wave_fwd(pl, h, &pN, st));
-  TRY(launch_project(wave_plan(pl), pN, g, nullptr, st));
+  TRY(launch_project(wave_plan(pl), pN, g, nullptr, st, nullptr, wave_in(pl)));
   return FFPAT_OK;
 }
 
@@ -635,9 +635,13 @@ int ffpat_project(const ffpat_problem* problem, const void* p, void* g, void* st
   TRY(validate(problem, pl));
   if (!p || !g) return fail(FFPAT_EINVAL, "p or g is NULL");
   void* tabs = nullptr;
+  void* tr = nullptr;
+  const size_t trb = project_scratch_bytes(wave_plan(pl));
   CK(cudaMallocAsync(&tabs, table_bytes(pl.nth), st));
+  if (trb) CK(cudaMallocAsync(&tr, trb, st));
   int rc = upload_tables(pl, tabs, st);
-  if (rc == FFPAT_OK) rc = launch_project(wave_plan(pl), p, g, nullptr, st);
+  if (rc == FFPAT_OK) rc = launch_project(wave_plan(pl), p, g, nullptr, st, nullptr, tr);
+  if (tr) CK(cudaFreeAsync(tr, st));
   CK(cudaFreeAsync(tabs, st));
   TRY(rc);
   CK(cudaStreamSynchronize(st));

@@ -101,7 +101,7 @@ int ffpat_forward_ckpt(const ffpat_problem* problem, const void* c, const void* 
         return check_launch("checkpoint copy");
     }
   }
-  return launch_project(pl, B, g, nullptr, st);
+  return launch_project(pl, B, g, nullptr, st, nullptr, pl.x);
 }
 
 int ffpat_backward(const ffpat_problem* problem, const void* c, const void* grad_g, void* grad_h,

@@ -117,8 +117,13 @@ int launch_wait_timeout(long long cycles, cudaStream_t st);
 
 // xray.cu
 // g = mask .* (P p - sub)  (sub, mask nullable)
+// scratch (nullable): a volume of the plan's grid that aliases neither p nor
+// g; when the planes are too large for shared memory it receives a transposed
+// copy of p, from which the steep angles read (same result, coalesced loads).
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st,
-                   const void* mask = nullptr);
+                   const void* mask = nullptr, void* scratch = nullptr);
+// bytes of that scratch (0 when the shared-memory kernel is used)
+size_t project_scratch_bytes(const Plan& pl);
 // h = mult * scale .* P^T g  (scale nullable)
 int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale, cudaStream_t st,
                        double mult = 1.0);

@@ -186,7 +186,8 @@ int after_wave(ffpat_server* S, Req& r) {
   const Plan& pl = r.pl;
   const bool power = r.it < r.power_iters;
   if (r.phase == kFwd) {
-    if (launch_project(pl, r.cur, pl.r, power ? nullptr : r.g_d, st) != FFPAT_OK) return FFPAT_ECUDA;
+    if (launch_project(pl, r.cur, pl.r, power ? nullptr : r.g_d, st, nullptr, pl.x) != FFPAT_OK)
+      return FFPAT_ECUDA;
     const void* lr = pl.r;
     if (pl.precond == FFPAT_PRECOND_RAMP) {
       if (launch_ramp(pl, pl.r, pl.r2, st) != FFPAT_OK) return FFPAT_ECUDA;

@@ -26,6 +26,12 @@
 // Lambda: one CTA per detector row, the row staged in shared memory, the odd
 // taps t_d = -1/(2 pi^2 d^2 dxi) and t_0 = 1/(8 dxi) applied as a linear
 // (non-circular) convolution.
+#include <limits.h>
+#include <math.h>
+#include <stdlib.h>
+
+#include <vector>
+
 #include "internal.cuh"
 
 namespace ffpat {
@@ -103,17 +109,33 @@ __device__ __forceinline__ void ray_range(float cs, float sn, int k, int n, int 
   if (mhi < mlo) mhi = mlo;
 }
 
+// Plane value at (row iy, column ix); `tr`: the plane is stored transposed
+// (column-major), so element (iy, ix) sits at ix * n + iy.
+template <typename T>
+__device__ __forceinline__ T pix2(const T* __restrict__ sl, int n, int iy, int ix, bool tr) {
+  return (ix >= 0 && iy >= 0 && ix < n && iy < n)
+             ? __ldg(sl + (tr ? (size_t)ix * n + iy : (size_t)iy * n + ix))
+             : T(0);
+}
+
+// P from global memory (planes too large for shared memory).  The threads of
+// a block are neighbouring detectors of one angle: at a given sample index
+// they sit one cell apart along (cos, sin).  For steep angles (|sin| > |cos|)
+// that is mostly along y, so their loads would touch one row each; given the
+// transposed planes `pt` the block reads those instead and the same loads run
+// along memory.  Same values, weights and summation order either way.
 template <typename T>
 __global__ void __launch_bounds__(128)
-    k_project(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
-              const T* __restrict__ mask, const double* __restrict__ tab,
-              const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n, int nth,
-              int ns, int nimg) {
+    k_project(const T* __restrict__ p, const T* __restrict__ pt, T* __restrict__ g,
+              const T* __restrict__ sub, const T* __restrict__ mask,
+              const double* __restrict__ tab, const float* __restrict__ tabf,
+              const int32_t* __restrict__ tabi, int n, int nth, int ns, int nimg) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int l = blockIdx.y;
   const int j = blockIdx.z;
-  const T* __restrict__ sl = p + (size_t)l * n * n;
   const float csf = tabf[j], snf = tabf[nth + j];
+  const bool tr = pt != nullptr && fabsf(snf) > fabsf(csf);
+  const T* __restrict__ sl = (tr ? pt : p) + (size_t)l * n * n;
   int mlo = 0, mhi = 0;
   if (k < n) ray_range(csf, snf, k, n, ns, mlo, mhi);
   T acc = T(0);
@@ -125,10 +147,10 @@ __global__ void __launch_bounds__(128)
       double fx, fy;
       sample64(cs, sn, k, m, ns, dx, half, L, i0, j0, fx, fy);
       const double ofx = __dsub_rn(1.0, fx), ofy = __dsub_rn(1.0, fy);
-      double b = __dmul_rn(__dmul_rn(ofx, ofy), pix(sl, n, j0, i0));
-      b = __dadd_rn(b, __dmul_rn(__dmul_rn(fx, ofy), pix(sl, n, j0, i0 + 1)));
-      b = __dadd_rn(b, __dmul_rn(__dmul_rn(ofx, fy), pix(sl, n, j0 + 1, i0)));
-      b = __dadd_rn(b, __dmul_rn(__dmul_rn(fx, fy), pix(sl, n, j0 + 1, i0 + 1)));
+      double b = __dmul_rn(__dmul_rn(ofx, ofy), pix2(sl, n, j0, i0, tr));
+      b = __dadd_rn(b, __dmul_rn(__dmul_rn(fx, ofy), pix2(sl, n, j0, i0 + 1, tr)));
+      b = __dadd_rn(b, __dmul_rn(__dmul_rn(ofx, fy), pix2(sl, n, j0 + 1, i0, tr)));
+      b = __dadd_rn(b, __dmul_rn(__dmul_rn(fx, fy), pix2(sl, n, j0 + 1, i0 + 1, tr)));
       acc = __dadd_rn(acc, b);
     }
     if (k < n) {
@@ -153,8 +175,8 @@ __global__ void __launch_bounds__(128)
       const float fx = frac31(GX), fy = frac31(GY);
       GX += dGX;
       GY += dGY;
-      const float v00 = pix(sl, n, j0, i0), v10 = pix(sl, n, j0, i0 + 1);
-      const float v01 = pix(sl, n, j0 + 1, i0), v11 = pix(sl, n, j0 + 1, i0 + 1);
+      const float v00 = pix2(sl, n, j0, i0, tr), v10 = pix2(sl, n, j0, i0 + 1, tr);
+      const float v01 = pix2(sl, n, j0 + 1, i0, tr), v11 = pix2(sl, n, j0 + 1, i0 + 1, tr);
       const float r0 = fmaf(fx, v10 - v00, v00);
       const float r1 = fmaf(fx, v11 - v01, v01);
       acc += fmaf(fy, r1 - r0, r0);
@@ -259,6 +281,105 @@ __global__ void __launch_bounds__(256)
       if (mask) out = out * mask[oo];
       g[oo] = out;
     }
+  }
+}
+
+// FP32 P for planes too large for shared memory, band by band.  A CTA owns
+// one plane and a group of angles whose rays all run the same way in y (cos
+// >= 0, or cos < 0): it stages the plane in bands of bh rows (plus the zero
+// border) and visits the bands in the order its rays cross them, so every ray
+// still adds its samples in increasing m, the order of k_project.  Between
+// bands each ray's next sample, end of range and running sum live in shared
+// memory.  A sample belongs to the band of its lower row j0 (the first and
+// last bands take the rows beyond), whose buffer also holds row j0 + 1.
+__global__ void __launch_bounds__(256)
+    k_project_band(const float* __restrict__ p, float* __restrict__ g,
+                   const float* __restrict__ sub, const float* __restrict__ mask,
+                   const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n,
+                   int nth, int ns, int nimg, int group, int jsplit, int bh, int nb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int W = plane_pitch(n);
+  const int HB = bh + 2 * kPad;  // rows of the band buffer
+  float* s = reinterpret_cast<float*>(smem_raw);
+  float* racc = s + (size_t)HB * W;
+  int* rm = reinterpret_cast<int*>(racc + (size_t)group * n);  // next sample of each ray
+  int* rend = rm + (size_t)group * n;                          // end of its sample range
+  const int l = blockIdx.x;
+  const int g1 = (jsplit + group - 1) / group;
+  int ja, jb;
+  if ((int)blockIdx.y < g1) {
+    ja = blockIdx.y * group;
+    jb = min(jsplit, ja + group);
+  } else {
+    ja = jsplit + (blockIdx.y - g1) * group;
+    jb = min(nth, ja + group);
+  }
+  const bool asc = ja < jsplit;
+  const float* __restrict__ sl = p + (size_t)l * n * n;
+  const int work = (jb - ja) * n;
+  for (int w = threadIdx.x; w < work; w += blockDim.x) {
+    const int j = ja + w / n, k = w % n;
+    int mlo, mhi;
+    ray_range(tabf[j], tabf[nth + j], k, n, ns, mlo, mhi);
+    racc[w] = 0.0f;
+    rm[w] = mlo;
+    rend[w] = mhi;
+  }
+  for (int bi = 0; bi < nb; ++bi) {
+    const int b = asc ? bi : nb - 1 - bi;
+    const int y_lo = b * bh;  // first row of the band
+    __syncthreads();
+    for (int yy = threadIdx.x / 32; yy < HB; yy += blockDim.x / 32) {
+      const int y = y_lo - kPad + yy;
+      for (int xx = threadIdx.x % 32; xx < W; xx += 32) {
+        const int x = xx - kPad;
+        s[yy * W + xx] =
+            (x >= 0 && y >= 0 && x < n && y < n) ? __ldg(sl + (size_t)y * n + x) : 0.0f;
+      }
+    }
+    __syncthreads();
+    // rows j0 of this band (the first and last bands take everything beyond)
+    const int jlo = b == 0 ? INT_MIN : y_lo;
+    const int jhi = b == nb - 1 ? INT_MAX : y_lo + bh;
+    for (int w = threadIdx.x; w < work; w += blockDim.x) {
+      const int j = ja + w / n, k = w % n;
+      int m = rm[w];
+      const int mhi = rend[w];
+      if (m >= mhi) continue;
+      float acc = racc[w];
+      const long long CS = tabi[j], SN = tabi[nth + j];
+      const long long u2 = 2LL * k + 1 - n, v2 = 2LL * m + 1 - ns;
+      const long long c2 = (long long)(n - 1) << 30;
+      long long GX = c2 + u2 * CS - v2 * SN;
+      long long GY = c2 + u2 * SN + v2 * CS;
+      const long long dGX = -2 * SN, dGY = 2 * CS;
+      for (; m < mhi; ++m) {
+        const int i0 = (int)(GX >> 31), j0 = (int)(GY >> 31);
+        if (j0 < jlo || j0 >= jhi) break;
+        const float fx = frac31(GX), fy = frac31(GY);
+        GX += dGX;
+        GY += dGY;
+        // buffer offset of corner (i0, j0), clamped into the buffer
+        const int jj = min(max(j0 - y_lo + kPad, 0), HB - 2);
+        const int ii = min(max(i0 + kPad, 0), n + 2 * kPad - 2);
+        const int o = jj * W + ii;
+        const float v00 = s[o], v10 = s[o + 1], v01 = s[o + W], v11 = s[o + W + 1];
+        const float r0 = fmaf(fx, v10 - v00, v00);
+        const float r1 = fmaf(fx, v11 - v01, v01);
+        acc += fmaf(fy, r1 - r0, r0);
+      }
+      racc[w] = acc;
+      rm[w] = m;
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < work; w += blockDim.x) {
+    const int j = ja + w / n, k = w % n;
+    const size_t oo = ((size_t)j * n + l) * n + k;
+    float out = (2.0f / (float)nimg) * racc[w];
+    if (sub) out = out - sub[oo];
+    if (mask) out = out * mask[oo];
+    g[oo] = out;
   }
 }
 
@@ -392,6 +513,24 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// out[l][x][y] = in[l][y][x] for every plane l (32 x 32 tiles through shared memory)
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose_planes(const T* __restrict__ in,
+                                                          T* __restrict__ out, int n) {
+  __shared__ T t[32][33];
+  const size_t off = (size_t)blockIdx.z * n * n;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int y = y0 + r, x = x0 + threadIdx.x;
+    if (x < n && y < n) t[r][threadIdx.x] = in[off + (size_t)y * n + x];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int x = x0 + r, y = y0 + threadIdx.x;
+    if (x < n && y < n) out[off + (size_t)x * n + y] = t[threadIdx.x][r];
+  }
+}
+
 __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int32_t* __restrict__ ij,
                                 double* __restrict__ f, const double* __restrict__ tab, int n,
                                 int nth, int ns, int nimg) {
@@ -411,9 +550,53 @@ __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int3
 
 }  // namespace
 
+static size_t project_smem_bytes(const Plan& pl) {
+  return (size_t)plane_pitch(pl.n) * (pl.n + 2 * kPad) * pl.esize;
+}
+
+// FFPAT_PROJECT_BAND=0 turns the banded projection off (a comparison knob)
+static bool project_band_off() {
+  static const bool off = [] {
+    const char* e = getenv("FFPAT_PROJECT_BAND");
+    return e && e[0] == '0';
+  }();
+  return off;
+}
+
+// The banded projection's shape: a group of angles whose per-ray state (sum
+// and sample range) takes <= 48 KB, and bands of bh >= 16 rows, so that one
+// CTA stays within ~110 KB of shared memory (two per SM).  False if the whole
+// plane fits (the one-pass kernel) or no such band fits (global memory).
+static bool band_plan(const Plan& pl, int* group, int* bh, int* nb, size_t* sm) {
+  // FP64 projections are bound by the FP64 pipes, not by loads: measured on
+  // GB300 the banded kernel gains nothing there (656 ms either way at 384^3, 180
+  // angles) and loses at 256^3, so FP64 keeps the global-memory kernel
+  if (pl.esize != 4 || project_smem_bytes(pl) <= 200 * 1024 || project_band_off()) return false;
+  const int W = plane_pitch(pl.n);
+  int gr = 8;
+  while (gr > 1 && (size_t)gr * pl.n * (pl.esize + 8) > 48 * 1024) gr /= 2;
+  const size_t state = (size_t)gr * pl.n * (pl.esize + 8);
+  const size_t budget = 110 * 1024;
+  const long long rows =
+      state < budget ? (long long)((budget - state) / ((size_t)W * pl.esize)) - 2 * kPad : 0;
+  if (rows < 16) return false;
+  *group = gr;
+  *nb = (int)((pl.n + rows - 1) / rows);
+  *bh = (pl.n + *nb - 1) / *nb;
+  *sm = (size_t)(*bh + 2 * kPad) * W * pl.esize + state;
+  return true;
+}
+
+size_t project_scratch_bytes(const Plan& pl) {
+  int group, bh, nb;
+  size_t sm;
+  if (project_smem_bytes(pl) <= 200 * 1024 || band_plan(pl, &group, &bh, &nb, &sm)) return 0;
+  return (size_t)pl.n * pl.n * pl.n * pl.esize;
+}
+
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st,
-                   const void* mask) {
-  const size_t smem = (size_t)plane_pitch(pl.n) * (pl.n + 2 * kPad) * pl.esize;
+                   const void* mask, void* scratch) {
+  const size_t smem = project_smem_bytes(pl);
   if (smem <= 200 * 1024) {
     // one CTA per (plane, group of 8 angles); the padded plane is read once per CTA
     const int group = 8;
@@ -443,16 +626,46 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
     count_launch();
     return check_launch(__func__);
   }
+  // FP32 planes too large for shared memory: band by band ...
+  int group, bh, nb;
+  size_t sm;
+  if (band_plan(pl, &group, &bh, &nb, &sm)) {
+    // angles with cos >= 0 first (the table is in increasing theta)
+    int jsplit = 0;
+    for (int j = 0; j < pl.nth; ++j)
+      if (cos((M_PI * j) / pl.nth) >= 0.0) jsplit = j + 1;
+    const int groups = (jsplit + group - 1) / group + (pl.nth - jsplit + group - 1) / group;
+    const dim3 grid(pl.n, groups);
+    cudaFuncSetAttribute(k_project_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_project_band<<<grid, 256, sm, st>>>((const float*)p, (float*)g, (const float*)sub,
+                                          (const float*)mask, pl.tabf, pl.tabi, pl.n, pl.nth,
+                                          pl.ns, pl.nimg, group, jsplit, bh, nb);
+    count_launch();
+    return check_launch("k_project_band");
+  }
+  // ... else from global memory; with scratch, the steep angles read a
+  // transposed copy of the volume
+  if (scratch) {
+    const dim3 tg((pl.n + 31) / 32, (pl.n + 31) / 32, pl.n);
+    if (pl.prec == FFPAT_FP64)
+      k_transpose_planes<double><<<tg, dim3(32, 8), 0, st>>>((const double*)p, (double*)scratch,
+                                                            pl.n);
+    else
+      k_transpose_planes<float><<<tg, dim3(32, 8), 0, st>>>((const float*)p, (float*)scratch,
+                                                           pl.n);
+    count_launch();
+    if (check_launch("transpose planes") != FFPAT_OK) return FFPAT_ECUDA;
+  }
   const dim3 block(128);
   const dim3 grid((pl.n + 127) / 128, pl.n, pl.nth);
   if (pl.prec == FFPAT_FP64)
-    k_project<double><<<grid, block, 0, st>>>((const double*)p, (double*)g, (const double*)sub,
-                                              (const double*)mask, pl.tab, pl.tabf, pl.tabi, pl.n,
-                                              pl.nth, pl.ns, pl.nimg);
+    k_project<double><<<grid, block, 0, st>>>((const double*)p, (const double*)scratch, (double*)g,
+                                              (const double*)sub, (const double*)mask, pl.tab,
+                                              pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns, pl.nimg);
   else
-    k_project<float><<<grid, block, 0, st>>>((const float*)p, (float*)g, (const float*)sub,
-                                             (const float*)mask, pl.tab, pl.tabf, pl.tabi, pl.n,
-                                             pl.nth, pl.ns, pl.nimg);
+    k_project<float><<<grid, block, 0, st>>>((const float*)p, (const float*)scratch, (float*)g,
+                                             (const float*)sub, (const float*)mask, pl.tab,
+                                             pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns, pl.nimg);
   count_launch();
   return check_launch(__func__);
 }

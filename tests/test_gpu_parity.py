@@ -71,6 +71,53 @@ def test_project_fp64_bit_exact(n, nth):
     assert np.array_equal(g, o.project(p, nth))
 
 
+# planes too large for shared memory: FP64 (from N ~ 155) from global memory,
+# steep angles through a transposed copy; FP32 (from N ~ 220) band by band,
+# bands visited in each ray's order (odd angle counts put angles on both sides
+# of 90 degrees in one call)
+@pytest.mark.parametrize("n,pad,nth", [(160, 0, 8), (120, 20, 7), (256, 0, 5)])
+def test_project_fp64_large_planes_bit_exact(n, pad, nth):
+    nw = n + 2 * pad
+    p = random_volume(nw, 110 + n)
+    prob = F.problem(n, 1.0, nth, pad=pad)
+    g = host(F.project(prob, dev(p, prob)))
+    assert np.array_equal(g, o.project(p, nth, nimg=n))
+
+
+@pytest.mark.parametrize("n,pad,nth", [(232, 0, 6), (200, 28, 7)])
+def test_project_fp32_large_planes(n, pad, nth):
+    p = random_volume(n + 2 * pad, 120)
+    prob = F.problem(n, 1.0, nth, F.FP32, pad=pad)
+    g = host(F.project(prob, dev(p, prob)))
+    assert rel(g, o.project(as_input(p, F.FP32), nth, nimg=n)) < 5e-7
+
+
+def test_project_fp32_global_fallback(tmp_path):
+    """The FP32 global-memory projection (planes too large even for a band,
+    N >= 1024), forced at N = 232 with FFPAT_PROJECT_BAND=0 in a child
+    process, steep angles through the transposed copy."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    n, nth = 232, 8
+    p = random_volume(n, 130).astype(np.float32)
+    np.save(tmp_path / "p.npy", p)
+    code = (
+        "import sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "from paper_1901_06503_gb300 import ffpat as F\n"
+        f"p = np.load({str(tmp_path / 'p.npy')!r})\n"
+        f"prob = F.problem({n}, 1.0, {nth}, F.FP32)\n"
+        "g = F.project(prob, torch.as_tensor(p, device='cuda'))\n"
+        "torch.cuda.synchronize()\n"
+        f"np.save({str(tmp_path / 'g.npy')!r}, g.cpu().numpy())\n")
+    env = dict(os.environ, FFPAT_PROJECT_BAND="0")
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, timeout=300)
+    g = np.load(tmp_path / "g.npy").astype(np.float64)
+    assert rel(g, o.project(p.astype(np.float64), nth)) < 5e-7
+
+
 @pytest.mark.parametrize("prec", [F.FP32])
 @pytest.mark.parametrize("n,nth", [(24, 6), (33, 7)])
 def test_project_fp32(n, nth, prec):
