@@ -352,6 +352,7 @@ static bool graphs_enabled() {
 
 static int run_wave(const Plan& pl, const void* in, void* out, const void** result,
                     cudaStream_t st) {
+  Trace trace_("W (leapfrog time loop)");
   ProfRec rec{};
   const bool prof = g_prof_on.load();
   if (prof) {
@@ -468,14 +469,17 @@ static int data_gradient(const Plan& pl, const void* v, const void* g, const voi
   const Plan wp = wave_plan(pl);
   const void* pN = nullptr;
   TRY(wave_fwd(pl, v, &pN, st));
-  TRY(launch_project(wp, pN, pl.r, g, st, mask, wave_in(pl)));
-  const void* lr = pl.r;
-  if (pl.precond == FFPAT_PRECOND_RAMP) {
-    TRY(launch_ramp(wp, pl.r, pl.r2, st, mask));
-    lr = pl.r2;
+  {
+    Trace trace_data("P, residual, Lambda, P^T");
+    TRY(launch_project(wp, pN, pl.r, g, st, mask, wave_in(pl)));
+    const void* lr = pl.r;
+    if (pl.precond == FFPAT_PRECOND_RAMP) {
+      TRY(launch_ramp(wp, pl.r, pl.r2, st, mask));
+      lr = pl.r2;
+    }
+    if (dots) TRY(launch_dot(pl, pl.nd, lr, pl.r, dots, st));
+    TRY(launch_backproject(wp, lr, wave_in(pl), wp.kap, st));
   }
-  if (dots) TRY(launch_dot(pl, pl.nd, lr, pl.r, dots, st));
-  TRY(launch_backproject(wp, lr, wave_in(pl), wp.kap, st));
   TRY(wave_back(pl, wave_in(pl), w, st));
   return FFPAT_OK;
 }
@@ -586,6 +590,7 @@ int ffpat_debug_samples(const ffpat_problem* problem, int32_t count, const int32
 
 int ffpat_forward(const ffpat_problem* problem, const void* c, const void* h, void* g, void* ws,
                   size_t ws_bytes, void* stream) {
+  Trace trace_("ffpat_forward");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
@@ -598,6 +603,7 @@ int ffpat_forward(const ffpat_problem* problem, const void* c, const void* h, vo
 
 int ffpat_adjoint(const ffpat_problem* problem, const void* c, const void* g, void* h, void* ws,
                   size_t ws_bytes, void* stream) {
+  Trace trace_("ffpat_adjoint");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
@@ -608,6 +614,7 @@ int ffpat_adjoint(const ffpat_problem* problem, const void* c, const void* g, vo
 
 int ffpat_wave(const ffpat_problem* problem, const void* c, const void* in, void* out,
                int32_t transpose, void* ws, size_t ws_bytes, void* stream) {
+  Trace trace_("ffpat_wave");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
@@ -629,6 +636,7 @@ int ffpat_wave(const ffpat_problem* problem, const void* c, const void* in, void
 }
 
 int ffpat_project(const ffpat_problem* problem, const void* p, void* g, void* stream) {
+  Trace trace_("ffpat_project");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   g_err[0] = 0;
@@ -649,6 +657,7 @@ int ffpat_project(const ffpat_problem* problem, const void* p, void* g, void* st
 }
 
 int ffpat_backproject(const ffpat_problem* problem, const void* g, void* h, void* stream) {
+  Trace trace_("ffpat_backproject");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   g_err[0] = 0;
@@ -665,6 +674,7 @@ int ffpat_backproject(const ffpat_problem* problem, const void* g, void* h, void
 }
 
 int ffpat_ramp(const ffpat_problem* problem, const void* r, void* out, void* stream) {
+  Trace trace_("ffpat_ramp");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   g_err[0] = 0;
@@ -677,6 +687,7 @@ int ffpat_ramp(const ffpat_problem* problem, const void* r, void* out, void* str
 
 int ffpat_prox_grad(const ffpat_problem* problem, double a, const void* f, void* out, void* ws,
                     size_t ws_bytes, void* stream) {
+  Trace trace_("ffpat_prox_grad");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   g_err[0] = 0;
@@ -690,6 +701,7 @@ int ffpat_prox_grad(const ffpat_problem* problem, double a, const void* f, void*
 
 int ffpat_opnorm(const ffpat_problem* problem, const void* c, const void* v0, int32_t iters,
                  double* opnorm_sq, void* ws, size_t ws_bytes, void* stream) {
+  Trace trace_("ffpat_opnorm");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
@@ -712,6 +724,7 @@ int ffpat_fb_solve_ex(const ffpat_problem* problem, const void* c, const void* g
                       double step, int32_t max_iters, double tol, void* h_inout,
                       ffpat_fb_stats* stats, double* history, void* ws, size_t ws_bytes,
                       void* stream) {
+  Trace trace_("ffpat_fb_solve");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
@@ -731,6 +744,7 @@ int ffpat_fb_solve_ex(const ffpat_problem* problem, const void* c, const void* g
   if (!isfinite(step)) return fail(FFPAT_EINVAL, "step is not finite");
   int k = 0;
   for (; k < max_iters; ++k) {
+    Trace trace_it("FB iteration (Algorithm 8)");
     double* hk = pl.hist + 8 * (size_t)k;
     const void* w = nullptr;
     TRY(data_gradient(pl, h_inout, g, &w, hk, st, mask));
@@ -776,6 +790,7 @@ int ffpat_fb_solve_ex(const ffpat_problem* problem, const void* c, const void* g
 
 int ffpat_fbp(const ffpat_problem* problem, const void* G, void* out, void* ws, size_t ws_bytes,
               void* stream) {
+  Trace trace_("ffpat_fbp");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   g_err[0] = 0;
@@ -821,6 +836,7 @@ int ffpat_fb_two_step_ex(const ffpat_problem* problem, const void* c, const void
                          int32_t regulariser, double lambda, double step, int32_t max_iters,
                          double tol, void* h_inout, ffpat_fb_stats* stats, double* history,
                          void* ws, size_t ws_bytes, void* stream) {
+  Trace trace_("ffpat_fb_two_step");
   cudaStream_t st = (cudaStream_t)stream;
   Plan pl;
   TRY(setup(problem, pl, c, ws, ws_bytes, st));
@@ -845,6 +861,7 @@ int ffpat_fb_two_step_ex(const ffpat_problem* problem, const void* c, const void
   TRY(launch_backproject(wp, pl.r2, gt, nullptr, st, 2.0 * M_PI / (pl.nth * pl.dx)));
   int k = 0;
   for (; k < max_iters; ++k) {
+    Trace trace_it("FB iteration (Algorithm 9)");
     double* hk = pl.hist + 8 * (size_t)k;
     const void* w = nullptr;
     TRY(wave_fwd(pl, h_inout, &w, st));

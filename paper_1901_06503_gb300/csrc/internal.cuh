@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ffpat.h"
 
 namespace ffpat {
@@ -67,6 +69,17 @@ int step3(const Plan& pl, bool tma, bool start, const void* p, const void* qin, 
 int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes);
 int time_steps(const Plan& pl, double cmax, int* nt, double* dt);
 void fill_tables_host(int nth, unsigned char* buf);  // table_bytes(nth) bytes
+
+// An NVTX range for the lifetime of a scope: the library's phases (entry
+// points, wave time loops, the data-side kernels, FB iterations, serving
+// ticks) appear by name in profiler timelines.  Without a profiler attached
+// the push and pop cost a few nanoseconds.
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
 
 // ---------------------------------------------------------------- launches --
 void count_launch(int k = 1);

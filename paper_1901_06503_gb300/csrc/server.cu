@@ -324,6 +324,7 @@ void worker_loop(ffpat_server* S) {
     // bounded run-ahead: at most kTickRing ticks queued on the stream
     cudaEvent_t& ev = S->ring[S->ring_pos];
     cudaEventSynchronize(ev);
+    Trace trace_tick("serving tick (batched leapfrog step)");
     int rc = launch_step_batch(batch.data(), (int)batch.size(), S->st);
     for (size_t i = 0; rc == FFPAT_OK && i < in_batch.size(); ++i) {
       Req& r = *in_batch[i];
