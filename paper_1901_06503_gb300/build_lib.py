@@ -45,15 +45,35 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+SAN_OUT = os.path.join(HERE, "_build_san")
+SAN_LIB = os.path.join(SAN_OUT, "libffpat_san.so")
+# (one host flag per -Xcompiler: nvcc splits its argument at commas)
+SAN_FLAGS = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+             "-Xcompiler", "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize-recover=all"]
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     if not force and up_to_date():
         return LIB
-    os.makedirs(OUT, exist_ok=True)
+    return _build(LIB, OUT, list(extra or []), [], verbose)
+
+
+def build_sanitized(force: bool = False, verbose: bool = False) -> str:
+    """The same library with the host code compiled under AddressSanitizer and
+    UndefinedBehaviorSanitizer (device code unchanged), for the host-side
+    tests; load it into a process that preloads the ASan runtime."""
+    if not force and os.path.exists(SAN_LIB) and all(
+            os.path.getmtime(d) <= os.path.getmtime(SAN_LIB) for d in _deps()):
+        return SAN_LIB
+    return _build(SAN_LIB, SAN_OUT, SAN_FLAGS, SAN_FLAGS, verbose)
+
+
+def _build(lib: str, out: str, extra: list[str], link_extra: list[str], verbose: bool) -> str:
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or [])
 
     def one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -66,13 +86,13 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [cc, *ARCH, *link_extra, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

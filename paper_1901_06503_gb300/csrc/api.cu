@@ -82,6 +82,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Validate the problem and fill the size fields of the plan.
 static int validate(const ffpat_problem* pr, Plan& pl) {
+  g_err[0] = 0;
   if (!pr) return fail(FFPAT_EINVAL, "problem is NULL");
   if (pr->n < 1 || pr->n > 2048) return fail(FFPAT_EINVAL, "n = %d outside [1, 2048]", pr->n);
   if (!(pr->T > 0.0) || !isfinite(pr->T)) return fail(FFPAT_EINVAL, "T must be finite and > 0");

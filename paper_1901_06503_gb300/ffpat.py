@@ -20,7 +20,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libffpat.so")
+# FFPAT_LIB=<path> loads another build of the same library (e.g. the sanitizer build)
+LIB_PATH = os.environ.get("FFPAT_LIB") or os.path.join(HERE, "libffpat.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ffpat.h")
 
 FP64, FP32, FP32_KAHAN = 0, 1, 2
