@@ -479,6 +479,98 @@ __global__ void __launch_bounds__(256)
   h[o] = out;
 }
 
+// FP32 P^T with the angles paired as theta_j and theta_j + 90 degrees (even
+// n_angles, even N).  With equal detector and sample spacing the rays of
+// theta + 90 degrees sample exactly the points of theta's lattice: detector
+// k' = m - (Ns - N)/2 and sample m' = (N + Ns)/2 - 1 - k of the rotated angle
+// is the point (k, m) of theta, in the fixed-point coordinates of P as well
+// (the tables hold cos(theta + 90) = -sin(theta), sin(theta + 90) = cos(theta)
+// to the rounding of the angle itself).  So the 3 x 3 candidate weights w_ij
+// that a voxel gets from theta's samples serve both angles: theta's detector
+// kb + i takes the row sum over valid samples, the rotated angle's detector
+// k'(mb + j) the column sum.  Half the weight evaluations of k_backproject2.
+__global__ void __launch_bounds__(256)
+    k_backproject_pair(const float* __restrict__ g, float* __restrict__ h,
+                       const float* __restrict__ scale, const float* __restrict__ tabf,
+                       const int32_t* __restrict__ tabi, int n, int nth, int ns, int nimg,
+                       float mult) {
+  __shared__ float s_cs[kAngleChunk], s_sn[kAngleChunk];
+  __shared__ int s_CS[kAngleChunk], s_SN[kAngleChunk];
+  const int ix = blockIdx.x * 32 + threadIdx.x;
+  const int iy = blockIdx.y * 8 + threadIdx.y;
+  const int l = blockIdx.z;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const bool in = ix < n && iy < n;
+  const int half = nth / 2;
+  const int koff = (ns - n) / 2;       // k' = m - koff
+  const int mrot = (n + ns) / 2 - 1;   // m' = mrot - k
+  const int X2 = 2 * ix - (n - 1), Y2 = 2 * iy - (n - 1);
+  float acc = 0.0f;
+  for (int ja = 0; ja < half; ja += kAngleChunk) {
+    const int jn = min(kAngleChunk, half - ja);
+    __syncthreads();
+    for (int t = tid; t < jn; t += 256) {
+      s_cs[t] = tabf[ja + t];
+      s_sn[t] = tabf[nth + ja + t];
+      s_CS[t] = tabi[ja + t];
+      s_SN[t] = tabi[nth + ja + t];
+    }
+    __syncthreads();
+    if (!in) continue;
+    for (int t = 0; t < jn; ++t) {
+      const float cs = s_cs[t], sn = s_sn[t];
+      const int CS = s_CS[t], SN = s_SN[t];
+      const long long KK = (long long)X2 * CS + (long long)Y2 * SN + ((long long)(n - 1) << 30);
+      const long long MM = (long long)Y2 * CS - (long long)X2 * SN + ((long long)(ns - 1) << 30);
+      const int KI = (int)(KK >> 31), MI = (int)(MM >> 31);
+      const float fk = frac31(KK), fm = frac31(MM);
+      const int hk = fk >= 0.5f ? 1 : 0, hm = fm >= 0.5f ? 1 : 0;
+      const int kb = KI - 1 + hk, mb = MI - 1 + hm;
+      const float du0 = (float)(hk - 1) - fk, dv0 = (float)(hm - 1) - fm;
+      const float a0 = du0 * cs - dv0 * sn, b0 = du0 * sn + dv0 * cs;
+      float w[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const float a = a0 + (float)i * cs - (float)jj * sn;
+          const float b = b0 + (float)i * sn + (float)jj * cs;
+          w[i][jj] = hat1(a) * hat1(b);
+        }
+      const float* __restrict__ row = g + ((size_t)(ja + t) * n + l) * n;
+      const float* __restrict__ row2 = g + ((size_t)(ja + t + half) * n + l) * n;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int k = kb + i;
+        float r = 0.0f;
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const int m = mb + jj;
+          if (m >= 0 && m < ns) r += w[i][jj];
+        }
+        if (k >= 0 && k < n) acc += r * __ldg(row + k);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        const int k2 = mb + jj - koff;
+        float c = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const int m2 = mrot - (kb + i);
+          if (m2 >= 0 && m2 < ns) c += w[i][jj];
+        }
+        if (k2 >= 0 && k2 < n) acc += c * __ldg(row2 + k2);
+      }
+    }
+  }
+  if (!in) return;
+  const size_t o = ((size_t)l * n + iy) * n + ix;
+  float out = (2.0f / (float)nimg) * acc;
+  if (scale) out *= scale[o];
+  if (mult != 1.0f) out *= mult;
+  h[o] = out;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_ramp(const T* __restrict__ r, T* __restrict__ out, const T* __restrict__ mask, int n,
@@ -552,6 +644,15 @@ __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int3
 
 static size_t project_smem_bytes(const Plan& pl) {
   return (size_t)plane_pitch(pl.n) * (pl.n + 2 * kPad) * pl.esize;
+}
+
+// FFPAT_BACKPROJECT_PAIR=0 turns the paired-angle transpose off (a comparison knob)
+static bool backproject_pair_off() {
+  static const bool off = [] {
+    const char* e = getenv("FFPAT_BACKPROJECT_PAIR");
+    return e && e[0] == '0';
+  }();
+  return off;
 }
 
 // FFPAT_PROJECT_BAND=0 turns the banded projection off (a comparison knob)
@@ -674,6 +775,13 @@ int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale
                        double mult) {
   const dim3 block(32, 8);
   const dim3 grid((pl.n + 31) / 32, (pl.n + 7) / 8, pl.n);
+  if (pl.prec != FFPAT_FP64 && pl.nth % 2 == 0 && pl.n % 2 == 0 && !backproject_pair_off()) {
+    k_backproject_pair<<<grid, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
+                                               pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns, pl.nimg,
+                                               (float)mult);
+    count_launch();
+    return check_launch("k_backproject_pair");
+  }
   if (pl.prec == FFPAT_FP64)
     k_backproject2<double><<<grid, block, 0, st>>>((const double*)g, (double*)h,
                                                   (const double*)scale, pl.tab, pl.tabf,

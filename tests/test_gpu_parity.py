@@ -127,8 +127,10 @@ def test_project_fp32(n, nth, prec):
     assert rel(g, o.project(as_input(p, prec), nth)) < 5e-7
 
 
+# FP32 with even N and an even angle count pairs theta with theta + 90 degrees
+# ((24, 6), (40, 12), (64, 90)); the others take the per-angle gather
 @pytest.mark.parametrize("prec", [F.FP64, F.FP32])
-@pytest.mark.parametrize("n,nth", [(24, 6), (33, 7), (40, 13)])
+@pytest.mark.parametrize("n,nth", [(24, 6), (33, 7), (40, 13), (40, 12), (33, 8), (64, 90)])
 def test_backproject(n, nth, prec):
     g = random_data(nth, n, 300 + n)
     prob = F.problem(n, 1.0, nth, prec)
