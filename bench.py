@@ -172,11 +172,14 @@ def run_reference(args):
     import oracle.oracle as o
     o.build()
     w, wl, prob = make_problem(args)
+    # each step is a bounded sample: the whole run stays within a few minutes
+    # whatever --steps is (about 150 s of timed oracle work at most)
+    per_step = min(args.ref_seconds, max(0.5, 150.0 / max(args.steps, 1)))
     for _ in range(args.warmup):
-        oracle_sample(w, seconds_target=1.0)
+        oracle_sample(w, seconds_target=min(1.0, per_step))
     vals, total_vs, total_s = [], 0.0, 0.0
     for _ in range(args.steps):
-        v, steps, el, cores = oracle_sample(w, seconds_target=args.ref_seconds)
+        v, steps, el, cores = oracle_sample(w, seconds_target=per_step)
         total_vs += steps * float(w.n) ** 3
         total_s += el
     value = total_vs / total_s
