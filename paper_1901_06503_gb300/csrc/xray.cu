@@ -304,14 +304,16 @@ __global__ void __launch_bounds__(256)
   float* racc = s + (size_t)HB * W;
   int* rm = reinterpret_cast<int*>(racc + (size_t)group * n);  // next sample of each ray
   int* rend = rm + (size_t)group * n;                          // end of its sample range
-  const int l = blockIdx.x;
+  // angle groups vary fastest, so the CTAs resident together read the same
+  // planes and the plane traffic hits L2
+  const int l = blockIdx.y;
   const int g1 = (jsplit + group - 1) / group;
   int ja, jb;
-  if ((int)blockIdx.y < g1) {
-    ja = blockIdx.y * group;
+  if ((int)blockIdx.x < g1) {
+    ja = blockIdx.x * group;
     jb = min(jsplit, ja + group);
   } else {
-    ja = jsplit + (blockIdx.y - g1) * group;
+    ja = jsplit + (blockIdx.x - g1) * group;
     jb = min(nth, ja + group);
   }
   const bool asc = ja < jsplit;
@@ -394,6 +396,14 @@ template <typename T>
 __device__ __forceinline__ T hat1(T a) {
   const T v = T(1) - fabs(a);
   return v > T(0) ? v : T(0);
+}
+
+// FP32 hat: 1 - |a| <= 1 always, so clamping to [0, 1] is max(0, .); one
+// saturating add on the FMA pipe instead of an add and a min/max on the ALU
+__device__ __forceinline__ float hat1f(float a) { return __saturatef(1.0f - fabsf(a)); }
+template <>
+__device__ __forceinline__ float hat1<float>(float a) {
+  return hat1f(a);
 }
 
 constexpr int kAngleChunk = 1024;
@@ -528,38 +538,36 @@ __global__ void __launch_bounds__(256)
       const int kb = KI - 1 + hk, mb = MI - 1 + hm;
       const float du0 = (float)(hk - 1) - fk, dv0 = (float)(hm - 1) - fm;
       const float a0 = du0 * cs - dv0 * sn, b0 = du0 * sn + dv0 * cs;
-      float w[3][3];
+      // validity of theta's samples mb + jj and of the rotated angle's
+      // samples (its m' = mrot - k) as 0/1 factors
+      float mv[3], mv2[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        mv[q] = (unsigned)(mb + q) < (unsigned)ns ? 1.0f : 0.0f;
+        mv2[q] = (unsigned)(mrot - (kb + q)) < (unsigned)ns ? 1.0f : 0.0f;
+      }
+      float r[3] = {0.0f, 0.0f, 0.0f}, cc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
           const float a = a0 + (float)i * cs - (float)jj * sn;
           const float b = b0 + (float)i * sn + (float)jj * cs;
-          w[i][jj] = hat1(a) * hat1(b);
+          const float w = hat1f(a) * hat1f(b);
+          r[i] = fmaf(w, mv[jj], r[i]);
+          cc[jj] = fmaf(w, mv2[i], cc[jj]);
         }
       const float* __restrict__ row = g + ((size_t)(ja + t) * n + l) * n;
       const float* __restrict__ row2 = g + ((size_t)(ja + t + half) * n + l) * n;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const int k = kb + i;
-        float r = 0.0f;
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const int m = mb + jj;
-          if (m >= 0 && m < ns) r += w[i][jj];
-        }
-        if (k >= 0 && k < n) acc += r * __ldg(row + k);
+        if ((unsigned)k < (unsigned)n) acc = fmaf(r[i], __ldg(row + k), acc);
       }
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) {
         const int k2 = mb + jj - koff;
-        float c = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const int m2 = mrot - (kb + i);
-          if (m2 >= 0 && m2 < ns) c += w[i][jj];
-        }
-        if (k2 >= 0 && k2 < n) acc += c * __ldg(row2 + k2);
+        if ((unsigned)k2 < (unsigned)n) acc = fmaf(cc[jj], __ldg(row2 + k2), acc);
       }
     }
   }
@@ -736,7 +744,7 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
     for (int j = 0; j < pl.nth; ++j)
       if (cos((M_PI * j) / pl.nth) >= 0.0) jsplit = j + 1;
     const int groups = (jsplit + group - 1) / group + (pl.nth - jsplit + group - 1) / group;
-    const dim3 grid(pl.n, groups);
+    const dim3 grid(groups, pl.n);
     cudaFuncSetAttribute(k_project_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_project_band<<<grid, 256, sm, st>>>((const float*)p, (float*)g, (const float*)sub,
                                           (const float*)mask, pl.tabf, pl.tabi, pl.n, pl.nth,
