@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(256)
 // bands each ray's next sample, end of range and running sum live in shared
 // memory.  A sample belongs to the band of its lower row j0 (the first and
 // last bands take the rows beyond), whose buffer also holds row j0 + 1.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
     k_project_band(const float* __restrict__ p, float* __restrict__ g,
                    const float* __restrict__ sub, const float* __restrict__ mask,
                    const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n,
@@ -746,7 +746,7 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
     const int groups = (jsplit + group - 1) / group + (pl.nth - jsplit + group - 1) / group;
     const dim3 grid(groups, pl.n);
     cudaFuncSetAttribute(k_project_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_project_band<<<grid, 256, sm, st>>>((const float*)p, (float*)g, (const float*)sub,
+    k_project_band<<<grid, 1024, sm, st>>>((const float*)p, (float*)g, (const float*)sub,
                                           (const float*)mask, pl.tabf, pl.tabi, pl.n, pl.nth,
                                           pl.ns, pl.nimg, group, jsplit, bh, nb);
     count_launch();
