@@ -41,13 +41,15 @@ constexpr int SP = 8;              // ring of p planes: z-2 .. z+5
 constexpr int SQ = 4;              // ring of per-point stream planes: z .. z+3
 constexpr long long kWaitCycles = 1LL << 31;
 
-template <typename T>
+// Tile geometry for RPT rows per thread: the output tile is TBX x (TBY RPT)
+template <typename T, int RPT = 1>
 struct Geo {
   static constexpr int XH = 16 / (int)sizeof(T);  // x halo rounded up to 16 bytes
+  static constexpr int TH = TBY * RPT;            // tile height
   static constexpr int BXH = TBX + 2 * XH;
-  static constexpr int BYH = TBY + 4;
+  static constexpr int BYH = TH + 4;
   static constexpr int PBYTES = BXH * BYH * (int)sizeof(T);
-  static constexpr int QBYTES = TBX * TBY * (int)sizeof(T);
+  static constexpr int QBYTES = TBX * TH * (int)sizeof(T);
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -187,10 +189,10 @@ __device__ __forceinline__ float3 kahan_update(float c, float k, float L, float 
 
 // Round R brings p plane R (needed while R <= z1 + 1) and the per-point
 // stream planes R - 2 (needed while z0 <= R - 2 < z1) of the item's tile.
-template <typename T, int NQ>
+template <typename T, int NQ, int RPT>
 __device__ __forceinline__ void issue_round(const Maps& maps, T* pst, T* qst, uint64_t* bar, int R,
                                             int z0, int z1, int x0, int y0) {
-  using G = Geo<T>;
+  using G = Geo<T, RPT>;
   const bool wp = R <= z1 + 1;
   const bool wq = (R - 2 >= z0) && (R - 2 < z1);
   if (!wp && !wq) return;
@@ -208,11 +210,11 @@ __device__ __forceinline__ void issue_round(const Maps& maps, T* pst, T* qst, ui
   }
 }
 
-template <typename T, int FORM, bool START>
+template <typename T, int FORM, bool START, int RPT>
 __global__ void __launch_bounds__(NTX* NTY, 2)
     k_step_tma(const __grid_constant__ Maps maps, T* __restrict__ o0, T* __restrict__ o1,
                T* __restrict__ o2, int n, int zc, int tiles_x, int tiles_y, int nitems) {
-  using G = Geo<T>;
+  using G = Geo<T, RPT>;
   constexpr int NQ = Streams<T, FORM, START>::NQ;
   extern __shared__ unsigned char smem_raw[];
   // TMA destinations must be 128-byte aligned: align the dynamic window to 1 KB
@@ -244,11 +246,11 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
     const int tiy = (item / tiles_x) % tiles_y;
     const int z0 = (item / (tiles_x * tiles_y)) * zc;
     const int z1 = min(n, z0 + zc);
-    const int x0 = tix * TBX, y0 = tiy * TBY;
+    const int x0 = tix * TBX, y0 = tiy * G::TH;
 
     if (tid == 0)
       for (int R = z0 - 2; R <= z0 + SP - 3; ++R)
-        issue_round<T, NQ>(maps, pst, qst, bar, R, z0, z1, x0, y0);
+        issue_round<T, NQ, RPT>(maps, pst, qst, bar, R, z0, z1, x0, y0);
 
     bool timed_out = false;
     int waited_upto = z0 - 3;  // last round this thread has waited for
@@ -266,65 +268,69 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
       const T* Pm2 = pst + (size_t)((z - 2) & (SP - 1)) * (G::PBYTES / sizeof(T));
       const T* Pp2 = pst + (size_t)((z + 2) & (SP - 1)) * (G::PBYTES / sizeof(T));
       const T* Q = qst + (size_t)((z & (SQ - 1)) * NQ) * (G::QBYTES / sizeof(T));
-      const int y = y0 + ty;
-      if constexpr (sizeof(T) == 4) {
-        // two x-adjacent points per thread, 64-bit shared and global accesses
-        const int xl = 2 * tx;
-        const int x = x0 + xl;
-        const int o = (ty + 2) * G::BXH + xl + G::XH;
-        const int qo = ty * TBX + xl;
-        constexpr int QS = G::QBYTES / 4;
-        Nb na, nb;
-        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
-        const float La = lap12_nb(na), Lb = lap12_nb(nb);
-        const float2 K = lds2(Q + (NQ - 1) * QS + qo);
-        if (x < n && y < n) {  // N is even, so x + 1 < n as well
-          const size_t gi = (size_t)z * plane + (size_t)y * n + x;
-          if constexpr (FORM == 0) {
-            if constexpr (START) {
-              *reinterpret_cast<float2*>(o0 + gi) =
-                  make_float2(na.c + 0.5f * K.x * La, nb.c + 0.5f * K.y * Lb);
-              if (o1) *reinterpret_cast<float2*>(o1 + gi) = make_float2(na.c, nb.c);
-            } else {
-              const float2 PM = lds2(Q + qo);
-              *reinterpret_cast<float2*>(o0 + gi) =
-                  make_float2(na.c + fmaf(K.x, La, na.c - PM.x), nb.c + fmaf(K.y, Lb, nb.c - PM.y));
-            }
-          } else {
-            float2 D = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
-            if constexpr (!START) {
-              D = lds2(Q + qo);
-              E = lds2(Q + QS + qo);
-            }
-            const float3 ra = kahan_update(na.c, K.x, La, D.x, E.x, START);
-            const float3 rb = kahan_update(nb.c, K.y, Lb, D.y, E.y, START);
-            *reinterpret_cast<float2*>(o0 + gi) = make_float2(ra.x, rb.x);
-            *reinterpret_cast<float2*>(o1 + gi) = make_float2(ra.y, rb.y);
-            *reinterpret_cast<float2*>(o2 + gi) = make_float2(ra.z, rb.z);
-          }
-        }
-      } else {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int xl = tx + 32 * h;
+      for (int rr = 0; rr < RPT; ++rr) {
+        const int ry = ty + TBY * rr;  // tile row of this thread
+        const int y = y0 + ry;
+        if constexpr (sizeof(T) == 4) {
+          // two x-adjacent points per thread, 64-bit shared and global accesses
+          const int xl = 2 * tx;
           const int x = x0 + xl;
-          const int o = (ty + 2) * G::BXH + xl + G::XH;
-          const int qo = ty * TBX + xl;
-          const T L = lap12_sum(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
-          const T c = P0[o];
-          const T k = Q[(NQ - 1) * (G::QBYTES / sizeof(T)) + qo];
-          if (x < n && y < n) {
+          const int o = (ry + 2) * G::BXH + xl + G::XH;
+          const int qo = ry * TBX + xl;
+          constexpr int QS = G::QBYTES / 4;
+          Nb na, nb;
+          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
+          const float La = lap12_nb(na), Lb = lap12_nb(nb);
+          const float2 K = lds2(Q + (NQ - 1) * QS + qo);
+          if (x < n && y < n) {  // N is even, so x + 1 < n as well
             const size_t gi = (size_t)z * plane + (size_t)y * n + x;
-            if constexpr (START) {
-              o0[gi] = c + T(0.5) * k * L;
-              if (o1) o1[gi] = c;
+            if constexpr (FORM == 0) {
+              if constexpr (START) {
+                *reinterpret_cast<float2*>(o0 + gi) =
+                    make_float2(na.c + 0.5f * K.x * La, nb.c + 0.5f * K.y * Lb);
+                if (o1) *reinterpret_cast<float2*>(o1 + gi) = make_float2(na.c, nb.c);
+              } else {
+                const float2 PM = lds2(Q + qo);
+                *reinterpret_cast<float2*>(o0 + gi) =
+                    make_float2(na.c + fmaf(K.x, La, na.c - PM.x), nb.c + fmaf(K.y, Lb, nb.c - PM.y));
+              }
             } else {
-              const T pm = Q[qo];
-              o0[gi] = fma(k, L, fma(2.0, c, -pm));
+              float2 D = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
+              if constexpr (!START) {
+                D = lds2(Q + qo);
+                E = lds2(Q + QS + qo);
+              }
+              const float3 ra = kahan_update(na.c, K.x, La, D.x, E.x, START);
+              const float3 rb = kahan_update(nb.c, K.y, Lb, D.y, E.y, START);
+              *reinterpret_cast<float2*>(o0 + gi) = make_float2(ra.x, rb.x);
+              *reinterpret_cast<float2*>(o1 + gi) = make_float2(ra.y, rb.y);
+              *reinterpret_cast<float2*>(o2 + gi) = make_float2(ra.z, rb.z);
+            }
+          }
+        } else {
+  #pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int xl = tx + 32 * h;
+            const int x = x0 + xl;
+            const int o = (ry + 2) * G::BXH + xl + G::XH;
+            const int qo = ry * TBX + xl;
+            const T L = lap12_sum(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH);
+            const T c = P0[o];
+            const T k = Q[(NQ - 1) * (G::QBYTES / sizeof(T)) + qo];
+            if (x < n && y < n) {
+              const size_t gi = (size_t)z * plane + (size_t)y * n + x;
+              if constexpr (START) {
+                o0[gi] = c + T(0.5) * k * L;
+                if (o1) o1[gi] = c;
+              } else {
+                const T pm = Q[qo];
+                o0[gi] = fma(k, L, fma(2.0, c, -pm));
+              }
             }
           }
         }
-      }
+      }  // rows of this thread
       if (__syncthreads_or(timed_out)) {
         if (tid == 0) {
           atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
         }
         return;
       }
-      if (tid == 0) issue_round<T, NQ>(maps, pst, qst, bar, z + SP - 2, z0, z1, x0, y0);
+      if (tid == 0) issue_round<T, NQ, RPT>(maps, pst, qst, bar, z + SP - 2, z0, z1, x0, y0);
     }
   }
 }
@@ -684,9 +690,9 @@ struct MapKeyHash {
 int make_map_box(CUtensorMap* m, const void* base, int n, int esize, int bx, int by);
 
 // the single-step kernels' boxes: p^n with the two-point halo, or the bare tile
-int make_map(CUtensorMap* m, const void* base, int n, int esize, bool halo) {
+int make_map(CUtensorMap* m, const void* base, int n, int esize, bool halo, int th = TBY) {
   const int xh = 16 / esize;
-  return make_map_box(m, base, n, esize, halo ? TBX + 2 * xh : TBX, halo ? TBY + 4 : TBY);
+  return make_map_box(m, base, n, esize, halo ? TBX + 2 * xh : TBX, halo ? th + 4 : th);
 }
 
 int make_map_box(CUtensorMap* m, const void* base, int n, int esize, int bx, int by) {
@@ -766,12 +772,12 @@ int choose_zchunk(int n, int tiles, int slots) {
   return (n + zchunks - 1) / zchunks;
 }
 
-template <typename T, int FORM, bool START>
+template <typename T, int FORM, bool START, int RPT>
 int launch_one(const Plan& pl, const Maps& maps, void* o0, void* o1, void* o2, cudaStream_t st) {
-  using G = Geo<T>;
+  using G = Geo<T, RPT>;
   constexpr int NQ = Streams<T, FORM, START>::NQ;
   const size_t smem = (size_t)SP * G::PBYTES + (size_t)SQ * NQ * G::QBYTES + SP * 8 + 1024;
-  auto kern = k_step_tma<T, FORM, START>;
+  auto kern = k_step_tma<T, FORM, START, RPT>;
   static int occ = 0;  // per instantiation
   static std::once_flag once;
   std::call_once(once, [&] {
@@ -780,7 +786,7 @@ int launch_one(const Plan& pl, const Maps& maps, void* o0, void* o1, void* o2, c
     if (occ < 1) occ = 1;
   });
   const int n = pl.n;
-  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + TBY - 1) / TBY;
+  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + G::TH - 1) / G::TH;
   const int slots = kNumSMs * occ;
   int zc = choose_zchunk(n, tiles_x * tiles_y, slots);
   if (zchunk_override() > 0) zc = zchunk_override() < n ? zchunk_override() : n;
@@ -807,29 +813,50 @@ bool tma_supported(const Plan& pl, const void* const* ptrs, int count) {
   return true;
 }
 
-int launch_step_tma(const Plan& pl, int form, bool start, const void* p, const void* const* q,
-                    void* o0, void* o1, void* o2, cudaStream_t st) {
+// FFPAT_RPT=<1|2> fixes the rows per thread of the single-step kernel (a
+// tuning knob for measurements; 0 or unset = 2: the 64 x 16 tile, measured
+// faster on GB300 at 128^3 - 384^3 in every precision: fewer halo rows per
+// output row and the per-plane waits and barrier shared by twice the points)
+static int rpt_override() {
+  static int v = [] {
+    const char* e = getenv("FFPAT_RPT");
+    return e ? atoi(e) : 0;
+  }();
+  return v;
+}
+
+template <int RPT>
+static int launch_step_tma_r(const Plan& pl, int form, bool start, const void* p,
+                             const void* const* q, void* o0, void* o1, void* o2, cudaStream_t st) {
   Maps maps;
   const int es = (int)pl.esize;
-  if (make_map(&maps.p, p, pl.n, es, true) != FFPAT_OK) return check_launch("tensor map (p)");
+  const int th = TBY * RPT;
+  if (make_map(&maps.p, p, pl.n, es, true, th) != FFPAT_OK) return check_launch("tensor map (p)");
   const int nq = start ? 1 : (form == 0 ? 2 : 3);
   for (int i = 0; i < 3; ++i) {
     if (i < nq) {
-      if (make_map(&maps.q[i], q[i], pl.n, es, false) != FFPAT_OK)
+      if (make_map(&maps.q[i], q[i], pl.n, es, false, th) != FFPAT_OK)
         return check_launch("tensor map (q)");
     } else {
       maps.q[i] = maps.p;
     }
   }
   if (pl.prec == FFPAT_FP64) {
-    return start ? launch_one<double, 0, true>(pl, maps, o0, o1, o2, st)
-                 : launch_one<double, 0, false>(pl, maps, o0, o1, o2, st);
+    return start ? launch_one<double, 0, true, RPT>(pl, maps, o0, o1, o2, st)
+                 : launch_one<double, 0, false, RPT>(pl, maps, o0, o1, o2, st);
   }
   if (form == 0)
-    return start ? launch_one<float, 0, true>(pl, maps, o0, o1, o2, st)
-                 : launch_one<float, 0, false>(pl, maps, o0, o1, o2, st);
-  return start ? launch_one<float, 1, true>(pl, maps, o0, o1, o2, st)
-               : launch_one<float, 1, false>(pl, maps, o0, o1, o2, st);
+    return start ? launch_one<float, 0, true, RPT>(pl, maps, o0, o1, o2, st)
+                 : launch_one<float, 0, false, RPT>(pl, maps, o0, o1, o2, st);
+  return start ? launch_one<float, 1, true, RPT>(pl, maps, o0, o1, o2, st)
+               : launch_one<float, 1, false, RPT>(pl, maps, o0, o1, o2, st);
+}
+
+int launch_step_tma(const Plan& pl, int form, bool start, const void* p, const void* const* q,
+                    void* o0, void* o1, void* o2, cudaStream_t st) {
+  const int rpt = rpt_override() == 1 ? 1 : 2;
+  if (rpt == 2) return launch_step_tma_r<2>(pl, form, start, p, q, o0, o1, o2, st);
+  return launch_step_tma_r<1>(pl, form, start, p, q, o0, o1, o2, st);
 }
 
 int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
