@@ -31,7 +31,7 @@ FALLBACK_HBM_GBS = 6800.0
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_step_tma_fp32kahan_n128.md,
 # vectorised single-step kernel, cold caches).  Keyed by (workload, precision);
 # None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 33.574656e6}
+NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 33.576448e6}
 
 WORKLOADS = {
     "cfg2": dict(cfg=2, label="single solve N=128^3, 90 angles, T=1.2, 20 balls, GRF sound speed"),
