@@ -372,8 +372,11 @@ struct BatchParams {
   BatchReq r[kMaxBatch];
 };
 
+// the batched kernel's tile: 64 x 16, as the single-step kernel's
+constexpr int kBatchRPT = 2;
+
 __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constant__ BatchParams bp) {
-  using G = Geo<float>;
+  using G = Geo<float, kBatchRPT>;
   constexpr int NQ = 3;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
     const int tiy = (local / q.tiles_x) % q.tiles_y;
     const int z0 = (local / (q.tiles_x * q.tiles_y)) * q.zc;
     const int z1 = min(n, z0 + q.zc);
-    const int x0 = tix * TBX, y0 = tiy * TBY;
+    const int x0 = tix * TBX, y0 = tiy * G::TH;
     const bool start = q.start != 0;
     const size_t plane = (size_t)n * n;
     // round R: p plane R and the stream planes R - 2 (kap only at a start step)
@@ -435,12 +438,14 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
       const float* Pm2 = pst + (size_t)((z - 2) & (SP - 1)) * (G::PBYTES / 4);
       const float* Pp2 = pst + (size_t)((z + 2) & (SP - 1)) * (G::PBYTES / 4);
       const float* Qd = qst + (size_t)((z & (SQ - 1)) * NQ) * (G::QBYTES / 4);
-      const int y = y0 + ty;
-      {
+#pragma unroll
+      for (int rr = 0; rr < kBatchRPT; ++rr) {
+        const int ry = ty + TBY * rr;  // tile row of this thread
+        const int y = y0 + ry;
         const int xl = 2 * tx;
         const int x = x0 + xl;
-        const int o = (ty + 2) * G::BXH + xl + G::XH;
-        const int qo = ty * TBX + xl;
+        const int o = (ry + 2) * G::BXH + xl + G::XH;
+        const int qo = ry * TBX + xl;
         constexpr int QS = G::QBYTES / 4;
         Nb na, nb;
         gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
@@ -862,7 +867,7 @@ int launch_step_tma(const Plan& pl, int form, bool start, const void* p, const v
 int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
   if (count < 1) return FFPAT_OK;
   if (count > kMaxBatch) return report(FFPAT_EINVAL, "batched step: %d requests > %d", count, kMaxBatch);
-  using G = Geo<float>;
+  using G = Geo<float, kBatchRPT>;
   const size_t smem = (size_t)SP * G::PBYTES + (size_t)SQ * 3 * G::QBYTES + SP * 8 + 1024;
   static int occ = 0;
   static std::once_flag once;
@@ -880,11 +885,12 @@ int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
   for (int i = 0; i < count; ++i) {
     const BatchStep& b = steps[i];
     BatchReq& r = bp.r[i];
-    if (make_map(&r.p, b.p, b.n, 4, true) != FFPAT_OK || make_map(&r.q[2], b.kap, b.n, 4, false) != FFPAT_OK)
+    if (make_map(&r.p, b.p, b.n, 4, true, G::TH) != FFPAT_OK ||
+        make_map(&r.q[2], b.kap, b.n, 4, false, G::TH) != FFPAT_OK)
       return report(FFPAT_ECUDA, "batched step: tensor map");
     if (!b.start) {
-      if (make_map(&r.q[0], b.d, b.n, 4, false) != FFPAT_OK ||
-          make_map(&r.q[1], b.e, b.n, 4, false) != FFPAT_OK)
+      if (make_map(&r.q[0], b.d, b.n, 4, false, G::TH) != FFPAT_OK ||
+          make_map(&r.q[1], b.e, b.n, 4, false, G::TH) != FFPAT_OK)
         return report(FFPAT_ECUDA, "batched step: tensor map");
     } else {
       r.q[0] = r.q[2];
@@ -896,7 +902,7 @@ int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
     r.n = b.n;
     r.start = b.start ? 1 : 0;
     r.tiles_x = (b.n + TBX - 1) / TBX;
-    r.tiles_y = (b.n + TBY - 1) / TBY;
+    r.tiles_y = (b.n + G::TH - 1) / G::TH;
     // z-chunks in proportion to this request's share of the points
     const double share = (double)b.n * b.n * b.n / (double)total_points;
     int zchunks = (int)((4.0 * slots * share) / (r.tiles_x * r.tiles_y) + 1.0);
