@@ -270,10 +270,11 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
                 pl.n);
   long long launches = 0;
   if (pl.prec == FFPAT_FP32_KAHAN) {
-    // two steps per pass halve the HBM bytes; below ~256^3 the single-step
-    // kernel wins (the step working set sits in L2 and the two-step kernel has
-    // too few CTAs in flight), measured on GB300
-    const bool two = tma && (path == 3 || (path == 0 && pl.n >= 256));
+    // two steps per pass halve the HBM bytes; up to 256^3 the single-step
+    // kernel wins (measured on GB300: 82 against 92 us per step at 256^3, 261
+    // against 222 at 384^3: the smaller grids give the two-step kernel, one
+    // 185 KB CTA per SM, too few work items)
+    const bool two = tma && (path == 3 || (path == 0 && pl.n >= 320));
     void* P[2] = {pl.s[0], pl.s[1]};
     void* D[2] = {pl.s[2], pl.s[4]};
     void* E[2] = {pl.s[3], pl.s[5]};

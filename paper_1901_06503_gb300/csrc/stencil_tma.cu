@@ -483,9 +483,9 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
 
 // ------------------------------------- two FP32-Kahan steps per pass ----
 // Temporal blocking: one launch advances (p, d, e) from level n to n + 2.
-// Step A recomputes level n + 1 on the 64 x 8 tile plus a two-point x/y halo
-// (68 x 12 points) from a halo-4 box of p^n (72 x 16, starting 16-byte aligned
-// at x0 - 4) and halo-2 boxes of d^n, e^n, kap (72 x 12); step B then forms
+// Step A recomputes level n + 1 on the 64 x 16 tile plus a two-point x/y halo
+// (68 x 20 points) from a halo-4 box of p^n (72 x 24, starting 16-byte aligned
+// at x0 - 4) and halo-2 boxes of d^n, e^n, kap (72 x 20); step B then forms
 // level n + 2 on the tile from the level-(n+1) planes kept in shared memory.
 // Each point's arithmetic is that of the single-step kernel (same Laplacian
 // order, same Kahan update), so two passes of this kernel give bit-identical
@@ -494,9 +494,10 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
 // Points outside the grid read kap = d = e = p = 0 and therefore produce
 // p^{n+1} = 0 there: the zero ghost values of step B come out of step A.
 namespace tb2 {
-constexpr int PW = 72, PH = 16;  // p^n box (x0-4 .., y0-4 ..)
-constexpr int QW = 72, QH = 12;  // d, e, kap, and level-(n+1) p boxes (x0-4 .., y0-2 ..)
-constexpr int PB = PW * PH * 4, QB = QW * QH * 4, TB = TBX * TBY * 4;
+constexpr int TH2 = 16;                // output tile 64 x 16
+constexpr int PW = 72, PH = TH2 + 8;   // p^n box (x0-4 .., y0-4 ..)
+constexpr int QW = 72, QH = TH2 + 4;   // d, e, kap, and level-(n+1) p boxes (x0-4 .., y0-2 ..)
+constexpr int PB = PW * PH * 4, QB = QW * QH * 4, TB = TBX * TH2 * 4;
 // Rings.  One block barrier per plane (after step A): a ring slot may be
 // refilled or rewritten only when its last reader ran before the latest
 // barrier, which sets the depths.
@@ -505,7 +506,7 @@ constexpr int RK = 6;   // kap planes zA-5 .. zA (zA+3 is loaded into zA-3's slo
 constexpr int RD = 3;   // d^n, e^n planes zA .. zA+2
 constexpr int RA = 6;   // level-(n+1) p planes zA-5 .. zA
 constexpr int RAD = 4;  // level-(n+1) d, e tile planes zA-3 .. zA
-constexpr int NTY2 = 13;  // 13 warps: step A's 34 x 12 point pairs take one round
+constexpr int NTY2 = 22;  // 22 warps: step A's 34 x 20 point pairs take one round
 constexpr int NT2 = NTX * NTY2;
 constexpr size_t kSmem = (size_t)RP * PB + (size_t)RK * QB + (size_t)RD * 2 * QB +
                          (size_t)RA * QB + (size_t)RAD * 2 * TB + RP * 8;
@@ -539,7 +540,7 @@ __device__ __forceinline__ void tb2_issue(const Maps2& m, unsigned char* sm, uin
   }
 }
 
-__global__ void __launch_bounds__(tb2::NT2, 2)
+__global__ void __launch_bounds__(tb2::NT2, 1)
     k_step2_kahan(const __grid_constant__ Maps2 maps, float* __restrict__ po,
                   float* __restrict__ dout, float* __restrict__ eout, int n, int zc, int tiles_x,
                   int tiles_y, int nitems) {
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(tb2::NT2, 2)
     const int tiy = (item / tiles_x) % tiles_y;
     const int z0 = (item / (tiles_x * tiles_y)) * zc;
     const int z1 = min(n, z0 + zc);
-    const int x0 = tix * TBX, y0 = tiy * TBY;
+    const int x0 = tix * TBX, y0 = tiy * TH2;
     if (tid == 0)
       for (int R = z0 - 4; R < z0 - 4 + RP; ++R) tb2_issue(maps, sm, bar, R, z0, z1, x0, y0);
     bool timed_out = false;
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(tb2::NT2, 2)
         phase ^= 1u << b;
       }
       waited_upto = zA + 2;
-      // ---- step A: level n+1 at plane zA on the 68 x 12 extended tile
+      // ---- step A: level n+1 at plane zA on the 68 x 20 extended tile
       {
         const float* P0 = P + slot(zA, RP) * (PB / 4);
         const float* Pm1 = P + slot(zA - 1, RP) * (PB / 4);
@@ -604,7 +605,7 @@ __global__ void __launch_bounds__(tb2::NT2, 2)
           const float3 ra = kahan_update(na.c, Kv.x, La, Dv.x, Ev.x, false);
           const float3 rb = kahan_update(nb.c, Kv.y, Lb, Dv.y, Ev.y, false);
           *reinterpret_cast<float2*>(Az + qo) = make_float2(ra.x, rb.x);
-          if (qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TBY) {
+          if (qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TH2) {
             const int to = (qy - 2) * TBX + (qx - 4);
             *reinterpret_cast<float2*>(ADz + to) = make_float2(ra.y, rb.y);
             *reinterpret_cast<float2*>(ADz + TB / 4 + to) = make_float2(ra.z, rb.z);
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__(tb2::NT2, 2)
       // writes zA+1's slots, last read by step B of plane zA-1 (before the
       // barrier above)
       const int zB = zA - 2;
-      if (zB >= z0 && ty < TBY) {
+      if (zB >= z0 && ty < TH2) {
         const float* A0 = A + slot(zB, RA) * (QB / 4);
         const float* Am1 = A + slot(zB - 1, RA) * (QB / 4);
         const float* Ap1 = A + slot(zB + 1, RA) * (QB / 4);
@@ -956,17 +957,13 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
     if (occ < 1) occ = 1;
   });
   const int n = pl.n;
-  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + TBY - 1) / TBY;
+  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + tb2::TH2 - 1) / tb2::TH2;
   const int slots = kNumSMs * occ;
-  // z-ranges: step A repeats 4 planes per range, so keep ranges long where the
-  // grid allows and use enough of them to fill the GPU
-  int zchunks = (2 * slots + tiles_x * tiles_y - 1) / (tiles_x * tiles_y);
-  const int zmax = n / 16 > 0 ? n / 16 : 1;
-  if (zchunks > zmax) zchunks = zmax;
-  if (zchunks < 1) zchunks = 1;
-  int zc = (n + zchunks - 1) / zchunks;
+  // z-ranges: step A repeats 4 planes per range, the same cost model as the
+  // single-step kernel (at 384^3 whole columns: 144 items for 152 slots)
+  int zc = choose_zchunk(n, tiles_x * tiles_y, slots);
   if (zchunk_override() > 0) zc = zchunk_override() < n ? zchunk_override() : n;
-  zchunks = (n + zc - 1) / zc;
+  const int zchunks = (n + zc - 1) / zc;
   const int nitems = tiles_x * tiles_y * zchunks;
   const int grid = nitems < slots ? nitems : slots;
   const cudaError_t le = launch_pdl(k_step2_kahan, dim3(grid), dim3(NTX, tb2::NTY2), smem, st, maps,
