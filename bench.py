@@ -28,10 +28,11 @@ sys.path.insert(0, ROOT)
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_step_tma_fp32kahan_n128.md,
-# vectorised single-step kernel, cold caches).  Keyed by (workload, precision);
-# None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 33.576448e6}
+# (dram__bytes_read.sum + dram__bytes_write.sum, cold caches): the single-step
+# kernel at 128^3 (profiles/k_step_tma_fp32kahan_n128.md) and the two-step
+# kernel at 384^3 (profiles/k_step2_kahan_fp32kahan_n384.md).  Keyed by
+# (workload, precision); None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 33.576448e6, ("cfg5", "fp32-kahan"): 1546.023424e6}
 
 WORKLOADS = {
     "cfg2": dict(cfg=2, label="single solve N=128^3, 90 angles, T=1.2, 20 balls, GRF sound speed"),
