@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(128)
 // the padded plane fits; one CTA per (plane, group of angles), threads over
 // (angle, detector) pairs).  Same per-sample arithmetic as k_project.
 constexpr int kPad = 3;
+constexpr int kProjThreads = 1024;  // threads of the whole-plane kernel (8 angles x N rays)
 
 // row pitch of the staged plane: at least n + 2 kPad, and 1 mod 32 so that the
 // 32 rays of a warp, which cross the plane along one direction, fall on
@@ -206,7 +207,7 @@ __host__ __device__ inline int plane_pitch(int n) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kProjThreads)
     k_project_smem(const T* __restrict__ p, T* __restrict__ g, const T* __restrict__ sub,
                    const T* __restrict__ mask, const double* __restrict__ tab,
                    const float* __restrict__ tabf, const int32_t* __restrict__ tabi, int n,
@@ -717,7 +718,7 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
                              200 * 1024);
         attr = true;
       }
-      k_project_smem<double><<<grid, 256, smem, st>>>((const double*)p, (double*)g,
+      k_project_smem<double><<<grid, kProjThreads, smem, st>>>((const double*)p, (double*)g,
                                                       (const double*)sub, (const double*)mask,
                                                       pl.tab, pl.tabf, pl.tabi, pl.n, pl.nth,
                                                       pl.ns, pl.nimg, group);
@@ -728,7 +729,7 @@ int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cuda
                              200 * 1024);
         attr = true;
       }
-      k_project_smem<float><<<grid, 256, smem, st>>>((const float*)p, (float*)g, (const float*)sub,
+      k_project_smem<float><<<grid, kProjThreads, smem, st>>>((const float*)p, (float*)g, (const float*)sub,
                                                      (const float*)mask, pl.tab, pl.tabf, pl.tabi,
                                                      pl.n, pl.nth, pl.ns, pl.nimg, group);
     }
