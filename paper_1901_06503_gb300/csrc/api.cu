@@ -114,7 +114,11 @@ static int validate(const ffpat_problem* pr, Plan& pl) {
   return FFPAT_OK;
 }
 
-static int nstate(const Plan& pl) { return pl.prec == FFPAT_FP32_KAHAN ? 6 : 2; }
+// state volumes: FP32-Kahan p, p' and double-buffered d, e; FP32 two pairs
+// (p^{n-1}, p^n in, p^{n+1}, p^{n+2} out of a two-step pass); FP64 one pair
+static int nstate(const Plan& pl) {
+  return pl.prec == FFPAT_FP32_KAHAN ? 6 : (pl.prec == FFPAT_FP32 ? 4 : 2);
+}
 
 // Carve the workspace (ws == nullptr: size only).
 static size_t carve(Plan& pl, void* ws) {
@@ -233,6 +237,16 @@ int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_
   return FFPAT_OK;
 }
 
+// FP32-Kahan runs two steps per pass from this N on, single steps below:
+// measured on GB300, 82 against 92 us per step at 256^3 and 261 against 222 at
+// 384^3 (smaller grids give the two-step kernel, one large CTA per SM, too few
+// work items)
+constexpr int kTwoStepMinN = 320;
+
+// algorithmic HBM bytes per point of a two-step pass beyond a single step's:
+// FP32-Kahan moves its 28 B once for both steps, FP32 20 B against 16 B
+static double pass_extra_bytes(const Plan& pl) { return pl.prec == FFPAT_FP32 ? 4.0 : 0.0; }
+
 static double bytes_per_point(const Plan& pl) {
   return pl.prec == FFPAT_FP64 ? 32.0 : (pl.prec == FFPAT_FP32 ? 16.0 : 28.0);
 }
@@ -260,7 +274,7 @@ static int step_inc(const Plan& pl, bool tma, bool start, const void* pin, void*
 // non-null, else it stays in a state buffer whose address is returned through
 // *result; *launches counts the leapfrog launches (one HBM pass each).
 static int wave_sequence(const Plan& pl, const void* in, void* out, const void** result,
-                         long long* nlaunch, cudaStream_t st) {
+                         long long* nlaunch, long long* npairs, cudaStream_t st) {
   const int nt = pl.nt;
   const void* ptrs[10] = {in, out, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3], pl.s[4], pl.s[5]};
   const int path = g_stencil_path.load();
@@ -268,13 +282,10 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
   if (path >= 2 && !tma)
     return fail(FFPAT_EINVAL, "TMA stencil requested but N = %d or an array alignment rules it out",
                 pl.n);
-  long long launches = 0;
+  long long launches = 0, pairs = 0;
   if (pl.prec == FFPAT_FP32_KAHAN) {
-    // two steps per pass halve the HBM bytes; up to 256^3 the single-step
-    // kernel wins (measured on GB300: 82 against 92 us per step at 256^3, 261
-    // against 222 at 384^3: the smaller grids give the two-step kernel, one
-    // 185 KB CTA per SM, too few work items)
-    const bool two = tma && (path == 3 || (path == 0 && pl.n >= 320));
+    // two steps per pass halve the HBM bytes (kTwoStepMinN)
+    const bool two = tma && (path == 3 || (path == 0 && pl.n >= kTwoStepMinN));
     void* P[2] = {pl.s[0], pl.s[1]};
     void* D[2] = {pl.s[2], pl.s[4]};
     void* E[2] = {pl.s[3], pl.s[5]};
@@ -289,6 +300,7 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
       if (two && left >= 2) {
         void* dst = (left == 2 && out) ? out : (cur == P[0] ? P[1] : P[0]);
         TRY(launch_step2_kahan(pl, cur, D[c], E[c], dst, D[o], E[o], st));
+        ++pairs;
         cur = dst;
         c = o;
         left -= 2;
@@ -302,6 +314,37 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
       ++launches;
     }
     if (result) *result = cur;
+  } else if (pl.prec == FFPAT_FP32 && tma && nt >= 3 && path == 3) {
+    // FP32 three-term, two steps per pass, on request only: the single-step
+    // kernel already runs at 0.98 of the HBM copy bandwidth at 384^3 (136 us
+    // per step) and the two-step pass, bound by its 2.3 stencils per point,
+    // takes 187 us per step (measured on GB300).  The pairs (S0, S1) and
+    // (S2, S3) alternate as (p^{n-1}, p^n) inputs and (p^{n+1}, p^{n+2}) outputs
+    void* S[4] = {pl.s[0], pl.s[1], pl.s[2], pl.s[3]};
+    TRY(step3(pl, tma, true, in, nullptr, S[1], S[0], st));  // S1 = p^1, S0 = p^0
+    ++launches;
+    int prev = 0, cur = 1;
+    int left = nt - 1;
+    const void* res = nullptr;
+    while (left >= 2) {
+      const int n1 = cur == 1 ? 2 : 0, n2 = n1 + 1;
+      void* d2 = (left == 2 && out) ? out : S[n2];
+      TRY(launch_step2_f32(pl, S[prev], S[cur], S[n1], d2, st));
+      ++launches;
+      ++pairs;
+      left -= 2;
+      prev = n1;
+      cur = n2;
+      res = d2;
+    }
+    if (left == 1) {
+      // p^{n+1} over p^{n-1}, in place as in the single-step loop
+      void* dst = out ? out : S[prev];
+      TRY(step3(pl, tma, false, S[cur], S[prev], dst, nullptr, st));
+      ++launches;
+      res = dst;
+    }
+    if (result) *result = res;
   } else {
     void* A = pl.s[0];  // p^{n-1}
     void* B = pl.s[1];  // p^n
@@ -324,6 +367,7 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
     }
   }
   *nlaunch = launches;
+  *npairs = pairs;
   return FFPAT_OK;
 }
 
@@ -338,6 +382,7 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   const void* result = nullptr;
   long long launches = 0;
+  long long pairs = 0;  // two-step passes among the launches
   int device = -1;
 };
 static std::mutex g_graph_mu;
@@ -362,7 +407,7 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
     CK(cudaEventCreate(&rec.b));
     CK(cudaEventRecord(rec.a, st));
   }
-  long long launches = 0;
+  long long launches = 0, pairs = 0;
   const void* res = nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(st, &cap));
@@ -391,7 +436,7 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
         static thread_local cudaStream_t cs = nullptr;
         if (!cs) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        const int rc = wave_sequence(pl, in, out, &e.result, &e.launches, cs);
+        const int rc = wave_sequence(pl, in, out, &e.result, &e.launches, &e.pairs, cs);
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
         if (rc != FFPAT_OK) return rc;
@@ -404,6 +449,7 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
       CK(cudaGraphLaunch(e.exec, st));
       res = e.result;
       launches = e.launches;
+      pairs = e.pairs;
       g_graphs.push_back(e);
       done = true;
     } else {
@@ -416,14 +462,15 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
       }
     }
   }
-  if (!done) TRY(wave_sequence(pl, in, out, &res, &launches, st));
+  if (!done) TRY(wave_sequence(pl, in, out, &res, &launches, &pairs, st));
   if (replay_only) count_launch((int)launches);  // the graph's kernels run again
   if (result) *result = res;
   if (prof) {
     CK(cudaEventRecord(rec.b, st));
     rec.steps = pl.nt;
     rec.launches = launches;
-    rec.bytes = (double)launches * (double)pl.n3 * bytes_per_point(pl);
+    rec.bytes = ((double)launches * bytes_per_point(pl) + (double)pairs * pass_extra_bytes(pl)) *
+                (double)pl.n3;
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.push_back(rec);
   }

@@ -123,6 +123,11 @@ constexpr int kMaxBatchRequests = 28;
 // alias the inputs.  TMA layout rules as launch_step_tma.
 int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void* e, void* po,
                        void* dout, void* eout, cudaStream_t st);
+// Two FP32 three-term leapfrog steps in one HBM pass (needs N % 4 == 0, 16-byte
+// aligned arrays): reads p^{n-1} (pm) and p^n (p), writes p^{n+1} (o1) and
+// p^{n+2} (o2); o1, o2 alias neither input.  Bit-identical to two single steps.
+int launch_step2_f32(const Plan& pl, const void* pm, const void* p, void* o1, void* o2,
+                     cudaStream_t st);
 
 // device status word of the TMA kernels (0 = ok, else -FFPAT_* of the first error)
 int read_device_status(unsigned* out, bool clear);

@@ -514,10 +514,10 @@ __host__ __device__ constexpr int slot(int z, int m) { return (z + 64 * m) % m; 
 }  // namespace tb2
 
 struct Maps2 {
-  CUtensorMap p;  // p^n, 72 x 16 box
-  CUtensorMap d;  // d^n, 72 x 12
-  CUtensorMap e;  // e^n, 72 x 12
-  CUtensorMap k;  // kap, 72 x 12
+  CUtensorMap p;  // p^n, 72 x 24 box
+  CUtensorMap d;  // d^n, 72 x 20
+  CUtensorMap e;  // e^n, 72 x 20
+  CUtensorMap k;  // kap, 72 x 20
 };
 
 __device__ __forceinline__ void tb2_issue(const Maps2& m, unsigned char* sm, uint64_t* bar, int R,
@@ -656,6 +656,174 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
           *reinterpret_cast<float2*>(po + gi) = make_float2(ra.x, rb.x);
           *reinterpret_cast<float2*>(dout + gi) = make_float2(ra.y, rb.y);
           *reinterpret_cast<float2*>(eout + gi) = make_float2(ra.z, rb.z);
+        }
+      }
+    }
+    // the next work item refills every ring from its first plane on
+    __syncthreads();
+  }
+}
+
+// ------------------------------- two FP32 three-term steps per pass ----
+// The same temporal blocking for p^{n+1} = 2 p^n - p^{n-1} + kap L p^n: step A
+// forms level n+1 on the 68 x 20 extended tile from a halo-4 box of p^n and
+// halo-2 boxes of p^{n-1} and kap, and writes its tile part; step B forms
+// level n+2 on the tile from the level-(n+1) planes and p^n.  Both levels are
+// outputs (the next pass reads them as p^{n-1}, p^n), so a pass moves 20 B per
+// point per two steps against 32 B for two single steps.  The arithmetic of
+// each point is the single-step kernel's, so results are bit-identical.
+namespace tb3 {
+constexpr int TH = 16;
+constexpr int PW = 72, PH = TH + 8;  // p^n box (x0-4 .., y0-4 ..)
+constexpr int QW = 72, QH = TH + 4;  // p^{n-1}, kap, level-(n+1) boxes (x0-4 .., y0-2 ..)
+constexpr int PB = PW * PH * 4, QB = QW * QH * 4;
+// ring depths (one block barrier per plane, after step A; a slot is refilled
+// or rewritten only after its last reader passed the latest barrier)
+constexpr int RP = 8;   // p^n planes zA-3 .. zA+4 (zA+5 is loaded into zA-3's slot)
+constexpr int RK = 6;   // kap planes zA-5 .. zA (zA+3 is loaded into zA-3's slot)
+constexpr int RM = 3;   // p^{n-1} planes zA .. zA+2 (zA+3 is loaded into zA's slot)
+constexpr int RA = 6;   // level-(n+1) planes zA-5 .. zA
+constexpr int NTY3 = 22;
+constexpr int NT3 = NTX * NTY3;
+constexpr size_t kSmem = (size_t)RP * PB + (size_t)RK * QB + (size_t)RM * QB + (size_t)RA * QB +
+                         RP * 8;
+__host__ __device__ constexpr int slot(int z, int m) { return (z + 64 * m) % m; }
+}  // namespace tb3
+
+struct Maps3 {
+  CUtensorMap p;   // p^n, 72 x 24 box
+  CUtensorMap pm;  // p^{n-1}, 72 x 20
+  CUtensorMap k;   // kap, 72 x 20
+};
+
+// round R: p^n plane R and the p^{n-1}, kap planes R - 2 of the item's tile
+__device__ __forceinline__ void tb3_issue(const Maps3& m, unsigned char* sm, uint64_t* bar, int R,
+                                          int z0, int z1, int x0, int y0) {
+  using namespace tb3;
+  const bool wp = R >= z0 - 4 && R <= z1 + 3;
+  const bool wq = R - 2 >= z0 - 2 && R - 2 <= z1 + 1;
+  if (!wp && !wq) return;
+  uint64_t* b = &bar[slot(R, RP)];
+  mbar_expect_tx(b, (wp ? PB : 0) + (wq ? 2 * QB : 0));
+  float* P = reinterpret_cast<float*>(sm);
+  float* K = reinterpret_cast<float*>(sm + RP * PB);
+  float* M = reinterpret_cast<float*>(sm + RP * PB + RK * QB);
+  if (wp) tma_load_3d(P + slot(R, RP) * (PB / 4), &m.p, x0 - 4, y0 - 4, R, b);
+  if (wq) {
+    const int z = R - 2;
+    tma_load_3d(K + slot(z, RK) * (QB / 4), &m.k, x0 - 4, y0 - 2, z, b);
+    tma_load_3d(M + slot(z, RM) * (QB / 4), &m.pm, x0 - 4, y0 - 2, z, b);
+  }
+}
+
+__global__ void __launch_bounds__(tb3::NT3, 1)
+    k_step2_f32(const __grid_constant__ Maps3 maps, float* __restrict__ o1,
+                float* __restrict__ o2, int n, int zc, int tiles_x, int tiles_y, int nitems) {
+  using namespace tb3;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const float* P = reinterpret_cast<const float*>(sm);
+  const float* K = reinterpret_cast<const float*>(sm + RP * PB);
+  const float* M = reinterpret_cast<const float*>(sm + RP * PB + RK * QB);
+  float* A = reinterpret_cast<float*>(sm + RP * PB + RK * QB + RM * QB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + RP * PB + RK * QB + RM * QB + RA * QB);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * NTX + tx;
+  if (tid == 0) {
+    for (int i = 0; i < RP; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  grid_dependency_sync();
+  if (*(volatile unsigned*)&g_tma_status != 0u) return;
+  __syncthreads();
+  unsigned phase = 0;
+  const size_t plane = (size_t)n * n;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tix = item % tiles_x;
+    const int tiy = (item / tiles_x) % tiles_y;
+    const int z0 = (item / (tiles_x * tiles_y)) * zc;
+    const int z1 = min(n, z0 + zc);
+    const int x0 = tix * TBX, y0 = tiy * TH;
+    if (tid == 0)
+      for (int R = z0 - 4; R <= z0 + 2; ++R) tb3_issue(maps, sm, bar, R, z0, z1, x0, y0);
+    bool timed_out = false;
+    int waited_upto = z0 - 5;
+    for (int zA = z0 - 2; zA <= z1 + 1; ++zA) {
+      for (int R = waited_upto + 1; R <= zA + 2; ++R) {
+        const int b = slot(R, RP);
+        if (!mbar_wait(&bar[b], (phase >> b) & 1u, kWaitCycles)) timed_out = true;
+        phase ^= 1u << b;
+      }
+      waited_upto = zA + 2;
+      // ---- step A: level n+1 at plane zA on the 68 x 20 extended tile
+      {
+        const float* P0 = P + slot(zA, RP) * (PB / 4);
+        const float* Pm1 = P + slot(zA - 1, RP) * (PB / 4);
+        const float* Pp1 = P + slot(zA + 1, RP) * (PB / 4);
+        const float* Pm2 = P + slot(zA - 2, RP) * (PB / 4);
+        const float* Pp2 = P + slot(zA + 2, RP) * (PB / 4);
+        const float* Kz = K + slot(zA, RK) * (QB / 4);
+        const float* Mz = M + slot(zA, RM) * (QB / 4);
+        float* Az = A + slot(zA, RA) * (QB / 4);
+        const bool zout = zA >= z0 && zA < z1;
+        for (int q = tid; q < 34 * QH; q += NT3) {
+          const int qy = q / 34, qx = 2 + 2 * (q % 34);
+          const int po_ = (qy + 2) * PW + qx;
+          const int qo = qy * QW + qx;
+          Nb na, nb;
+          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, na, nb);
+          const float La = lap12_nb(na), Lb = lap12_nb(nb);
+          const float2 Kv = lds2(Kz + qo), PM = lds2(Mz + qo);
+          const float2 r = make_float2(na.c + fmaf(Kv.x, La, na.c - PM.x),
+                                       nb.c + fmaf(Kv.y, Lb, nb.c - PM.y));
+          *reinterpret_cast<float2*>(Az + qo) = r;
+          if (zout && qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TH) {
+            const int x = x0 + qx - 4, y = y0 + qy - 2;
+            if (x < n && y < n)
+              *reinterpret_cast<float2*>(o1 + (size_t)zA * plane + (size_t)y * n + x) = r;
+          }
+        }
+      }
+      // the plane's only block barrier, also the vote on a timed-out wait
+      if (__syncthreads_or(timed_out)) {
+        if (tid == 0) {
+          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+          for (int R = waited_upto + 1; R <= min(z1 + 3, zA + 4); ++R) {
+            const int b = slot(R, RP);
+            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
+            phase ^= 1u << b;
+          }
+        }
+        return;
+      }
+      // refill: p^n plane zA+5 into zA-3's slot (last read by step B of the
+      // previous plane), kap zA+3 into zA-3's (likewise), p^{n-1} zA+3 into
+      // zA's (last read by step A above)
+      if (tid == 0) tb3_issue(maps, sm, bar, zA + 5, z0, z1, x0, y0);
+      // ---- step B: level n+2 at plane zB = zA - 2 on the tile: reads the
+      // level-(n+1) planes zA-4 .. zA, p^n and kap at zB; step A of plane zA+1
+      // rewrites zA-5's level-(n+1) slot, last read by step B of plane zA-1
+      const int zB = zA - 2;
+      if (zB >= z0 && ty < TH) {
+        const float* A0 = A + slot(zB, RA) * (QB / 4);
+        const float* Am1 = A + slot(zB - 1, RA) * (QB / 4);
+        const float* Ap1 = A + slot(zB + 1, RA) * (QB / 4);
+        const float* Am2 = A + slot(zB - 2, RA) * (QB / 4);
+        const float* Ap2 = A + slot(zB + 2, RA) * (QB / 4);
+        const float* Kz = K + slot(zB, RK) * (QB / 4);
+        const float* Pz = P + slot(zB, RP) * (PB / 4);
+        const int xl = 2 * tx;
+        const int x = x0 + xl, y = y0 + ty;
+        const int qo = (ty + 2) * QW + xl + 4;
+        const int po_ = (ty + 4) * PW + xl + 4;
+        Nb na, nb;
+        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, na, nb);
+        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        const float2 Kv = lds2(Kz + qo), PN = lds2(Pz + po_);
+        if (x < n && y < n) {
+          const size_t gi = (size_t)zB * plane + (size_t)y * n + x;
+          *reinterpret_cast<float2*>(o2 + gi) =
+              make_float2(na.c + fmaf(Kv.x, La, na.c - PN.x), nb.c + fmaf(Kv.y, Lb, nb.c - PN.y));
         }
       }
     }
@@ -975,6 +1143,39 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
     return report(FFPAT_ECUDA, "k_step2_kahan launch: %s", cudaGetErrorString(le));
   }
   return check_launch("k_step2_kahan");
+}
+
+int launch_step2_f32(const Plan& pl, const void* pm, const void* p, void* o1, void* o2,
+                     cudaStream_t st) {
+  Maps3 maps;
+  if (make_map_box(&maps.p, p, pl.n, 4, tb3::PW, tb3::PH) != FFPAT_OK ||
+      make_map_box(&maps.pm, pm, pl.n, 4, tb3::QW, tb3::QH) != FFPAT_OK ||
+      make_map_box(&maps.k, pl.kap, pl.n, 4, tb3::QW, tb3::QH) != FFPAT_OK)
+    return report(FFPAT_ECUDA, "two-step kernel: tensor map");
+  const size_t smem = tb3::kSmem + 1024;
+  static int occ = 0;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute(k_step2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step2_f32, tb3::NT3, smem);
+    if (occ < 1) occ = 1;
+  });
+  const int n = pl.n;
+  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + tb3::TH - 1) / tb3::TH;
+  const int slots = kNumSMs * occ;
+  int zc = choose_zchunk(n, tiles_x * tiles_y, slots);
+  if (zchunk_override() > 0) zc = zchunk_override() < n ? zchunk_override() : n;
+  const int zchunks = (n + zc - 1) / zc;
+  const int nitems = tiles_x * tiles_y * zchunks;
+  const int grid = nitems < slots ? nitems : slots;
+  const cudaError_t le = launch_pdl(k_step2_f32, dim3(grid), dim3(NTX, tb3::NTY3), smem, st, maps,
+                                    (float*)o1, (float*)o2, n, zc, tiles_x, tiles_y, nitems);
+  count_launch();
+  if (le != cudaSuccess) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "k_step2_f32 launch: %s", cudaGetErrorString(le));
+  }
+  return check_launch("k_step2_f32");
 }
 
 int read_device_status(unsigned* out, bool clear) {

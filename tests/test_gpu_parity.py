@@ -394,6 +394,30 @@ def test_two_step_kahan_bit_identical(n, T):
     assert F.device_status() == 0
 
 
+@pytest.mark.parametrize("n,T", [(36, 0.4), (36, 0.41), (64, 0.3), (96, 0.21), (128, 0.05)])
+def test_two_step_fp32_bit_identical(n, T):
+    """Two FP32 three-term steps per pass against one step per pass (K1 and,
+    through W^T = K^-1 W K, K3): bit-identical for even and odd step counts
+    and ragged tiles, and matching the oracle."""
+    prec = F.FP32
+    c = as_input(random_speed(n, 1200 + n), prec)
+    h = as_input(random_volume(n, 1201 + n), prec)
+    prob = F.problem(n, T, 4, prec)
+    outs = {}
+    try:
+        for path in (2, 3):
+            F.set_stencil_path(path)
+            outs[path] = (host(F.wave(prob, dev(c, prob), dev(h, prob))),
+                          host(F.wave(prob, dev(c, prob), dev(h, prob), transpose=True)))
+    finally:
+        F.set_stencil_path(0)
+    assert np.array_equal(outs[2][0], outs[3][0])
+    assert np.array_equal(outs[2][1], outs[3][1])
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    assert rel(outs[3][0], o.wave(o.kappa(n, dt, c), h, nt)) < TOL[prec]
+    assert F.device_status() == 0
+
+
 # ---------------------------------------------------- two-step method (Alg. 9) --
 
 @pytest.mark.parametrize("prec", PRECS)
