@@ -574,6 +574,37 @@ static int prox_grad_step(const Plan& pl, void* h, const void* w, double step, d
   return FFPAT_OK;
 }
 
+// After k FB iterations: one device-to-host read of the per-iteration rows
+// (8 doubles: <Lambda r, r>, <r, r>, R(h_k), ||h_k||^2, ||h_{k+1} - h_k||^2,
+// ||h_{k+1}||^2, ...) into the caller's history (4 per iteration: objective,
+// residual norm, relative change, ||h_{k+1}||) and summary.  Synchronises.
+static int report_fb(const Plan& pl, int k, double lambda, double step, double opn,
+                     ffpat_fb_stats* stats, double* history, cudaStream_t st) {
+  std::vector<double> hh(8 * (size_t)(k > 0 ? k : 1), 0.0);
+  if (k > 0) CK(cudaMemcpyAsync(hh.data(), pl.hist, 8 * sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < k && history; ++i) {
+    const double* q = &hh[8 * (size_t)i];
+    history[4 * i + 0] = 0.5 * q[0] + lambda * q[2];
+    history[4 * i + 1] = sqrt(q[1]);
+    history[4 * i + 2] = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
+    history[4 * i + 3] = sqrt(q[5]);
+  }
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->iters_done = k;
+    stats->step = step;
+    stats->opnorm_sq = opn;
+    if (k > 0) {
+      const double* q = &hh[8 * (size_t)(k - 1)];
+      stats->objective = 0.5 * q[0] + lambda * q[2];
+      stats->resid_norm = sqrt(q[1]);
+      stats->rel_change = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
+    }
+  }
+  return FFPAT_OK;
+}
+
 }  // namespace ffpat
 
 using namespace ffpat;
@@ -812,29 +843,7 @@ int ffpat_fb_solve_ex(const ffpat_problem* problem, const void* c, const void* g
       }
     }
   }
-  std::vector<double> hh(8 * (size_t)(k > 0 ? k : 1), 0.0);
-  if (k > 0) CK(cudaMemcpyAsync(hh.data(), pl.hist, 8 * sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  for (int i = 0; i < k && history; ++i) {
-    const double* q = &hh[8 * (size_t)i];
-    history[4 * i + 0] = 0.5 * q[0] + lambda * q[2];
-    history[4 * i + 1] = sqrt(q[1]);
-    history[4 * i + 2] = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
-    history[4 * i + 3] = sqrt(q[5]);
-  }
-  if (stats) {
-    memset(stats, 0, sizeof *stats);
-    stats->iters_done = k;
-    stats->step = step;
-    stats->opnorm_sq = opn;
-    if (k > 0) {
-      const double* q = &hh[8 * (size_t)(k - 1)];
-      stats->objective = 0.5 * q[0] + lambda * q[2];
-      stats->resid_norm = sqrt(q[1]);
-      stats->rel_change = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
-    }
-  }
-  return FFPAT_OK;
+  return report_fb(pl, k, lambda, step, opn, stats, history, st);
 }
 
 int ffpat_fbp(const ffpat_problem* problem, const void* G, void* out, void* ws, size_t ws_bytes,
@@ -930,29 +939,7 @@ int ffpat_fb_two_step_ex(const ffpat_problem* problem, const void* c, const void
       }
     }
   }
-  std::vector<double> hh(8 * (size_t)(k > 0 ? k : 1), 0.0);
-  if (k > 0) CK(cudaMemcpyAsync(hh.data(), pl.hist, 8 * sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  for (int i = 0; i < k && history; ++i) {
-    const double* q = &hh[8 * (size_t)i];
-    history[4 * i + 0] = 0.5 * q[0] + lambda * q[2];
-    history[4 * i + 1] = sqrt(q[1]);
-    history[4 * i + 2] = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
-    history[4 * i + 3] = sqrt(q[5]);
-  }
-  if (stats) {
-    memset(stats, 0, sizeof *stats);
-    stats->iters_done = k;
-    stats->step = step;
-    stats->opnorm_sq = opn;
-    if (k > 0) {
-      const double* q = &hh[8 * (size_t)(k - 1)];
-      stats->objective = 0.5 * q[0] + lambda * q[2];
-      stats->resid_norm = sqrt(q[1]);
-      stats->rel_change = sqrt(q[4]) / fmax(sqrt(q[3]), 1e-300);
-    }
-  }
-  return FFPAT_OK;
+  return report_fb(pl, k, lambda, step, opn, stats, history, st);
 }
 
 int ffpat_profile_enable(int32_t on) {
