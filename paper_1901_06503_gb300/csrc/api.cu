@@ -389,6 +389,13 @@ static std::mutex g_graph_mu;
 static std::vector<GraphEntry> g_graphs;  // most recently used last
 constexpr size_t kMaxGraphs = 32;
 
+// NoGraphs scopes on this host thread: while one is open, time loops are
+// launched step by step and never captured (capture creates a stream and an
+// executable graph, both of which allocate)
+static thread_local int g_no_graphs = 0;
+NoGraphs::NoGraphs() { ++g_no_graphs; }
+NoGraphs::~NoGraphs() { --g_no_graphs; }
+
 static bool graphs_enabled() {
   static const bool on = [] {
     const char* e = getenv("FFPAT_GRAPHS");
@@ -414,7 +421,7 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
   int dev = 0;
   CK(cudaGetDevice(&dev));
   bool done = false, replay_only = false;
-  if (graphs_enabled() && cap == cudaStreamCaptureStatusNone && pl.nt >= 8) {
+  if (graphs_enabled() && g_no_graphs == 0 && cap == cudaStreamCaptureStatusNone && pl.nt >= 8) {
     std::vector<const void*> key = {in, out, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3],
                                     pl.s[4], pl.s[5], (const void*)(intptr_t)pl.nt,
                                     (const void*)(intptr_t)pl.prec,

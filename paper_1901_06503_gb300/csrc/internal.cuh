@@ -81,6 +81,15 @@ struct Trace {
   Trace& operator=(const Trace&) = delete;
 };
 
+// While an object of this type lives, wave time loops on this host thread are
+// not captured into CUDA graphs (used by the allocation-free entry point).
+struct NoGraphs {
+  NoGraphs();
+  ~NoGraphs();
+  NoGraphs(const NoGraphs&) = delete;
+  NoGraphs& operator=(const NoGraphs&) = delete;
+};
+
 // ---------------------------------------------------------------- launches --
 void count_launch(int k = 1);
 // FFPAT_OK, or FFPAT_ECUDA with the pending launch error recorded for ffpat_last_error()

@@ -7,7 +7,9 @@
 // that must never enter the allocator, or host code holding device pointers it
 // received but no allocator of its own.  For them this entry point runs the
 // same forward operator as ffpat_forward, with its scratch in a file-scope
-// device array instead of a caller workspace.
+// device array instead of a caller workspace, and with the time loop launched
+// step by step (ffpat_forward replays repeated time loops from CUDA graphs,
+// whose capture and instantiation allocate).
 //
 // The array is kScratchBytes (32 MiB) of device memory that every GPU which
 // loads the library holds until the process exits; problems whose workspace
@@ -72,5 +74,8 @@ extern "C" int ffpat_forward_noalloc(const ffpat_problem* problem, const void* c
   if (ffpat::scratch_address(&ws) != FFPAT_OK)
     return ffpat::report(FFPAT_ECUDA,
                          "ffpat_forward_noalloc: cudaGetSymbolAddress of the static scratch failed");
+  // launch the time loop step by step: the library's CUDA-graph replay would
+  // create a capture stream and instantiate a graph, which allocate
+  ffpat::NoGraphs no_graphs;
   return ffpat_forward(problem, c, h, g, ws, ffpat::kScratchBytes, stream);
 }
