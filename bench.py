@@ -469,7 +469,9 @@ def run_serve_vs_fp64(args):
 def run_precision(args):
     """FP64 vs FP32 vs FP32-Kahan on the 128^3 single solve: time per FB
     iteration and the relative L2 difference of the iterate from the FP64 GPU
-    iterate after the same number of iterations."""
+    iterate after the same number of iterations; and the relative L2
+    difference of one W application (1344 leapfrog steps) on the 384^3
+    workload from the FP64 GPU result."""
     import numpy as np
     import torch
 
@@ -505,6 +507,22 @@ def run_precision(args):
         out[name] = {"ms_per_fb_iter": ms,
                      "rel_l2_vs_fp64_gpu": float((h - ref).norm() / ref.norm()),
                      "speedup_vs_fp64": res["fp64"][1] / ms}
+    # one application of W on the long 384^3 workload (1344 steps), where the
+    # rounding of the FP32 forms accumulates longest
+    w5 = config(5)
+    waves = {}
+    for name, prec in (("fp64", F.FP64), ("fp32", F.FP32), ("fp32-kahan", F.FP32_KAHAN)):
+        prob = F.problem(w5.n, w5.T, w5.n_angles, prec)
+        dt = F.torch_dtype(prob)
+        c5 = torch.as_tensor(w5.c, device=dev).to(dt)
+        h5 = torch.as_tensor(w5.h, device=dev).to(dt)
+        waves[name] = F.wave(prob, c5, h5).double()
+        del c5, h5
+        torch.cuda.synchronize()
+    r5 = waves["fp64"]
+    nt5, _, _ = F.problem_info(F.problem(w5.n, w5.T, w5.n_angles), float(w5.c.max()))
+    out["wave_384"] = {"nt": nt5, **{name: float((v - r5).norm() / r5.norm())
+                                     for name, v in waves.items() if name != "fp64"}}
     print(json.dumps(out))
     return 0
 
