@@ -295,9 +295,18 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, steps, el, cores = oracle_sample(w, seconds_target=args.ref_seconds)
+        # and on one core, a shorter sample
+        import oracle.oracle as o
+        o.set_num_threads(1)
+        try:
+            v1, steps1, el1, _ = oracle_sample(w, seconds_target=min(3.0, args.ref_seconds))
+        finally:
+            o.set_num_threads(cores)
         cpu = {"value": v, "unit": "voxel-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"FP64 CPU oracle wave operator W: {steps} leapfrog steps on the "
-                         f"{w.n}^3 grid ({el:.1f} s)"}
+                         f"{w.n}^3 grid ({el:.1f} s)",
+               "value_1core": v1,
+               "sample_1core": f"the same on one core: {steps1} steps ({el1:.1f} s)"}
     bpp = {F.FP64: 32, F.FP32: 16, F.FP32_KAHAN: 28}[prob.precision]
     line = {
         "metric": "voxel-steps/s", "value": value, "unit": "voxel-steps/s", "n_gpus": world,
