@@ -3,15 +3,16 @@
 //
 // Same arithmetic as stencil.cu (see there for the two time-update forms);
 // what changes is how the data reach the SM:
-//   * every CTA owns a 64 x 8 (x, y) column tile and a z-range; a persistent
-//     grid walks the (tile, z-range) work items;
+//   * every CTA owns a 64 x (8 RPT) (x, y) column tile and a z-range (RPT =
+//     2 rows per thread by default: 64 x 16 tiles); a persistent grid walks
+//     the (tile, z-range) work items;
 //   * one thread issues cp.async.bulk.tensor (TMA) copies: the plane of p^n
-//     with its two-point x/y halo (a 72 x 12 float box starting 16-byte
-//     aligned at x0 - 4) into an 8-deep ring of shared-memory planes, and the
-//     halo-free tiles of the per-point streams (p^{n-1}, or d and e, and kap)
-//     into a 4-deep ring; an mbarrier per round counts the bytes in;
-//   * the ring runs three planes ahead of the plane being computed, so about
-//     30 KB per CTA are always in flight;
+//     with its two-point x/y halo (a 72 x 20 float box for 64 x 16 tiles,
+//     starting 16-byte aligned at x0 - 4) into an 8-deep ring of
+//     shared-memory planes, and the halo-free tiles of the per-point streams
+//     (p^{n-1}, or d and e, and kap) into a 4-deep ring; an mbarrier per
+//     round counts the bytes in;
+//   * the ring runs three planes ahead of the plane being computed;
 //   * zero ghost values outside the box come for free: TMA fills boxes that
 //     cross the tensor bounds with zeros, including whole planes z < 0, z >= N;
 //   * the z-neighbours z +- 1, z +- 2 are read from the neighbouring ring
