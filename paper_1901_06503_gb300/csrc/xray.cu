@@ -580,6 +580,147 @@ __global__ void __launch_bounds__(256)
   h[o] = out;
 }
 
+// The 3 x 3 candidate weights of one voxel for angle theta (fixed-point
+// frame KK, MM), reduced to row sums over theta's valid samples (r) and
+// column sums over the rotated angle's valid samples (c), with the first
+// candidate detector kb and sample mb (see k_backproject_pair).
+struct Sums3 {
+  float r[3], c[3];
+  int kb, mb;
+};
+
+__device__ __forceinline__ Sums3 candidate_sums(long long KK, long long MM, float cs, float sn,
+                                                int ns, int mrot) {
+  Sums3 o;
+  const int KI = (int)(KK >> 31), MI = (int)(MM >> 31);
+  const float fk = frac31(KK), fm = frac31(MM);
+  const int hk = fk >= 0.5f ? 1 : 0, hm = fm >= 0.5f ? 1 : 0;
+  o.kb = KI - 1 + hk;
+  o.mb = MI - 1 + hm;
+  const float du0 = (float)(hk - 1) - fk, dv0 = (float)(hm - 1) - fm;
+  const float a0 = du0 * cs - dv0 * sn, b0 = du0 * sn + dv0 * cs;
+  float mv[3], mv2[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    mv[q] = (unsigned)(o.mb + q) < (unsigned)ns ? 1.0f : 0.0f;
+    mv2[q] = (unsigned)(mrot - (o.kb + q)) < (unsigned)ns ? 1.0f : 0.0f;
+    o.r[q] = 0.0f;
+    o.c[q] = 0.0f;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) {
+      const float a = a0 + (float)i * cs - (float)jj * sn;
+      const float b = b0 + (float)i * sn + (float)jj * cs;
+      const float w = hat1f(a) * hat1f(b);
+      o.r[i] = fmaf(w, mv[jj], o.r[i]);
+      o.c[jj] = fmaf(w, mv2[i], o.c[jj]);
+    }
+  return o;
+}
+
+// acc += sum_i r_i row[kb + i] + sum_j c_j row2[mb + j - koff] (valid detectors)
+__device__ __forceinline__ float apply_sums(const Sums3& s, const float* __restrict__ row,
+                                            const float* __restrict__ row2, int n, int koff,
+                                            float acc) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = s.kb + i;
+    if ((unsigned)k < (unsigned)n) acc = fmaf(s.r[i], __ldg(row + k), acc);
+  }
+#pragma unroll
+  for (int jj = 0; jj < 3; ++jj) {
+    const int k2 = s.mb + jj - koff;
+    if ((unsigned)k2 < (unsigned)n) acc = fmaf(s.c[jj], __ldg(row2 + k2), acc);
+  }
+  return acc;
+}
+
+// FP32 P^T using two exact symmetries of the sample lattices (even N, even
+// n_angles = 2h).  (1) theta + 90 deg samples theta's lattice points (see
+// k_backproject_pair).  (2) pi - theta samples the mirror image x -> N-1-x of
+// theta's lattice with the sample index reversed (m -> Ns-1-m), which keeps
+// the detector index and the row sums; so the weight sums a voxel u gets at
+// theta are those its mirror u' gets at pi - theta, and (through (1) for the
+// pair pi/2 - theta, pi - theta) at pi/2 - theta with the same column sums and
+// detectors.  A thread owns u and u': for each angle class j = 1 .. h/2 with
+// 2j != h it evaluates the weights of u and u' at theta_j once and applies
+// each set to four angles {j, j + h, 2h - j, h - j}; j = 0 and j = h/2 (0 and
+// 45 degrees) have only the pair (j, j + h).  A quarter of the weight
+// evaluations of k_backproject2.  In fixed point the mirror frame is exact
+// (KK' = -X2 CS + Y2 SN + c, MM' = Y2 CS + X2 SN + c); the tables of
+// pi - theta and pi/2 - theta agree with -cos, sin and sin, cos of theta to the
+// rounding of the angles themselves.
+__global__ void __launch_bounds__(256)
+    k_backproject_quad(const float* __restrict__ g, float* __restrict__ h,
+                       const float* __restrict__ scale, const float* __restrict__ tabf,
+                       const int32_t* __restrict__ tabi, int n, int nth, int ns, int nimg,
+                       float mult) {
+  __shared__ float s_cs[kAngleChunk], s_sn[kAngleChunk];
+  __shared__ int s_CS[kAngleChunk], s_SN[kAngleChunk];
+  const int ix = blockIdx.x * 32 + threadIdx.x;  // voxel u; its mirror is n - 1 - ix
+  const int iy = blockIdx.y * 8 + threadIdx.y;
+  const int l = blockIdx.z;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int nh = n / 2;
+  const bool in = ix < nh && iy < n;
+  const int hh = nth / 2;
+  const int nclass = hh / 2 + 1;        // classes j = 0 .. hh/2
+  const int koff = (ns - n) / 2;
+  const int mrot = (n + ns) / 2 - 1;
+  const long long X2 = 2 * ix - (n - 1), Y2 = 2 * iy - (n - 1);
+  const long long ck = (long long)(n - 1) << 30, cm = (long long)(ns - 1) << 30;
+  const size_t rows = (size_t)n * n;    // stride between the angles' data
+  const float* __restrict__ gl = g + (size_t)l * n;
+  float acc_u = 0.0f, acc_m = 0.0f;
+  for (int ja = 0; ja < nclass; ja += kAngleChunk) {
+    const int jn = min(kAngleChunk, nclass - ja);
+    __syncthreads();
+    for (int t = tid; t < jn; t += 256) {
+      s_cs[t] = tabf[ja + t];
+      s_sn[t] = tabf[nth + ja + t];
+      s_CS[t] = tabi[ja + t];
+      s_SN[t] = tabi[nth + ja + t];
+    }
+    __syncthreads();
+    if (!in) continue;
+    for (int t = 0; t < jn; ++t) {
+      const int j = ja + t;
+      const float cs = s_cs[t], sn = s_sn[t];
+      const long long CS = s_CS[t], SN = s_SN[t];
+      const long long A = X2 * CS, B = Y2 * SN, C = Y2 * CS, D = X2 * SN;
+      const Sums3 su = candidate_sums(A + B + ck, C - D + cm, cs, sn, ns, mrot);
+      const Sums3 sm = candidate_sums(-A + B + ck, C + D + cm, cs, sn, ns, mrot);
+      const float* __restrict__ r0 = gl + (size_t)j * rows;         // theta_j
+      const float* __restrict__ r1 = gl + (size_t)(j + hh) * rows;  // theta_j + 90
+      acc_u = apply_sums(su, r0, r1, n, koff, acc_u);
+      acc_m = apply_sums(sm, r0, r1, n, koff, acc_m);
+      if (j != 0 && 2 * j != hh) {
+        const float* __restrict__ r2 = gl + (size_t)(nth - j) * rows;  // pi - theta_j
+        const float* __restrict__ r3 = gl + (size_t)(hh - j) * rows;   // pi/2 - theta_j
+        acc_m = apply_sums(su, r2, r3, n, koff, acc_m);
+        acc_u = apply_sums(sm, r2, r3, n, koff, acc_u);
+      }
+    }
+  }
+  if (!in) return;
+  const float f = 2.0f / (float)nimg;
+  const size_t ou = ((size_t)l * n + iy) * n + ix;
+  const size_t om = ((size_t)l * n + iy) * n + (n - 1 - ix);
+  float out_u = f * acc_u, out_m = f * acc_m;
+  if (scale) {
+    out_u *= scale[ou];
+    out_m *= scale[om];
+  }
+  if (mult != 1.0f) {
+    out_u *= mult;
+    out_m *= mult;
+  }
+  h[ou] = out_u;
+  h[om] = out_m;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_ramp(const T* __restrict__ r, T* __restrict__ out, const T* __restrict__ mask, int n,
@@ -653,6 +794,15 @@ __global__ void k_debug_samples(int count, const int32_t* __restrict__ jkm, int3
 
 static size_t project_smem_bytes(const Plan& pl) {
   return (size_t)plane_pitch(pl.n) * (pl.n + 2 * kPad) * pl.esize;
+}
+
+// FFPAT_BACKPROJECT_QUAD=0 turns the four-angle transpose off (a comparison knob)
+static bool backproject_quad_off() {
+  static const bool off = [] {
+    const char* e = getenv("FFPAT_BACKPROJECT_QUAD");
+    return e && e[0] == '0';
+  }();
+  return off;
 }
 
 // FFPAT_BACKPROJECT_PAIR=0 turns the paired-angle transpose off (a comparison knob)
@@ -784,6 +934,15 @@ int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale
                        double mult) {
   const dim3 block(32, 8);
   const dim3 grid((pl.n + 31) / 32, (pl.n + 7) / 8, pl.n);
+  if (pl.prec != FFPAT_FP64 && pl.nth % 2 == 0 && pl.n % 2 == 0 && !backproject_quad_off() &&
+      !backproject_pair_off()) {
+    const dim3 gq((pl.n / 2 + 31) / 32, (pl.n + 7) / 8, pl.n);
+    k_backproject_quad<<<gq, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
+                                             pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns, pl.nimg,
+                                             (float)mult);
+    count_launch();
+    return check_launch("k_backproject_quad");
+  }
   if (pl.prec != FFPAT_FP64 && pl.nth % 2 == 0 && pl.n % 2 == 0 && !backproject_pair_off()) {
     k_backproject_pair<<<grid, block, 0, st>>>((const float*)g, (float*)h, (const float*)scale,
                                                pl.tabf, pl.tabi, pl.n, pl.nth, pl.ns, pl.nimg,

@@ -127,16 +127,51 @@ def test_project_fp32(n, nth, prec):
     assert rel(g, o.project(as_input(p, prec), nth)) < 5e-7
 
 
-# FP32 with even N and an even angle count pairs theta with theta + 90 degrees
-# ((24, 6), (40, 12), (64, 90)); the others take the per-angle gather
+# FP32 with even N and an even angle count 2h applies each weight set to the
+# four angles theta, theta + 90, 180 - theta, 90 - theta ((24, 6) and (64, 90):
+# h odd; (40, 12), (24, 4), (48, 16): h even, with the 45-degree class; (16, 2):
+# the pair 0, 90 alone); the others take the per-angle gather
+BP_CASES = [(24, 6), (33, 7), (40, 13), (40, 12), (33, 8), (64, 90), (24, 4), (48, 16), (16, 2)]
+
+
 @pytest.mark.parametrize("prec", [F.FP64, F.FP32])
-@pytest.mark.parametrize("n,nth", [(24, 6), (33, 7), (40, 13), (40, 12), (33, 8), (64, 90)])
+@pytest.mark.parametrize("n,nth", BP_CASES)
 def test_backproject(n, nth, prec):
     g = random_data(nth, n, 300 + n)
     prob = F.problem(n, 1.0, nth, prec)
     h = host(F.backproject(prob, dev(g, prob)))
     want = o.backproject(as_input(g, prec), n)
     assert rel(h, want) < (1e-12 if prec == F.FP64 else 5e-7)
+
+
+@pytest.mark.parametrize("knob", ["FFPAT_BACKPROJECT_QUAD", "FFPAT_BACKPROJECT_PAIR"])
+def test_backproject_fp32_other_kernels(tmp_path, knob):
+    """The FP32 transposes the four-angle kernel replaces, forced in a child
+    process: the theta / theta + 90 pair (QUAD=0) and the per-angle gather
+    (PAIR=0), on the even cases."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cases = [(24, 6), (40, 12), (64, 90)]
+    for i, (n, nth) in enumerate(cases):
+        np.save(tmp_path / f"g{i}.npy", random_data(nth, n, 300 + n).astype(np.float32))
+    code = (
+        "import sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "from paper_1901_06503_gb300 import ffpat as F\n"
+        f"for i, (n, nth) in enumerate({cases!r}):\n"
+        f"    g = np.load({str(tmp_path)!r} + f'/g{{i}}.npy')\n"
+        "    prob = F.problem(n, 1.0, nth, F.FP32)\n"
+        "    h = F.backproject(prob, torch.as_tensor(g, device='cuda'))\n"
+        "    torch.cuda.synchronize()\n"
+        f"    np.save({str(tmp_path)!r} + f'/h{{i}}.npy', h.cpu().numpy())\n")
+    env = dict(os.environ, **{knob: "0"})
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, timeout=300)
+    for i, (n, nth) in enumerate(cases):
+        g = np.load(tmp_path / f"g{i}.npy").astype(np.float64)
+        h = np.load(tmp_path / f"h{i}.npy").astype(np.float64)
+        assert rel(h, o.backproject(g, n)) < 5e-7, (knob, n, nth)
 
 
 @pytest.mark.parametrize("prec", [F.FP64, F.FP32])
