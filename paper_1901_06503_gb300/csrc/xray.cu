@@ -805,7 +805,7 @@ static bool backproject_quad_off() {
   return off;
 }
 
-// FFPAT_BACKPROJECT_PAIR=0 turns the paired-angle transpose off (a comparison knob)
+// FFPAT_BACKPROJECT_PAIR=0 turns both multi-angle transposes off: the per-angle gather runs
 static bool backproject_pair_off() {
   static const bool off = [] {
     const char* e = getenv("FFPAT_BACKPROJECT_PAIR");
