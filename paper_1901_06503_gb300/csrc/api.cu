@@ -26,7 +26,8 @@ static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
 static std::atomic<long long> g_prof_launches{0};
 static std::atomic<int> g_prof_on{0};
-// 0 auto, 1 plain 2.5D kernel, 2 single-step TMA kernel, 3 two-step TMA kernel (FP32-Kahan)
+// 0 auto, 1 plain 2.5D kernel, 2 single-step TMA kernel, 3 two-step TMA kernel (FP32-Kahan),
+// 4 resident time loop (FP32, FP32-Kahan)
 static std::atomic<int> g_stencil_path{0};
 
 struct ProfRec {
@@ -149,6 +150,7 @@ static size_t carve(Plan& pl, void* ws) {
   pl.tabi = tabs ? (int32_t*)((char*)tabs + 24 * (size_t)pl.nth) : nullptr;
   pl.dct = take(dct_bytes(pl.n, pl.esize));
   pl.dct_mu = pl.dct ? (const double*)((char*)pl.dct + 2 * (size_t)pl.n * pl.n * pl.esize) : nullptr;
+  pl.sync = (unsigned*)take(256);
   return off;
 }
 
@@ -418,6 +420,32 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
   const void* res = nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(st, &cap));
+  // grids that fit the GPU's CTA slots run the whole loop in one cooperative
+  // launch (no graph: there is one launch to make; a caller that is capturing
+  // gets the step-by-step loop)
+  const int path = g_stencil_path.load();
+  const int form = pl.prec == FFPAT_FP32_KAHAN ? 1 : 0;
+  if (pl.prec != FFPAT_FP64 && (path == 4 || (path == 0 && cap == cudaStreamCaptureStatusNone))) {
+    const void* ptrs[5] = {in, out, pl.kap, pl.s[0], pl.s[1]};
+    const bool fits = tma_supported(pl, ptrs, 5) && resident_zc(pl, form) > 0;
+    if (path == 4 && !fits)
+      return fail(FFPAT_EINVAL,
+                  "resident time loop requested but N = %d, the precision or an array alignment "
+                  "rules it out", pl.n);
+    if (fits) {
+      TRY(launch_wave_resident(pl, form, in, out, pl.s[0], pl.s[1], &res, st));
+      if (result) *result = res;
+      if (prof) {
+        CK(cudaEventRecord(rec.b, st));
+        rec.steps = pl.nt;
+        rec.launches = 1;
+        rec.bytes = (double)pl.nt * bytes_per_point(pl) * (double)pl.n3;
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        g_prof.push_back(rec);
+      }
+      return FFPAT_OK;
+    }
+  }
   int dev = 0;
   CK(cudaGetDevice(&dev));
   bool done = false, replay_only = false;
@@ -986,7 +1014,7 @@ int64_t ffpat_launch_count(void) { return g_launches.load(); }
 
 int ffpat_set_stencil_path(int32_t path) {
   g_err[0] = 0;
-  if (path < 0 || path > 3) return fail(FFPAT_EINVAL, "stencil path %d not in {0, 1, 2, 3}", path);
+  if (path < 0 || path > 4) return fail(FFPAT_EINVAL, "stencil path %d not in {0, ..., 4}", path);
   g_stencil_path = path;
   return FFPAT_OK;
 }

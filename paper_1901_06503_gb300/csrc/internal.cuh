@@ -46,6 +46,7 @@ struct Plan {
   int32_t* tabi = nullptr;     // cos[nth], sin[nth] in fixed point, round(. * 2^30)
   void* dct = nullptr;         // DCT-II matrix C and C^T (n^2 each, element type), then mu[n] (double)
   const double* dct_mu = nullptr;
+  unsigned* sync = nullptr;    // grid barrier counter of the resident time loop
 };
 // The plan as the wave kernels see it: the wave grid and its kappa.
 inline Plan wave_plan(const Plan& pl) {
@@ -132,6 +133,16 @@ constexpr int kMaxBatchRequests = 28;
 // alias the inputs.  TMA layout rules as launch_step_tma.
 int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void* e, void* po,
                        void* dout, void* eout, cudaStream_t st);
+// The whole FP32 time loop of W in one cooperative launch (grids whose work
+// items fit the GPU's CTA slots, N <= 128 on GB300; see stencil_tma.cu):
+// form 1 increment with Kahan carry, form 0 three-term.  Reads p^0 from `in`,
+// ping-pongs p through b0 (even steps) and b1 (odd steps), writes the last
+// step to `out` when non-null; *result = the buffer holding p^{nt}.  Bit for
+// bit the single-step loop.  resident_zc: the z-range of its work items, 0
+// when the grid does not fit (the step-by-step loop runs instead).
+int resident_zc(const Plan& pl, int form);
+int launch_wave_resident(const Plan& pl, int form, const void* in, void* out, void* b0, void* b1,
+                         const void** result, cudaStream_t st);
 // Two FP32 three-term leapfrog steps in one HBM pass (needs N % 4 == 0, 16-byte
 // aligned arrays): reads p^{n-1} (pm) and p^n (p), writes p^{n+1} (o1) and
 // p^{n+2} (o2); o1, o2 alias neither input.  Bit-identical to two single steps.

@@ -833,6 +833,188 @@ __global__ void __launch_bounds__(tb3::NT3, 1)
   }
 }
 
+// ------------------------------------ resident time loop (small grids) --
+// When the work items of a grid fit the CTA slots of the GPU at one item per
+// CTA, one cooperative launch runs the whole time loop.  Every CTA keeps its
+// item (a 64 x 16 tile and up to rs::ZM planes) for all steps: the per-point
+// state that no other CTA reads -- d and e of the increment form, p^{n-1} of
+// the three-term form -- stays in registers, kap / 12 in shared memory, and
+// only p^n moves through memory, in two ping-pong buffers that live in L2 at
+// these sizes.  A grid-wide barrier separates the steps.  Each step loads the
+// item's zc + 4 halo planes of p^n by TMA at once (one mbarrier per plane) and
+// computes the planes as they arrive, with the single-step kernel's
+// arithmetic (gather_pair, lap12_nb, kahan_update or the three-term update),
+// so the result is bit for bit that of the step-by-step loop.  A step-by-step
+// launch pays the launch, the ring's fill and its drain every step (about
+// 3 us plus 0.55 us per plane of a work item on GB300), which at N <= 128 is
+// most of the step.
+namespace rs {
+constexpr int ZM = 8;          // planes of one work item at most (registers)
+constexpr int NPL = ZM + 4;    // p planes one item reads per step
+using G = Geo<float, 2>;       // 64 x 16 tiles, 72 x 20 halo boxes
+constexpr int PF = G::PBYTES / 4, QF = G::QBYTES / 4;
+constexpr size_t kSmem = (size_t)NPL * G::PBYTES + (size_t)ZM * G::QBYTES + (NPL + 1) * 8 + 1024;
+}  // namespace rs
+
+struct ResParams {
+  CUtensorMap pin;    // p^0 (halo box)
+  CUtensorMap pb[2];  // the state buffers (halo box)
+  CUtensorMap kap;    // kap / 12 (tile box)
+  float* buf[2];      // step s writes buf[s & 1] ...
+  float* out;         // ... except the last step, which writes here when non-null
+  unsigned* sync;     // grid barrier counter, zero at launch
+  int n, zc, tiles_x, tiles_y, nt;
+};
+
+// Grid-wide barrier number k (1, 2, ...): all CTAs' global stores before it
+// are visible to every CTA's loads after it, TMA loads included.  Bounded:
+// false (and nothing else) when the others did not arrive in time.
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target) {
+  // this thread's generic-proxy stores before any later async-proxy (TMA) read
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  int fail = 0;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+    const long long t0 = clock64();
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if (clock64() - t0 > kWaitCycles) {
+        fail = 1;
+        break;
+      }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  return __syncthreads_or(fail) == 0;
+}
+
+// One step of the resident loop over the item's planes.  sa, sb: the
+// register state of the thread's points (form 1: d, e; form 0: p^{n-1} in sa).
+template <int FORM, bool START>
+__device__ __forceinline__ bool res_step(const float* pst, const float* kst, uint64_t* bar,
+                                         unsigned parity, float (&sa)[rs::ZM][2][2],
+                                         float (&sb)[rs::ZM][2][2], float* __restrict__ dst,
+                                         int n, int nz, int z0, int x0, int y0) {
+  using G = rs::G;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (ok) ok = mbar_wait(&bar[i], parity, kWaitCycles);
+#pragma unroll
+  for (int zi = 0; zi < rs::ZM; ++zi) {
+    if (zi < nz) {
+      if (ok) ok = mbar_wait(&bar[zi + 4], parity, kWaitCycles);
+      const float* Pm2 = pst + zi * rs::PF;
+      const float* Pm1 = Pm2 + rs::PF;
+      const float* P0 = Pm1 + rs::PF;
+      const float* Pp1 = P0 + rs::PF;
+      const float* Pp2 = Pp1 + rs::PF;
+      const float* Kz = kst + zi * rs::QF;
+      const size_t zoff = (size_t)(z0 + zi) * n * n;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int ry = ty + TBY * rr, y = y0 + ry;
+        const int xl = 2 * tx, x = x0 + xl;
+        const int o = (ry + 2) * G::BXH + xl + G::XH;
+        Nb na, nb;
+        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
+        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        const float2 K = lds2(Kz + ry * TBX + xl);
+        float2 w;
+        if constexpr (FORM == 1) {
+          const float3 ra = kahan_update(na.c, K.x, La, sa[zi][rr][0], sb[zi][rr][0], START);
+          const float3 rb = kahan_update(nb.c, K.y, Lb, sa[zi][rr][1], sb[zi][rr][1], START);
+          sa[zi][rr][0] = ra.y;
+          sb[zi][rr][0] = ra.z;
+          sa[zi][rr][1] = rb.y;
+          sb[zi][rr][1] = rb.z;
+          w = make_float2(ra.x, rb.x);
+        } else {
+          if constexpr (START)
+            w = make_float2(na.c + 0.5f * K.x * La, nb.c + 0.5f * K.y * Lb);
+          else
+            w = make_float2(na.c + fmaf(K.x, La, na.c - sa[zi][rr][0]),
+                            nb.c + fmaf(K.y, Lb, nb.c - sa[zi][rr][1]));
+          sa[zi][rr][0] = na.c;
+          sa[zi][rr][1] = nb.c;
+        }
+        if (x < n && y < n)  // N % 4 == 0, so x + 1 < n as well
+          *reinterpret_cast<float2*>(dst + zoff + (size_t)y * n + x) = w;
+      }
+    }
+  }
+  return ok;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_constant__ ResParams rp) {
+  using G = rs::G;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  float* pst = reinterpret_cast<float*>(smem);                          // NPL halo planes
+  float* kst = reinterpret_cast<float*>(smem + rs::NPL * G::PBYTES);    // ZM kap tiles
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + rs::NPL * G::PBYTES + rs::ZM * G::QBYTES);
+  const int tid = threadIdx.y * NTX + threadIdx.x;
+  const int n = rp.n, item = blockIdx.x;
+  const int tix = item % rp.tiles_x, tiy = (item / rp.tiles_x) % rp.tiles_y;
+  const int z0 = (item / (rp.tiles_x * rp.tiles_y)) * rp.zc;
+  const int nz = min(n - z0, rp.zc);
+  const int x0 = tix * TBX, y0 = tiy * G::TH;
+  if (tid == 0) {
+    for (int i = 0; i <= rs::NPL; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // after a device-side failure of an earlier launch every CTA returns at once
+  if (*(volatile unsigned*)&g_tma_status != 0u) return;
+  if (tid == 0) {
+    mbar_expect_tx(&bar[rs::NPL], (unsigned)(nz * G::QBYTES));
+    for (int zi = 0; zi < nz; ++zi)
+      tma_load_3d(kst + zi * rs::QF, &rp.kap, x0, y0, z0 + zi, &bar[rs::NPL]);
+  }
+  float sa[rs::ZM][2][2], sb[rs::ZM][2][2];
+#pragma unroll
+  for (int zi = 0; zi < rs::ZM; ++zi)
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) sa[zi][rr][0] = sa[zi][rr][1] = sb[zi][rr][0] = sb[zi][rr][1] = 0.f;
+  bool ok = mbar_wait(&bar[rs::NPL], 0, kWaitCycles);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+      mbar_wait(&bar[rs::NPL], 0, 1 << 24);
+    }
+    return;
+  }
+  for (int s = 0; s < rp.nt; ++s) {
+    const CUtensorMap* src = s == 0 ? &rp.pin : &rp.pb[(s - 1) & 1];
+    float* dst = (s == rp.nt - 1 && rp.out) ? rp.out : rp.buf[s & 1];
+    if (tid == 0)
+      for (int i = 0; i < nz + 4; ++i) {
+        mbar_expect_tx(&bar[i], G::PBYTES);
+        tma_load_3d(pst + i * rs::PF, src, x0 - G::XH, y0 - 2, z0 - 2 + i, &bar[i]);
+      }
+    const unsigned parity = (unsigned)s & 1u;
+    ok = s == 0 ? res_step<FORM, true>(pst, kst, bar, parity, sa, sb, dst, n, nz, z0, x0, y0)
+                : res_step<FORM, false>(pst, kst, bar, parity, sa, sb, dst, n, nz, z0, x0, y0);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+        // bounded wait for this CTA's copies of the step still in flight
+        for (int i = 0; i < nz + 4; ++i) mbar_wait(&bar[i], parity, 1 << 24);
+      }
+      return;
+    }
+    if (s + 1 < rp.nt && !grid_barrier(rp.sync, (unsigned)(s + 1) * gridDim.x)) {
+      if (tid == 0) atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
+      return;
+    }
+  }
+}
+
 // ------------------------------------------------------------- host side --
 
 // FFPAT_ZCHUNK=<planes> fixes the z-range of one work item of the TMA
@@ -1177,6 +1359,102 @@ int launch_step2_f32(const Plan& pl, const void* pm, const void* p, void* o1, vo
     return report(FFPAT_ECUDA, "k_step2_f32 launch: %s", cudaGetErrorString(le));
   }
   return check_launch("k_step2_f32");
+}
+
+// ---- the resident time loop (host side)
+namespace {
+template <int FORM>
+int resident_slots(int* occ_out) {
+  static int occ = 0, sms = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto kern = k_wave_resident<FORM>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs::kSmem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTX * NTY, rs::kSmem) !=
+        cudaSuccess)
+      occ = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 0;
+    cudaGetLastError();
+  });
+  if (occ_out) *occ_out = occ;
+  return occ * sms;
+}
+
+// z-range of the resident loop's items: one item per CTA slot, at most rs::ZM
+// planes; among the ranges that fit, the least (items per SM) x (zc + 2), the
+// longer range on ties.  0 if none fits.
+int resident_zchunk(int n, int slots, int sms) {
+  const int tiles = ((n + TBX - 1) / TBX) * ((n + rs::G::TH - 1) / rs::G::TH);
+  const int ov = zchunk_override();
+  int best = 0;
+  long long best_cost = 0;
+  for (int zc = 1; zc <= rs::ZM; ++zc) {
+    const long long items = (long long)tiles * ((n + zc - 1) / zc);
+    if (items > slots) continue;
+    if (ov > 0 && zc != ov) continue;
+    const long long cost = ((items + sms - 1) / sms) * (zc + 2);
+    if (best == 0 || cost <= best_cost) {
+      best = zc;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+}  // namespace
+
+int resident_zc(const Plan& pl, int form) {
+  if (pl.esize != 4 || pl.n % 4 != 0 || pl.n < 4 || !pl.sync) return 0;
+  int occ = 0;
+  const int slots = form == 1 ? resident_slots<1>(&occ) : resident_slots<0>(&occ);
+  if (slots <= 0 || occ <= 0) return 0;
+  return resident_zchunk(pl.n, slots, slots / occ);
+}
+
+int launch_wave_resident(const Plan& pl, int form, const void* in, void* out, void* b0, void* b1,
+                         const void** result, cudaStream_t st) {
+  const int zc = resident_zc(pl, form);
+  if (zc <= 0) return report(FFPAT_EINVAL, "resident time loop: N = %d does not fit", pl.n);
+  static thread_local ResParams rp;
+  const int n = pl.n;
+  if (make_map(&rp.pin, in, n, 4, true, rs::G::TH) != FFPAT_OK ||
+      make_map(&rp.pb[0], b0, n, 4, true, rs::G::TH) != FFPAT_OK ||
+      make_map(&rp.pb[1], b1, n, 4, true, rs::G::TH) != FFPAT_OK ||
+      make_map(&rp.kap, pl.kap, n, 4, false, rs::G::TH) != FFPAT_OK)
+    return report(FFPAT_ECUDA, "resident time loop: tensor map");
+  rp.buf[0] = (float*)b0;
+  rp.buf[1] = (float*)b1;
+  rp.out = (float*)out;
+  rp.sync = pl.sync;
+  rp.n = n;
+  rp.zc = zc;
+  rp.tiles_x = (n + TBX - 1) / TBX;
+  rp.tiles_y = (n + rs::G::TH - 1) / rs::G::TH;
+  rp.nt = pl.nt;
+  const int items = rp.tiles_x * rp.tiles_y * ((n + zc - 1) / zc);
+  if (cudaMemsetAsync(pl.sync, 0, sizeof(unsigned), st) != cudaSuccess)
+    return check_launch("resident time loop: barrier reset");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(items);
+  cfg.blockDim = dim3(NTX, NTY);
+  cfg.dynamicSmemBytes = rs::kSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = form == 1 ? cudaLaunchKernelEx(&cfg, k_wave_resident<1>, rp)
+                                  : cudaLaunchKernelEx(&cfg, k_wave_resident<0>, rp);
+  count_launch();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "k_wave_resident launch: %s", cudaGetErrorString(e));
+  }
+  if (result) *result = (pl.nt >= 1 && out) ? out : (pl.nt >= 1 ? rp.buf[(pl.nt - 1) & 1] : in);
+  return check_launch("k_wave_resident");
 }
 
 int read_device_status(unsigned* out, bool clear) {

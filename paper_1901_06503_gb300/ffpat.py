@@ -450,7 +450,8 @@ def launch_count() -> int:
 
 
 def set_stencil_path(path: int) -> None:
-    """0 automatic, 1 plain 2.5D kernel, 2 single-step TMA kernel, 3 two-step TMA kernel."""
+    """0 automatic, 1 plain 2.5D kernel, 2 single-step TMA kernel, 3 two-step TMA kernel,
+    4 resident time loop (one cooperative launch, FP32 and FP32-Kahan, N <= 128)."""
     _check(lib().ffpat_set_stencil_path(int(path)))
 
 

@@ -35,7 +35,7 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-kahan"], default="fp32-kahan")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--path", type=int, default=0, help="leapfrog kernel: 0 auto, 1 plain, 2 TMA")
+    ap.add_argument("--path", type=int, default=0, help="leapfrog kernel: 0 auto, 1 plain, 2 TMA, 3 two-step, 4 resident loop")
     a = ap.parse_args(argv)
     build_lib.build()
     F.set_stencil_path(a.path)

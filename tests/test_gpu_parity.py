@@ -453,6 +453,38 @@ def test_two_step_fp32_bit_identical(n, T):
     assert F.device_status() == 0
 
 
+@pytest.mark.parametrize("prec", [F.FP32, F.FP32_KAHAN])
+@pytest.mark.parametrize("n,T", [(24, 0.004), (24, 0.03), (36, 0.41), (64, 0.3), (96, 0.21),
+                                 (128, 0.05), (132, 0.03)])
+def test_resident_loop_bit_identical(prec, n, T):
+    """The whole time loop in one cooperative launch (registers and shared
+    memory hold the per-point state, a grid barrier separates the steps)
+    against one launch per step: W and W^T bit for bit, for one, two, odd and
+    even step counts and ragged tiles; N = 132 does not fit the CTA slots, so
+    forcing it fails and the automatic choice runs the step-by-step loop."""
+    c = as_input(random_speed(n, 1300 + n), prec)
+    h = as_input(random_volume(n, 1301 + n), prec)
+    prob = F.problem(n, T, 4, prec)
+    outs = {}
+    try:
+        for path in (2, 0, 4):
+            F.set_stencil_path(path)
+            if path == 4 and n > 128:
+                with pytest.raises(F.FFPATError):
+                    F.wave(prob, dev(c, prob), dev(h, prob))
+                continue
+            outs[path] = (host(F.wave(prob, dev(c, prob), dev(h, prob))),
+                          host(F.wave(prob, dev(c, prob), dev(h, prob), transpose=True)))
+    finally:
+        F.set_stencil_path(0)
+    for path in outs:
+        assert np.array_equal(outs[2][0], outs[path][0]), path
+        assert np.array_equal(outs[2][1], outs[path][1]), path
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    assert rel(outs[0][0], o.wave(o.kappa(n, dt, c), h, nt)) < TOL[prec]
+    assert F.device_status() == 0
+
+
 # ---------------------------------------------------- two-step method (Alg. 9) --
 
 @pytest.mark.parametrize("prec", PRECS)
