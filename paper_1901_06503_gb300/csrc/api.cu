@@ -150,7 +150,7 @@ static size_t carve(Plan& pl, void* ws) {
   pl.tabi = tabs ? (int32_t*)((char*)tabs + 24 * (size_t)pl.nth) : nullptr;
   pl.dct = take(dct_bytes(pl.n, pl.esize));
   pl.dct_mu = pl.dct ? (const double*)((char*)pl.dct + 2 * (size_t)pl.n * pl.n * pl.esize) : nullptr;
-  pl.sync = (unsigned*)take(256);
+  pl.sync = (unsigned*)take(128 * (size_t)kResidentMaxItems);
   return off;
 }
 

@@ -46,7 +46,7 @@ struct Plan {
   int32_t* tabi = nullptr;     // cos[nth], sin[nth] in fixed point, round(. * 2^30)
   void* dct = nullptr;         // DCT-II matrix C and C^T (n^2 each, element type), then mu[n] (double)
   const double* dct_mu = nullptr;
-  unsigned* sync = nullptr;    // grid barrier counter of the resident time loop
+  unsigned* sync = nullptr;    // step flags of the resident time loop (kResidentMaxItems)
 };
 // The plan as the wave kernels see it: the wave grid and its kappa.
 inline Plan wave_plan(const Plan& pl) {
@@ -59,6 +59,7 @@ inline Plan wave_plan(const Plan& pl) {
 // bytes of the three angle tables (double, float, fixed point) for nth angles
 inline size_t table_bytes(int nth) { return (size_t)nth * 2 * (8 + 4 + 4); }
 constexpr int kMaxHist = 4096;
+constexpr int kResidentMaxItems = 1024;  // work items (step flags) of the resident time loop
 constexpr int kScal = 64;
 
 // api.cu helpers shared with the server and the gradient path

@@ -118,18 +118,6 @@ struct Streams {
   static constexpr int NQ = START ? 1 : (FORM == 0 ? 2 : 3);
 };
 
-__device__ __forceinline__ float lap12_diff(const float* P0, const float* Pm1, const float* Pp1,
-                                            const float* Pm2, const float* Pp2, int o, int row) {
-  const float c = P0[o];
-  float d1 = (P0[o - 1] - c) + (P0[o + 1] - c);
-  d1 += (P0[o - row] - c) + (P0[o + row] - c);
-  d1 += (Pm1[o] - c) + (Pp1[o] - c);
-  float d2 = (P0[o - 2] - c) + (P0[o + 2] - c);
-  d2 += (P0[o - 2 * row] - c) + (P0[o + 2 * row] - c);
-  d2 += (Pm2[o] - c) + (Pp2[o] - c);
-  return fmaf(16.0f, d1, -d2);
-}
-
 __device__ __forceinline__ double lap12_sum(const double* P0, const double* Pm1, const double* Pp1,
                                             const double* Pm2, const double* Pp2, int o, int row) {
   const double c = P0[o];
@@ -147,45 +135,78 @@ __device__ __forceinline__ double lap12_sum(const double* P0, const double* Pm1,
   return fma(16.0, s1, -s2);
 }
 
-// Neighbourhood of one point for the FP32 difference-form Laplacian.
-struct Nb {
-  float c, xm1, xp1, ym1, yp1, zm1, zp1, xm2, xp2, ym2, yp2, zm2, zp2;
-};
-
-// same operations in the same order as lap12_diff
-__device__ __forceinline__ float lap12_nb(const Nb& v) {
-  float d1 = (v.xm1 - v.c) + (v.xp1 - v.c);
-  d1 += (v.ym1 - v.c) + (v.yp1 - v.c);
-  d1 += (v.zm1 - v.c) + (v.zp1 - v.c);
-  float d2 = (v.xm2 - v.c) + (v.xp2 - v.c);
-  d2 += (v.ym2 - v.c) + (v.yp2 - v.c);
-  d2 += (v.zm2 - v.c) + (v.zp2 - v.c);
-  return fmaf(16.0f, d1, -d2);
+// Two x-adjacent points are updated together with the packed two-lane FP32
+// instructions of sm_100+ (lane x: the point at o, lane y: o + 1).  Each lane
+// is exactly the IEEE single-precision operation (round to nearest even), so a
+// pair computes what two scalar updates with the same operation order would;
+// the packed forms halve the arithmetic instructions of a step.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));  // a - b, exactly
 }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 __device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
-// the neighbourhoods of the two x-adjacent points at o and o + 1 (o even),
-// read with eleven 64-bit shared-memory loads
-__device__ __forceinline__ void gather_pair(const float* P0, const float* Pm1, const float* Pp1,
-                                            const float* Pm2, const float* Pp2, int o, int row,
-                                            Nb& a, Nb& b) {
-  const float2 C = lds2(P0 + o), XM = lds2(P0 + o - 2), XP = lds2(P0 + o + 2);
-  const float2 YM1 = lds2(P0 + o - row), YP1 = lds2(P0 + o + row);
-  const float2 YM2 = lds2(P0 + o - 2 * row), YP2 = lds2(P0 + o + 2 * row);
-  const float2 ZM1 = lds2(Pm1 + o), ZP1 = lds2(Pp1 + o), ZM2 = lds2(Pm2 + o), ZP2 = lds2(Pp2 + o);
-  a = Nb{C.x, XM.y, C.y, YM1.x, YP1.x, ZM1.x, ZP1.x, XM.x, XP.x, YM2.x, YP2.x, ZM2.x, ZP2.x};
-  b = Nb{C.y, C.x, XP.x, YM1.y, YP1.y, ZM1.y, ZP1.y, XM.y, XP.y, YM2.y, YP2.y, ZM2.y, ZP2.y};
+// Neighbourhood of a pair of points for the FP32 difference-form Laplacian.
+struct Nb2 {
+  float2 c, xm1, xp1, ym1, yp1, zm1, zp1, xm2, xp2, ym2, yp2, zm2, zp2;
+};
+
+// 12 (h^2 L4 p) at both points, difference form:
+// 16 sum_axes (p(-1) - c + p(+1) - c) - sum_axes (p(-2) - c + p(+2) - c)
+__device__ __forceinline__ float2 lap12_pair(const Nb2& v) {
+  float2 d1 = add2(sub2(v.xm1, v.c), sub2(v.xp1, v.c));
+  d1 = add2(d1, add2(sub2(v.ym1, v.c), sub2(v.yp1, v.c)));
+  d1 = add2(d1, add2(sub2(v.zm1, v.c), sub2(v.zp1, v.c)));
+  float2 d2 = add2(sub2(v.xm2, v.c), sub2(v.xp2, v.c));
+  d2 = add2(d2, add2(sub2(v.ym2, v.c), sub2(v.yp2, v.c)));
+  d2 = add2(d2, add2(sub2(v.zm2, v.c), sub2(v.zp2, v.c)));
+  return fma2(make_float2(16.0f, 16.0f), d1, make_float2(-d2.x, -d2.y));
 }
 
-// Kahan-compensated increment update of one point; returns (p', d', e')
-__device__ __forceinline__ float3 kahan_update(float c, float k, float L, float dold, float eold,
-                                               bool start) {
-  const float dn = start ? 0.5f * k * L : fmaf(k, L, dold);
-  const float ev = start ? 0.0f : eold;
-  const float yv = dn - ev;
-  const float tv = c + yv;
-  return make_float3(tv, dn, (tv - c) - yv);
+// the neighbourhoods of the points at o and o + 1 (o even), read with eleven
+// 64-bit shared-memory loads
+__device__ __forceinline__ void gather_pair(const float* P0, const float* Pm1, const float* Pp1,
+                                            const float* Pm2, const float* Pp2, int o, int row,
+                                            Nb2& v) {
+  const float2 C = lds2(P0 + o), XM = lds2(P0 + o - 2), XP = lds2(P0 + o + 2);
+  v.c = C;
+  v.xm1 = make_float2(XM.y, C.x);
+  v.xp1 = make_float2(C.y, XP.x);
+  v.xm2 = XM;
+  v.xp2 = XP;
+  v.ym1 = lds2(P0 + o - row);
+  v.yp1 = lds2(P0 + o + row);
+  v.ym2 = lds2(P0 + o - 2 * row);
+  v.yp2 = lds2(P0 + o + 2 * row);
+  v.zm1 = lds2(Pm1 + o);
+  v.zp1 = lds2(Pp1 + o);
+  v.zm2 = lds2(Pm2 + o);
+  v.zp2 = lds2(Pp2 + o);
+}
+
+// Kahan-compensated increment update of a pair: p' = p + d' with carry e',
+// d' = k L + d (start: d' = k L / 2, no carry in)
+struct Kp2 {
+  float2 p, d, e;
+};
+__device__ __forceinline__ Kp2 kahan_pair(float2 c, float2 k, float2 L, float2 dold, float2 eold,
+                                          bool start) {
+  const float2 dn = start ? mul2(mul2(make_float2(0.5f, 0.5f), k), L) : fma2(k, L, dold);
+  const float2 yv = start ? dn : sub2(dn, eold);
+  const float2 tv = add2(c, yv);
+  return Kp2{tv, dn, sub2(sub2(tv, c), yv)};
+}
+
+// three-term update of a pair: p^{n+1} = p^n + (k L + (p^n - p^{n-1}));
+// start: p^1 = p^0 + (k / 2) L
+__device__ __forceinline__ float2 three_term_pair(float2 c, float2 k, float2 L, float2 pm) {
+  return add2(c, fma2(k, L, sub2(c, pm)));
+}
+__device__ __forceinline__ float2 start_pair(float2 c, float2 k, float2 L) {
+  return add2(c, mul2(mul2(make_float2(0.5f, 0.5f), k), L));
 }
 
 // Round R brings p plane R (needed while R <= z1 + 1) and the per-point
@@ -280,21 +301,18 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
           const int o = (ry + 2) * G::BXH + xl + G::XH;
           const int qo = ry * TBX + xl;
           constexpr int QS = G::QBYTES / 4;
-          Nb na, nb;
-          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
-          const float La = lap12_nb(na), Lb = lap12_nb(nb);
+          Nb2 v;
+          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, v);
+          const float2 L = lap12_pair(v);
           const float2 K = lds2(Q + (NQ - 1) * QS + qo);
           if (x < n && y < n) {  // N is even, so x + 1 < n as well
             const size_t gi = (size_t)z * plane + (size_t)y * n + x;
             if constexpr (FORM == 0) {
               if constexpr (START) {
-                *reinterpret_cast<float2*>(o0 + gi) =
-                    make_float2(na.c + 0.5f * K.x * La, nb.c + 0.5f * K.y * Lb);
-                if (o1) *reinterpret_cast<float2*>(o1 + gi) = make_float2(na.c, nb.c);
+                *reinterpret_cast<float2*>(o0 + gi) = start_pair(v.c, K, L);
+                if (o1) *reinterpret_cast<float2*>(o1 + gi) = v.c;
               } else {
-                const float2 PM = lds2(Q + qo);
-                *reinterpret_cast<float2*>(o0 + gi) =
-                    make_float2(na.c + fmaf(K.x, La, na.c - PM.x), nb.c + fmaf(K.y, Lb, nb.c - PM.y));
+                *reinterpret_cast<float2*>(o0 + gi) = three_term_pair(v.c, K, L, lds2(Q + qo));
               }
             } else {
               float2 D = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
@@ -302,11 +320,10 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
                 D = lds2(Q + qo);
                 E = lds2(Q + QS + qo);
               }
-              const float3 ra = kahan_update(na.c, K.x, La, D.x, E.x, START);
-              const float3 rb = kahan_update(nb.c, K.y, Lb, D.y, E.y, START);
-              *reinterpret_cast<float2*>(o0 + gi) = make_float2(ra.x, rb.x);
-              *reinterpret_cast<float2*>(o1 + gi) = make_float2(ra.y, rb.y);
-              *reinterpret_cast<float2*>(o2 + gi) = make_float2(ra.z, rb.z);
+              const Kp2 r = kahan_pair(v.c, K, L, D, E, START);
+              *reinterpret_cast<float2*>(o0 + gi) = r.p;
+              *reinterpret_cast<float2*>(o1 + gi) = r.d;
+              *reinterpret_cast<float2*>(o2 + gi) = r.e;
             }
           }
         } else {
@@ -448,9 +465,9 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
         const int o = (ry + 2) * G::BXH + xl + G::XH;
         const int qo = ry * TBX + xl;
         constexpr int QS = G::QBYTES / 4;
-        Nb na, nb;
-        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
-        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        Nb2 v;
+        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, v);
+        const float2 L = lap12_pair(v);
         const float2 K = lds2(Qd + 2 * QS + qo);
         if (x < n && y < n) {
           const size_t gi = (size_t)z * plane + (size_t)y * n + x;
@@ -459,11 +476,10 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
             D = lds2(Qd + qo);
             E = lds2(Qd + QS + qo);
           }
-          const float3 ra = kahan_update(na.c, K.x, La, D.x, E.x, start);
-          const float3 rb = kahan_update(nb.c, K.y, Lb, D.y, E.y, start);
-          *reinterpret_cast<float2*>(q.o0 + gi) = make_float2(ra.x, rb.x);
-          *reinterpret_cast<float2*>(q.o1 + gi) = make_float2(ra.y, rb.y);
-          *reinterpret_cast<float2*>(q.o2 + gi) = make_float2(ra.z, rb.z);
+          const Kp2 r = kahan_pair(v.c, K, L, D, E, start);
+          *reinterpret_cast<float2*>(q.o0 + gi) = r.p;
+          *reinterpret_cast<float2*>(q.o1 + gi) = r.d;
+          *reinterpret_cast<float2*>(q.o2 + gi) = r.e;
         }
       }
       if (__syncthreads_or(timed_out)) {
@@ -599,17 +615,16 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
           const int qy = q / 34, qx = 2 + 2 * (q % 34);
           const int po_ = (qy + 2) * PW + qx;  // same x origin, two more rows of halo
           const int qo = qy * QW + qx;
-          Nb na, nb;
-          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, na, nb);
-          const float La = lap12_nb(na), Lb = lap12_nb(nb);
+          Nb2 v;
+          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, v);
+          const float2 L = lap12_pair(v);
           const float2 Kv = lds2(Kz + qo), Dv = lds2(Dz + qo), Ev = lds2(Ez + qo);
-          const float3 ra = kahan_update(na.c, Kv.x, La, Dv.x, Ev.x, false);
-          const float3 rb = kahan_update(nb.c, Kv.y, Lb, Dv.y, Ev.y, false);
-          *reinterpret_cast<float2*>(Az + qo) = make_float2(ra.x, rb.x);
+          const Kp2 r = kahan_pair(v.c, Kv, L, Dv, Ev, false);
+          *reinterpret_cast<float2*>(Az + qo) = r.p;
           if (qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TH2) {
             const int to = (qy - 2) * TBX + (qx - 4);
-            *reinterpret_cast<float2*>(ADz + to) = make_float2(ra.y, rb.y);
-            *reinterpret_cast<float2*>(ADz + TB / 4 + to) = make_float2(ra.z, rb.z);
+            *reinterpret_cast<float2*>(ADz + to) = r.d;
+            *reinterpret_cast<float2*>(ADz + TB / 4 + to) = r.e;
           }
         }
       }
@@ -646,17 +661,16 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
         const int x = x0 + xl, y = y0 + ty;
         const int qo = (ty + 2) * QW + xl + 4;
         const int to = ty * TBX + xl;
-        Nb na, nb;
-        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, na, nb);
-        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        Nb2 v;
+        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, v);
+        const float2 L = lap12_pair(v);
         const float2 Kv = lds2(Kz + qo), Dv = lds2(ADz + to), Ev = lds2(ADz + TB / 4 + to);
         if (x < n && y < n) {
-          const float3 ra = kahan_update(na.c, Kv.x, La, Dv.x, Ev.x, false);
-          const float3 rb = kahan_update(nb.c, Kv.y, Lb, Dv.y, Ev.y, false);
+          const Kp2 r = kahan_pair(v.c, Kv, L, Dv, Ev, false);
           const size_t gi = (size_t)zB * plane + (size_t)y * n + x;
-          *reinterpret_cast<float2*>(po + gi) = make_float2(ra.x, rb.x);
-          *reinterpret_cast<float2*>(dout + gi) = make_float2(ra.y, rb.y);
-          *reinterpret_cast<float2*>(eout + gi) = make_float2(ra.z, rb.z);
+          *reinterpret_cast<float2*>(po + gi) = r.p;
+          *reinterpret_cast<float2*>(dout + gi) = r.d;
+          *reinterpret_cast<float2*>(eout + gi) = r.e;
         }
       }
     }
@@ -771,12 +785,10 @@ __global__ void __launch_bounds__(tb3::NT3, 1)
           const int qy = q / 34, qx = 2 + 2 * (q % 34);
           const int po_ = (qy + 2) * PW + qx;
           const int qo = qy * QW + qx;
-          Nb na, nb;
-          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, na, nb);
-          const float La = lap12_nb(na), Lb = lap12_nb(nb);
-          const float2 Kv = lds2(Kz + qo), PM = lds2(Mz + qo);
-          const float2 r = make_float2(na.c + fmaf(Kv.x, La, na.c - PM.x),
-                                       nb.c + fmaf(Kv.y, Lb, nb.c - PM.y));
+          Nb2 v;
+          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, v);
+          const float2 L = lap12_pair(v);
+          const float2 r = three_term_pair(v.c, lds2(Kz + qo), L, lds2(Mz + qo));
           *reinterpret_cast<float2*>(Az + qo) = r;
           if (zout && qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TH) {
             const int x = x0 + qx - 4, y = y0 + qy - 2;
@@ -817,14 +829,13 @@ __global__ void __launch_bounds__(tb3::NT3, 1)
         const int x = x0 + xl, y = y0 + ty;
         const int qo = (ty + 2) * QW + xl + 4;
         const int po_ = (ty + 4) * PW + xl + 4;
-        Nb na, nb;
-        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, na, nb);
-        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        Nb2 v;
+        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, v);
+        const float2 L = lap12_pair(v);
         const float2 Kv = lds2(Kz + qo), PN = lds2(Pz + po_);
         if (x < n && y < n) {
           const size_t gi = (size_t)zB * plane + (size_t)y * n + x;
-          *reinterpret_cast<float2*>(o2 + gi) =
-              make_float2(na.c + fmaf(Kv.x, La, na.c - PN.x), nb.c + fmaf(Kv.y, Lb, nb.c - PN.y));
+          *reinterpret_cast<float2*>(o2 + gi) = three_term_pair(v.c, Kv, L, PN);
         }
       }
     }
@@ -840,10 +851,11 @@ __global__ void __launch_bounds__(tb3::NT3, 1)
 // state that no other CTA reads -- d and e of the increment form, p^{n-1} of
 // the three-term form -- stays in registers, kap / 12 in shared memory, and
 // only p^n moves through memory, in two ping-pong buffers that live in L2 at
-// these sizes.  A grid-wide barrier separates the steps.  Each step loads the
+// these sizes.  Between steps a CTA waits only for its neighbouring items
+// (neighbour_sync), not for the whole grid.  Each step loads the
 // item's zc + 4 halo planes of p^n by TMA at once (one mbarrier per plane) and
 // computes the planes as they arrive, with the single-step kernel's
-// arithmetic (gather_pair, lap12_nb, kahan_update or the three-term update),
+// arithmetic (gather_pair, lap12_pair, kahan_pair or the three-term update),
 // so the result is bit for bit that of the step-by-step loop.  A step-by-step
 // launch pays the launch, the ring's fill and its drain every step (about
 // 3 us plus 0.55 us per plane of a work item on GB300), which at N <= 128 is
@@ -862,41 +874,63 @@ struct ResParams {
   CUtensorMap kap;    // kap / 12 (tile box)
   float* buf[2];      // step s writes buf[s & 1] ...
   float* out;         // ... except the last step, which writes here when non-null
-  unsigned* sync;     // grid barrier counter, zero at launch
+  unsigned* sync;     // one step flag per work item, zero at launch
   int n, zc, tiles_x, tiles_y, nt;
 };
 
-// Grid-wide barrier number k (1, 2, ...): all CTAs' global stores before it
-// are visible to every CTA's loads after it, TMA loads included.  Bounded:
-// false (and nothing else) when the others did not arrive in time.
-__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target) {
+// Step boundary of the resident loop, point to point: a CTA publishes that
+// it finished step s (its stores of p^{s+1} done, its loads of p^s complete)
+// in its own flag, and before step s + 1 waits only for the items whose
+// regions its halo reads (the neighbours within one tile in x and y and
+// within two planes in z).  That covers both hazards of the two ping-pong
+// buffers: the neighbours' p^{s+1} is written before it is read, and the
+// buffer step s + 1 overwrites (p^{s-1}) is no longer read by any neighbour.
+// Bounded: false when a neighbour did not arrive in time.
+constexpr int kFlagStride = 32;  // one flag per 128-byte line
+
+__device__ __forceinline__ bool neighbour_sync(unsigned* flags, unsigned s1, int tix, int tiy,
+                                               int tz, int tiles_x, int tiles_y, int nzc,
+                                               int zr) {
+  const int tid = threadIdx.y * NTX + threadIdx.x;
   // this thread's generic-proxy stores before any later async-proxy (TMA) read
   asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
-  int fail = 0;
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
-    const long long t0 = clock64();
-    while (true) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-      if ((int)(v - target) >= 0) break;
-      if (clock64() - t0 > kWaitCycles) {
-        fail = 1;
-        break;
-      }
-    }
-    asm volatile("fence.proxy.async.global;" ::: "memory");
+  if (tid == 0) {
+    unsigned* f = flags + kFlagStride * ((tz * tiles_y + tiy) * tiles_x + tix);
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(s1) : "memory");
   }
-  return __syncthreads_or(fail) == 0;
+  int fail = 0;
+  const int nzr = 2 * zr + 1;
+  if (tid < 9 * nzr) {
+    const int jx = tix + tid % 3 - 1, jy = tiy + (tid / 3) % 3 - 1, jz = tz + tid / 9 - zr;
+    const bool self = jx == tix && jy == tiy && jz == tz;
+    if (!self && jx >= 0 && jx < tiles_x && jy >= 0 && jy < tiles_y && jz >= 0 && jz < nzc) {
+      const unsigned* f = flags + kFlagStride * ((jz * tiles_y + jy) * tiles_x + jx);
+      const long long t0 = clock64();
+      while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if ((int)(v - s1) >= 0) break;
+        if (clock64() - t0 > kWaitCycles) {
+          fail = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+  }
+  const int any = __syncthreads_or(fail);
+  if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+  return any == 0;
 }
 
 // One step of the resident loop over the item's planes.  sa, sb: the
 // register state of the thread's points (form 1: d, e; form 0: p^{n-1} in sa).
 template <int FORM, bool START>
 __device__ __forceinline__ bool res_step(const float* pst, const float* kst, uint64_t* bar,
-                                         unsigned parity, float (&sa)[rs::ZM][2][2],
-                                         float (&sb)[rs::ZM][2][2], float* __restrict__ dst,
+                                         unsigned parity, float2 (&sa)[rs::ZM][2],
+                                         float2 (&sb)[rs::ZM][2], float* __restrict__ dst,
                                          int n, int nz, int z0, int x0, int y0) {
   using G = rs::G;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -920,27 +954,19 @@ __device__ __forceinline__ bool res_step(const float* pst, const float* kst, uin
         const int ry = ty + TBY * rr, y = y0 + ry;
         const int xl = 2 * tx, x = x0 + xl;
         const int o = (ry + 2) * G::BXH + xl + G::XH;
-        Nb na, nb;
-        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, na, nb);
-        const float La = lap12_nb(na), Lb = lap12_nb(nb);
+        Nb2 v;
+        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, v);
+        const float2 L = lap12_pair(v);
         const float2 K = lds2(Kz + ry * TBX + xl);
         float2 w;
         if constexpr (FORM == 1) {
-          const float3 ra = kahan_update(na.c, K.x, La, sa[zi][rr][0], sb[zi][rr][0], START);
-          const float3 rb = kahan_update(nb.c, K.y, Lb, sa[zi][rr][1], sb[zi][rr][1], START);
-          sa[zi][rr][0] = ra.y;
-          sb[zi][rr][0] = ra.z;
-          sa[zi][rr][1] = rb.y;
-          sb[zi][rr][1] = rb.z;
-          w = make_float2(ra.x, rb.x);
+          const Kp2 r = kahan_pair(v.c, K, L, sa[zi][rr], sb[zi][rr], START);
+          sa[zi][rr] = r.d;
+          sb[zi][rr] = r.e;
+          w = r.p;
         } else {
-          if constexpr (START)
-            w = make_float2(na.c + 0.5f * K.x * La, nb.c + 0.5f * K.y * Lb);
-          else
-            w = make_float2(na.c + fmaf(K.x, La, na.c - sa[zi][rr][0]),
-                            nb.c + fmaf(K.y, Lb, nb.c - sa[zi][rr][1]));
-          sa[zi][rr][0] = na.c;
-          sa[zi][rr][1] = nb.c;
+          w = START ? start_pair(v.c, K, L) : three_term_pair(v.c, K, L, sa[zi][rr]);
+          sa[zi][rr] = v.c;
         }
         if (x < n && y < n)  // N % 4 == 0, so x + 1 < n as well
           *reinterpret_cast<float2*>(dst + zoff + (size_t)y * n + x) = w;
@@ -961,8 +987,11 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_cons
   const int tid = threadIdx.y * NTX + threadIdx.x;
   const int n = rp.n, item = blockIdx.x;
   const int tix = item % rp.tiles_x, tiy = (item / rp.tiles_x) % rp.tiles_y;
-  const int z0 = (item / (rp.tiles_x * rp.tiles_y)) * rp.zc;
+  const int tz = item / (rp.tiles_x * rp.tiles_y);
+  const int z0 = tz * rp.zc;
   const int nz = min(n - z0, rp.zc);
+  const int nzc = (n + rp.zc - 1) / rp.zc;
+  const int zr = rp.zc >= 2 ? 1 : 2;  // z-chunks a two-plane halo reaches
   const int x0 = tix * TBX, y0 = tiy * G::TH;
   if (tid == 0) {
     for (int i = 0; i <= rs::NPL; ++i) mbar_init(&bar[i], 1);
@@ -976,11 +1005,11 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_cons
     for (int zi = 0; zi < nz; ++zi)
       tma_load_3d(kst + zi * rs::QF, &rp.kap, x0, y0, z0 + zi, &bar[rs::NPL]);
   }
-  float sa[rs::ZM][2][2], sb[rs::ZM][2][2];
+  float2 sa[rs::ZM][2], sb[rs::ZM][2];
 #pragma unroll
   for (int zi = 0; zi < rs::ZM; ++zi)
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) sa[zi][rr][0] = sa[zi][rr][1] = sb[zi][rr][0] = sb[zi][rr][1] = 0.f;
+    for (int rr = 0; rr < 2; ++rr) sa[zi][rr] = sb[zi][rr] = make_float2(0.f, 0.f);
   bool ok = mbar_wait(&bar[rs::NPL], 0, kWaitCycles);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) {
@@ -1008,7 +1037,8 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_cons
       }
       return;
     }
-    if (s + 1 < rp.nt && !grid_barrier(rp.sync, (unsigned)(s + 1) * gridDim.x)) {
+    if (s + 1 < rp.nt && !neighbour_sync(rp.sync, (unsigned)(s + 1), tix, tiy, tz, rp.tiles_x,
+                                         rp.tiles_y, nzc, zr)) {
       if (tid == 0) atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
       return;
     }
@@ -1393,7 +1423,7 @@ int resident_zchunk(int n, int slots, int sms) {
   long long best_cost = 0;
   for (int zc = 1; zc <= rs::ZM; ++zc) {
     const long long items = (long long)tiles * ((n + zc - 1) / zc);
-    if (items > slots) continue;
+    if (items > slots || items > kResidentMaxItems) continue;
     if (ov > 0 && zc != ov) continue;
     const long long cost = ((items + sms - 1) / sms) * (zc + 2);
     if (best == 0 || cost <= best_cost) {
@@ -1434,7 +1464,9 @@ int launch_wave_resident(const Plan& pl, int form, const void* in, void* out, vo
   rp.tiles_y = (n + rs::G::TH - 1) / rs::G::TH;
   rp.nt = pl.nt;
   const int items = rp.tiles_x * rp.tiles_y * ((n + zc - 1) / zc);
-  if (cudaMemsetAsync(pl.sync, 0, sizeof(unsigned), st) != cudaSuccess)
+  if (items > kResidentMaxItems)
+    return report(FFPAT_EINVAL, "resident time loop: %d work items > %d", items, kResidentMaxItems);
+  if (cudaMemsetAsync(pl.sync, 0, sizeof(unsigned) * kFlagStride * items, st) != cudaSuccess)
     return check_launch("resident time loop: barrier reset");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(items);
