@@ -32,7 +32,18 @@ FALLBACK_HBM_GBS = 6800.0
 # kernel at 128^3 (profiles/k_step_tma_fp32kahan_n128.md) and the two-step
 # kernel at 384^3 (profiles/k_step2_kahan_fp32kahan_n384.md).  Keyed by
 # (workload, precision); None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 33.576448e6, ("cfg5", "fp32-kahan"): 1546.023424e6}
+# DRAM bytes per launch of the dominant kernel, from one ncu capture each
+# (profiles/): the step pass of the 384^3 workload; at 128^3 the resident time
+# loop, whose DRAM traffic is its first load of p^0 and kap / 12 (the state
+# stays on chip, so it does not grow with the step count)
+NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 17.155584e6, ("cfg5", "fp32-kahan"): 1544.919808e6}
+
+# algorithmic FP32 operations per point-step of the difference-form update:
+# 12 subtractions, 10 additions and one FMA (2) for 12 h^2 L4 p, then the
+# Kahan increment (FMA + 4 adds) or the three-term update (FMA + 2 adds)
+FLOP_PER_POINT_STEP = {"fp32-kahan": 30, "fp32": 28}
+# FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) per clock
+FP32_LANES = 152 * 128
 
 WORKLOADS = {
     "cfg2": dict(cfg=2, label="single solve N=128^3, 90 angles, T=1.2, 20 balls, GRF sound speed"),
@@ -308,6 +319,30 @@ def run_ours(args):
                "value_1core": v1,
                "sample_1core": f"the same on one core: {steps1} steps ({el1:.1f} s)"}
     bpp = {F.FP64: 32, F.FP32: 16, F.FP32_KAHAN: 28}[prob.precision]
+    steps_per_pass = prof["steps"] / max(prof["step_launches"], 1)
+    common = {"traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
+              "traffic_source": "ncu capture of the same kernel (cold caches), DRAM bytes per launch",
+              "steps_per_pass": steps_per_pass, "launch_ms": launch_ms,
+              "launches_timed": prof["step_launches"], "steps_timed": prof["steps"]}
+    if steps_per_pass > 2 and args.precision in FLOP_PER_POINT_STEP:
+        # the resident time loop (one launch per W): the state never leaves
+        # the chip, so HBM is not its bound; report its arithmetic against
+        # the FP32 CUDA-core peak at the maximum SM clock
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = FP32_LANES * 2 * mhz * 1e6 / 1e12
+        flops = FLOP_PER_POINT_STEP[args.precision] * prof["steps"] * float(w.n) ** 3
+        ach = flops / (prof["step_ms"] / 1e3) / 1e12 if prof["step_ms"] > 0 else None
+        roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (ach / peak) if ach else None,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz",
+                    "kernel": "resident time loop (k_wave_resident)",
+                    "flop_per_point_step": FLOP_PER_POINT_STEP[args.precision],
+                    "algorithmic_state_gbs": achieved, **common}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": (achieved / hbm) if achieved else None,
+                    "peak_source": f"{src} hbm_gbs", "kernel": "leapfrog pass",
+                    "bytes_per_point_pass": bpp, **common}
     line = {
         "metric": "voxel-steps/s", "value": value, "unit": "voxel-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
@@ -321,15 +356,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "fb_iters_per_s": world * args.steps / (dev_ms / 1e3),
         "wall_s": wall,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None,
-                     "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
-                     "traffic_source": "ncu capture of the same kernel at this size (cold caches)",
-                     "peak_source": f"{src} hbm_gbs", "kernel": "leapfrog pass",
-                     "bytes_per_point_pass": bpp,
-                     "steps_per_pass": prof["steps"] / max(prof["step_launches"], 1),
-                     "launch_ms": launch_ms, "launches_timed": prof["step_launches"],
-                     "steps_timed": prof["steps"]},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": world * vs_per_iter / e2e_s, "unit": "voxel-steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
