@@ -920,9 +920,7 @@ __device__ __forceinline__ bool neighbour_sync(unsigned* flags, unsigned s1, int
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
   }
-  const int any = __syncthreads_or(fail);
-  if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
-  return any == 0;
+  return __syncthreads_or(fail) == 0;
 }
 
 // One step of the resident loop over the item's planes.  sa, sb: the
@@ -1021,11 +1019,13 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_cons
   for (int s = 0; s < rp.nt; ++s) {
     const CUtensorMap* src = s == 0 ? &rp.pin : &rp.pb[(s - 1) & 1];
     float* dst = (s == rp.nt - 1 && rp.out) ? rp.out : rp.buf[s & 1];
-    if (tid == 0)
-      for (int i = 0; i < nz + 4; ++i) {
-        mbar_expect_tx(&bar[i], G::PBYTES);
-        tma_load_3d(pst + i * rs::PF, src, x0 - G::XH, y0 - 2, z0 - 2 + i, &bar[i]);
-      }
+    // one lane of warp 0 per plane issues its copy (after its own proxy fence:
+    // the neighbours' generic-proxy stores before this async-proxy read)
+    if (tid < nz + 4) {
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      mbar_expect_tx(&bar[tid], G::PBYTES);
+      tma_load_3d(pst + tid * rs::PF, src, x0 - G::XH, y0 - 2, z0 - 2 + tid, &bar[tid]);
+    }
     const unsigned parity = (unsigned)s & 1u;
     ok = s == 0 ? res_step<FORM, true>(pst, kst, bar, parity, sa, sb, dst, n, nz, z0, x0, y0)
                 : res_step<FORM, false>(pst, kst, bar, parity, sa, sb, dst, n, nz, z0, x0, y0);
