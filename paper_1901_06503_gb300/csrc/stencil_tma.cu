@@ -139,13 +139,40 @@ __device__ __forceinline__ double lap12_sum(const double* P0, const double* Pm1,
 // instructions of sm_100+ (lane x: the point at o, lane y: o + 1).  Each lane
 // is exactly the IEEE single-precision operation (round to nearest even), so a
 // pair computes what two scalar updates with the same operation order would;
-// the packed forms halve the arithmetic instructions of a step.
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));  // a - b, exactly
+// the packed forms halve the arithmetic instructions of a step.  They are
+// written as PTX with an explicit rounding mode, which the compiler never
+// contracts (a multiply followed by an add stays two roundings in every
+// kernel), so all stencil kernels agree bit for bit whatever their code shape.
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
 }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 up2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return up2(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return up2(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return up2(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return up2(r);
+}
 
 __device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
@@ -861,7 +888,7 @@ __global__ void __launch_bounds__(tb3::NT3, 1)
 // 3 us plus 0.55 us per plane of a work item on GB300), which at N <= 128 is
 // most of the step.
 namespace rs {
-constexpr int ZM = 8;          // planes of one work item at most (registers)
+constexpr int ZM = 7;          // planes of one work item at most (registers)
 constexpr int NPL = ZM + 4;    // p planes one item reads per step
 using G = Geo<float, 2>;       // 64 x 16 tiles, 72 x 20 halo boxes
 constexpr int PF = G::PBYTES / 4, QF = G::QBYTES / 4;
@@ -925,6 +952,10 @@ __device__ __forceinline__ bool neighbour_sync(unsigned* flags, unsigned s1, int
 
 // One step of the resident loop over the item's planes.  sa, sb: the
 // register state of the thread's points (form 1: d, e; form 0: p^{n-1} in sa).
+// Rows outer, planes inner: a thread walks the z-column of each of its two
+// rows and keeps the four column values it already read (z-2 .. z+1) in
+// registers, so each plane costs one new column load (z+2) and the six x/y
+// neighbour loads; the arithmetic is gather_pair's, value for value.
 template <int FORM, bool START>
 __device__ __forceinline__ bool res_step(const float* pst, const float* kst, uint64_t* bar,
                                          unsigned parity, float2 (&sa)[rs::ZM][2],
@@ -936,26 +967,37 @@ __device__ __forceinline__ bool res_step(const float* pst, const float* kst, uin
 #pragma unroll
   for (int i = 0; i < 4; ++i)
     if (ok) ok = mbar_wait(&bar[i], parity, kWaitCycles);
+  const int xl = 2 * tx, x = x0 + xl;
 #pragma unroll
-  for (int zi = 0; zi < rs::ZM; ++zi) {
-    if (zi < nz) {
-      if (ok) ok = mbar_wait(&bar[zi + 4], parity, kWaitCycles);
-      const float* Pm2 = pst + zi * rs::PF;
-      const float* Pm1 = Pm2 + rs::PF;
-      const float* P0 = Pm1 + rs::PF;
-      const float* Pp1 = P0 + rs::PF;
-      const float* Pp2 = Pp1 + rs::PF;
-      const float* Kz = kst + zi * rs::QF;
-      const size_t zoff = (size_t)(z0 + zi) * n * n;
+  for (int rr = 0; rr < 2; ++rr) {
+    const int ry = ty + TBY * rr, y = y0 + ry;
+    const int o = (ry + 2) * G::BXH + xl + G::XH;
+    float2 c0 = lds2(pst + o), c1 = lds2(pst + rs::PF + o);
+    float2 c2 = lds2(pst + 2 * rs::PF + o), c3 = lds2(pst + 3 * rs::PF + o);
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int ry = ty + TBY * rr, y = y0 + ry;
-        const int xl = 2 * tx, x = x0 + xl;
-        const int o = (ry + 2) * G::BXH + xl + G::XH;
+    for (int zi = 0; zi < rs::ZM; ++zi) {
+      if (zi < nz) {
+        // the first row's pass waits for each plane; the second finds them complete
+        if (rr == 0 && ok) ok = mbar_wait(&bar[zi + 4], parity, kWaitCycles);
+        const float* P0 = pst + (zi + 2) * rs::PF;
+        const float2 c4 = lds2(pst + (zi + 4) * rs::PF + o);
+        const float2 XM = lds2(P0 + o - 2), XP = lds2(P0 + o + 2);
         Nb2 v;
-        gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, v);
+        v.c = c2;
+        v.xm1 = make_float2(XM.y, c2.x);
+        v.xp1 = make_float2(c2.y, XP.x);
+        v.xm2 = XM;
+        v.xp2 = XP;
+        v.ym1 = lds2(P0 + o - G::BXH);
+        v.yp1 = lds2(P0 + o + G::BXH);
+        v.ym2 = lds2(P0 + o - 2 * G::BXH);
+        v.yp2 = lds2(P0 + o + 2 * G::BXH);
+        v.zm1 = c1;
+        v.zp1 = c3;
+        v.zm2 = c0;
+        v.zp2 = c4;
         const float2 L = lap12_pair(v);
-        const float2 K = lds2(Kz + ry * TBX + xl);
+        const float2 K = lds2(kst + zi * rs::QF + ry * TBX + xl);
         float2 w;
         if constexpr (FORM == 1) {
           const Kp2 r = kahan_pair(v.c, K, L, sa[zi][rr], sb[zi][rr], START);
@@ -967,7 +1009,13 @@ __device__ __forceinline__ bool res_step(const float* pst, const float* kst, uin
           sa[zi][rr] = v.c;
         }
         if (x < n && y < n)  // N % 4 == 0, so x + 1 < n as well
-          *reinterpret_cast<float2*>(dst + zoff + (size_t)y * n + x) = w;
+          *reinterpret_cast<float2*>(dst + (size_t)(z0 + zi) * n * n + (size_t)y * n + x) = w;
+        c0 = c1;
+        c1 = c2;
+        c2 = c3;
+        c3 = c4;
+        // keep the next plane's loads behind this one (register pressure)
+        asm volatile("" ::: "memory");
       }
     }
   }
