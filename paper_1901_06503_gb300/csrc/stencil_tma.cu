@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include <stdlib.h>
+#include <string.h>
 
 #include <mutex>
 #include <unordered_map>
@@ -143,14 +144,16 @@ __device__ __forceinline__ double lap12_sum(const double* P0, const double* Pm1,
 // written as PTX with an explicit rounding mode, which the compiler never
 // contracts (a multiply followed by an add stays two roundings in every
 // kernel), so all stencil kernels agree bit for bit whatever their code shape.
+// bit copies between a float pair and the 64-bit register the packed
+// instructions take (no instruction: the pair already is a register pair)
 __device__ __forceinline__ unsigned long long pk2(float2 a) {
   unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  memcpy(&r, &a, sizeof r);
   return r;
 }
 __device__ __forceinline__ float2 up2(unsigned long long r) {
   float2 a;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  memcpy(&a, &r, sizeof a);
   return a;
 }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) {
@@ -182,15 +185,18 @@ struct Nb2 {
 };
 
 // 12 (h^2 L4 p) at both points, difference form:
-// 16 sum_axes (p(-1) - c + p(+1) - c) - sum_axes (p(-2) - c + p(+2) - c)
+// 16 sum_axes (p(-1) - c + p(+1) - c) - sum_axes (p(-2) - c + p(+2) - c).
+// The far sum is accumulated negated, as (c - p(-2)) + (c - p(+2)) ..., which
+// is exactly its negative (a - b = -(b - a) in IEEE arithmetic), so the last
+// step is one fused 16 d1 + (-d2) without a separate negation.
 __device__ __forceinline__ float2 lap12_pair(const Nb2& v) {
   float2 d1 = add2(sub2(v.xm1, v.c), sub2(v.xp1, v.c));
   d1 = add2(d1, add2(sub2(v.ym1, v.c), sub2(v.yp1, v.c)));
   d1 = add2(d1, add2(sub2(v.zm1, v.c), sub2(v.zp1, v.c)));
-  float2 d2 = add2(sub2(v.xm2, v.c), sub2(v.xp2, v.c));
-  d2 = add2(d2, add2(sub2(v.ym2, v.c), sub2(v.yp2, v.c)));
-  d2 = add2(d2, add2(sub2(v.zm2, v.c), sub2(v.zp2, v.c)));
-  return fma2(make_float2(16.0f, 16.0f), d1, make_float2(-d2.x, -d2.y));
+  float2 nd2 = add2(sub2(v.c, v.xm2), sub2(v.c, v.xp2));
+  nd2 = add2(nd2, add2(sub2(v.c, v.ym2), sub2(v.c, v.yp2)));
+  nd2 = add2(nd2, add2(sub2(v.c, v.zm2), sub2(v.c, v.zp2)));
+  return fma2(make_float2(16.0f, 16.0f), d1, nd2);
 }
 
 // the neighbourhoods of the points at o and o + 1 (o even), read with eleven
