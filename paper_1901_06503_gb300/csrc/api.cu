@@ -432,8 +432,14 @@ static int run_wave(const Plan& pl, const void* in, void* out, const void** resu
       return fail(FFPAT_EINVAL,
                   "resident time loop requested but N = %d, the precision or an array alignment "
                   "rules it out", pl.n);
-    if (fits) {
-      TRY(launch_wave_resident(pl, form, in, out, pl.s[0], pl.s[1], &res, st));
+    bool refused = false;
+    const int rc = fits ? launch_wave_resident(pl, form, in, out, pl.s[0], pl.s[1], &res, st,
+                                               &refused)
+                        : FFPAT_EINVAL;
+    // a cooperative launch turned down for lack of room falls back to the
+    // step-by-step loop below unless the resident loop was asked for
+    if (fits && rc != FFPAT_OK && !(refused && path == 0)) return rc;
+    if (fits && rc == FFPAT_OK) {
       if (result) *result = res;
       if (prof) {
         CK(cudaEventRecord(rec.b, st));

@@ -140,10 +140,12 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
 // ping-pongs p through b0 (even steps) and b1 (odd steps), writes the last
 // step to `out` when non-null; *result = the buffer holding p^{nt}.  Bit for
 // bit the single-step loop.  resident_zc: the z-range of its work items, 0
-// when the grid does not fit (the step-by-step loop runs instead).
+// when the grid does not fit (the step-by-step loop runs instead).  *refused
+// (may be null) is set when the cooperative launch was turned down because
+// the grid cannot be co-resident at the moment: nothing ran.
 int resident_zc(const Plan& pl, int form);
 int launch_wave_resident(const Plan& pl, int form, const void* in, void* out, void* b0, void* b1,
-                         const void** result, cudaStream_t st);
+                         const void** result, cudaStream_t st, bool* refused = nullptr);
 // Two FP32 three-term leapfrog steps in one HBM pass (needs N % 4 == 0, 16-byte
 // aligned arrays): reads p^{n-1} (pm) and p^n (p), writes p^{n+1} (o1) and
 // p^{n+2} (o2); o1, o2 alias neither input.  Bit-identical to two single steps.

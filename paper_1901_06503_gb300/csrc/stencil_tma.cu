@@ -1498,7 +1498,8 @@ int resident_zc(const Plan& pl, int form) {
 }
 
 int launch_wave_resident(const Plan& pl, int form, const void* in, void* out, void* b0, void* b1,
-                         const void** result, cudaStream_t st) {
+                         const void** result, cudaStream_t st, bool* refused) {
+  if (refused) *refused = false;
   const int zc = resident_zc(pl, form);
   if (zc <= 0) return report(FFPAT_EINVAL, "resident time loop: N = %d does not fit", pl.n);
   static thread_local ResParams rp;
@@ -1534,11 +1535,14 @@ int launch_wave_resident(const Plan& pl, int form, const void* in, void* out, vo
   cfg.numAttrs = 1;
   const cudaError_t e = form == 1 ? cudaLaunchKernelEx(&cfg, k_wave_resident<1>, rp)
                                   : cudaLaunchKernelEx(&cfg, k_wave_resident<0>, rp);
-  count_launch();
   if (e != cudaSuccess) {
     cudaGetLastError();
+    // the grid could not be made co-resident now (fewer SMs than the
+    // occupancy query promised): nothing ran, the caller may step instead
+    if (refused && e == cudaErrorCooperativeLaunchTooLarge) *refused = true;
     return report(FFPAT_ECUDA, "k_wave_resident launch: %s", cudaGetErrorString(e));
   }
+  count_launch();
   if (result) *result = (pl.nt >= 1 && out) ? out : (pl.nt >= 1 ? rp.buf[(pl.nt - 1) & 1] : in);
   return check_launch("k_wave_resident");
 }
