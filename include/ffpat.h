@@ -148,7 +148,8 @@ int ffpat_adjoint(const ffpat_problem *problem, const void *c, const void *g, vo
                   size_t ws_bytes, void *stream);
 
 /* out = W in (transpose = 0; in: N^3 box source, out: Nw^3 field) or
- * out = W^T in (transpose = 1; in: Nw^3, out: N^3), eq. (3). */
+ * out = W^T in (transpose = 1; in: Nw^3, out: N^3), eq. (3).  out may be in
+ * itself (in place). */
 int ffpat_wave(const ffpat_problem *problem, const void *c, const void *in, void *out,
                int32_t transpose, void *ws, size_t ws_bytes, void *stream);
 

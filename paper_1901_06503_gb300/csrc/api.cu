@@ -742,7 +742,17 @@ int ffpat_wave(const ffpat_problem* problem, const void* c, const void* in, void
   if (!in || !out) return fail(FFPAT_EINVAL, "in or out is NULL");
   if (!transpose) {
     if (pl.pad == 0) {
-      TRY(run_wave(pl, in, out, nullptr, st));
+      // out may overlap in: then the loop ends in a state buffer and is
+      // copied out (a step must not write the array it reads)
+      const size_t bytes = pl.n3 * pl.esize;
+      const char *a = (const char*)in, *b = (const char*)out;
+      if (a < b + bytes && b < a + bytes) {
+        const void* w = nullptr;
+        TRY(run_wave(pl, in, nullptr, &w, st));
+        CK(cudaMemcpyAsync(out, w, bytes, cudaMemcpyDeviceToDevice, st));
+      } else {
+        TRY(run_wave(pl, in, out, nullptr, st));
+      }
     } else {
       TRY(launch_embed(pl, in, pl.xw, st));
       TRY(run_wave(wave_plan(pl), pl.xw, out, nullptr, st));

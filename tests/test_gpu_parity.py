@@ -485,6 +485,27 @@ def test_resident_loop_bit_identical(prec, n, T):
     assert F.device_status() == 0
 
 
+@pytest.mark.parametrize("prec", [F.FP32, F.FP32_KAHAN])
+@pytest.mark.parametrize("path", [0, 2])
+@pytest.mark.parametrize("T", [0.004, 0.1])
+def test_wave_in_place(prec, path, T):
+    """W with out = in (one step and several; resident loop and step loop)
+    equals the out-of-place result."""
+    n = 24
+    c = as_input(random_speed(n, 1400), prec)
+    h = as_input(random_volume(n, 1401), prec)
+    prob = F.problem(n, T, 4, prec)
+    try:
+        F.set_stencil_path(path)
+        ref = host(F.wave(prob, dev(c, prob), dev(h, prob)))
+        x = dev(h, prob)
+        F.wave(prob, dev(c, prob), x, out=x)
+        got = host(x)
+    finally:
+        F.set_stencil_path(0)
+    assert np.array_equal(got, ref)
+
+
 # ---------------------------------------------------- two-step method (Alg. 9) --
 
 @pytest.mark.parametrize("prec", PRECS)
