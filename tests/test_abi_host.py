@@ -89,3 +89,16 @@ def test_missing_workspace_rejected(L):
 def test_problem_info_rejects_bad_speed(L):
     with pytest.raises(F.FFPATError):
         F.problem_info(F.problem(16, 1.0, 4), 0.0)
+
+
+def test_stencil_path_range(L):
+    """Paths 0 (automatic) to 4 (resident time loop) are accepted without a
+    GPU; anything else is rejected with a message."""
+    try:
+        for path in range(5):
+            assert L.ffpat_set_stencil_path(path) == 0
+        for bad in (-1, 5):
+            assert L.ffpat_set_stencil_path(bad) == F.EINVAL
+            assert b"stencil path" in L.ffpat_last_error()
+    finally:
+        L.ffpat_set_stencil_path(0)
