@@ -47,7 +47,10 @@
  *   - `ws` is caller-owned device scratch of at least
  *     ffpat_workspace_bytes(problem) bytes, 256-byte aligned; its contents on
  *     entry do not matter.  Two calls that run concurrently need two
- *     workspaces.
+ *     workspaces.  For FP32 grids up to 128^3 the wave time loop is one
+ *     cooperative launch that occupies every SM while it runs, so such loops
+ *     issued on several streams run one after another rather than side by
+ *     side (the results do not depend on it).
  *   - Return value: FFPAT_OK (0) or a negative ffpat_status.  On error,
  *     ffpat_last_error() (per host thread) describes it.  No call aborts the
  *     process and no C++ exception crosses this boundary.

@@ -458,7 +458,7 @@ def test_two_step_fp32_bit_identical(n, T):
                                  (128, 0.05), (132, 0.03)])
 def test_resident_loop_bit_identical(prec, n, T):
     """The whole time loop in one cooperative launch (registers and shared
-    memory hold the per-point state, a grid barrier separates the steps)
+    memory hold the per-point state, neighbour flags separate the steps)
     against one launch per step: W and W^T bit for bit, for one, two, odd and
     even step counts and ragged tiles; N = 132 does not fit the CTA slots, so
     forcing it fails and the automatic choice runs the step-by-step loop."""
