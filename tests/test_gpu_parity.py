@@ -485,6 +485,28 @@ def test_resident_loop_bit_identical(prec, n, T):
     assert F.device_status() == 0
 
 
+def test_resident_loops_on_two_streams():
+    """Two resident time loops queued on two streams at once (each with its
+    own workspace; each cooperative launch wants every SM) give the results
+    of one stream, and no bounded wait runs out."""
+    n, T, prec = 128, 1.2, F.FP32_KAHAN
+    c = as_input(random_speed(n, 1500), prec)
+    h1, h2 = as_input(random_volume(n, 1501), prec), as_input(random_volume(n, 1502), prec)
+    prob = F.problem(n, T, 4, prec)
+    cd, x1, x2 = dev(c, prob), dev(h1, prob), dev(h2, prob)
+    ref1, ref2 = host(F.wave(prob, cd, x1)), host(F.wave(prob, cd, x2))
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ws1, ws2 = F.workspace(prob), F.workspace(prob)
+    o1, o2 = torch.empty_like(x1), torch.empty_like(x2)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        F.wave(prob, cd, x1, o1, ws=ws1, stream=s1)
+        F.wave(prob, cd, x2, o2, ws=ws2, stream=s2)
+    torch.cuda.synchronize()
+    assert F.device_status() == 0
+    assert np.array_equal(host(o1), ref1) and np.array_equal(host(o2), ref2)
+
+
 @pytest.mark.parametrize("prec", [F.FP32, F.FP32_KAHAN])
 @pytest.mark.parametrize("path", [0, 2])
 @pytest.mark.parametrize("T", [0.004, 0.1])
