@@ -368,6 +368,34 @@ def test_full_size_n384_fp32_spot_checks():
     assert abs(lhs - rhs) < 1e-6 * abs(lhs)
 
 
+def test_full_size_n384_two_step_pass():
+    """N = 384 FP32-Kahan as the large solve runs it: the start step, then
+    one two-step pass (the automatic choice at this size), bit for bit the
+    step-by-step loop and within tolerance of the oracle, for W and W^T."""
+    n = 384
+    rng = np.random.default_rng(13)
+    c = as_input(np.clip(1 + 0.2 * rng.standard_normal((n, n, n)), 0.75, 1.4), F.FP32)
+    h = as_input(rng.standard_normal((n, n, n)), F.FP32)
+    cmax = c.max()
+    T3 = 3 * 0.3 * (2.0 / n) / cmax * 0.999  # exactly three time steps
+    nt, dt = o.time_steps(n, T3, 0.3, cmax)
+    assert nt == 3
+    prob = F.problem(n, T3, 4, F.FP32_KAHAN)
+    outs = {}
+    try:
+        for path in (0, 2):
+            F.set_stencil_path(path)
+            outs[path] = (host(F.wave(prob, dev(c, prob), dev(h, prob))),
+                          host(F.wave(prob, dev(c, prob), dev(h, prob), transpose=True)))
+    finally:
+        F.set_stencil_path(0)
+    assert np.array_equal(outs[0][0], outs[2][0]) and np.array_equal(outs[0][1], outs[2][1])
+    kap = o.kappa(n, dt, c)
+    assert rel(outs[0][0], o.wave(kap, h, nt)) < 1e-6
+    assert rel(outs[0][1], o.wave_adjoint(kap, h, nt)) < 1e-6
+    assert F.device_status() == 0
+
+
 # ------------------------------------------------- the two stencil kernels --
 
 @pytest.mark.parametrize("prec", PRECS)
