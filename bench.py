@@ -9,7 +9,7 @@ FB iterations per second alongside.  Prints ONE JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload cfg2|cfg5|cfg1] [--precision fp32-kahan|fp32|fp64]
 
-Multi-GPU: the problem does not shard across GPUs in this build; N GPUs run N
+Multi-GPU: the reconstruction does not shard across GPUs; N GPUs run N
 independent replicas (one reconstruction each) and `value` is the sum.
 """
 from __future__ import annotations
