@@ -482,8 +482,8 @@ def test_two_step_fp32_bit_identical(n, T):
 
 
 @pytest.mark.parametrize("prec", [F.FP32, F.FP32_KAHAN])
-@pytest.mark.parametrize("n,T", [(24, 0.004), (24, 0.03), (36, 0.41), (64, 0.3), (96, 0.21),
-                                 (128, 0.05), (132, 0.03)])
+@pytest.mark.parametrize("n,T", [(4, 0.9), (8, 0.5), (24, 0.004), (24, 0.03), (36, 0.41),
+                                 (64, 0.3), (96, 0.21), (128, 0.05), (132, 0.03)])
 def test_resident_loop_bit_identical(prec, n, T):
     """The whole time loop in one cooperative launch (registers and shared
     memory hold the per-point state, neighbour flags separate the steps)
