@@ -58,17 +58,21 @@ __global__ void __launch_bounds__(kReduceThreads)
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads)
     k_speed_stats(const T* __restrict__ c, size_t len, double* __restrict__ partials) {
-  double mx = -INFINITY, mn = INFINITY, bad = 0.0;
+  // the element loop runs in the input's own type (max and min of floats are
+  // exact in float, and the count is an integer): FP32 input stays off the
+  // FP64 pipe; only the per-thread results go through the FP64 block reductions
+  T mxt = T(-INFINITY), mnt = T(INFINITY);
+  unsigned nbad = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len;
        i += (size_t)gridDim.x * blockDim.x) {
-    const double v = (double)c[i];
-    if (!(v > 0.0) || !isfinite(v)) bad += 1.0;
-    mx = fmax(mx, v);
-    mn = fmin(mn, v);
+    const T v = c[i];
+    if (!(v > T(0)) || !isfinite(v)) ++nbad;
+    mxt = fmax(mxt, v);
+    mnt = fmin(mnt, v);
   }
-  mx = block_max(mx);
-  const double nmn = block_max(-mn);
-  bad = block_sum(bad);
+  const double mx = block_max((double)mxt);
+  const double nmn = block_max(-(double)mnt);
+  const double bad = block_sum((double)nbad);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = mx;
     partials[kReduceBlocks + blockIdx.x] = nmn;
