@@ -667,6 +667,59 @@ def run_paper(args):
     return 0
 
 
+def run_grad(args):
+    """The differentiable operator on the 192^3 workload (FP32, 90 angles,
+    T = 1): loss 1/2 |A(h, c) - g|^2 through torch.autograd, gradients for h
+    and c (wavefield checkpoints every 16 steps, each segment recomputed in
+    the backward pass), and for h alone (the adjoint).  Reports milliseconds
+    per forward + backward and the voxel-steps they run (forward Nt steps;
+    backward Nt recomputed plus Nt transposed steps when c needs a gradient,
+    Nt transposed steps for h alone)."""
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    from paper_1901_06503_gb300.autograd import forward_op
+    from paper_1901_06503_gb300.inputs import config
+
+    build_lib.build()
+    dev = torch.device("cuda", 0)
+    w = config(3)
+    prob = F.problem(w.n, w.T, w.n_angles, F.FP32)
+    c0 = torch.as_tensor(w.c, device=dev).float()
+    h0 = torch.as_tensor(w.h, device=dev).float()
+    nt, _, _ = F.problem_info(prob, float(c0.double().max()))
+    g = (F.forward(prob, c0, h0) * 1.01).detach()
+    reps = max(1, args.iters)
+    out = {"mode": "grad", "workload": w.name, "n": w.n, "nt": nt, "every": 16,
+           "precision": "fp32", "reps": reps}
+    for name, want_c in (("grad_h_and_c", True), ("grad_h", False)):
+        h = h0.clone().requires_grad_(True)
+        c = c0.clone().requires_grad_(want_c)
+
+        def step():
+            loss = 0.5 * ((forward_op(h, c, prob, 16) - g) ** 2).sum()
+            loss.backward()
+            return loss
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            h.grad = None
+            c.grad = None
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        steps = nt * (3 if want_c else 2)
+        out[name] = {"ms_per_forward_backward": ms, "wave_steps": steps,
+                     "voxel_steps_per_s": steps * float(w.n) ** 3 / (ms / 1e3)}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -677,12 +730,14 @@ def main():
     ap.add_argument("--precision", choices=["fp32-kahan", "fp32", "fp64"], default="fp32-kahan")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["fb", "serve", "serve_vs_fp64", "precision", "paper"],
+    ap.add_argument("--mode", choices=["fb", "serve", "serve_vs_fp64", "precision", "paper",
+                                       "grad"],
                     default="fb",
                     help="fb: the default FB-iteration line; serve: the serving mix; "
                          "precision: FP64 vs FP32 vs FP32-Kahan on the 128^3 solve; "
                          "paper: the paper's experimental setting in 3D (one- vs two-step); "
-                         "serve_vs_fp64: served FP32 burst vs plain FP64 GPU solves")
+                         "serve_vs_fp64: served FP32 burst vs plain FP64 GPU solves; "
+                         "grad: forward + backward of the differentiable 192^3 operator")
     ap.add_argument("--paper-n", type=int, default=64, help="paper: source box points per axis")
     ap.add_argument("--paper-angles", type=int, default=180, help="paper: projection angles")
     ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window (s)")
@@ -698,6 +753,8 @@ def main():
         return run_precision(args)
     if args.mode == "serve_vs_fp64":
         return run_serve_vs_fp64(args)
+    if args.mode == "grad":
+        return run_grad(args)
     if args.mode == "paper":
         return run_paper(args)
     if args.impl == "reference":
