@@ -898,7 +898,11 @@ constexpr int ZM = 7;          // planes of one work item at most (registers)
 constexpr int NPL = ZM + 4;    // p planes one item reads per step
 using G = Geo<float, 2>;       // 64 x 16 tiles, 72 x 20 halo boxes
 constexpr int PF = G::PBYTES / 4, QF = G::QBYTES / 4;
-constexpr size_t kSmem = (size_t)NPL * G::PBYTES + (size_t)ZM * G::QBYTES + (NPL + 1) * 8 + 1024;
+// the Kahan carries of each thread's second row live in shared memory (the
+// first row's, and every d, in registers): 128 registers hold the rest
+constexpr int EBYTES = ZM * TBY * NTX * 8;
+constexpr size_t kSmem =
+    (size_t)NPL * G::PBYTES + (size_t)ZM * G::QBYTES + EBYTES + (NPL + 1) * 8 + 1024;
 }  // namespace rs
 
 struct ResParams {
@@ -956,8 +960,9 @@ __device__ __forceinline__ bool neighbour_sync(unsigned* flags, unsigned s1, int
   return __syncthreads_or(fail) == 0;
 }
 
-// One step of the resident loop over the item's planes.  sa, sb: the
-// register state of the thread's points (form 1: d, e; form 0: p^{n-1} in sa).
+// One step of the resident loop over the item's planes.  sa, sb, es: the
+// state of the thread's points (form 1: d in sa, e in sb for the first row
+// and in shared memory es for the second; form 0: p^{n-1} in sa).
 // Rows outer, planes inner: a thread walks the z-column of each of its two
 // rows and keeps the four column values it already read (z-2 .. z+1) in
 // registers, so each plane costs one new column load (z+2) and the six x/y
@@ -965,7 +970,8 @@ __device__ __forceinline__ bool neighbour_sync(unsigned* flags, unsigned s1, int
 template <int FORM, bool START>
 __device__ __forceinline__ bool res_step(const float* pst, const float* kst, uint64_t* bar,
                                          unsigned parity, float2 (&sa)[rs::ZM][2],
-                                         float2 (&sb)[rs::ZM][2], float* __restrict__ dst,
+                                         float2 (&sb)[rs::ZM], float2* __restrict__ es,
+                                         float* __restrict__ dst,
                                          int n, int nz, int z0, int x0, int y0) {
   using G = rs::G;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -1006,9 +1012,13 @@ __device__ __forceinline__ bool res_step(const float* pst, const float* kst, uin
         const float2 K = lds2(kst + zi * rs::QF + ry * TBX + xl);
         float2 w;
         if constexpr (FORM == 1) {
-          const Kp2 r = kahan_pair(v.c, K, L, sa[zi][rr], sb[zi][rr], START);
+          float2* ep = es + (zi * TBY + ty) * NTX + tx;
+          const Kp2 r = kahan_pair(v.c, K, L, sa[zi][rr], rr == 0 ? sb[zi] : *ep, START);
           sa[zi][rr] = r.d;
-          sb[zi][rr] = r.e;
+          if (rr == 0)
+            sb[zi] = r.e;
+          else
+            *ep = r.e;
           w = r.p;
         } else {
           w = START ? start_pair(v.c, K, L) : three_term_pair(v.c, K, L, sa[zi][rr]);
@@ -1035,7 +1045,9 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_cons
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* pst = reinterpret_cast<float*>(smem);                          // NPL halo planes
   float* kst = reinterpret_cast<float*>(smem + rs::NPL * G::PBYTES);    // ZM kap tiles
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + rs::NPL * G::PBYTES + rs::ZM * G::QBYTES);
+  float2* es = reinterpret_cast<float2*>(smem + rs::NPL * G::PBYTES + rs::ZM * G::QBYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + rs::NPL * G::PBYTES + rs::ZM * G::QBYTES +
+                                              rs::EBYTES);
   const int tid = threadIdx.y * NTX + threadIdx.x;
   const int n = rp.n, item = blockIdx.x;
   const int tix = item % rp.tiles_x, tiy = (item / rp.tiles_x) % rp.tiles_y;
@@ -1057,11 +1069,12 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_cons
     for (int zi = 0; zi < nz; ++zi)
       tma_load_3d(kst + zi * rs::QF, &rp.kap, x0, y0, z0 + zi, &bar[rs::NPL]);
   }
-  float2 sa[rs::ZM][2], sb[rs::ZM][2];
+  float2 sa[rs::ZM][2], sb[rs::ZM];
 #pragma unroll
-  for (int zi = 0; zi < rs::ZM; ++zi)
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) sa[zi][rr] = sb[zi][rr] = make_float2(0.f, 0.f);
+  for (int zi = 0; zi < rs::ZM; ++zi) {
+    sa[zi][0] = sa[zi][1] = sb[zi] = make_float2(0.f, 0.f);
+    es[(zi * TBY + threadIdx.y) * NTX + threadIdx.x] = make_float2(0.f, 0.f);
+  }
   bool ok = mbar_wait(&bar[rs::NPL], 0, kWaitCycles);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) {
@@ -1081,8 +1094,8 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_wave_resident(const __grid_cons
       tma_load_3d(pst + tid * rs::PF, src, x0 - G::XH, y0 - 2, z0 - 2 + tid, &bar[tid]);
     }
     const unsigned parity = (unsigned)s & 1u;
-    ok = s == 0 ? res_step<FORM, true>(pst, kst, bar, parity, sa, sb, dst, n, nz, z0, x0, y0)
-                : res_step<FORM, false>(pst, kst, bar, parity, sa, sb, dst, n, nz, z0, x0, y0);
+    ok = s == 0 ? res_step<FORM, true>(pst, kst, bar, parity, sa, sb, es, dst, n, nz, z0, x0, y0)
+                : res_step<FORM, false>(pst, kst, bar, parity, sa, sb, es, dst, n, nz, z0, x0, y0);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
