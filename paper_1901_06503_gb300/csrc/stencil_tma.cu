@@ -899,7 +899,8 @@ constexpr int NPL = ZM + 4;    // p planes one item reads per step
 using G = Geo<float, 2>;       // 64 x 16 tiles, 72 x 20 halo boxes
 constexpr int PF = G::PBYTES / 4, QF = G::QBYTES / 4;
 // the Kahan carries of each thread's second row live in shared memory (the
-// first row's, and every d, in registers): 128 registers hold the rest
+// first row's, and every d, in registers): the rest fits 128 registers
+// without spilling
 constexpr int EBYTES = ZM * TBY * NTX * 8;
 constexpr size_t kSmem =
     (size_t)NPL * G::PBYTES + (size_t)ZM * G::QBYTES + EBYTES + (NPL + 1) * 8 + 1024;
@@ -962,7 +963,8 @@ __device__ __forceinline__ bool neighbour_sync(unsigned* flags, unsigned s1, int
 
 // One step of the resident loop over the item's planes.  sa, sb, es: the
 // state of the thread's points (form 1: d in sa, e in sb for the first row
-// and in shared memory es for the second; form 0: p^{n-1} in sa).
+// and in shared memory es for the second; form 0: p^{n-1} in sa; moving its
+// second row to es as well measured slower).
 // Rows outer, planes inner: a thread walks the z-column of each of its two
 // rows and keeps the four column values it already read (z-2 .. z+1) in
 // registers, so each plane costs one new column load (z+2) and the six x/y
