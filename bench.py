@@ -36,7 +36,7 @@ FALLBACK_HBM_GBS = 6800.0
 # (profiles/): the step pass of the 384^3 workload; at 128^3 the resident time
 # loop, whose DRAM traffic is its first load of p^0 and kap / 12 (the state
 # stays on chip, so it does not grow with the step count)
-NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 17.44896e6, ("cfg5", "fp32-kahan"): 1544.95488e6}
+NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 17.167104e6, ("cfg5", "fp32-kahan"): 1544.95488e6}
 
 # algorithmic FP32 operations per point-step of the difference-form update:
 # 12 subtractions, 10 additions and one FMA (2) for 12 h^2 L4 p, then the
