@@ -20,6 +20,13 @@
 // Every mbarrier wait is bounded (about a second of clock64 time); on a
 // timeout the CTA records FFPAT_ETIMEDOUT in a device status word, waits a
 // bounded time for its own copies in flight, and returns.
+//
+// Also here: the batched step of the server (k_step_batch), two steps per
+// pass (k_step2_kahan, k_step2_f32), and, for grids whose work items all fit
+// the GPU at once (N <= 128), the whole time loop in one cooperative launch
+// (k_wave_resident: per-point state on chip, p^n through L2, neighbour step
+// flags between steps).  All FP32 kernels share the packed two-lane pair
+// arithmetic below, so they agree bit for bit.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
