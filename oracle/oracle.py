@@ -343,7 +343,9 @@ def grad_energy(h) -> float:
 
 
 def prox_grad(f, a: float) -> np.ndarray:
-    """(I + a D^T D)^{-1} f: the prox of s lambda R, R = 1/2 |grad h|^2, a = s lambda / dx^2."""
+    """(I + a D^T D)^{-1} f: the prox of s lambda R, R = 1/2 |grad h|^2, a = s lambda / dx^2
+    (Sec. 3.2 proximal map, Sec. 5 regulariser), by conjugate gradients on the
+    difference definition of D^T D."""
     f = _f64(f)
     out = np.empty_like(f)
     lib().ffo_prox_grad(f.shape[0], float(a), _p(f), _p(out))

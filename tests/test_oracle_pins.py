@@ -694,6 +694,21 @@ def test_prox_grad_is_the_dense_solve(n):
         assert np.max(np.abs(got - want)) < 1e-12 * np.abs(f).max()
 
 
+def test_prox_grad_on_cosine_modes():
+    """The separable cosine modes cos(pi k (2i + 1) / (2n)) are eigenvectors of
+    the zero-flux D^T D with eigenvalue sum_axes 4 sin^2(pi k / (2n)), so the
+    prox divides them by 1 + a mu (closed form), on grids larger than the dense
+    check reaches, ragged and even."""
+    for n, a in ((13, 0.7), (24, 5.0)):
+        i = np.arange(n)
+        for kz, ky, kx in ((0, 0, 1), (1, 2, 3), (n - 1, 5, 0), (4, n - 2, n - 1)):
+            fz, fy, fx = (np.cos(np.pi * k * (2 * i + 1) / (2 * n)) for k in (kz, ky, kx))
+            f = fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+            mu = sum(4 * np.sin(np.pi * k / (2 * n)) ** 2 for k in (kz, ky, kx))
+            got = o.prox_grad(f, a)
+            assert np.max(np.abs(got - f / (1 + a * mu))) < 1e-12
+
+
 def test_prox_grad_optimality_and_kernel():
     """The prox satisfies h - f + a D^T D h = 0 (first-order optimality of
     1/2 ||h - f||^2 + a/2 ||D h||^2) on a ragged grid, and leaves constants,
