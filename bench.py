@@ -1,13 +1,18 @@
-"""Benchmark of the hot path: iterations of Algorithm 8 (one-step FB) on the
-single-instance 128^3 workload (90 angles, T = 1.2, FP32-Kahan wavefields).
+"""Benchmark of the hot path: iterations of Algorithm 8 (one-step FB, ramp
+preconditioner of Sec. 3.1) on the large single-solve workload (N = 384^3,
+180 angles, T = 1.5, FP32-Kahan wavefields, FP64 reductions).
 
-One step = one FB iteration = W (333 leapfrog steps) + P + residual + P^T +
-W^T (333 steps) + the fused prox update with FP64 norms.  The metric is
-voxel-steps per second (2 Nt N^3 per iteration over the device time), with
-FB iterations per second alongside.  Prints ONE JSON line.
+One step = one FB iteration = W (1344 leapfrog steps) + P + residual + Lambda
++ P^T + W^T (1344 steps) + the fused prox update with FP64 norms.  The metric
+is voxel-steps per second (2 Nt N^3 per iteration over the device time), with
+FB iterations per second alongside.  Prints ONE JSON line; unless
+--no-extras, the line also carries the FP32-vs-FP64 comparison on the 128^3
+solve, the measured FMA rates of the FP64 and FP32 pipes, a short serving-mix
+run (p50 / p99, recons/s) and served FP32 against plain FP64 reconstructions.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload cfg2|cfg5|cfg1] [--precision fp32-kahan|fp32|fp64]
+                  [--workload cfg5|cfg2|cfg1] [--precision fp32-kahan|fp32|fp64]
+  python bench.py --mode op --op wave --n 384 --op-steps 12 --path 3   # one operation
 
 Multi-GPU: the reconstruction does not shard across GPUs; N GPUs run N
 independent replicas (one reconstruction each) and `value` is the sum.
@@ -27,27 +32,26 @@ sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, cold caches): the single-step
-# kernel at 128^3 (profiles/k_step_tma_fp32kahan_n128.md) and the two-step
-# kernel at 384^3 (profiles/k_step2_kahan_fp32kahan_n384.md).  Keyed by
-# (workload, precision); None where no capture of the current kernel exists.
-# DRAM bytes per launch of the dominant kernel, from one ncu capture each
-# (profiles/): the step pass of the 384^3 workload; at 128^3 the resident time
-# loop, whose DRAM traffic is its first load of p^0 and kap / 12 (the state
-# stays on chip, so it does not grow with the step count)
-NCU_TRAFFIC = {("cfg2", "fp32-kahan"): 17.167104e6, ("cfg5", "fp32-kahan"): 1544.95488e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant leapfrog kernel, taken from one ncu capture of that kernel on
+# the same grid, keyed by (workload, precision, kernel).  An entry is dropped
+# whenever its kernel changes, until it has been captured again.
+NCU_TRAFFIC = {("cfg2", "fp32-kahan", "resident"): 17.167104e6}
 
 # algorithmic FP32 operations per point-step of the difference-form update:
 # 12 subtractions, 10 additions and one FMA (2) for 12 h^2 L4 p, then the
 # Kahan increment (FMA + 4 adds) or the three-term update (FMA + 2 adds)
 FLOP_PER_POINT_STEP = {"fp32-kahan": 30, "fp32": 28}
-# FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) per clock
+# FP64 pipe instructions per point-step of the FP64 leapfrog: 10 additions
+# and 2 FMAs for 12 h^2 L4 p, two FMAs for the three-term update
+FP64_OPS_PER_POINT_STEP = 14
+# FP32 CUDA-core lanes: 152 SMs x 128
 FP32_LANES = 152 * 128
 
 WORKLOADS = {
+    "cfg5": dict(cfg=5, label="large single solve N=384^3, 180 angles, T=1.5, 200 balls + 5 "
+                              "tubes, GRF sound speed, ramp-preconditioned FB"),
     "cfg2": dict(cfg=2, label="single solve N=128^3, 90 angles, T=1.2, 20 balls, GRF sound speed"),
-    "cfg5": dict(cfg=5, label="large solve N=384^3, 180 angles, T=1.5, ramp-preconditioned"),
     "cfg1": dict(cfg=1, label="small solve N=32^3, 24 angles, T=1"),
 }
 
@@ -149,6 +153,14 @@ def max_over_ranks(x, world, device=None):
     return float(t.item())
 
 
+def replica_throughput(world, steps, units_per_step, dev_ms_local, device=None):
+    """Whole-job throughput of `world` independent replicas that each ran
+    `steps` steps of `units_per_step` units: all ranks' units over the slowest
+    rank's time.  Returns (value per second, slowest time in ms)."""
+    slowest = max_over_ranks(dev_ms_local, world, device)
+    return world * steps * units_per_step / (slowest / 1e3), slowest
+
+
 def make_problem(args):
     from paper_1901_06503_gb300 import ffpat as F
     from paper_1901_06503_gb300.inputs import config
@@ -240,6 +252,8 @@ def run_ours(args):
     L = F.opnorm(prob, c, v0, iters=20, ws=ws)
     step = 1.0 / L
     h = torch.zeros_like(h_true)
+    # inputs larger than L2 at 384^3; the 256 MB write flushes L2 between
+    # timed steps at every size
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -270,10 +284,9 @@ def run_ours(args):
     prof = F.profile_read()
     launches = F.launch_count() - launches0
     F.profile_enable(False)
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    dev_ms = max_over_ranks(dev_ms, world, dev)
     vs_per_iter = 2.0 * nt * float(w.n) ** 3
-    value = world * args.steps * vs_per_iter / (dev_ms / 1e3)
+    value, dev_ms = replica_throughput(world, args.steps, vs_per_iter,
+                                       sum(a.elapsed_time(b) for a, b in ev), dev)
     clocks = clk.summary()
 
     # ---- end to end through the public API with host buffers
@@ -297,6 +310,7 @@ def run_ours(args):
     esz = 8 if prob.precision == F.FP64 else 4
     h2d = (2 * w.n**3 + w.n_angles * w.n**2) * esz
     d2h = w.n**3 * esz
+    del c_d, g_d, h_d, ws
 
     hbm, src = peaks()
     achieved = prof["step_bytes"] / (prof["step_ms"] / 1e3) / 1e9 if prof["step_ms"] > 0 else None
@@ -320,28 +334,37 @@ def run_ours(args):
                "sample_1core": f"the same on one core: {steps1} steps ({el1:.1f} s)"}
     bpp = {F.FP64: 32, F.FP32: 16, F.FP32_KAHAN: 28}[prob.precision]
     steps_per_pass = prof["steps"] / max(prof["step_launches"], 1)
-    common = {"traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
-              "traffic_source": "ncu capture of the same kernel (cold caches), DRAM bytes per launch",
+    kernel = ("resident" if steps_per_pass > 2 else
+              "two-step" if steps_per_pass > 1.5 else "single-step")
+    common = {"traffic": NCU_TRAFFIC.get((args.workload, args.precision, kernel)),
+              "traffic_source": "one ncu capture of the same kernel on the same grid (cold "
+                                "caches), DRAM read + write bytes per launch",
               "steps_per_pass": steps_per_pass, "launch_ms": launch_ms,
               "launches_timed": prof["step_launches"], "steps_timed": prof["steps"]}
-    if steps_per_pass > 2 and args.precision in FLOP_PER_POINT_STEP:
+    rates = None if args.no_extras else fma_rates(F)
+    if kernel == "resident" and args.precision in FLOP_PER_POINT_STEP:
         # the resident time loop (one launch per W): the state never leaves
         # the chip, so HBM is not its bound; report its arithmetic against
-        # the FP32 CUDA-core peak at the maximum SM clock
+        # the measured FP32 FMA rate (else the rate derived from the clock)
         mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-        peak = FP32_LANES * 2 * mhz * 1e6 / 1e12
+        if rates:
+            peak, psrc = rates["fp32x2_tflops"], "measured: ffpat_debug_fma_rate (packed FP32)"
+        else:
+            peak = FP32_LANES * 2 * mhz * 1e6 / 1e12
+            psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
         flops = FLOP_PER_POINT_STEP[args.precision] * prof["steps"] * float(w.n) ** 3
         ach = flops / (prof["step_ms"] / 1e3) / 1e12 if prof["step_ms"] > 0 else None
         roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": (ach / peak) if ach else None,
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz",
+                    "frac": (ach / peak) if ach else None, "peak_source": psrc,
                     "kernel": "resident time loop (k_wave_resident)",
                     "flop_per_point_step": FLOP_PER_POINT_STEP[args.precision],
                     "algorithmic_state_gbs": achieved, **common}
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": (achieved / hbm) if achieved else None,
-                    "peak_source": f"{src} hbm_gbs", "kernel": "leapfrog pass",
+                    "peak_source": f"{src} hbm_gbs",
+                    "kernel": ("two-step leapfrog pass (k_step2_kahan)" if kernel == "two-step"
+                               else "leapfrog step"),
                     "bytes_per_point_pass": bpp, **common}
     line = {
         "metric": "voxel-steps/s", "value": value, "unit": "voxel-steps/s", "n_gpus": world,
@@ -351,8 +374,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": wl["label"], "n": w.n, "n_angles": w.n_angles, "T": w.T,
                    "nt": nt, "precision": F.PRECISION_NAMES[prob.precision],
-                   "fb_iteration": "W + P + residual + P^T + W^T + prox update",
-                   "l2": "flushed (256 MB write) between timed steps",
+                   "precond": "ramp" if w.precond else "identity",
+                   "fb_iteration": "W + P + residual + Lambda + P^T + W^T + prox update",
+                   "l2": ("inputs larger than L2 and flushed (256 MB write) between timed "
+                          "steps"),
                    "parallelism": "replicas" if world > 1 else "single"},
         "fb_iters_per_s": world * args.steps / (dev_ms / 1e3),
         "wall_s": wall,
@@ -363,6 +388,12 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_extras:
+        line["fma_rates"] = rates
+        line["fp32_vs_fp64"] = extra_precision(F, dev, rates, args.extra_iters)
+        pool = serving_pool(F, dev, args.pool)
+        line["serving"] = extra_serving(F, pool, args)
+        line["serve_vs_fp64"] = extra_serve_vs_fp64(F, dev, pool[:args.fp64_pool], args)
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -370,30 +401,103 @@ def run_ours(args):
     return 0
 
 
-def run_serve(args):
-    """Serving mix (Poisson arrivals of requests of mixed size) through the
-    continuous-batching server; prints one JSON line with recons/s and p50/p99."""
+def fma_rates(F):
+    """Measured FMA rates of the FP64, FP32 and packed FP32 pipes (TFLOP/s)."""
+    return {"fp64_tflops": F.debug_fma_rate(F.FMA_FP64) / 1e12,
+            "fp32_tflops": F.debug_fma_rate(F.FMA_FP32) / 1e12,
+            "fp32x2_tflops": F.debug_fma_rate(F.FMA_FP32X2) / 1e12,
+            "how": "ffpat_debug_fma_rate: every SM full, 8 independent FMA chains per thread, "
+                   "best of 3 launches, CUDA events"}
+
+
+def extra_precision(F, dev, rates, iters):
+    """The 128^3 solve (90 angles, T = 1.2, identity Lambda) in FP64, FP32 and
+    FP32-Kahan with the same step from h = 0: milliseconds per FB iteration
+    (CUDA events, after one warm-up iteration), the relative L2 difference of
+    each FP32 iterate from the FP64 GPU iterate after `iters` iterations, and
+    the FP64 leapfrog's use of the FP64 pipe against its measured FMA rate."""
     import numpy as np
     import torch
 
-    from paper_1901_06503_gb300 import build_lib
-    from paper_1901_06503_gb300 import ffpat as F
     from paper_1901_06503_gb300.inputs import add_noise, config
+    w = config(2)
+    p64 = F.problem(w.n, w.T, w.n_angles, F.FP64)
+    c64 = torch.as_tensor(w.c, device=dev)
+    g64 = F.forward(p64, c64, torch.as_tensor(w.h, device=dev))
+    gd = torch.as_tensor(add_noise(g64.cpu().numpy(), w.noise, w.noise_rel), device=dev)
+    step = 1.0 / F.opnorm(p64, c64, torch.ones_like(c64), iters=20)
+    nt, _, _ = F.problem_info(p64, float(w.c.max()))
+    out = {"workload": "single solve N=128^3, 90 angles, T=1.2, identity Lambda", "nt": nt,
+           "iters": iters, "step": step}
+    res = {}
+    for name, prec in (("fp64", F.FP64), ("fp32", F.FP32), ("fp32-kahan", F.FP32_KAHAN)):
+        prob = F.problem(w.n, w.T, w.n_angles, prec)
+        dt = F.torch_dtype(prob)
+        c, g = c64.to(dt), gd.to(dt)
+        ws = F.workspace(prob, dev)
+        F.fb_solve(prob, c, g, w.lam, step, 1, ws=ws, history=False)
+        torch.cuda.synchronize()
+        F.profile_enable(True)
+        F.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h, _, _ = F.fb_solve(prob, c, g, w.lam, step, iters, ws=ws, history=False)
+        e1.record()
+        torch.cuda.synchronize()
+        prof = F.profile_read()
+        F.profile_enable(False)
+        res[name] = (h.double(), e0.elapsed_time(e1) / iters, prof)
+        del ws
+    ref = res["fp64"][0]
+    for name, (h, ms, prof) in res.items():
+        out[name] = {"ms_per_fb_iter": ms,
+                     "voxel_steps_per_s": 2.0 * nt * w.n ** 3 / (ms / 1e3),
+                     "rel_l2_vs_fp64_gpu": float((h - ref).norm() / ref.norm()),
+                     "speedup_vs_fp64": res["fp64"][1] / ms}
+    prof = res["fp64"][2]
+    if prof["steps"] and rates:
+        rate = prof["steps"] * float(w.n) ** 3 / (prof["step_ms"] / 1e3)
+        ops = FP64_OPS_PER_POINT_STEP * rate
+        # the probe counts 2 FLOP per DFMA: its instruction rate is half its FLOP rate
+        peak_ops = rates["fp64_tflops"] * 1e12 / 2
+        out["fp64_leapfrog"] = {"point_steps_per_s": rate, "us_per_step":
+                                1e3 * prof["step_ms"] / prof["steps"],
+                                "fp64_ops_per_point_step": FP64_OPS_PER_POINT_STEP,
+                                "fp64_pipe_frac": ops / peak_ops, "bound": "fp64 alu",
+                                "peak_source": "measured: ffpat_debug_fma_rate (FP64)"}
+    return out
 
-    build_lib.build()
-    F.lib()
-    dev = torch.device("cuda", 0)
+
+def serving_pool(F, dev, count):
+    """`count` requests of the serving mix (sizes from {64, 96, 128, 192}^3,
+    45 / 90 / 180 angles, T in [0.8, 1.4], 20-60 iterations, each from its own
+    seed): FP64 sound speed, FP64 data (library FP64 forward + 1 % noise) and
+    the step 1/L from 20 power iterations of the FP32-Kahan operator."""
+    import numpy as np
+    import torch
+
+    from paper_1901_06503_gb300.inputs import add_noise, config
     pool = []
-    for s in range(1, args.pool + 1):
+    for s in range(1, count + 1):
         w = config(4, seed=1000 + s)
-        prob = F.problem(w.n, w.T, w.n_angles, F.FP32_KAHAN)
-        c = torch.as_tensor(w.c, device=dev).float()
-        g = F.forward(prob, c, torch.as_tensor(w.h, device=dev).float())
-        gd = add_noise(g.double().cpu().numpy(), w.noise, w.noise_rel).astype(np.float32)
-        step = 1.0 / F.opnorm(prob, c, torch.ones_like(c), iters=20)
-        nt, _, _ = F.problem_info(prob, float(w.c.astype(np.float32).max()))
-        pool.append((prob, w.c.astype(np.float32), gd, step, w.iters, nt, w.n))
+        p32 = F.problem(w.n, w.T, w.n_angles, F.FP32_KAHAN)
+        p64 = F.problem(w.n, w.T, w.n_angles, F.FP64)
+        c64 = torch.as_tensor(w.c, device=dev)
+        g64 = F.forward(p64, c64, torch.as_tensor(w.h, device=dev))
+        gd = add_noise(g64.cpu().numpy(), w.noise, w.noise_rel)
+        c32 = c64.float()
+        step = 1.0 / F.opnorm(p32, c32, torch.ones_like(c32), iters=20)
+        nt, _, _ = F.problem_info(p32, float(w.c.astype(np.float32).max()))
+        pool.append(dict(p32=p32, p64=p64, c=w.c, g=gd, step=step, iters=w.iters, nt=nt,
+                         n=w.n, nth=w.n_angles))
     torch.cuda.synchronize()
+    return pool
+
+
+def extra_serving(F, pool, args):
+    """Poisson arrivals (rate args.rate) over args.window seconds, cycling the
+    pool, through the continuous-batching server; then drained."""
+    import numpy as np
     rng = np.random.default_rng(4)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=100000))
     arrivals = arrivals[arrivals < args.window]
@@ -405,8 +509,10 @@ def run_serve(args):
         while k < len(arrivals) or any(t is not None for t in tickets):
             now = time.perf_counter() - t0
             while k < len(arrivals) and arrivals[k] <= now:
-                prob, c, gd, step, iters, nt, n = pool[k % len(pool)]
-                tickets.append(srv.submit(prob, c, gd, 1e-3, step, iters))
+                r = pool[k % len(pool)]
+                tickets.append(srv.submit(r["p32"], r["c"].astype(np.float32),
+                                          r["g"].astype(np.float32), 1e-3, r["step"],
+                                          r["iters"]))
                 k += 1
             for i, t in enumerate(tickets):
                 if t is not None and srv.poll(t) is not None:
@@ -414,91 +520,176 @@ def run_serve(args):
             time.sleep(0.001)
         elapsed = time.perf_counter() - t0
         st = srv.stats()
-    ps = st["point_steps"]
-    line = {"mode": "serve", "metric": "recons/s", "value": st["completed"] / elapsed,
-            "unit": "recons/s", "n_gpus": 1, "higher_is_better": True,
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-            "max_ms": st["max_ms"], "completed": st["completed"], "failed": st["failed"],
-            "window_s": args.window, "elapsed_s": elapsed, "arrival_rate": args.rate,
-            "voxel_steps_per_s": ps / elapsed, "ticks": st["ticks"],
-            "config": {"workload": "serving mix: N in {64,96,128,192}, 45/90/180 angles, "
-                                   "T in [0.8,1.4], 20-60 FB iterations, FP32-Kahan",
-                       "pool": args.pool, "slots": args.slots, "budget_gb": args.budget_gb},
-            "clocks": clk.summary(), "dtype": "f32", "data": "synthetic"}
-    print(json.dumps(line))
-    return 0
+    return {"recons_per_s": st["completed"] / elapsed, "p50_ms": st["p50_ms"],
+            "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "completed": st["completed"], "failed": st["failed"], "window_s": args.window,
+            "elapsed_s": elapsed, "arrival_rate_per_s": args.rate,
+            "voxel_steps_per_s": st["point_steps"] / elapsed, "ticks": st["ticks"],
+            "pool": len(pool), "slots": args.slots, "precision": "fp32-kahan",
+            "requests": [{"n": r["n"], "angles": r["nth"], "iters": r["iters"]} for r in pool],
+            "clocks": clk.summary()}
 
 
-def run_serve_vs_fp64(args):
+def extra_serve_vs_fp64(F, dev, pool, args):
     """The served FP32 path against the plain FP64 GPU path on the same
-    requests: a burst of the serving pool through the continuous-batching
-    server (FP32-Kahan, all submitted at once: saturated throughput) and the
-    same reconstructions one after another through ffpat_fb_solve in FP64,
-    with the same step and iteration count.  Prints recons/s of both, their
-    ratio and the largest relative L2 difference of a served image from its
-    FP64 reconstruction."""
+    requests: the pool as one burst through the server (FP32-Kahan, all
+    submitted at once) and the same reconstructions one after another through
+    ffpat_fb_solve in FP64, same step and iteration count; recons/s of both,
+    their ratio and the largest relative L2 difference of a served image from
+    its FP64 reconstruction."""
     import numpy as np
     import torch
-
-    from paper_1901_06503_gb300 import build_lib
-    from paper_1901_06503_gb300 import ffpat as F
-    from paper_1901_06503_gb300.inputs import add_noise, config
-
-    build_lib.build()
-    F.lib()
-    dev = torch.device("cuda", 0)
-    pool = []
-    for s in range(1, args.pool + 1):
-        w = config(4, seed=1000 + s)
-        p32 = F.problem(w.n, w.T, w.n_angles, F.FP32_KAHAN)
-        p64 = F.problem(w.n, w.T, w.n_angles, F.FP64)
-        c64 = torch.as_tensor(w.c, device=dev)
-        g64 = F.forward(p64, c64, torch.as_tensor(w.h, device=dev))
-        gd = add_noise(g64.cpu().numpy(), w.noise, w.noise_rel)
-        step = 1.0 / F.opnorm(p64, c64, torch.ones_like(c64), iters=20)
-        pool.append((p32, p64, w.c, gd, step, w.iters, w.n))
-    torch.cuda.synchronize()
     budget = int(args.budget_gb * (1 << 30))
     served = {}
     with F.Server(budget, args.slots) as srv:
-        # warm-up: one request through the server
-        p32, _, c, gd, step, iters, _ = pool[0]
-        srv.wait(srv.submit(p32, c.astype(np.float32), gd.astype(np.float32), 1e-3, step, 1))
+        r = pool[0]
+        srv.wait(srv.submit(r["p32"], r["c"].astype(np.float32), r["g"].astype(np.float32),
+                            1e-3, r["step"], 1))
         t0 = time.perf_counter()
-        tickets = [(i, srv.submit(p32, c.astype(np.float32), gd.astype(np.float32), 1e-3, step,
-                                  iters))
-                   for i, (p32, _, c, gd, step, iters, _) in enumerate(pool)]
+        tickets = [(i, srv.submit(r["p32"], r["c"].astype(np.float32),
+                                  r["g"].astype(np.float32), 1e-3, r["step"], r["iters"]))
+                   for i, r in enumerate(pool)]
         for i, t in tickets:
             served[i] = srv.wait(t)[0]
         t_served = time.perf_counter() - t0
-    # FP64, one reconstruction after another (device-resident inputs)
-    t64 = 0.0
-    errs = []
-    for i, (_, p64, c, gd, step, iters, _) in enumerate(pool):
-        c_d = torch.as_tensor(c, device=dev)
-        g_d = torch.as_tensor(gd, device=dev)
-        ws = F.workspace(p64, dev)
+    t64, errs = 0.0, []
+    for i, r in enumerate(pool):
+        c_d = torch.as_tensor(r["c"], device=dev)
+        g_d = torch.as_tensor(r["g"], device=dev)
+        ws = F.workspace(r["p64"], dev)
         torch.cuda.synchronize()
         a = time.perf_counter()
-        h64, _, _ = F.fb_solve(p64, c_d, g_d, 1e-3, step, iters, ws=ws, history=False)
+        h64, _, _ = F.fb_solve(r["p64"], c_d, g_d, 1e-3, r["step"], r["iters"], ws=ws,
+                               history=False)
         torch.cuda.synchronize()
         t64 += time.perf_counter() - a
         h64 = h64.cpu().numpy()
         h32 = np.asarray(served[i], dtype=np.float64)
         errs.append(float(np.linalg.norm(h32 - h64) / np.linalg.norm(h64)))
         del ws
-    r_served = len(pool) / t_served
-    r64 = len(pool) / t64
-    line = {"mode": "serve_vs_fp64", "metric": "recons/s", "unit": "recons/s",
-            "served_fp32_kahan": r_served, "plain_fp64_gpu": r64, "ratio": r_served / r64,
-            "max_rel_l2_vs_fp64": max(errs), "rel_l2_vs_fp64": errs,
-            "requests": [{"n": n, "iters": it} for (_, _, _, _, _, it, n) in pool],
-            "config": {"workload": "serving pool: N in {64,96,128,192}, 45/90/180 angles, "
-                                   "T in [0.8,1.4], 20-60 FB iterations; FP32-Kahan served as "
-                                   "one burst vs FP64 ffpat_fb_solve one after another",
-                       "pool": args.pool, "slots": args.slots},
-            "dtype": "f32 vs f64", "data": "synthetic"}
-    print(json.dumps(line))
+    r_served, r64 = len(pool) / t_served, len(pool) / t64
+    return {"served_fp32_kahan_recons_per_s": r_served, "plain_fp64_gpu_recons_per_s": r64,
+            "ratio": r_served / r64, "max_rel_l2_vs_fp64": max(errs), "rel_l2_vs_fp64": errs,
+            "pool": len(pool),
+            "how": "pool served as one burst (FP32-Kahan) vs ffpat_fb_solve in FP64 one "
+                   "request after another, same step and iterations, wall time"}
+
+
+def run_serve(args):
+    """Serving mix (Poisson arrivals of requests of mixed size) through the
+    continuous-batching server; prints one JSON line with recons/s and p50/p99."""
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    build_lib.build()
+    F.lib()
+    dev = torch.device("cuda", 0)
+    res = extra_serving(F, serving_pool(F, dev, args.pool), args)
+    print(json.dumps({"mode": "serve", "metric": "recons/s", "value": res["recons_per_s"],
+                      "unit": "recons/s", "n_gpus": 1, "higher_is_better": True, **res,
+                      "config": {"workload": "serving mix: N in {64,96,128,192}, 45/90/180 "
+                                             "angles, T in [0.8,1.4], 20-60 FB iterations, "
+                                             "FP32-Kahan", "budget_gb": args.budget_gb},
+                      "dtype": "f32", "data": "synthetic"}))
+    return 0
+
+
+def run_serve_vs_fp64(args):
+    """The served FP32 path against the plain FP64 GPU path on the same
+    requests (see extra_serve_vs_fp64); prints one JSON line."""
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+    build_lib.build()
+    F.lib()
+    dev = torch.device("cuda", 0)
+    pool = serving_pool(F, dev, args.pool)
+    res = extra_serve_vs_fp64(F, dev, pool, args)
+    print(json.dumps({"mode": "serve_vs_fp64", "metric": "recons/s", "unit": "recons/s", **res,
+                      "requests": [{"n": r["n"], "iters": r["iters"]} for r in pool],
+                      "config": {"workload": "serving pool: N in {64,96,128,192}, 45/90/180 "
+                                             "angles, T in [0.8,1.4], 20-60 FB iterations; "
+                                             "FP32-Kahan served as one burst vs FP64 "
+                                             "ffpat_fb_solve one after another",
+                                 "pool": args.pool, "slots": args.slots},
+                      "dtype": "f32 vs f64", "data": "synthetic"}))
+    return 0
+
+
+def run_op(args):
+    """One library operation on a seeded random problem, timed with CUDA
+    events: the driver for timing and profiling single kernels.  --op-steps
+    sets T so that the wave operator takes exactly that many leapfrog steps
+    (c in [0.75, 1.4], cfl 0.3); --path picks the leapfrog kernel."""
+    import numpy as np
+    import torch
+
+    from paper_1901_06503_gb300 import build_lib
+    from paper_1901_06503_gb300 import ffpat as F
+
+    build_lib.build()
+    F.set_stencil_path(args.path)
+    prec = {"fp64": F.FP64, "fp32": F.FP32, "fp32-kahan": F.FP32_KAHAN}[args.precision]
+    n = args.n
+    cmax = 1.4
+    T = args.op_steps * 0.3 * (2.0 / n) / cmax * (1 - 1e-9)
+    prob = F.problem(n, T, args.angles, prec, precond=1 if args.op == "ramp" else 0)
+    nt, _, _ = F.problem_info(prob, cmax)
+    dt = F.torch_dtype(prob)
+    gen = torch.Generator(device="cuda").manual_seed(args.seed)
+    c = (0.75 + 0.65 * torch.rand((n, n, n), generator=gen, device="cuda", dtype=torch.float64))
+    c.view(-1)[0] = cmax
+    c = c.to(dt)
+    h = torch.randn((n, n, n), generator=gen, device="cuda", dtype=torch.float64).to(dt)
+    g = torch.randn((args.angles, n, n), generator=gen, device="cuda",
+                    dtype=torch.float64).to(dt)
+    ws = F.workspace(prob)
+    out_v = torch.empty_like(h)
+    out_d = torch.empty_like(g)
+
+    def run():
+        if args.op == "wave":
+            F.wave(prob, c, h, out_v, ws=ws)
+        elif args.op == "wave_t":
+            F.wave(prob, c, h, out_v, transpose=True, ws=ws)
+        elif args.op == "forward":
+            F.forward(prob, c, h, out_d, ws=ws)
+        elif args.op == "adjoint":
+            F.adjoint(prob, c, g, out_v, ws=ws)
+        elif args.op == "project":
+            F.project(prob, h, out_d)
+        elif args.op == "backproject":
+            F.backproject(prob, g, out_v)
+        elif args.op == "ramp":
+            F.ramp(prob, g, out_d)
+        elif args.op == "fb":
+            F.fb_solve(prob, c, g, 1e-3, 1e-3, 1, h=out_v.zero_(), ws=ws, history=False)
+
+    run()
+    torch.cuda.synchronize()
+    F.profile_enable(True)
+    F.profile_read()
+    times = []
+    for _ in range(args.repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    prof = F.profile_read()
+    F.profile_enable(False)
+    res = {"mode": "op", "op": args.op, "path": args.path, "n": n, "angles": args.angles,
+           "nt": nt, "precision": args.precision, "ms": times, "ms_min": min(times)}
+    if prof["step_launches"]:
+        res["step_ms_avg"] = prof["step_ms"] / prof["step_launches"]
+        res["step_gbs"] = prof["step_bytes"] / (prof["step_ms"] / 1e3) / 1e9
+        res["voxel_steps_per_s"] = prof["steps"] * n**3 / (prof["step_ms"] / 1e3)
+        res["step_ms_per_step"] = prof["step_ms"] / max(prof["steps"], 1)
+    assert np.isfinite(out_v.double().sum().item()) or args.op in ("forward", "project", "ramp")
+    print(json.dumps(res))
     return 0
 
 
@@ -723,30 +914,49 @@ def run_grad(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg5")
     ap.add_argument("--precision", choices=["fp32-kahan", "fp32", "fp64"], default="fp32-kahan")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["fb", "serve", "serve_vs_fp64", "precision", "paper",
-                                       "grad"],
+    ap.add_argument("--no-extras", action="store_true",
+                    help="fb: leave out the FP32-vs-FP64, FMA-rate and serving keys")
+    ap.add_argument("--mode", choices=["fb", "op", "serve", "serve_vs_fp64", "precision",
+                                       "paper", "grad"],
                     default="fb",
-                    help="fb: the default FB-iteration line; serve: the serving mix; "
+                    help="fb: the default FB-iteration line; op: one library operation "
+                         "(kernel timing and profiling); serve: the serving mix; "
                          "precision: FP64 vs FP32 vs FP32-Kahan on the 128^3 solve; "
                          "paper: the paper's experimental setting in 3D (one- vs two-step); "
                          "serve_vs_fp64: served FP32 burst vs plain FP64 GPU solves; "
                          "grad: forward + backward of the differentiable 192^3 operator")
     ap.add_argument("--paper-n", type=int, default=64, help="paper: source box points per axis")
     ap.add_argument("--paper-angles", type=int, default=180, help="paper: projection angles")
-    ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window (s)")
+    ap.add_argument("--window", type=float, default=10.0, help="serve: arrival window (s)")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate (1/s)")
-    ap.add_argument("--pool", type=int, default=12, help="serve: distinct requests cycled")
+    ap.add_argument("--pool", type=int, default=8, help="serve: distinct requests cycled")
+    ap.add_argument("--fp64-pool", type=int, default=6,
+                    help="fb extras: requests of the pool solved in FP64 for the comparison")
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--iters", type=int, default=20, help="precision / paper: FB iterations")
+    ap.add_argument("--extra-iters", type=int, default=100,
+                    help="fb extras: FB iterations of the FP32-vs-FP64 comparison (128^3)")
+    # --mode op
+    ap.add_argument("--op", choices=["wave", "wave_t", "forward", "adjoint", "project",
+                                     "backproject", "ramp", "fb"], default="wave")
+    ap.add_argument("--n", type=int, default=128, help="op: grid points per axis")
+    ap.add_argument("--angles", type=int, default=90, help="op: projection angles")
+    ap.add_argument("--op-steps", type=int, default=16, help="op: leapfrog steps of W")
+    ap.add_argument("--repeat", type=int, default=3, help="op: timed repetitions")
+    ap.add_argument("--seed", type=int, default=0, help="op: random seed")
+    ap.add_argument("--path", type=int, default=0,
+                    help="op: leapfrog kernel: 0 auto, 1 plain, 2 TMA, 3 two-step, 4 resident")
     args = ap.parse_args()
+    if args.mode == "op":
+        return run_op(args)
     if args.mode == "serve":
         return run_serve(args)
     if args.mode == "precision":

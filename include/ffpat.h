@@ -288,6 +288,17 @@ int ffpat_device_status(int32_t clear);
  * context stays usable.  Synchronises the stream. */
 int ffpat_debug_wait_timeout(int32_t microseconds, void *stream);
 
+/* Arithmetic throughput probe (not part of the method; the paper has no
+ * counterpart): the fused multiply-add rate of one pipe of the current
+ * device, kind 0 = FP64 (fma), 1 = FP32 (fmaf), 2 = packed two-lane FP32
+ * (fma.rn.f32x2, the form the FP32 stencils use), measured with CUDA events
+ * on `stream` over a grid that fills every SM with eight independent FMA
+ * chains per thread; *flops_per_s receives the best of three launches
+ * (2 operations per FMA and lane).  Kernels that are bound by arithmetic
+ * rather than memory report their fraction of this measured rate.
+ * Synchronises the stream; FFPAT_EINVAL for another kind or a null output. */
+int ffpat_debug_fma_rate(int32_t kind, double *flops_per_s, void *stream);
+
 /* ---- Differentiation of g = P W(c) h with respect to h and the sound speed c.
  * The forward pass runs the three-term leapfrog (FFPAT_FP32_KAHAN problems
  * take FP32 three-term steps on this path) and saves (p^{sk}, p^{sk+1}) every
@@ -370,14 +381,18 @@ int ffpat_server_destroy(ffpat_server *server);
  * memory or pass a workspace (code inside an application that owns all device
  * memory, fixed-budget or real-time pipelines that must not enter an
  * allocator).  The paper has no counterpart; this is a deployment variant.
- * It allocates nothing: its scratch is a 32 MiB file-scope device array that
- * every GPU loading the library holds until exit, so problems whose
- * ffpat_workspace_bytes exceeds 32 MiB fail with FFPAT_EINVAL (N <= 64 with up
- * to 180 angles fits every precision).  The first call on a device looks up
- * the array's device address (with that device current); make it before any
- * stream capture.  All calls on a device share the array: calls that overlap
- * on the GPU race and must be serialised by the caller.  Nothing in the array
- * needs to start at zero; it keeps the last call's contents. */
+ * Its scratch is a 32 MiB file-scope device array, committed when the
+ * library's device code is loaded on a device and held until exit; under
+ * CUDA's lazy module loading (the default) that load happens during the first
+ * call on each device, which may allocate once; later calls allocate nothing.
+ * Problems whose ffpat_workspace_bytes exceeds 32 MiB fail with FFPAT_EINVAL
+ * (a wave grid N + 2 pad <= 64 with up to 180 angles fits every precision;
+ * without padding that is N <= 64); a device index >= 64 fails with
+ * FFPAT_EINVAL.  The first call on a device looks up the array's device
+ * address (with that device current); make it before any stream capture.
+ * All calls on a device share the array: calls that overlap on the GPU race
+ * and must be serialised by the caller.  Nothing in the array needs to start
+ * at zero; it keeps the last call's contents. */
 int ffpat_forward_noalloc(const ffpat_problem *problem, const void *c, const void *h, void *g,
                           void *stream);
 

@@ -11,10 +11,15 @@
 // step by step (ffpat_forward replays repeated time loops from CUDA graphs,
 // whose capture and instantiation allocate).
 //
-// The array is kScratchBytes (32 MiB) of device memory that every GPU which
-// loads the library holds until the process exits; problems whose workspace
-// (ffpat_workspace_bytes) is larger are rejected.  That admits N <= 64 with up
-// to 180 angles in every precision (and larger angle counts for FP32).
+// The array is kScratchBytes (32 MiB) of device memory on every GPU where
+// the library's device code is loaded, held until the process exits.  The
+// array is committed when that module is loaded on a device; under CUDA's
+// lazy module loading (the default) that happens during the first call on
+// each device, which may therefore allocate device memory once; later calls
+// allocate nothing.  Problems whose workspace (ffpat_workspace_bytes) is larger
+// are rejected.  The workspace grows with the wave grid N_w = N + 2 pad:
+// without padding, N <= 64 with up to 180 angles fits in every precision
+// (N_w <= 64 with up to 180 angles in general).
 //
 // In host code the array's name is only a host-side stand-in, not a device
 // address, so the first call on each device (made with that device current)
@@ -42,15 +47,22 @@ void* g_scratch_addr[kMaxDevices] = {};
 // Device address of the static scratch on the current device (looked up once).
 int scratch_address(void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return check_launch("cudaGetDevice");
+  const cudaError_t eg = cudaGetDevice(&dev);
+  if (eg != cudaSuccess) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "ffpat_forward_noalloc: cudaGetDevice: %s", cudaGetErrorString(eg));
+  }
+  if (dev < 0 || dev >= kMaxDevices)
+    return report(FFPAT_EINVAL, "ffpat_forward_noalloc: device %d >= %d (the static scratch "
+                  "addresses are kept for devices 0 .. %d)", dev, kMaxDevices, kMaxDevices - 1);
   std::lock_guard<std::mutex> g(g_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
-      return FFPAT_ECUDA;
+      return report(FFPAT_ECUDA, "ffpat_forward_noalloc: cudaGetSymbolAddress of the static "
+                    "scratch: %s", cudaGetErrorString(e));
     }
     g_scratch_addr[dev] = p;
   }
@@ -68,12 +80,12 @@ extern "C" int ffpat_forward_noalloc(const ffpat_problem* problem, const void* c
   if (need > ffpat::kScratchBytes)
     return ffpat::report(FFPAT_EINVAL,
                          "ffpat_forward_noalloc: the problem needs %zu bytes of scratch but the "
-                         "static scratch holds %zu (N <= 64 with <= 180 angles fits every precision)",
+                         "static scratch holds %zu (a wave grid N + 2 pad <= 64 with <= 180 "
+                         "angles fits every precision)",
                          need, ffpat::kScratchBytes);
   void* ws = nullptr;
-  if (ffpat::scratch_address(&ws) != FFPAT_OK)
-    return ffpat::report(FFPAT_ECUDA,
-                         "ffpat_forward_noalloc: cudaGetSymbolAddress of the static scratch failed");
+  const int rc = ffpat::scratch_address(&ws);
+  if (rc != FFPAT_OK) return rc;
   // launch the time loop step by step: the library's CUDA-graph replay would
   // create a capture stream and instantiate a graph, which allocate
   ffpat::NoGraphs no_graphs;

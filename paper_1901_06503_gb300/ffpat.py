@@ -111,6 +111,7 @@ def _declare(L):
         "ffpat_set_stencil_path": (ctypes.c_int, [i32]),
         "ffpat_device_status": (ctypes.c_int, [i32]),
         "ffpat_debug_wait_timeout": (ctypes.c_int, [i32, _P]),
+        "ffpat_debug_fma_rate": (ctypes.c_int, [i32, ctypes.POINTER(f64), _P]),
         "ffpat_forward_noalloc": (ctypes.c_int, [_PR, _P, _P, _P, _P]),
         "ffpat_ckpt_bytes": (sz, [_PR, i32, i32]),
         "ffpat_forward_ckpt": (ctypes.c_int, [_PR, _P, _P, _P, i32, _P, sz, _P, sz, _P]),
@@ -265,7 +266,8 @@ def forward(prob, c, h, g=None, ws=None, stream=None):
 
 def forward_noalloc(prob, c, h, g, stream=None):
     """g = P W h through the entry point that allocates nothing (static
-    device scratch; N <= 64 with <= 180 angles).  `g` must be preallocated."""
+    device scratch; wave grid N + 2 pad <= 64 with <= 180 angles).  `g` must be
+    preallocated."""
     _check(lib().ffpat_forward_noalloc(ctypes.byref(prob), _dev(c, prob, wave_shape(prob), "c"),
                                        _dev(h, prob, vol_shape(prob), "h"),
                                        _dev(g, prob, data_shape(prob), "g"), _stream(stream)))
@@ -463,6 +465,17 @@ def device_status(clear: bool = False) -> int:
 def debug_wait_timeout(microseconds: int = 20000, stream=None) -> None:
     """Run a bounded device wait that cannot complete (sets FFPAT_ETIMEDOUT)."""
     _check(lib().ffpat_debug_wait_timeout(int(microseconds), _stream(stream)))
+
+
+FMA_FP64, FMA_FP32, FMA_FP32X2 = 0, 1, 2
+
+
+def debug_fma_rate(kind: int, stream=None) -> float:
+    """Measured fused multiply-add rate of one pipe in FLOP/s (kind 0 FP64,
+    1 FP32, 2 packed two-lane FP32)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().ffpat_debug_fma_rate(int(kind), ctypes.byref(out), _stream(stream)))
+    return float(out.value)
 
 
 def version() -> str:

@@ -14,6 +14,8 @@ from paper_1901_06503_gb300 import ffpat as F
 from paper_1901_06503_gb300.inputs import (add_noise, config, extend_speed, padded_axis,
                                            random_data, random_volume)
 
+from tolerances import hist_dev, hist_tol, tol
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -132,10 +134,9 @@ def test_padded_limited_view_fb(prec, precond):
     hg = host(h_gpu)
     assert st["iters_done"] == k == 6
     assert np.all(hg[sup == 0] == 0)
-    assert rel(hg, h_or) < (1e-10 if prec == F.FP64 else 5e-5)
-    tol = 1e-9 if prec == F.FP64 else 1e-4
+    assert rel(hg, h_or) < tol(prec)
     for col in (0, 1, 3):
-        assert np.max(np.abs(hist[:, col] - hist_or[:, col]) / np.abs(hist_or[:, col])) < tol
+        assert hist_dev(hist, hist_or, cols=(col,)) < hist_tol(prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -147,7 +148,7 @@ def test_padded_two_step(prec):
     h_gpu, st, hist = F.fb_two_step(prob, dev(c, prob), dev(G, prob), w.lam, 0.5, 5)
     h_or, hist_or, k = o.fb_two_step(c, G, w.T, w.lam, 0.5, 5, pad=pad)
     assert st["iters_done"] == k == 5
-    assert rel(host(h_gpu), h_or) < (1e-10 if prec == F.FP64 else 5e-5)
+    assert rel(host(h_gpu), h_or) < tol(prec)
 
 
 def test_padding_rejected_by_gradient_path():

@@ -5,6 +5,8 @@ Tolerances (relative L2): 1e-10 for FP64 problems, 2e-5 for the FP32 and
 FP32-Kahan wavefields; bit-exact for the FP64 projection's index arithmetic and
 for the FP64 projection itself on identical input.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -13,6 +15,7 @@ from paper_1901_06503_gb300 import build_lib
 from paper_1901_06503_gb300 import ffpat as F
 from paper_1901_06503_gb300.inputs import (add_noise, config, random_data, random_speed,
                                            random_volume)
+from tolerances import FP32_TOL, hist_dev, hist_tol, tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -238,7 +241,7 @@ def test_dot_product_gpu_fp64():
     assert abs(lhs - rhs) <= 1e-12 * float(Ah.norm() * g.norm())
 
 
-@pytest.mark.parametrize("prec", [F.FP64, F.FP32_KAHAN])
+@pytest.mark.parametrize("prec", PRECS)
 def test_forward_adjoint_config2_full(prec):
     """N = 128, 90 angles, T = 1.2 (333 steps): the whole operator pair."""
     w = config(2)
@@ -250,6 +253,32 @@ def test_forward_adjoint_config2_full(prec):
     gd = as_input(add_noise(g_or, w.noise, w.noise_rel), prec)
     a_gpu = host(F.adjoint(prob, dev(c, prob), dev(gd, prob)))
     assert rel(a_gpu, o.adjoint(c, gd, w.T)) < TOL[prec]
+
+
+def test_config2_fp32_vs_fp64_100_iterations():
+    """The 128^3 solve (90 angles, T = 1.2, 2 % noise, identity Lambda) for
+    the workload's 100 FB iterations in FP32 and FP32-Kahan against the FP64
+    GPU path with the same step (1/L from 8 oracle power iterations), and the
+    FP64 GPU path against the oracle over the first 10 iterations (the
+    oracle's scope at this size)."""
+    w = config(2)
+    c64 = w.c
+    g64 = add_noise(o.forward(c64, w.h, w.T, w.n_angles), w.noise, w.noise_rel)
+    s = 1.0 / o.power(c64, np.ones_like(c64), w.T, w.n_angles, iters=8)
+    res = {}
+    for prec in PRECS:
+        prob = F.problem(w.n, w.T, w.n_angles, prec)
+        h, st, _ = F.fb_solve(prob, dev(c64, prob), dev(g64, prob), w.lam, s, 100,
+                              history=False)
+        assert st["iters_done"] == 100
+        res[prec] = host(h)
+    for prec in (F.FP32, F.FP32_KAHAN):
+        assert rel(res[prec], res[F.FP64]) < FP32_TOL
+    p64 = F.problem(w.n, w.T, w.n_angles, F.FP64)
+    h10, _, _ = F.fb_solve(p64, dev(c64, p64), dev(g64, p64), w.lam, s, 10, history=False)
+    h_or, _, k = o.fb(c64, g64, w.T, w.lam, s, 10)
+    assert k == 10
+    assert rel(host(h10), h_or) < tol(F.FP64)
 
 
 # ------------------------------------------------------------ Algorithm 8 --
@@ -270,11 +299,9 @@ def test_fb_config1(prec):
     h_gpu, st, hist = F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, s, w.iters)
     h_or, hist_or, k = o.fb(c, g, w.T, w.lam, s, w.iters)
     assert st["iters_done"] == k == w.iters
-    assert rel(host(h_gpu), h_or) < (1e-10 if prec == F.FP64 else 5e-5)
-    tol = 1e-9 if prec == F.FP64 else 1e-4
-    for col in (0, 1, 3):
-        assert np.max(np.abs(hist[:, col] - hist_or[:, col]) / np.abs(hist_or[:, col])) < tol
-    assert abs(st["objective"] - hist_or[-1, 0]) < tol * abs(hist_or[-1, 0])
+    assert rel(host(h_gpu), h_or) < tol(prec)
+    assert hist_dev(hist, hist_or) < hist_tol(prec)
+    assert abs(st["objective"] - hist_or[-1, 0]) < hist_tol(prec) * abs(hist_or[-1, 0])
 
 
 def test_fb_preconditioned_fp64():
@@ -396,6 +423,57 @@ def test_full_size_n384_two_step_pass():
     assert F.device_status() == 0
 
 
+def _config5_problem():
+    w = config(5)
+    prec = F.FP32_KAHAN
+    c, h = as_input(w.c, prec), as_input(w.h, prec)
+    return w, prec, c, h, F.problem(w.n, w.T, w.n_angles, prec, w.precond)
+
+
+def test_config5_forward_adjoint_full_length():
+    """The large solve's operator pair at full length: N = 384, 180 angles,
+    T = 1.5 (1344 leapfrog steps: the start step, then two steps per pass,
+    the automatic path at this size), FP32-Kahan.  The forward of the
+    workload's phantom and the adjoint of its noisy data (Problem 1 of
+    Sec. 2.1), element by element against the oracle on every projection and
+    on the whole grid."""
+    w, prec, c, h, prob = _config5_problem()
+    cd = dev(c, prob)
+    F.profile_enable(True)
+    F.profile_read()
+    g_gpu = host(F.forward(prob, cd, dev(h, prob)))
+    prof = F.profile_read()
+    F.profile_enable(False)
+    nt, _ = o.time_steps(w.n, w.T, 0.3, float(c.max()))
+    assert nt == 1344 and prof["steps"] == nt
+    assert prof["step_launches"] < 0.51 * nt  # two steps per pass
+    g_or = o.forward(c, h, w.T, w.n_angles)
+    assert rel(g_gpu, g_or) < FP32_TOL
+    gd = as_input(add_noise(g_or, w.noise, w.noise_rel), prec)
+    del g_gpu, g_or
+    a_gpu = host(F.adjoint(prob, cd, dev(gd, prob)))
+    assert rel(a_gpu, o.adjoint(c, gd, w.T)) < FP32_TOL
+    assert F.device_status() == 0
+
+
+@pytest.mark.skipif(os.environ.get("FFPAT_LONG_TESTS") != "1",
+                    reason="about 15 minutes of oracle time on 16 cores; FFPAT_LONG_TESTS=1")
+def test_config5_first_two_fb_iterations():
+    """The first two iterations of the ramp-preconditioned Algorithm 8 on the
+    large solve (N = 384, 180 angles, T = 1.5, 1 % noise, FP32-Kahan) against
+    the oracle, iterates and history.  The step only scales the iterates, so
+    a fixed s stands in for 1/L here (the oracle's power iteration would add
+    40 wave solves)."""
+    w, prec, c, h, prob = _config5_problem()
+    g = as_input(add_noise(o.forward(c, h, w.T, w.n_angles), w.noise, w.noise_rel), prec)
+    s = 1e-3
+    hg, st, hist = F.fb_solve(prob, dev(c, prob), dev(g, prob), w.lam, s, 2)
+    h_or, hist_or, k = o.fb(c, g, w.T, w.lam, s, 2, precond=1)
+    assert st["iters_done"] == k == 2
+    assert rel(host(hg), h_or) < FP32_TOL
+    assert hist_dev(hist, hist_or) < FP32_TOL
+
+
 # ------------------------------------------------- the two stencil kernels --
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -455,6 +533,42 @@ def test_two_step_kahan_bit_identical(n, T):
     nt, dt = o.time_steps(n, T, 0.3, c.max())
     assert rel(outs[3][0], o.wave(o.kappa(n, dt, c), h, nt)) < TOL[prec]
     assert F.device_status() == 0
+
+
+@pytest.mark.parametrize("zc", [1, 3])
+def test_two_step_kahan_many_items_per_cta(tmp_path, zc):
+    """The two-step pass with short z-ranges (FFPAT_ZCHUNK, in a child
+    process): at N = 128 that is 688 or 2048 work items for 152 CTAs, so every
+    CTA walks several items and re-arms its barriers between them; W and W^T
+    stay bit for bit those of single steps."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    n, T = 128, 0.05
+    c = as_input(random_speed(n, 1300), F.FP32)
+    h = as_input(random_volume(n, 1301), F.FP32)
+    np.save(tmp_path / "c.npy", c.astype(np.float32))
+    np.save(tmp_path / "h.npy", h.astype(np.float32))
+    code = (
+        "import sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "from paper_1901_06503_gb300 import ffpat as F\n"
+        f"c = torch.as_tensor(np.load({str(tmp_path / 'c.npy')!r}), device='cuda')\n"
+        f"h = torch.as_tensor(np.load({str(tmp_path / 'h.npy')!r}), device='cuda')\n"
+        f"prob = F.problem({n}, {T}, 4, F.FP32_KAHAN)\n"
+        "out = []\n"
+        "for path in (2, 3):\n"
+        "    F.set_stencil_path(path)\n"
+        "    out += [F.wave(prob, c, h).cpu().numpy(), F.wave(prob, c, h, transpose=True).cpu().numpy()]\n"
+        "assert F.device_status() == 0\n"
+        f"np.save({str(tmp_path / 'out.npy')!r}, np.stack(out))\n")
+    env = dict(os.environ, FFPAT_ZCHUNK=str(zc))
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, timeout=300)
+    w2, wt2, w3, wt3 = np.load(tmp_path / "out.npy").astype(np.float64)
+    assert np.array_equal(w2, w3) and np.array_equal(wt2, wt3)
+    nt, dt = o.time_steps(n, T, 0.3, c.max())
+    assert nt >= 4
+    assert rel(w3, o.wave(o.kappa(n, dt, c), h, nt)) < FP32_TOL
 
 
 @pytest.mark.parametrize("n,T", [(36, 0.4), (36, 0.41), (64, 0.3), (96, 0.21), (128, 0.05)])
@@ -568,9 +682,8 @@ def test_fbp_and_two_step_fb(prec):
     h_gpu, st, hist = F.fb_two_step(prob, dev(c, prob), dev(G, prob), w.lam, 0.5, 6)
     h_or, hist_or, k = o.fb_two_step(c, G, w.T, w.lam, 0.5, 6)
     assert st["iters_done"] == k == 6
-    assert rel(host(h_gpu), h_or) < (1e-10 if prec == F.FP64 else 5e-5)
-    tol = 1e-9 if prec == F.FP64 else 1e-4
-    assert np.max(np.abs(hist[:, 0] - hist_or[:, 0]) / np.abs(hist_or[:, 0])) < tol
+    assert rel(host(h_gpu), h_or) < tol(prec)
+    assert hist_dev(hist, hist_or, cols=(0,)) < hist_tol(prec)
 
 
 def test_two_step_automatic_step():
@@ -601,7 +714,5 @@ def test_masked_fb(prec, precond):
     hg = host(h_gpu)
     assert st["iters_done"] == k == 6
     assert np.all(hg[sup == 0] == 0)
-    assert rel(hg, h_or) < (1e-10 if prec == F.FP64 else 5e-5)
-    tol = 1e-9 if prec == F.FP64 else 1e-4
-    for col in (0, 1, 3):
-        assert np.max(np.abs(hist[:, col] - hist_or[:, col]) / np.abs(hist_or[:, col])) < tol
+    assert rel(hg, h_or) < tol(prec)
+    assert hist_dev(hist, hist_or) < hist_tol(prec)

@@ -12,6 +12,8 @@ from paper_1901_06503_gb300 import ffpat as F
 from paper_1901_06503_gb300.inputs import (add_noise, axis, config, extend_speed, padded_axis,
                                            random_data, random_volume)
 
+from tolerances import hist_dev, hist_tol, tol
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -73,10 +75,9 @@ def test_fb_gradient_regulariser(prec, precond):
                                         mask=dev(mask, prob), reg=F.REG_GRAD2)
     h_or, hist_or, k = o.fb_masked(c, g, w.T, lam, 1.0 / L, 6, mask=mask, precond=precond, reg=1)
     assert st["iters_done"] == k == 6
-    assert rel(host(h_gpu), h_or) < (1e-10 if prec == F.FP64 else 5e-5)
-    tol = 1e-9 if prec == F.FP64 else 1e-4
+    assert rel(host(h_gpu), h_or) < tol(prec)
     for col in (0, 1, 3):
-        assert np.max(np.abs(hist[:, col] - hist_or[:, col]) / np.abs(hist_or[:, col])) < tol
+        assert hist_dev(hist, hist_or, cols=(col,)) < hist_tol(prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -93,9 +94,8 @@ def test_two_step_gradient_regulariser_padded(prec):
                                     reg=F.REG_GRAD2)
     h_or, hist_or, k = o.fb_two_step(c, G, w.T, 0.5 * 0.3, 0.3, 5, pad=pad, reg=1)
     assert st["iters_done"] == k == 5
-    assert rel(host(h_gpu), h_or) < (1e-10 if prec == F.FP64 else 5e-5)
-    tol = 1e-9 if prec == F.FP64 else 1e-4
-    assert np.max(np.abs(hist[:, 0] - hist_or[:, 0]) / np.abs(hist_or[:, 0])) < tol
+    assert rel(host(h_gpu), h_or) < tol(prec)
+    assert hist_dev(hist, hist_or, cols=(0,)) < hist_tol(prec)
 
 
 def test_gradient_regulariser_rejects_support_and_unknown():

@@ -13,6 +13,8 @@ from paper_1901_06503_gb300 import build_lib
 from paper_1901_06503_gb300 import ffpat as F
 from paper_1901_06503_gb300.inputs import add_noise, config
 
+from tolerances import FP32_TOL
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -21,6 +23,12 @@ pytestmark = pytest.mark.gpu
 def _lib():
     build_lib.build()
     F.lib()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def request(n, nth, T, seed, iters=3, noise=0.01):
@@ -92,7 +100,30 @@ def test_served_vs_oracle():
     with F.Server(1 << 30, 2) as srv:
         h, _ = srv.wait(srv.submit(prob, c, g, 1e-3, 0.02, iters))
     h_or, _, _ = o.fb(c.astype(np.float64), g.astype(np.float64), 0.5, 1e-3, 0.02, iters)
-    assert np.linalg.norm(h - h_or) / np.linalg.norm(h_or) < 5e-5
+    assert rel(h, h_or) < FP32_TOL
+
+
+def test_served_mix_vs_oracle_up_to_96():
+    """A mix served concurrently -- requests of the serving workload's sizes
+    64^3 (45 angles) and 96^3 (90 angles) beside a 128^3 request -- each
+    request of at most 96^3 against the oracle's Algorithm 8 with the same
+    step (1/L from the oracle's power iteration) and iteration count."""
+    reqs = []
+    for n, nth, T, seed, iters in ((64, 45, 0.8, 41, 5), (96, 90, 0.9, 42, 4),
+                                   (128, 45, 0.8, 43, 3), (64, 90, 1.1, 44, 6)):
+        prob, c, g, it = request(n, nth, T, seed, iters=iters)
+        L = o.power(c.astype(np.float64), np.ones((n, n, n)), T, nth, iters=8) if n <= 96 else 0
+        reqs.append((prob, c, g, it, T, nth, 1.0 / L if L else 0.02))
+    with F.Server(8 << 30, 4) as srv:
+        tickets = [srv.submit(prob, c, g, 1e-3, s, it) for prob, c, g, it, _, _, s in reqs]
+        done = [srv.wait(t)[0] for t in tickets]
+        assert srv.stats()["completed"] == len(reqs)
+    for (prob, c, g, it, T, nth, s), h in zip(reqs, done):
+        if prob.n > 96:
+            continue
+        h_or, _, k = o.fb(c.astype(np.float64), g.astype(np.float64), T, 1e-3, s, it)
+        assert k == it
+        assert rel(h, h_or) < FP32_TOL, (prob.n, rel(h, h_or))
 
 
 def test_invalid_requests_rejected():
