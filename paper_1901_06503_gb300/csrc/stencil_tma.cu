@@ -541,33 +541,56 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
 // ------------------------------------- two FP32-Kahan steps per pass ----
 // Temporal blocking: one launch advances (p, d, e) from level n to n + 2.
 // Step A recomputes level n + 1 on the 64 x 16 tile plus a two-point x/y halo
-// (68 x 20 points) from a halo-4 box of p^n (72 x 24, starting 16-byte aligned
-// at x0 - 4) and halo-2 boxes of d^n, e^n, kap (72 x 20); step B then forms
-// level n + 2 on the tile from the level-(n+1) planes kept in shared memory.
+// (the 68 x 20 extended tile) from a halo-4 box of p^n (72 x 24, starting
+// 16-byte aligned at x0 - 4) and halo-2 boxes of d^n, e^n, kap (72 x 20);
+// step B then forms level n + 2 on the tile from the level-(n+1) planes.
 // Each point's arithmetic is that of the single-step kernel (same Laplacian
 // order, same Kahan update), so two passes of this kernel give bit-identical
 // results to four single steps.  HBM traffic is 28 B per point per TWO steps;
 // d and e are read with a halo, so they are double-buffered (no in place).
 // Points outside the grid read kap = d = e = p = 0 and therefore produce
 // p^{n+1} = 0 there: the zero ghost values of step B come out of step A.
+//
+// Organisation (one CTA per SM walks whole z-columns of its tile):
+//   * a producer warp issues the TMA copies, one round per plane z: p^n, d^n,
+//     e^n and kap of that plane into slot z mod 8 of an 8-deep ring; it
+//     refills a slot once every compute thread has reported the iteration
+//     that last read it (iteration-done mbarriers), so copies run up to about
+//     five planes ahead of the planes being computed;
+//   * 22 compute warps, one point pair per thread: 16 warps own the tile's
+//     rows and compute both steps of their pair, 6 warps the 168 halo pairs
+//     (step A only).  The thread that computes step B of a pair computed its
+//     step A as well, so d^{n+1}, e^{n+1}, kap and the level-(n+1) z-column
+//     of its pair stay in registers; p^n's z-column too (one new value per
+//     plane).  Only the x/y neighbours come from shared memory: six 64-bit
+//     loads per step, plus three for d, e, kap in step A;
+//   * level n + 1 goes through a 4-deep shared ring; a plane written in
+//     iteration i is read by step B in iteration i + 2, after the
+//     iteration-done barrier of iteration i, which every compute thread has
+//     long passed by then (split arrive / wait, no block-wide barrier);
+//   * the z-loop is unrolled by the ring depth, so every ring slot and
+//     barrier index is a compile-time constant.
+// Every wait is bounded (about a second of clock64 time) and gives up early
+// once another thread of the CTA has recorded a timeout; the producer then
+// waits a bounded time for its copies in flight, and the CTA returns after
+// recording FFPAT_ETIMEDOUT in the device status word.
 namespace tb2 {
-constexpr int TH2 = 16;                // output tile 64 x 16
-constexpr int PW = 72, PH = TH2 + 8;   // p^n box (x0-4 .., y0-4 ..)
-constexpr int QW = 72, QH = TH2 + 4;   // d, e, kap, and level-(n+1) p boxes (x0-4 .., y0-2 ..)
-constexpr int PB = PW * PH * 4, QB = QW * QH * 4, TB = TBX * TH2 * 4;
-// Rings.  One block barrier per plane (after step A): a ring slot may be
-// refilled or rewritten only when its last reader ran before the latest
-// barrier, which sets the depths.
-constexpr int RP = 7;   // p^n planes zA-2 .. zA+4 (plane zA+5 is loaded into zA-2's slot)
-constexpr int RK = 6;   // kap planes zA-5 .. zA (zA+3 is loaded into zA-3's slot)
-constexpr int RD = 3;   // d^n, e^n planes zA .. zA+2
-constexpr int RA = 6;   // level-(n+1) p planes zA-5 .. zA
-constexpr int RAD = 4;  // level-(n+1) d, e tile planes zA-3 .. zA
-constexpr int NTY2 = 22;  // 22 warps: step A's 34 x 20 point pairs take one round
-constexpr int NT2 = NTX * NTY2;
-constexpr size_t kSmem = (size_t)RP * PB + (size_t)RK * QB + (size_t)RD * 2 * QB +
-                         (size_t)RA * QB + (size_t)RAD * 2 * TB + RP * 8;
-__host__ __device__ constexpr int slot(int z, int m) { return (z + 64 * m) % m; }
+constexpr int TH2 = 16;                  // output tile 64 x 16
+constexpr int PW = 72, PH = TH2 + 8;     // p^n box (x0-4 .., y0-4 ..)
+constexpr int QW = 72, QH = TH2 + 4;     // d, e, kap boxes (x0-4 .., y0-2 ..)
+constexpr int AW = 68, AH = TH2 + 4;     // level-(n+1) planes on the extended tile (x0-2 .., y0-2 ..)
+constexpr int PB = PW * PH * 4, QB = QW * QH * 4, AB = AW * AH * 4;
+constexpr int RING = 8;                  // rounds in flight: p^n, d, e, kap planes
+constexpr int RA = 4;                    // level-(n+1) planes
+constexpr int NIN = TH2;                 // compute warps owning one tile row each
+constexpr int NCW = NIN + 6;             // + the halo warps
+constexpr int NHALO = 2 * 34 * 2 + 2 * TH2;  // 168 halo pairs of the 34 x 20 pair grid
+constexpr int NCT = NCW * 32;            // compute threads (arrivals per iteration)
+constexpr int NT2 = NCT + 32;            // + the producer warp
+constexpr size_t kBarOff = (size_t)RING * PB + (size_t)RING * 3 * QB + (size_t)RA * AB;
+constexpr size_t kSmem = kBarOff + 2 * RING * 8 + 16;
+static_assert(PB % 128 == 0 && QB % 128 == 0, "TMA destinations stay 128-byte aligned");
+static_assert(NCW * 32 - NIN * 32 >= NHALO, "halo warps cover the halo pairs");
 }  // namespace tb2
 
 struct Maps2 {
@@ -577,24 +600,30 @@ struct Maps2 {
   CUtensorMap k;  // kap, 72 x 20
 };
 
-__device__ __forceinline__ void tb2_issue(const Maps2& m, unsigned char* sm, uint64_t* bar, int R,
-                                          int z0, int z1, int x0, int y0) {
-  using namespace tb2;
-  const bool wp = R >= z0 - 4 && R <= z1 + 3;
-  const bool wq = R - 2 >= z0 - 2 && R - 2 <= z1 + 1;
-  if (!wp && !wq) return;
-  uint64_t* b = &bar[slot(R, RP)];
-  mbar_expect_tx(b, (wp ? PB : 0) + (wq ? 3 * QB : 0));
-  float* P = reinterpret_cast<float*>(sm);
-  float* K = reinterpret_cast<float*>(sm + RP * PB);
-  float* D = reinterpret_cast<float*>(sm + RP * PB + RK * QB);
-  if (wp) tma_load_3d(P + slot(R, RP) * (PB / 4), &m.p, x0 - 4, y0 - 4, R, b);
-  if (wq) {
-    const int z = R - 2;
-    tma_load_3d(K + slot(z, RK) * (QB / 4), &m.k, x0 - 4, y0 - 2, z, b);
-    tma_load_3d(D + slot(z, RD) * 2 * (QB / 4), &m.d, x0 - 4, y0 - 2, z, b);
-    tma_load_3d(D + (slot(z, RD) * 2 + 1) * (QB / 4), &m.e, x0 - 4, y0 - 2, z, b);
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up once another thread of the CTA recorded a
+// failure in *abort.
+__device__ __forceinline__ bool tb2_wait(uint64_t* bar, unsigned parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) return false;
   }
+}
+
+__device__ __forceinline__ void tb2_fail(volatile int* abort) {
+  *abort = 1;
+  atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
 }
 
 __global__ void __launch_bounds__(tb2::NT2, 1)
@@ -604,117 +633,206 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
   using namespace tb2;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const float* P = reinterpret_cast<const float*>(sm);
-  const float* K = reinterpret_cast<const float*>(sm + RP * PB);
-  const float* D = reinterpret_cast<const float*>(sm + RP * PB + RK * QB);
-  float* A = reinterpret_cast<float*>(sm + RP * PB + RK * QB + RD * 2 * QB);
-  float* AD = reinterpret_cast<float*>(sm + RP * PB + RK * QB + RD * 2 * QB + RA * QB);
-  uint64_t* bar =
-      reinterpret_cast<uint64_t*>(sm + RP * PB + RK * QB + RD * 2 * QB + RA * QB + RAD * 2 * TB);
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * NTX + tx;
+  float* P = reinterpret_cast<float*>(sm);
+  float* Q = reinterpret_cast<float*>(sm + RING * PB);
+  float* A = reinterpret_cast<float*>(sm + RING * PB + RING * 3 * QB);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kBarOff);  // round landed
+  uint64_t* done = full + RING;                                 // iteration finished
+  volatile int* abort = reinterpret_cast<volatile int*>(done + RING);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int i = 0; i < RP; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < RING; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&done[i], NCT);
+    }
+    *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   grid_dependency_sync();
   if (*(volatile unsigned*)&g_tma_status != 0u) return;
   __syncthreads();
-  unsigned phase = 0;
-  const size_t plane = (size_t)n * n;
+
+  // this thread's point pair on the 34 x 20 pair grid of the extended tile
+  const bool inner = warp < NIN;
+  int qx = 0, qy = 0;
+  bool active = inner;
+  if (inner) {
+    qx = lane + 1;
+    qy = warp + 2;
+  } else if (warp < NCW) {
+    const int t = (warp - NIN) * 32 + lane;
+    active = t < NHALO;
+    if (t < 136) {  // the two rows above and the two below the tile
+      const int row = t / 34;
+      qx = t - 34 * row;
+      qy = row < 2 ? row : row + TH2;
+    } else if (t < 136 + TH2) {  // the pair left of each tile row
+      qy = 2 + (t - 136);
+    } else if (t < NHALO) {  // and the pair right of it
+      qx = 33;
+      qy = 2 + (t - 136 - TH2);
+    }
+  }
+  const int o = (qy + 2) * PW + 2 * qx + 2;  // in the p^n box
+  const int qo = qy * QW + 2 * qx + 2;       // in the d, e, kap boxes
+  const int ao = qy * AW + 2 * qx;           // in the level-(n+1) planes
+  const unsigned plane = (unsigned)n * (unsigned)n;
+
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int tix = item % tiles_x;
     const int tiy = (item / tiles_x) % tiles_y;
     const int z0 = (item / (tiles_x * tiles_y)) * zc;
     const int z1 = min(n, z0 + zc);
     const int x0 = tix * TBX, y0 = tiy * TH2;
-    if (tid == 0)
-      for (int R = z0 - 4; R < z0 - 4 + RP; ++R) tb2_issue(maps, sm, bar, R, z0, z1, x0, y0);
-    bool timed_out = false;
-    int waited_upto = z0 - 5;
-    for (int zA = z0 - 2; zA <= z1 + 1; ++zA) {
-      for (int R = waited_upto + 1; R <= zA + 2; ++R) {
-        const int b = slot(R, RP);
-        if (!mbar_wait(&bar[b], (phase >> b) & 1u, kWaitCycles)) timed_out = true;
-        phase ^= 1u << b;
-      }
-      waited_upto = zA + 2;
-      // ---- step A: level n+1 at plane zA on the 68 x 20 extended tile
-      {
-        const float* P0 = P + slot(zA, RP) * (PB / 4);
-        const float* Pm1 = P + slot(zA - 1, RP) * (PB / 4);
-        const float* Pp1 = P + slot(zA + 1, RP) * (PB / 4);
-        const float* Pm2 = P + slot(zA - 2, RP) * (PB / 4);
-        const float* Pp2 = P + slot(zA + 2, RP) * (PB / 4);
-        const float* Kz = K + slot(zA, RK) * (QB / 4);
-        const float* Dz = D + slot(zA, RD) * 2 * (QB / 4);
-        const float* Ez = Dz + QB / 4;
-        float* Az = A + slot(zA, RA) * (QB / 4);
-        float* ADz = AD + slot(zA, RAD) * 2 * (TB / 4);
-        for (int q = tid; q < 34 * QH; q += NT2) {
-          const int qy = q / 34, qx = 2 + 2 * (q % 34);
-          const int po_ = (qy + 2) * PW + qx;  // same x origin, two more rows of halo
-          const int qo = qy * QW + qx;
-          Nb2 v;
-          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, v);
-          const float2 L = lap12_pair(v);
-          const float2 Kv = lds2(Kz + qo), Dv = lds2(Dz + qo), Ev = lds2(Ez + qo);
-          const Kp2 r = kahan_pair(v.c, Kv, L, Dv, Ev, false);
-          *reinterpret_cast<float2*>(Az + qo) = r.p;
-          if (qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TH2) {
-            const int to = (qy - 2) * TBX + (qx - 4);
-            *reinterpret_cast<float2*>(ADz + to) = r.d;
-            *reinterpret_cast<float2*>(ADz + TB / 4 + to) = r.e;
+    // iteration i computes step A at plane z0 - 2 + i and step B at z0 - 4 + i;
+    // round r brings plane z0 - 4 + r of p^n (for r <= M + 3) and of d, e, kap
+    // (for 2 <= r <= M + 1)
+    const int M = z1 - z0 + 4;
+    bool ok = true;
+    if (warp == NCW) {
+      // ---- producer
+      if (lane == 0) {
+        int issued = 0;
+        for (int r = 0; r < M + 4; ++r) {
+          if (r >= RING) {
+            // slot r mod 8 was last read in iteration r - 10 (iteration 0
+            // follows every thread's read of the first planes)
+            const int it = r - 10 > 0 ? r - 10 : 0;
+            if (!tb2_wait(&done[it & (RING - 1)], (unsigned)(it >> 3) & 1u, abort)) {
+              ok = false;
+              break;
+            }
           }
+          const int s = r & (RING - 1), z = z0 - 4 + r;
+          const bool wq = r >= 2 && r <= M + 1;
+          uint64_t* b = &full[s];
+          mbar_expect_tx(b, PB + (wq ? 3 * QB : 0));
+          tma_load_3d(P + s * (PB / 4), &maps.p, x0 - 4, y0 - 4, z, b);
+          if (wq) {
+            float* q = Q + 3 * s * (QB / 4);
+            tma_load_3d(q, &maps.d, x0 - 4, y0 - 2, z, b);
+            tma_load_3d(q + QB / 4, &maps.e, x0 - 4, y0 - 2, z, b);
+            tma_load_3d(q + 2 * (QB / 4), &maps.k, x0 - 4, y0 - 2, z, b);
+          }
+          issued = r + 1;
+        }
+        if (!ok) {
+          tb2_fail(abort);
+          // bounded wait for the copies still in flight
+          for (int r = issued - RING > 0 ? issued - RING : 0; r < issued; ++r)
+            mbar_wait(&full[r & (RING - 1)], (unsigned)(r >> 3) & 1u, 1 << 24);
         }
       }
-      // the plane's only block barrier, also the vote on a timed-out wait
-      if (__syncthreads_or(timed_out)) {
-        if (tid == 0) {
-          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
-          for (int R = waited_upto + 1; R <= min(z1 + 3, zA + RP - 3); ++R) {
-            const int b = slot(R, RP);
-            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
-            phase ^= 1u << b;
+      __syncwarp();
+    } else {
+      // ---- compute warps
+      for (int r = 0; r < 4 && ok; ++r) ok = tb2_wait(&full[r], 0u, abort);
+      if (!ok) tb2_fail(abort);
+      // z-columns of the pair: p^n at z - 2 .. z + 1 of the step-A plane z,
+      // level n + 1 at zB - 2 .. zB + 1 of the step-B plane zB, and the
+      // point's d^{n+1}, e^{n+1}, kap of the last two step-A planes
+      float2 c0 = lds2(P + 0 * (PB / 4) + o), c1 = lds2(P + 1 * (PB / 4) + o);
+      float2 c2 = lds2(P + 2 * (PB / 4) + o), c3 = lds2(P + 3 * (PB / 4) + o);
+      const float2 zero = make_float2(0.f, 0.f);
+      float2 a0 = zero, a1 = zero, a2 = zero, a3 = zero;
+      float2 dq0 = zero, dq1 = zero, eq0 = zero, eq1 = zero, kq0 = zero, kq1 = zero;
+      const int x = x0 + 2 * lane, y = y0 + warp;
+      const bool store = inner && x < n && y < n;  // N % 4 == 0: x + 1 < n as well
+      unsigned gi = (unsigned)z0 * plane + (unsigned)y * (unsigned)n + (unsigned)x;
+      for (int ib = 0; ib < M; ib += RING) {
+#pragma unroll
+        for (int u = 0; u < RING; ++u) {
+          const int i = ib + u;
+          if (i < M) {
+            // round i + 4 brings p^n at z + 2 (the column's new value)
+            if (ok && !(ok = tb2_wait(&full[(u + 4) & 7], (unsigned)((i + 4) >> 3) & 1u, abort)))
+              tb2_fail(abort);
+            // ---- step A: level n + 1 at plane z = z0 - 2 + i
+            const float* P0 = P + ((u + 2) & 7) * (PB / 4);
+            const float* Qz = Q + 3 * ((u + 2) & 7) * (QB / 4);
+            const float2 c4 = lds2(P + ((u + 4) & 7) * (PB / 4) + o);
+            Nb2 v;
+            const float2 XM = lds2(P0 + o - 2), XP = lds2(P0 + o + 2);
+            v.c = c2;
+            v.xm1 = make_float2(XM.y, c2.x);
+            v.xp1 = make_float2(c2.y, XP.x);
+            v.xm2 = XM;
+            v.xp2 = XP;
+            v.ym1 = lds2(P0 + o - PW);
+            v.yp1 = lds2(P0 + o + PW);
+            v.ym2 = lds2(P0 + o - 2 * PW);
+            v.yp2 = lds2(P0 + o + 2 * PW);
+            v.zm1 = c1;
+            v.zp1 = c3;
+            v.zm2 = c0;
+            v.zp2 = c4;
+            const float2 L = lap12_pair(v);
+            const float2 Kv = lds2(Qz + 2 * (QB / 4) + qo);
+            const Kp2 ra = kahan_pair(c2, Kv, L, lds2(Qz + qo), lds2(Qz + QB / 4 + qo), false);
+            // the level-(n+1) slot of this plane was last read by step B of
+            // iteration i - 2, and step B below reads the plane iteration
+            // i - 2 wrote: both wait for iteration i - 2 to be done everywhere
+            if (i >= 2 && ok &&
+                !(ok = tb2_wait(&done[(u + 6) & 7], (unsigned)((i - 2) >> 3) & 1u, abort)))
+              tb2_fail(abort);
+            if (active) *reinterpret_cast<float2*>(A + (u & 3) * (AB / 4) + ao) = ra.p;
+            // ---- step B: level n + 2 at plane zB = z - 2 (tile rows only)
+            if (inner && i >= 4) {
+              const float* A0 = A + ((u + 2) & 3) * (AB / 4);
+              Nb2 w;
+              const float2 YM = lds2(A0 + ao - 2), YP = lds2(A0 + ao + 2);
+              w.c = a2;
+              w.xm1 = make_float2(YM.y, a2.x);
+              w.xp1 = make_float2(a2.y, YP.x);
+              w.xm2 = YM;
+              w.xp2 = YP;
+              w.ym1 = lds2(A0 + ao - AW);
+              w.yp1 = lds2(A0 + ao + AW);
+              w.ym2 = lds2(A0 + ao - 2 * AW);
+              w.yp2 = lds2(A0 + ao + 2 * AW);
+              w.zm1 = a1;
+              w.zp1 = a3;
+              w.zm2 = a0;
+              w.zp2 = ra.p;
+              const float2 LB = lap12_pair(w);
+              const Kp2 rb = kahan_pair(a2, kq0, LB, dq0, eq0, false);
+              if (store) {
+                *reinterpret_cast<float2*>(po + gi) = rb.p;
+                *reinterpret_cast<float2*>(dout + gi) = rb.d;
+                *reinterpret_cast<float2*>(eout + gi) = rb.e;
+              }
+              gi += plane;
+            }
+            c0 = c1;
+            c1 = c2;
+            c2 = c3;
+            c3 = c4;
+            a0 = a1;
+            a1 = a2;
+            a2 = a3;
+            a3 = ra.p;
+            dq0 = dq1;
+            dq1 = ra.d;
+            eq0 = eq1;
+            eq1 = ra.e;
+            kq0 = kq1;
+            kq1 = Kv;
+            mbar_arrive(&done[u]);
           }
-        }
-        return;
-      }
-      // refill: p plane zA+5 into zA-2's slot (last read by step A above),
-      // kap zA+3 into zA-3's (last read by step B of the previous plane),
-      // d, e zA+3 into zA's (last read by step A above)
-      if (tid == 0) tb2_issue(maps, sm, bar, zA + RP - 2, z0, z1, x0, y0);
-      // ---- step B: level n+2 at plane zB = zA - 2 on the tile.  It reads
-      // level-(n+1) planes zA-4 .. zA and tiles zA-2; step A of plane zA+1
-      // writes zA+1's slots, last read by step B of plane zA-1 (before the
-      // barrier above)
-      const int zB = zA - 2;
-      if (zB >= z0 && ty < TH2) {
-        const float* A0 = A + slot(zB, RA) * (QB / 4);
-        const float* Am1 = A + slot(zB - 1, RA) * (QB / 4);
-        const float* Ap1 = A + slot(zB + 1, RA) * (QB / 4);
-        const float* Am2 = A + slot(zB - 2, RA) * (QB / 4);
-        const float* Ap2 = A + slot(zB + 2, RA) * (QB / 4);
-        const float* Kz = K + slot(zB, RK) * (QB / 4);
-        const float* ADz = AD + slot(zB, RAD) * 2 * (TB / 4);
-        const int xl = 2 * tx;
-        const int x = x0 + xl, y = y0 + ty;
-        const int qo = (ty + 2) * QW + xl + 4;
-        const int to = ty * TBX + xl;
-        Nb2 v;
-        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, v);
-        const float2 L = lap12_pair(v);
-        const float2 Kv = lds2(Kz + qo), Dv = lds2(ADz + to), Ev = lds2(ADz + TB / 4 + to);
-        if (x < n && y < n) {
-          const Kp2 r = kahan_pair(v.c, Kv, L, Dv, Ev, false);
-          const size_t gi = (size_t)zB * plane + (size_t)y * n + x;
-          *reinterpret_cast<float2*>(po + gi) = r.p;
-          *reinterpret_cast<float2*>(dout + gi) = r.d;
-          *reinterpret_cast<float2*>(eout + gi) = r.e;
         }
       }
     }
-    // the next work item refills every ring from its first plane on
+    // every round issued was waited for by the compute warps: the rings are idle
+    if (__syncthreads_or(!ok)) return;
+    if (tid == 0) {
+      for (int i = 0; i < RING; ++i) {
+        mbar_inval(&full[i]);
+        mbar_inval(&done[i]);
+        mbar_init(&full[i], 1);
+        mbar_init(&done[i], NCT);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
   }
 }
@@ -1423,7 +1541,7 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
   const int zchunks = (n + zc - 1) / zc;
   const int nitems = tiles_x * tiles_y * zchunks;
   const int grid = nitems < slots ? nitems : slots;
-  const cudaError_t le = launch_pdl(k_step2_kahan, dim3(grid), dim3(NTX, tb2::NTY2), smem, st, maps,
+  const cudaError_t le = launch_pdl(k_step2_kahan, dim3(grid), dim3(tb2::NT2), smem, st, maps,
                                     (float*)po, (float*)dout, (float*)eout, n, zc, tiles_x,
                                     tiles_y, nitems);
   count_launch();
