@@ -36,7 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # the dominant leapfrog kernel, taken from one ncu capture of that kernel on
 # the same grid, keyed by (workload, precision, kernel).  An entry is dropped
 # whenever its kernel changes, until it has been captured again.
-NCU_TRAFFIC = {("cfg2", "fp32-kahan", "resident"): 17.167104e6}
+NCU_TRAFFIC = {("cfg2", "fp32-kahan", "resident"): 17.167104e6,
+               ("cfg5", "fp32-kahan", "two-step"): 1541.44256e6}
 
 # algorithmic FP32 operations per point-step of the difference-form update:
 # 12 subtractions, 10 additions and one FMA (2) for 12 h^2 L4 p, then the
@@ -635,7 +636,7 @@ def run_op(args):
     n = args.n
     cmax = 1.4
     T = args.op_steps * 0.3 * (2.0 / n) / cmax * (1 - 1e-9)
-    prob = F.problem(n, T, args.angles, prec, precond=1 if args.op == "ramp" else 0)
+    prob = F.problem(n, T, args.angles, prec, precond=1 if (args.op == "ramp" or args.ramp) else 0)
     nt, _, _ = F.problem_info(prob, cmax)
     dt = F.torch_dtype(prob)
     gen = torch.Generator(device="cuda").manual_seed(args.seed)
@@ -952,6 +953,7 @@ def main():
     ap.add_argument("--op-steps", type=int, default=16, help="op: leapfrog steps of W")
     ap.add_argument("--repeat", type=int, default=3, help="op: timed repetitions")
     ap.add_argument("--seed", type=int, default=0, help="op: random seed")
+    ap.add_argument("--ramp", action="store_true", help="op: ramp preconditioner (Lambda)")
     ap.add_argument("--path", type=int, default=0,
                     help="op: leapfrog kernel: 0 auto, 1 plain, 2 TMA, 3 two-step, 4 resident")
     args = ap.parse_args()

@@ -239,11 +239,12 @@ int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_
   return FFPAT_OK;
 }
 
-// FP32-Kahan runs two steps per pass from this N on, single steps below:
-// measured on GB300, 82 against 92 us per step at 256^3 and 261 against 222 at
-// 384^3 (smaller grids give the two-step kernel, one large CTA per SM, too few
-// work items)
-constexpr int kTwoStepMinN = 320;
+// FP32 and FP32-Kahan run two steps per pass (where the resident time loop
+// does not run): measured on GB300 the two-step passes win at every size from
+// 128^3 to 384^3 (FP32-Kahan 15.5 / 47.5 / 133 against 18.1 / 82.5 / 262 us per
+// step at 160^3 / 256^3 / 384^3; FP32 three-term 14.0 / 42.3 / 118 against
+// 15.4 / 46.9 / 135), and tie at 144^3, whose 64-wide tiles are a third empty
+constexpr int kTwoStepMinN = 128;
 
 // algorithmic HBM bytes per point of a two-step pass beyond a single step's:
 // FP32-Kahan moves its 28 B once for both steps, FP32 20 B against 16 B
@@ -316,12 +317,11 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
       ++launches;
     }
     if (result) *result = cur;
-  } else if (pl.prec == FFPAT_FP32 && tma && nt >= 3 && path == 3) {
-    // FP32 three-term, two steps per pass, on request only: the single-step
-    // kernel already runs at 0.98 of the HBM copy bandwidth at 384^3 (136 us
-    // per step) and the two-step pass, bound by its 2.3 stencils per point,
-    // takes 187 us per step (measured on GB300).  The pairs (S0, S1) and
-    // (S2, S3) alternate as (p^{n-1}, p^n) inputs and (p^{n+1}, p^{n+2}) outputs
+  } else if (pl.prec == FFPAT_FP32 && tma && nt >= 3 &&
+             (path == 3 || (path == 0 && pl.n >= kTwoStepMinN))) {
+    // FP32 three-term, two steps per pass (kTwoStepMinN): 20 B per point per
+    // two steps against 32 B.  The pairs (S0, S1) and (S2, S3) alternate as
+    // (p^{n-1}, p^n) inputs and (p^{n+1}, p^{n+2}) outputs
     void* S[4] = {pl.s[0], pl.s[1], pl.s[2], pl.s[3]};
     TRY(step3(pl, tma, true, in, nullptr, S[1], S[0], st));  // S1 = p^1, S0 = p^0
     ++launches;

@@ -241,6 +241,13 @@ dim3 step_grid(int n, int* zc) {
 
 int launch_lap_accum(const Plan& pl, void* acc, const void* u, const void* p, double w,
                      cudaStream_t st) {
+  // FP32 on TMA-aligned arrays: the single-step TMA kernel's accumulation form
+  // (p through its plane ring with the halo, mu and acc as halo-free tiles)
+  const void* ptrs[3] = {acc, u, p};
+  if (pl.prec != FFPAT_FP64 && (w == 1.0 || w == 0.5) && tma_supported(pl, ptrs, 3)) {
+    const void* q[2] = {u, acc};
+    return launch_step_tma(pl, 2, w == 0.5, p, q, acc, nullptr, nullptr, st);
+  }
   int zc;
   const dim3 grid = step_grid(pl.n, &zc);
   const dim3 block(BX, BY);

@@ -22,8 +22,9 @@
 // bounded time for its own copies in flight, and returns.
 //
 // Also here: the batched step of the server (k_step_batch), two steps per
-// pass (k_step2_kahan, k_step2_f32), and, for grids whose work items all fit
-// the GPU at once (N <= 128), the whole time loop in one cooperative launch
+// pass (k_step2_kahan, k_step2_f32: one kernel body for both forms), and, for
+// grids whose work items all fit the GPU at once (N <= 128), the whole time
+// loop in one cooperative launch
 // (k_wave_resident: per-point state on chip, p^n through L2, neighbour step
 // flags between steps).  All FP32 kernels share the packed two-lane pair
 // arithmetic below, so they agree bit for bit.
@@ -120,10 +121,12 @@ struct Maps {
 };
 
 // FORM 0: three-term (q = {p^{n-1}, kap} or, at START, {kap});
-// FORM 1: increment with Kahan carry (q = {d, e, kap} or, at START, {kap}).
+// FORM 1: increment with Kahan carry (q = {d, e, kap} or, at START, {kap});
+// FORM 2: the kappa-derivative accumulation of the differentiated operator,
+//         acc += w mu L(p) with w = 1/2 at START, else 1 (q = {mu, acc}; FP32).
 template <typename T, int FORM, bool START>
 struct Streams {
-  static constexpr int NQ = START ? 1 : (FORM == 0 ? 2 : 3);
+  static constexpr int NQ = FORM == 2 ? 2 : (START ? 1 : (FORM == 0 ? 2 : 3));
 };
 
 __device__ __forceinline__ double lap12_sum(const double* P0, const double* Pm1, const double* Pp1,
@@ -344,6 +347,15 @@ __global__ void __launch_bounds__(NTX* NTY, 2)
           Nb2 v;
           gather_pair(P0, Pm1, Pp1, Pm2, Pp2, o, G::BXH, v);
           const float2 L = lap12_pair(v);
+          if constexpr (FORM == 2) {
+            // acc + (w mu) L, one rounding of w mu and one fused multiply-add
+            const float w = START ? 0.5f : 1.0f;
+            const float2 wu = mul2(make_float2(w, w), lds2(Q + qo));
+            if (x < n && y < n)
+              *reinterpret_cast<float2*>(o0 + (size_t)z * plane + (size_t)y * n + x) =
+                  fma2(wu, L, lds2(Q + QS + qo));
+            continue;
+          }
           const float2 K = lds2(Q + (NQ - 1) * QS + qo);
           if (x < n && y < n) {  // N is even, so x + 1 < n as well
             const size_t gi = (size_t)z * plane + (size_t)y * n + x;
@@ -538,32 +550,37 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
   }
 }
 
-// ------------------------------------- two FP32-Kahan steps per pass ----
-// Temporal blocking: one launch advances (p, d, e) from level n to n + 2.
-// Step A recomputes level n + 1 on the 64 x 16 tile plus a two-point x/y halo
-// (the 68 x 20 extended tile) from a halo-4 box of p^n (72 x 24, starting
-// 16-byte aligned at x0 - 4) and halo-2 boxes of d^n, e^n, kap (72 x 20);
+// ------------------------------------------------ two steps per pass ----
+// Temporal blocking: one launch advances the leapfrog by two steps.  Step A
+// recomputes level n + 1 on the 64 x 16 tile plus a two-point x/y halo (the
+// 68 x 20 extended tile) from a halo-4 box of p^n (72 x 24, starting 16-byte
+// aligned at x0 - 4) and halo-2 boxes (72 x 20) of the per-point streams;
 // step B then forms level n + 2 on the tile from the level-(n+1) planes.
+//   * FP32-Kahan (k_step2_kahan): the streams are d^n, e^n, kap; the pass
+//     writes p, d, e of level n + 2: 28 B per point per TWO steps (d and e are
+//     read with a halo, so they are double-buffered, no in place);
+//   * FP32 three-term (k_step2_f32): the streams are p^{n-1}, kap; the pass
+//     writes p^{n+1} (step A, tile points) and p^{n+2} (step B): 20 B per point
+//     per two steps, against 32 B for two single steps.
 // Each point's arithmetic is that of the single-step kernel (same Laplacian
-// order, same Kahan update), so two passes of this kernel give bit-identical
-// results to four single steps.  HBM traffic is 28 B per point per TWO steps;
-// d and e are read with a halo, so they are double-buffered (no in place).
-// Points outside the grid read kap = d = e = p = 0 and therefore produce
-// p^{n+1} = 0 there: the zero ghost values of step B come out of step A.
+// order, same update), so results are bit-identical to single steps.  Points
+// outside the grid read kap = 0 and zero state and therefore produce level
+// n + 1 = 0 there: the zero ghost values of step B come out of step A.
 //
 // Organisation (one CTA per SM walks whole z-columns of its tile):
-//   * a producer warp issues the TMA copies, one round per plane z: p^n, d^n,
-//     e^n and kap of that plane into slot z mod 8 of an 8-deep ring; it
-//     refills a slot once every compute thread has reported the iteration
-//     that last read it (iteration-done mbarriers), so copies run up to about
-//     five planes ahead of the planes being computed;
+//   * a producer warp issues the TMA copies, one round per plane z: p^n and
+//     the stream planes of z into slot z mod 8 of an 8-deep ring; it refills
+//     a slot once every compute thread has reported the iteration that last
+//     read it (iteration-done mbarriers), so copies run up to about five
+//     planes ahead of the planes being computed;
 //   * 22 compute warps, one point pair per thread: 16 warps own the tile's
 //     rows and compute both steps of their pair, 6 warps the 168 halo pairs
 //     (step A only).  The thread that computes step B of a pair computed its
-//     step A as well, so d^{n+1}, e^{n+1}, kap and the level-(n+1) z-column
-//     of its pair stay in registers; p^n's z-column too (one new value per
-//     plane).  Only the x/y neighbours come from shared memory: six 64-bit
-//     loads per step, plus three for d, e, kap in step A;
+//     step A as well, so the pair's level-(n+1) z-column and the point values
+//     step B needs (d^{n+1}, e^{n+1} or p^n; kap) stay in registers; p^n's
+//     z-column too (one new value per plane).  Only the x/y neighbours come
+//     from shared memory: six 64-bit loads per step, plus the streams in
+//     step A;
 //   * level n + 1 goes through a 4-deep shared ring; a plane written in
 //     iteration i is read by step B in iteration i + 2, after the
 //     iteration-done barrier of iteration i, which every compute thread has
@@ -577,27 +594,34 @@ __global__ void __launch_bounds__(NTX* NTY, 2) k_step_batch(const __grid_constan
 namespace tb2 {
 constexpr int TH2 = 16;                  // output tile 64 x 16
 constexpr int PW = 72, PH = TH2 + 8;     // p^n box (x0-4 .., y0-4 ..)
-constexpr int QW = 72, QH = TH2 + 4;     // d, e, kap boxes (x0-4 .., y0-2 ..)
+constexpr int QW = 72, QH = TH2 + 4;     // stream boxes (x0-4 .., y0-2 ..)
 constexpr int AW = 68, AH = TH2 + 4;     // level-(n+1) planes on the extended tile (x0-2 .., y0-2 ..)
 constexpr int PB = PW * PH * 4, QB = QW * QH * 4, AB = AW * AH * 4;
-constexpr int RING = 8;                  // rounds in flight: p^n, d, e, kap planes
+constexpr int RING = 8;                  // rounds in flight: p^n and stream planes
 constexpr int RA = 4;                    // level-(n+1) planes
 constexpr int NIN = TH2;                 // compute warps owning one tile row each
 constexpr int NCW = NIN + 6;             // + the halo warps
 constexpr int NHALO = 2 * 34 * 2 + 2 * TH2;  // 168 halo pairs of the 34 x 20 pair grid
 constexpr int NCT = NCW * 32;            // compute threads (arrivals per iteration)
 constexpr int NT2 = NCT + 32;            // + the producer warp
-constexpr size_t kBarOff = (size_t)RING * PB + (size_t)RING * 3 * QB + (size_t)RA * AB;
-constexpr size_t kSmem = kBarOff + 2 * RING * 8 + 16;
+// streams per plane: d, e, kap (FP32-Kahan) or p^{n-1}, kap (three-term)
+template <int FORM>
+constexpr int NQ = FORM == 1 ? 3 : 2;
+template <int FORM>
+constexpr size_t bar_off() {
+  return (size_t)RING * PB + (size_t)RING * NQ<FORM> * QB + (size_t)RA * AB;
+}
+template <int FORM>
+constexpr size_t smem_bytes() {
+  return bar_off<FORM>() + 2 * RING * 8 + 16;
+}
 static_assert(PB % 128 == 0 && QB % 128 == 0, "TMA destinations stay 128-byte aligned");
 static_assert(NCW * 32 - NIN * 32 >= NHALO, "halo warps cover the halo pairs");
 }  // namespace tb2
 
 struct Maps2 {
-  CUtensorMap p;  // p^n, 72 x 24 box
-  CUtensorMap d;  // d^n, 72 x 20
-  CUtensorMap e;  // e^n, 72 x 20
-  CUtensorMap k;  // kap, 72 x 20
+  CUtensorMap p;     // p^n, 72 x 24 box
+  CUtensorMap q[3];  // the streams, 72 x 20 boxes (kap last)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -608,14 +632,29 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// try_wait with a suspend-time hint: a thread whose phase has not completed
+// is suspended (it takes no issue slots) until the phase completes or about
+// `ns` nanoseconds have passed
+__device__ __forceinline__ bool mbar_try_wait_ns(uint64_t* bar, unsigned parity, unsigned ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait that also gives up once another thread of the CTA recorded a
-// failure in *abort.
+// failure in *abort.  Waiting threads sleep in the barrier instead of
+// spinning, so the warps that have work keep the issue slots.
 __device__ __forceinline__ bool tb2_wait(uint64_t* bar, unsigned parity, volatile int* abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    for (int i = 0; i < 32; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
+    for (int i = 0; i < 8; ++i)
+      if (mbar_try_wait_ns(bar, parity, 20000u)) return true;
     if (*abort) return false;
     if (clock64() - t0 > kWaitCycles) return false;
   }
@@ -626,18 +665,21 @@ __device__ __forceinline__ void tb2_fail(volatile int* abort) {
   atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
 }
 
-__global__ void __launch_bounds__(tb2::NT2, 1)
-    k_step2_kahan(const __grid_constant__ Maps2 maps, float* __restrict__ po,
-                  float* __restrict__ dout, float* __restrict__ eout, int n, int zc, int tiles_x,
-                  int tiles_y, int nitems) {
+// FORM 1: FP32-Kahan, o0/o1/o2 = p, d, e of level n + 2.
+// FORM 0: three-term, o0 = p^{n+1}, o1 = p^{n+2} (o2 unused).
+template <int FORM>
+__device__ __forceinline__ void step2_body(const Maps2& maps, float* __restrict__ o0,
+                                           float* __restrict__ o1, float* __restrict__ o2, int n,
+                                           int zc, int tiles_x, int tiles_y, int nitems) {
   using namespace tb2;
+  constexpr int NQF = NQ<FORM>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* P = reinterpret_cast<float*>(sm);
   float* Q = reinterpret_cast<float*>(sm + RING * PB);
-  float* A = reinterpret_cast<float*>(sm + RING * PB + RING * 3 * QB);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kBarOff);  // round landed
-  uint64_t* done = full + RING;                                 // iteration finished
+  float* A = reinterpret_cast<float*>(sm + RING * PB + RING * NQF * QB);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + bar_off<FORM>());  // round landed
+  uint64_t* done = full + RING;                                         // iteration finished
   volatile int* abort = reinterpret_cast<volatile int*>(done + RING);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -674,7 +716,7 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
     }
   }
   const int o = (qy + 2) * PW + 2 * qx + 2;  // in the p^n box
-  const int qo = qy * QW + 2 * qx + 2;       // in the d, e, kap boxes
+  const int qo = qy * QW + 2 * qx + 2;       // in the stream boxes
   const int ao = qy * AW + 2 * qx;           // in the level-(n+1) planes
   const unsigned plane = (unsigned)n * (unsigned)n;
 
@@ -685,8 +727,8 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
     const int z1 = min(n, z0 + zc);
     const int x0 = tix * TBX, y0 = tiy * TH2;
     // iteration i computes step A at plane z0 - 2 + i and step B at z0 - 4 + i;
-    // round r brings plane z0 - 4 + r of p^n (for r <= M + 3) and of d, e, kap
-    // (for 2 <= r <= M + 1)
+    // round r brings plane z0 - 4 + r of p^n (for r <= M + 3) and of the
+    // streams (for 2 <= r <= M + 1)
     const int M = z1 - z0 + 4;
     bool ok = true;
     if (warp == NCW) {
@@ -706,13 +748,12 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
           const int s = r & (RING - 1), z = z0 - 4 + r;
           const bool wq = r >= 2 && r <= M + 1;
           uint64_t* b = &full[s];
-          mbar_expect_tx(b, PB + (wq ? 3 * QB : 0));
+          mbar_expect_tx(b, PB + (wq ? NQF * QB : 0));
           tma_load_3d(P + s * (PB / 4), &maps.p, x0 - 4, y0 - 4, z, b);
           if (wq) {
-            float* q = Q + 3 * s * (QB / 4);
-            tma_load_3d(q, &maps.d, x0 - 4, y0 - 2, z, b);
-            tma_load_3d(q + QB / 4, &maps.e, x0 - 4, y0 - 2, z, b);
-            tma_load_3d(q + 2 * (QB / 4), &maps.k, x0 - 4, y0 - 2, z, b);
+#pragma unroll
+            for (int k = 0; k < NQF; ++k)
+              tma_load_3d(Q + (NQF * s + k) * (QB / 4), &maps.q[k], x0 - 4, y0 - 2, z, b);
           }
           issued = r + 1;
         }
@@ -729,16 +770,18 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
       for (int r = 0; r < 4 && ok; ++r) ok = tb2_wait(&full[r], 0u, abort);
       if (!ok) tb2_fail(abort);
       // z-columns of the pair: p^n at z - 2 .. z + 1 of the step-A plane z,
-      // level n + 1 at zB - 2 .. zB + 1 of the step-B plane zB, and the
-      // point's d^{n+1}, e^{n+1}, kap of the last two step-A planes
+      // level n + 1 at zB - 2 .. zB + 1 of the step-B plane zB, and the point
+      // values step B takes from the last two step-A planes: d^{n+1} and
+      // e^{n+1} (Kahan) or p^n (three-term), and kap
       float2 c0 = lds2(P + 0 * (PB / 4) + o), c1 = lds2(P + 1 * (PB / 4) + o);
       float2 c2 = lds2(P + 2 * (PB / 4) + o), c3 = lds2(P + 3 * (PB / 4) + o);
       const float2 zero = make_float2(0.f, 0.f);
       float2 a0 = zero, a1 = zero, a2 = zero, a3 = zero;
-      float2 dq0 = zero, dq1 = zero, eq0 = zero, eq1 = zero, kq0 = zero, kq1 = zero;
+      float2 uq0 = zero, uq1 = zero, vq0 = zero, vq1 = zero, kq0 = zero, kq1 = zero;
       const int x = x0 + 2 * lane, y = y0 + warp;
       const bool store = inner && x < n && y < n;  // N % 4 == 0: x + 1 < n as well
-      unsigned gi = (unsigned)z0 * plane + (unsigned)y * (unsigned)n + (unsigned)x;
+      // offset of plane z0 - 4 + i (unsigned arithmetic: early values wrap and are unused)
+      unsigned gi = (unsigned)z0 * plane + (unsigned)y * (unsigned)n + (unsigned)x - 4u * plane;
       for (int ib = 0; ib < M; ib += RING) {
 #pragma unroll
         for (int u = 0; u < RING; ++u) {
@@ -749,7 +792,7 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
               tb2_fail(abort);
             // ---- step A: level n + 1 at plane z = z0 - 2 + i
             const float* P0 = P + ((u + 2) & 7) * (PB / 4);
-            const float* Qz = Q + 3 * ((u + 2) & 7) * (QB / 4);
+            const float* Qz = Q + NQF * ((u + 2) & 7) * (QB / 4);
             const float2 c4 = lds2(P + ((u + 4) & 7) * (PB / 4) + o);
             Nb2 v;
             const float2 XM = lds2(P0 + o - 2), XP = lds2(P0 + o + 2);
@@ -767,15 +810,28 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
             v.zm2 = c0;
             v.zp2 = c4;
             const float2 L = lap12_pair(v);
-            const float2 Kv = lds2(Qz + 2 * (QB / 4) + qo);
-            const Kp2 ra = kahan_pair(c2, Kv, L, lds2(Qz + qo), lds2(Qz + QB / 4 + qo), false);
+            const float2 Kv = lds2(Qz + (NQF - 1) * (QB / 4) + qo);
+            float2 an, un, vn;  // level n + 1 at the pair; the values step B takes
+            if constexpr (FORM == 1) {
+              const Kp2 ra = kahan_pair(c2, Kv, L, lds2(Qz + qo), lds2(Qz + QB / 4 + qo), false);
+              an = ra.p;
+              un = ra.d;
+              vn = ra.e;
+            } else {
+              an = three_term_pair(c2, Kv, L, lds2(Qz + qo));
+              un = c2;
+              vn = zero;
+              // p^{n+1} of the tile's planes is an output of the pass
+              if (store && i >= 2 && i < M - 2)
+                *reinterpret_cast<float2*>(o0 + (gi + 2u * plane)) = an;
+            }
             // the level-(n+1) slot of this plane was last read by step B of
             // iteration i - 2, and step B below reads the plane iteration
             // i - 2 wrote: both wait for iteration i - 2 to be done everywhere
             if (i >= 2 && ok &&
                 !(ok = tb2_wait(&done[(u + 6) & 7], (unsigned)((i - 2) >> 3) & 1u, abort)))
               tb2_fail(abort);
-            if (active) *reinterpret_cast<float2*>(A + (u & 3) * (AB / 4) + ao) = ra.p;
+            if (active) *reinterpret_cast<float2*>(A + (u & 3) * (AB / 4) + ao) = an;
             // ---- step B: level n + 2 at plane zB = z - 2 (tile rows only)
             if (inner && i >= 4) {
               const float* A0 = A + ((u + 2) & 3) * (AB / 4);
@@ -793,16 +849,21 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
               w.zm1 = a1;
               w.zp1 = a3;
               w.zm2 = a0;
-              w.zp2 = ra.p;
+              w.zp2 = an;
               const float2 LB = lap12_pair(w);
-              const Kp2 rb = kahan_pair(a2, kq0, LB, dq0, eq0, false);
-              if (store) {
-                *reinterpret_cast<float2*>(po + gi) = rb.p;
-                *reinterpret_cast<float2*>(dout + gi) = rb.d;
-                *reinterpret_cast<float2*>(eout + gi) = rb.e;
+              if constexpr (FORM == 1) {
+                const Kp2 rb = kahan_pair(a2, kq0, LB, uq0, vq0, false);
+                if (store) {
+                  *reinterpret_cast<float2*>(o0 + gi) = rb.p;
+                  *reinterpret_cast<float2*>(o1 + gi) = rb.d;
+                  *reinterpret_cast<float2*>(o2 + gi) = rb.e;
+                }
+              } else {
+                const float2 pb = three_term_pair(a2, kq0, LB, uq0);
+                if (store) *reinterpret_cast<float2*>(o1 + gi) = pb;
               }
-              gi += plane;
             }
+            gi += plane;
             c0 = c1;
             c1 = c2;
             c2 = c3;
@@ -810,11 +871,11 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
             a0 = a1;
             a1 = a2;
             a2 = a3;
-            a3 = ra.p;
-            dq0 = dq1;
-            dq1 = ra.d;
-            eq0 = eq1;
-            eq1 = ra.e;
+            a3 = an;
+            uq0 = uq1;
+            uq1 = un;
+            vq0 = vq1;
+            vq1 = vn;
             kq0 = kq1;
             kq1 = Kv;
             mbar_arrive(&done[u]);
@@ -837,169 +898,17 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
   }
 }
 
-// ------------------------------- two FP32 three-term steps per pass ----
-// The same temporal blocking for p^{n+1} = 2 p^n - p^{n-1} + kap L p^n: step A
-// forms level n+1 on the 68 x 20 extended tile from a halo-4 box of p^n and
-// halo-2 boxes of p^{n-1} and kap, and writes its tile part; step B forms
-// level n+2 on the tile from the level-(n+1) planes and p^n.  Both levels are
-// outputs (the next pass reads them as p^{n-1}, p^n), so a pass moves 20 B per
-// point per two steps against 32 B for two single steps.  The arithmetic of
-// each point is the single-step kernel's, so results are bit-identical.
-namespace tb3 {
-constexpr int TH = 16;
-constexpr int PW = 72, PH = TH + 8;  // p^n box (x0-4 .., y0-4 ..)
-constexpr int QW = 72, QH = TH + 4;  // p^{n-1}, kap, level-(n+1) boxes (x0-4 .., y0-2 ..)
-constexpr int PB = PW * PH * 4, QB = QW * QH * 4;
-// ring depths (one block barrier per plane, after step A; a slot is refilled
-// or rewritten only after its last reader passed the latest barrier)
-constexpr int RP = 8;   // p^n planes zA-3 .. zA+4 (zA+5 is loaded into zA-3's slot)
-constexpr int RK = 6;   // kap planes zA-5 .. zA (zA+3 is loaded into zA-3's slot)
-constexpr int RM = 3;   // p^{n-1} planes zA .. zA+2 (zA+3 is loaded into zA's slot)
-constexpr int RA = 6;   // level-(n+1) planes zA-5 .. zA
-constexpr int NTY3 = 22;
-constexpr int NT3 = NTX * NTY3;
-constexpr size_t kSmem = (size_t)RP * PB + (size_t)RK * QB + (size_t)RM * QB + (size_t)RA * QB +
-                         RP * 8;
-__host__ __device__ constexpr int slot(int z, int m) { return (z + 64 * m) % m; }
-}  // namespace tb3
-
-struct Maps3 {
-  CUtensorMap p;   // p^n, 72 x 24 box
-  CUtensorMap pm;  // p^{n-1}, 72 x 20
-  CUtensorMap k;   // kap, 72 x 20
-};
-
-// round R: p^n plane R and the p^{n-1}, kap planes R - 2 of the item's tile
-__device__ __forceinline__ void tb3_issue(const Maps3& m, unsigned char* sm, uint64_t* bar, int R,
-                                          int z0, int z1, int x0, int y0) {
-  using namespace tb3;
-  const bool wp = R >= z0 - 4 && R <= z1 + 3;
-  const bool wq = R - 2 >= z0 - 2 && R - 2 <= z1 + 1;
-  if (!wp && !wq) return;
-  uint64_t* b = &bar[slot(R, RP)];
-  mbar_expect_tx(b, (wp ? PB : 0) + (wq ? 2 * QB : 0));
-  float* P = reinterpret_cast<float*>(sm);
-  float* K = reinterpret_cast<float*>(sm + RP * PB);
-  float* M = reinterpret_cast<float*>(sm + RP * PB + RK * QB);
-  if (wp) tma_load_3d(P + slot(R, RP) * (PB / 4), &m.p, x0 - 4, y0 - 4, R, b);
-  if (wq) {
-    const int z = R - 2;
-    tma_load_3d(K + slot(z, RK) * (QB / 4), &m.k, x0 - 4, y0 - 2, z, b);
-    tma_load_3d(M + slot(z, RM) * (QB / 4), &m.pm, x0 - 4, y0 - 2, z, b);
-  }
+__global__ void __launch_bounds__(tb2::NT2, 1)
+    k_step2_kahan(const __grid_constant__ Maps2 maps, float* __restrict__ po,
+                  float* __restrict__ dout, float* __restrict__ eout, int n, int zc, int tiles_x,
+                  int tiles_y, int nitems) {
+  step2_body<1>(maps, po, dout, eout, n, zc, tiles_x, tiles_y, nitems);
 }
 
-__global__ void __launch_bounds__(tb3::NT3, 1)
-    k_step2_f32(const __grid_constant__ Maps3 maps, float* __restrict__ o1,
+__global__ void __launch_bounds__(tb2::NT2, 1)
+    k_step2_f32(const __grid_constant__ Maps2 maps, float* __restrict__ o1,
                 float* __restrict__ o2, int n, int zc, int tiles_x, int tiles_y, int nitems) {
-  using namespace tb3;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const float* P = reinterpret_cast<const float*>(sm);
-  const float* K = reinterpret_cast<const float*>(sm + RP * PB);
-  const float* M = reinterpret_cast<const float*>(sm + RP * PB + RK * QB);
-  float* A = reinterpret_cast<float*>(sm + RP * PB + RK * QB + RM * QB);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + RP * PB + RK * QB + RM * QB + RA * QB);
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * NTX + tx;
-  if (tid == 0) {
-    for (int i = 0; i < RP; ++i) mbar_init(&bar[i], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  grid_dependency_sync();
-  if (*(volatile unsigned*)&g_tma_status != 0u) return;
-  __syncthreads();
-  unsigned phase = 0;
-  const size_t plane = (size_t)n * n;
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int tix = item % tiles_x;
-    const int tiy = (item / tiles_x) % tiles_y;
-    const int z0 = (item / (tiles_x * tiles_y)) * zc;
-    const int z1 = min(n, z0 + zc);
-    const int x0 = tix * TBX, y0 = tiy * TH;
-    if (tid == 0)
-      for (int R = z0 - 4; R <= z0 + 2; ++R) tb3_issue(maps, sm, bar, R, z0, z1, x0, y0);
-    bool timed_out = false;
-    int waited_upto = z0 - 5;
-    for (int zA = z0 - 2; zA <= z1 + 1; ++zA) {
-      for (int R = waited_upto + 1; R <= zA + 2; ++R) {
-        const int b = slot(R, RP);
-        if (!mbar_wait(&bar[b], (phase >> b) & 1u, kWaitCycles)) timed_out = true;
-        phase ^= 1u << b;
-      }
-      waited_upto = zA + 2;
-      // ---- step A: level n+1 at plane zA on the 68 x 20 extended tile
-      {
-        const float* P0 = P + slot(zA, RP) * (PB / 4);
-        const float* Pm1 = P + slot(zA - 1, RP) * (PB / 4);
-        const float* Pp1 = P + slot(zA + 1, RP) * (PB / 4);
-        const float* Pm2 = P + slot(zA - 2, RP) * (PB / 4);
-        const float* Pp2 = P + slot(zA + 2, RP) * (PB / 4);
-        const float* Kz = K + slot(zA, RK) * (QB / 4);
-        const float* Mz = M + slot(zA, RM) * (QB / 4);
-        float* Az = A + slot(zA, RA) * (QB / 4);
-        const bool zout = zA >= z0 && zA < z1;
-        for (int q = tid; q < 34 * QH; q += NT3) {
-          const int qy = q / 34, qx = 2 + 2 * (q % 34);
-          const int po_ = (qy + 2) * PW + qx;
-          const int qo = qy * QW + qx;
-          Nb2 v;
-          gather_pair(P0, Pm1, Pp1, Pm2, Pp2, po_, PW, v);
-          const float2 L = lap12_pair(v);
-          const float2 r = three_term_pair(v.c, lds2(Kz + qo), L, lds2(Mz + qo));
-          *reinterpret_cast<float2*>(Az + qo) = r;
-          if (zout && qx >= 4 && qx < 4 + TBX && qy >= 2 && qy < 2 + TH) {
-            const int x = x0 + qx - 4, y = y0 + qy - 2;
-            if (x < n && y < n)
-              *reinterpret_cast<float2*>(o1 + (size_t)zA * plane + (size_t)y * n + x) = r;
-          }
-        }
-      }
-      // the plane's only block barrier, also the vote on a timed-out wait
-      if (__syncthreads_or(timed_out)) {
-        if (tid == 0) {
-          atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
-          for (int R = waited_upto + 1; R <= min(z1 + 3, zA + 4); ++R) {
-            const int b = slot(R, RP);
-            mbar_wait(&bar[b], (phase >> b) & 1u, 1 << 24);
-            phase ^= 1u << b;
-          }
-        }
-        return;
-      }
-      // refill: p^n plane zA+5 into zA-3's slot (last read by step B of the
-      // previous plane), kap zA+3 into zA-3's (likewise), p^{n-1} zA+3 into
-      // zA's (last read by step A above)
-      if (tid == 0) tb3_issue(maps, sm, bar, zA + 5, z0, z1, x0, y0);
-      // ---- step B: level n+2 at plane zB = zA - 2 on the tile: reads the
-      // level-(n+1) planes zA-4 .. zA, p^n and kap at zB; step A of plane zA+1
-      // rewrites zA-5's level-(n+1) slot, last read by step B of plane zA-1
-      const int zB = zA - 2;
-      if (zB >= z0 && ty < TH) {
-        const float* A0 = A + slot(zB, RA) * (QB / 4);
-        const float* Am1 = A + slot(zB - 1, RA) * (QB / 4);
-        const float* Ap1 = A + slot(zB + 1, RA) * (QB / 4);
-        const float* Am2 = A + slot(zB - 2, RA) * (QB / 4);
-        const float* Ap2 = A + slot(zB + 2, RA) * (QB / 4);
-        const float* Kz = K + slot(zB, RK) * (QB / 4);
-        const float* Pz = P + slot(zB, RP) * (PB / 4);
-        const int xl = 2 * tx;
-        const int x = x0 + xl, y = y0 + ty;
-        const int qo = (ty + 2) * QW + xl + 4;
-        const int po_ = (ty + 4) * PW + xl + 4;
-        Nb2 v;
-        gather_pair(A0, Am1, Ap1, Am2, Ap2, qo, QW, v);
-        const float2 L = lap12_pair(v);
-        const float2 Kv = lds2(Kz + qo), PN = lds2(Pz + po_);
-        if (x < n && y < n) {
-          const size_t gi = (size_t)zB * plane + (size_t)y * n + x;
-          *reinterpret_cast<float2*>(o2 + gi) = three_term_pair(v.c, Kv, L, PN);
-        }
-      }
-    }
-    // the next work item refills every ring from its first plane on
-    __syncthreads();
-  }
+  step2_body<0>(maps, o1, o2, nullptr, n, zc, tiles_x, tiles_y, nitems);
 }
 
 // ------------------------------------ resident time loop (small grids) --
@@ -1413,7 +1322,7 @@ static int launch_step_tma_r(const Plan& pl, int form, bool start, const void* p
   const int es = (int)pl.esize;
   const int th = TBY * RPT;
   if (make_map(&maps.p, p, pl.n, es, true, th) != FFPAT_OK) return check_launch("tensor map (p)");
-  const int nq = start ? 1 : (form == 0 ? 2 : 3);
+  const int nq = form == 2 ? 2 : (start ? 1 : (form == 0 ? 2 : 3));
   for (int i = 0; i < 3; ++i) {
     if (i < nq) {
       if (make_map(&maps.q[i], q[i], pl.n, es, false, th) != FFPAT_OK)
@@ -1426,6 +1335,9 @@ static int launch_step_tma_r(const Plan& pl, int form, bool start, const void* p
     return start ? launch_one<double, 0, true, RPT>(pl, maps, o0, o1, o2, st)
                  : launch_one<double, 0, false, RPT>(pl, maps, o0, o1, o2, st);
   }
+  if (form == 2)
+    return start ? launch_one<float, 2, true, RPT>(pl, maps, o0, o1, o2, st)
+                 : launch_one<float, 2, false, RPT>(pl, maps, o0, o1, o2, st);
   if (form == 0)
     return start ? launch_one<float, 0, true, RPT>(pl, maps, o0, o1, o2, st)
                  : launch_one<float, 0, false, RPT>(pl, maps, o0, o1, o2, st);
@@ -1515,25 +1427,24 @@ int launch_wait_timeout(long long cycles, cudaStream_t st) {
   return check_launch("k_wait_timeout");
 }
 
-int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void* e, void* po,
-                       void* dout, void* eout, cudaStream_t st) {
-  Maps2 maps;
-  if (make_map_box(&maps.p, p, pl.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
-      make_map_box(&maps.d, d, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
-      make_map_box(&maps.e, e, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
-      make_map_box(&maps.k, pl.kap, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK)
-    return report(FFPAT_ECUDA, "two-step kernel: tensor map");
-  const size_t smem = tb2::kSmem + 1024;
-  static int occ = 0;
+// One two-step pass: grid of one CTA per SM over (64 x 16 tile, z-range) items.
+template <typename Kern, typename... Outs>
+int launch_step2(Kern kern, size_t smem_need, const char* name, const Plan& pl, const Maps2& maps,
+                 cudaStream_t st, Outs... outs) {
+  const size_t smem = smem_need + 1024;
+  // the shared-memory opt-in, once per kernel (per instantiation of this template)
+  static cudaError_t attr = cudaErrorUnknown;
   static std::once_flag once;
   std::call_once(once, [&] {
-    cudaFuncSetAttribute(k_step2_kahan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step2_kahan, tb2::NT2, smem);
-    if (occ < 1) occ = 1;
+    attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
+  if (attr != cudaSuccess) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "%s: %zu bytes of shared memory refused", name, smem);
+  }
   const int n = pl.n;
   const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + tb2::TH2 - 1) / tb2::TH2;
-  const int slots = kNumSMs * occ;
+  const int slots = kNumSMs;  // one CTA per SM
   // z-ranges: step A repeats 4 planes per range, the same cost model as the
   // single-step kernel (at 384^3 whole columns: 144 items for 152 slots)
   int zc = choose_zchunk(n, tiles_x * tiles_y, slots);
@@ -1541,48 +1452,38 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
   const int zchunks = (n + zc - 1) / zc;
   const int nitems = tiles_x * tiles_y * zchunks;
   const int grid = nitems < slots ? nitems : slots;
-  const cudaError_t le = launch_pdl(k_step2_kahan, dim3(grid), dim3(tb2::NT2), smem, st, maps,
-                                    (float*)po, (float*)dout, (float*)eout, n, zc, tiles_x,
-                                    tiles_y, nitems);
+  const cudaError_t le = launch_pdl(kern, dim3(grid), dim3(tb2::NT2), smem, st, maps, outs..., n,
+                                    zc, tiles_x, tiles_y, nitems);
   count_launch();
   if (le != cudaSuccess) {
     cudaGetLastError();
-    return report(FFPAT_ECUDA, "k_step2_kahan launch: %s", cudaGetErrorString(le));
+    return report(FFPAT_ECUDA, "%s launch: %s", name, cudaGetErrorString(le));
   }
-  return check_launch("k_step2_kahan");
+  return check_launch(name);
+}
+
+int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void* e, void* po,
+                       void* dout, void* eout, cudaStream_t st) {
+  Maps2 maps;
+  if (make_map_box(&maps.p, p, pl.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
+      make_map_box(&maps.q[0], d, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
+      make_map_box(&maps.q[1], e, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
+      make_map_box(&maps.q[2], pl.kap, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK)
+    return report(FFPAT_ECUDA, "two-step kernel: tensor map");
+  return launch_step2(k_step2_kahan, tb2::smem_bytes<1>(), "k_step2_kahan", pl, maps, st,
+                      (float*)po, (float*)dout, (float*)eout);
 }
 
 int launch_step2_f32(const Plan& pl, const void* pm, const void* p, void* o1, void* o2,
                      cudaStream_t st) {
-  Maps3 maps;
-  if (make_map_box(&maps.p, p, pl.n, 4, tb3::PW, tb3::PH) != FFPAT_OK ||
-      make_map_box(&maps.pm, pm, pl.n, 4, tb3::QW, tb3::QH) != FFPAT_OK ||
-      make_map_box(&maps.k, pl.kap, pl.n, 4, tb3::QW, tb3::QH) != FFPAT_OK)
+  Maps2 maps;
+  if (make_map_box(&maps.p, p, pl.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
+      make_map_box(&maps.q[0], pm, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
+      make_map_box(&maps.q[1], pl.kap, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK)
     return report(FFPAT_ECUDA, "two-step kernel: tensor map");
-  const size_t smem = tb3::kSmem + 1024;
-  static int occ = 0;
-  static std::once_flag once;
-  std::call_once(once, [&] {
-    cudaFuncSetAttribute(k_step2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step2_f32, tb3::NT3, smem);
-    if (occ < 1) occ = 1;
-  });
-  const int n = pl.n;
-  const int tiles_x = (n + TBX - 1) / TBX, tiles_y = (n + tb3::TH - 1) / tb3::TH;
-  const int slots = kNumSMs * occ;
-  int zc = choose_zchunk(n, tiles_x * tiles_y, slots);
-  if (zchunk_override() > 0) zc = zchunk_override() < n ? zchunk_override() : n;
-  const int zchunks = (n + zc - 1) / zc;
-  const int nitems = tiles_x * tiles_y * zchunks;
-  const int grid = nitems < slots ? nitems : slots;
-  const cudaError_t le = launch_pdl(k_step2_f32, dim3(grid), dim3(NTX, tb3::NTY3), smem, st, maps,
-                                    (float*)o1, (float*)o2, n, zc, tiles_x, tiles_y, nitems);
-  count_launch();
-  if (le != cudaSuccess) {
-    cudaGetLastError();
-    return report(FFPAT_ECUDA, "k_step2_f32 launch: %s", cudaGetErrorString(le));
-  }
-  return check_launch("k_step2_f32");
+  maps.q[2] = maps.q[1];
+  return launch_step2(k_step2_f32, tb2::smem_bytes<0>(), "k_step2_f32", pl, maps, st,
+                      (float*)o1, (float*)o2);
 }
 
 // ---- the resident time loop (host side)

@@ -10,6 +10,8 @@ from paper_1901_06503_gb300 import ffpat as F
 from paper_1901_06503_gb300.autograd import forward_op
 from paper_1901_06503_gb300.inputs import config, random_data, random_speed, random_volume
 
+from tolerances import FP32_TOL
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +65,8 @@ def test_fp32_gradient_matches_oracle_at_48():
     g = forward_op(ht, ct, prob, 16)
     (g * torch.tensor(w, device="cuda", dtype=torch.float32)).sum().backward()
     gh_or, gc_or = o.grad(c, h, w, wl.T)
-    assert rel(ht.grad.double().cpu().numpy(), gh_or) < 2e-5
-    assert rel(ct.grad.double().cpu().numpy(), gc_or) < 1e-4
+    assert rel(ht.grad.double().cpu().numpy(), gh_or) < FP32_TOL
+    assert rel(ct.grad.double().cpu().numpy(), gc_or) < FP32_TOL
 
 
 def test_central_differences_fp64():
@@ -106,3 +108,78 @@ def test_central_differences_fp64():
             fd_h = (loss(hh + eps * dh, cc) - loss(hh - eps * dh, cc)) / (2 * eps)
             an_h = float((ht.grad * dh).sum())
             assert abs(fd_h - an_h) < 1e-8 * abs(an_h)
+
+
+def test_config3_central_differences_fp32_192():
+    """The differentiable operator as the 192^3 workload runs it: FP32,
+    90 angles, T = 1, checkpoints every 16 steps, loss 1/2 ||A(c) h - g||^2
+    with g = A h_true + 1 % noise and h = h_true + a smooth perturbation.
+    32 random directions (dh, dc) -- smooth fields; dc vanishes wherever c is
+    within reach of its maximum, so that Nt and dt (from max c) stay fixed --
+    each checked against <grad_h, dh> +
+    <grad_c, dc> from the hand-written FP32 backward pass:
+
+    * central differences of the FP32 operator at eps = 1e-3 within 1 %: the
+      h-part of the loss is quadratic (exact), the c-part carries the
+      truncation eps^2 |d^3 L / d eps^3| / 6 (a relative speed change of 1e-3
+      over the workload's shortest wavelengths and T = 1 keeps it below 1 %),
+      and the FP32 rounding of the two loss values divided by 2 eps;
+    * central differences of the same discretisation in FP64 at eps and
+      eps / 2 converge onto the analytic value at second order (the error
+      shrinks at least ~3x) until they reach the FP32 gradient's own accuracy.
+
+    The loss differences are formed in FP64 from the residuals."""
+    from paper_1901_06503_gb300.inputs import gaussian_random_field
+    wl = config(3)
+    n, nth, T = wl.n, wl.n_angles, wl.T
+    prob = F.problem(n, T, nth, F.FP32)
+    p64 = F.problem(n, T, nth, F.FP64)
+    c = wl.c
+    ct0 = torch.tensor(c, device="cuda", dtype=torch.float32)
+    ht_true = torch.tensor(wl.h, device="cuda", dtype=torch.float32)
+    with torch.no_grad():
+        g = F.forward(prob, ct0, ht_true).double()
+        g = g + 0.01 * float(g.norm()) / g.numel() ** 0.5 * torch.tensor(
+            wl.noise, device="cuda")
+    h0 = wl.h + 0.05 * gaussian_random_field(n, 0.2, np.random.default_rng(31))
+    ht = torch.tensor(h0, device="cuda", dtype=torch.float32, requires_grad=True)
+    ct = torch.tensor(c, device="cuda", dtype=torch.float32, requires_grad=True)
+    r = forward_op(ht, ct, prob, 16).double() - g
+    (0.5 * (r * r).sum()).backward()
+    gh, gc = ht.grad.double(), ct.grad.double()
+    # the FP32 operator sees the FP32-rounded point; the FP64 one the same point
+    hh = torch.tensor(h0, device="cuda", dtype=torch.float32).double()
+    cc = torch.tensor(c, device="cuda", dtype=torch.float32).double()
+    ws32, ws64 = F.workspace(prob), F.workspace(p64)
+
+    def central(e, dh, dc, fp64):
+        def res(s):
+            with torch.no_grad():
+                if fp64:
+                    return F.forward(p64, cc + s * dc, hh + s * dh, ws=ws64) - g
+                return F.forward(prob, (cc + s * dc).float(), (hh + s * dh).float(),
+                                 ws=ws32).double() - g
+        rp, rm = res(e), res(-e)
+        return float(0.5 * ((rp - rm) * (rp + rm)).sum()) / (2 * e)
+
+    eps, errs32, errs64 = 1e-3, [], []
+    for i in range(32):
+        rng = np.random.default_rng(300 + i)
+        dc = gaussian_random_field(n, 0.3, rng) * c
+        # no perturbation where it could lift c above its maximum: Nt and dt
+        # (from max c) stay those of the unperturbed problem on both sides
+        dc[c > c.max() - 4 * eps * np.abs(dc).max()] = 0.0
+        dh = gaussian_random_field(n, 0.15, rng)
+        dct = torch.tensor(dc, device="cuda")
+        dht = torch.tensor(dh, device="cuda")
+        an = float((gh * dht).sum() + (gc * dct).sum())
+        e32 = abs(central(eps, dht, dct, False) - an)
+        assert e32 < 1e-2 * abs(an), (i, e32, an)
+        e64 = abs(central(eps, dht, dct, True) - an)
+        e64h = abs(central(eps / 2, dht, dct, True) - an)
+        assert e64h < 0.35 * e64 or e64h < FP32_TOL * abs(an), (i, e64, e64h, an)
+        errs32.append(e32 / abs(an))
+        errs64.append((e64 / abs(an), e64h / abs(an)))
+    print(f"config-3 FD: FP32 eps=1e-3 max rel err {max(errs32):.3e} median "
+          f"{float(np.median(errs32)):.3e}; FP64 eps, eps/2 max "
+          f"{max(e[0] for e in errs64):.3e}, {max(e[1] for e in errs64):.3e}")

@@ -535,9 +535,10 @@ def test_two_step_kahan_bit_identical(n, T):
     assert F.device_status() == 0
 
 
+@pytest.mark.parametrize("prec", [F.FP32_KAHAN, F.FP32])
 @pytest.mark.parametrize("zc", [1, 3])
-def test_two_step_kahan_many_items_per_cta(tmp_path, zc):
-    """The two-step pass with short z-ranges (FFPAT_ZCHUNK, in a child
+def test_two_step_many_items_per_cta(tmp_path, zc, prec):
+    """The two-step passes with short z-ranges (FFPAT_ZCHUNK, in a child
     process): at N = 128 that is 688 or 2048 work items for 152 CTAs, so every
     CTA walks several items and re-arms its barriers between them; W and W^T
     stay bit for bit those of single steps."""
@@ -555,7 +556,7 @@ def test_two_step_kahan_many_items_per_cta(tmp_path, zc):
         "from paper_1901_06503_gb300 import ffpat as F\n"
         f"c = torch.as_tensor(np.load({str(tmp_path / 'c.npy')!r}), device='cuda')\n"
         f"h = torch.as_tensor(np.load({str(tmp_path / 'h.npy')!r}), device='cuda')\n"
-        f"prob = F.problem({n}, {T}, 4, F.FP32_KAHAN)\n"
+        f"prob = F.problem({n}, {T}, 4, {prec})\n"
         "out = []\n"
         "for path in (2, 3):\n"
         "    F.set_stencil_path(path)\n"
@@ -650,11 +651,11 @@ def test_resident_loops_on_two_streams():
 
 
 @pytest.mark.parametrize("prec", [F.FP32, F.FP32_KAHAN])
-@pytest.mark.parametrize("path", [0, 2])
+@pytest.mark.parametrize("path", [0, 2, 3])
 @pytest.mark.parametrize("T", [0.004, 0.1])
 def test_wave_in_place(prec, path, T):
-    """W with out = in (one step and several; resident loop and step loop)
-    equals the out-of-place result."""
+    """W with out = in (one step and several; resident loop, single steps and
+    two steps per pass) equals the out-of-place result."""
     n = 24
     c = as_input(random_speed(n, 1400), prec)
     h = as_input(random_volume(n, 1401), prec)
