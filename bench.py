@@ -173,6 +173,15 @@ def make_problem(args):
     return w, wl, prob
 
 
+def workload_config(w, wl, nt, precision, world):
+    """The `config` object of both arms' lines: the workload by name and sizes."""
+    return {"workload": wl["label"], "n": w.n, "n_angles": w.n_angles, "T": w.T, "nt": nt,
+            "precision": precision, "precond": "ramp" if w.precond else "identity",
+            "fb_iteration": "W + P + residual + Lambda + P^T + W^T + prox update",
+            "l2": "inputs larger than L2 and flushed (256 MB write) between timed steps",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def oracle_sample(w, seconds_target=10.0):
     """Time the oracle's wave operator (the dominant loop) on the workload's
     grid for a bounded number of leapfrog steps; returns voxel-steps/s."""
@@ -214,7 +223,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["label"], "n": w.n, "n_angles": w.n_angles, "T": w.T},
+        "config": workload_config(w, wl, o.time_steps(w.n, w.T, w.cfl, float(w.c.max()))[0],
+                                  "f64 (the oracle)", 1),
         "cpu_baseline": {"value": value, "unit": "voxel-steps/s", "cores": cores, "kind": "oracle",
                          "sample": f"FP64 CPU oracle wave operator W, {steps} leapfrog steps on "
                                    f"the {w.n}^3 grid per step (the FB iteration's dominant loop)"},
@@ -374,13 +384,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {F.FP64: "f64", F.FP32: "f32", F.FP32_KAHAN: "f32"}[prob.precision],
         "data": "synthetic",
-        "config": {"workload": wl["label"], "n": w.n, "n_angles": w.n_angles, "T": w.T,
-                   "nt": nt, "precision": F.PRECISION_NAMES[prob.precision],
-                   "precond": "ramp" if w.precond else "identity",
-                   "fb_iteration": "W + P + residual + Lambda + P^T + W^T + prox update",
-                   "l2": ("inputs larger than L2 and flushed (256 MB write) between timed "
-                          "steps"),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(w, wl, nt, F.PRECISION_NAMES[prob.precision], world),
         "fb_iters_per_s": world * args.steps / (dev_ms / 1e3),
         "wall_s": wall,
         "roofline": roofline,

@@ -166,14 +166,21 @@ __device__ __forceinline__ float2 up2(unsigned long long r) {
   memcpy(&a, &r, sizeof a);
   return a;
 }
+// a + b and a - b as one packed fused multiply-add each, a * 1 + b and
+// b * (-1) + a: the exact sum rounded once, i.e. the IEEE addition and
+// subtraction bit for bit (signed zeros included)
 __device__ __forceinline__ float2 add2(float2 a, float2 b) {
   unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(r)
+      : "l"(pk2(a)), "l"(pk2(make_float2(1.0f, 1.0f))), "l"(pk2(b)));
   return up2(r);
 }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(r)
+      : "l"(pk2(b)), "l"(pk2(make_float2(-1.0f, -1.0f))), "l"(pk2(a)));
   return up2(r);
 }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
