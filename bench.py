@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # the same grid, keyed by (workload, precision, kernel).  An entry is dropped
 # whenever its kernel changes, until it has been captured again.
 NCU_TRAFFIC = {("cfg2", "fp32-kahan", "resident"): 17.167104e6,
-               ("cfg5", "fp32-kahan", "two-step"): 1541.481728e6,
-               ("cfg5", "fp32", "two-step"): 1095.35488e6}
+               ("cfg5", "fp32-kahan", "two-step"): 1541.066496e6,
+               ("cfg5", "fp32", "two-step"): 1095.204864e6}
 
 # algorithmic FP32 operations per point-step of the difference-form update:
 # 12 subtractions, 10 additions and one FMA (2) for 12 h^2 L4 p, then the
