@@ -127,6 +127,20 @@ struct BatchStep {
   bool start;
 };
 int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st);
+// Two FP32-Kahan steps for several problems in one launch (the two-step pass
+// of launch_step2_kahan per problem; d and e are read with a halo, so they go
+// to separate output buffers).
+struct BatchStep2 {
+  const float* p;    // p^n
+  float* pout;       // p^{n+2}
+  const float* d;    // d^n, e^n
+  const float* e;
+  float* dout;       // d^{n+2}, e^{n+2}
+  float* eout;
+  const float* kap;  // kappa / 12
+  int n;
+};
+int launch_step2_batch(const BatchStep2* steps, int count, cudaStream_t st);
 constexpr int kMaxBatchRequests = 28;
 
 // Two FP32-Kahan steps in one pass (temporal blocking): reads (p, d, e) at

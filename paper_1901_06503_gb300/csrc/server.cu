@@ -7,9 +7,11 @@
 // iterate and workspace) fits the HBM budget; each admitted request carries a
 // host-side phase machine (power iteration if no step was given, then FB
 // iterations: forward W, P + residual (+ Lambda), P^T, adjoint W, update).
-// Every "tick" the worker gathers the current leapfrog step of every request
-// that is inside a W phase and advances all of them with ONE batched launch
-// (launch_step_batch); requests whose W phase ended get their projection /
+// Every "tick" the worker gathers the next leapfrog work of every request that
+// is inside a W phase and advances all of them with at most two batched
+// launches: one single step for the requests at their start step or last odd
+// step (launch_step_batch) and one two-step pass for the others
+// (launch_step2_batch); requests whose W phase ended get their projection /
 // update kernels queued behind it.  Nothing on this path waits for the GPU
 // except a bounded run-ahead (a ring of tick events) and the completion event
 // of each request, so requests that arrive while others run join the next
@@ -64,6 +66,7 @@ struct Req {
   Phase phase = kQueued;
   int it = 0;     // iterations done (power, then FB)
   int wstep = 0;  // leapfrog step inside the current W
+  int de = 0;     // which pair of (d, e) buffers holds the current level
   const float* w_in = nullptr;
   const float* cur = nullptr;
   cudaEvent_t done_ev = nullptr;
@@ -166,15 +169,41 @@ int admit(ffpat_server* S, Req& r) {
   return FFPAT_OK;
 }
 
-// the step of request r in this tick's batch
+// The state of a request inside a W: p in s[0] / s[1] (alternating), the
+// increment d and the Kahan carry e in the pair (s[2], s[3]) or (s[4], s[5])
+// (`de`).  A W runs the start step, then two steps per pass while at least two
+// remain, then a last single step if one is left -- the sequence of
+// ffpat_fb_solve's time loop, so the served result is the same bit for bit.
+float* d_buf(const Req& r, int k) { return (float*)r.pl.s[k ? 4 : 2]; }
+float* e_buf(const Req& r, int k) { return (float*)r.pl.s[k ? 5 : 3]; }
+
+bool two_steps_next(const Req& r) { return r.wstep > 0 && r.pl.nt - r.wstep >= 2; }
+
+// the single step of request r in this tick (start step or the last one)
 BatchStep next_step(Req& r) {
   BatchStep b;
   const Plan& pl = r.pl;
   b.start = r.wstep == 0;
+  if (b.start) r.de = 0;
   b.p = b.start ? r.w_in : r.cur;
   b.pout = (float*)(b.start ? pl.s[0] : (r.cur == pl.s[0] ? pl.s[1] : pl.s[0]));
-  b.d = (float*)pl.s[2];
-  b.e = (float*)pl.s[3];
+  b.d = d_buf(r, r.de);
+  b.e = e_buf(r, r.de);
+  b.kap = (const float*)pl.kap;
+  b.n = pl.n;
+  return b;
+}
+
+// the two-step pass of request r in this tick (d, e go to the other pair)
+BatchStep2 next_pass(const Req& r) {
+  BatchStep2 b;
+  const Plan& pl = r.pl;
+  b.p = r.cur;
+  b.pout = (float*)(r.cur == pl.s[0] ? pl.s[1] : pl.s[0]);
+  b.d = d_buf(r, r.de);
+  b.e = e_buf(r, r.de);
+  b.dout = d_buf(r, 1 - r.de);
+  b.eout = e_buf(r, 1 - r.de);
   b.kap = (const float*)pl.kap;
   b.n = pl.n;
   return b;
@@ -258,7 +287,8 @@ void finish(ffpat_server* S, Req& r, int status) {
 void worker_loop(ffpat_server* S) {
   cudaSetDevice(S->device);
   std::vector<BatchStep> batch;
-  std::vector<Req*> in_batch;
+  std::vector<BatchStep2> batch2;
+  std::vector<Req*> in_batch, in_batch2;
   while (true) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
@@ -301,16 +331,23 @@ void worker_loop(ffpat_server* S) {
       }
       if (S->stop) break;
       batch.clear();
+      batch2.clear();
       in_batch.clear();
+      in_batch2.clear();
       bool any_finish = false;
       for (auto& r : S->active) {
         if (r->phase == kFwd || r->phase == kAdj) {
-          batch.push_back(next_step(*r));
-          in_batch.push_back(r.get());
+          if (two_steps_next(*r)) {
+            batch2.push_back(next_pass(*r));
+            in_batch2.push_back(r.get());
+          } else {
+            batch.push_back(next_step(*r));
+            in_batch.push_back(r.get());
+          }
         }
         any_finish |= r->phase == kFinish;
       }
-      if (batch.empty()) {
+      if (batch.empty() && batch2.empty()) {
         S->cv.notify_all();
         if (any_finish) {
           lk.unlock();
@@ -324,12 +361,22 @@ void worker_loop(ffpat_server* S) {
     // bounded run-ahead: at most kTickRing ticks queued on the stream
     cudaEvent_t& ev = S->ring[S->ring_pos];
     cudaEventSynchronize(ev);
-    Trace trace_tick("serving tick (batched leapfrog step)");
+    Trace trace_tick("serving tick (batched leapfrog steps)");
+    // single steps (start steps, last odd steps) in one launch, two-step
+    // passes in another; a request takes part in at most one of them
     int rc = launch_step_batch(batch.data(), (int)batch.size(), S->st);
+    if (rc == FFPAT_OK) rc = launch_step2_batch(batch2.data(), (int)batch2.size(), S->st);
     for (size_t i = 0; rc == FFPAT_OK && i < in_batch.size(); ++i) {
       Req& r = *in_batch[i];
       r.cur = batch[i].pout;
       r.wstep += 1;
+      if (r.wstep == r.pl.nt) rc = after_wave(S, r);
+    }
+    for (size_t i = 0; rc == FFPAT_OK && i < in_batch2.size(); ++i) {
+      Req& r = *in_batch2[i];
+      r.cur = batch2[i].pout;
+      r.de = 1 - r.de;
+      r.wstep += 2;
       if (r.wstep == r.pl.nt) rc = after_wave(S, r);
     }
     cudaEventRecord(ev, S->st);

@@ -672,12 +672,33 @@ __device__ __forceinline__ void tb2_fail(volatile int* abort) {
   atomicCAS(&g_tma_status, 0u, (unsigned)(-FFPAT_ETIMEDOUT));
 }
 
+// One work item of a two-step pass: a 64 x 16 tile and a z-range of one
+// problem, with that problem's tensor maps and outputs.
 // FORM 1: FP32-Kahan, o0/o1/o2 = p, d, e of level n + 2.
 // FORM 0: three-term, o0 = p^{n+1}, o1 = p^{n+2} (o2 unused).
-template <int FORM>
-__device__ __forceinline__ void step2_body(const Maps2& maps, float* __restrict__ o0,
-                                           float* __restrict__ o1, float* __restrict__ o2, int n,
-                                           int zc, int tiles_x, int tiles_y, int nitems) {
+struct Step2Item {
+  const Maps2* maps;
+  float* o0;
+  float* o1;
+  float* o2;
+  int n, x0, y0, z0, z1;
+};
+
+// a single problem: items are (tile, z-range) in x, y, z order
+struct Step2One {
+  const Maps2* maps;
+  float *o0, *o1, *o2;
+  int n, zc, tiles_x, tiles_y;
+  __device__ Step2Item operator()(int item) const {
+    const int tix = item % tiles_x;
+    const int tiy = (item / tiles_x) % tiles_y;
+    const int z0 = (item / (tiles_x * tiles_y)) * zc;
+    return Step2Item{maps, o0, o1, o2, n, tix * TBX, tiy * tb2::TH2, z0, min(n, z0 + zc)};
+  }
+};
+
+template <int FORM, class Items>
+__device__ __forceinline__ void step2_body(const Items& items, int nitems) {
   using namespace tb2;
   constexpr int NQF = NQ<FORM>;
   extern __shared__ unsigned char smem_raw[];
@@ -725,14 +746,15 @@ __device__ __forceinline__ void step2_body(const Maps2& maps, float* __restrict_
   const int o = (qy + 2) * PW + 2 * qx + 2;  // in the p^n box
   const int qo = qy * QW + 2 * qx + 2;       // in the stream boxes
   const int ao = qy * AW + 2 * qx;           // in the level-(n+1) planes
-  const unsigned plane = (unsigned)n * (unsigned)n;
 
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int tix = item % tiles_x;
-    const int tiy = (item / tiles_x) % tiles_y;
-    const int z0 = (item / (tiles_x * tiles_y)) * zc;
-    const int z1 = min(n, z0 + zc);
-    const int x0 = tix * TBX, y0 = tiy * TH2;
+    const Step2Item it = items(item);
+    const Maps2& maps = *it.maps;
+    float* __restrict__ o0 = it.o0;
+    float* __restrict__ o1 = it.o1;
+    float* __restrict__ o2 = it.o2;
+    const int n = it.n, x0 = it.x0, y0 = it.y0, z0 = it.z0, z1 = it.z1;
+    const unsigned plane = (unsigned)n * (unsigned)n;
     // iteration i computes step A at plane z0 - 2 + i and step B at z0 - 4 + i;
     // round r brings plane z0 - 4 + r of p^n (for r <= M + 3) and of the
     // streams (for 2 <= r <= M + 1)
@@ -746,8 +768,8 @@ __device__ __forceinline__ void step2_body(const Maps2& maps, float* __restrict_
           if (r >= RING) {
             // slot r mod 8 was last read in iteration r - 10 (iteration 0
             // follows every thread's read of the first planes)
-            const int it = r - 10 > 0 ? r - 10 : 0;
-            if (!tb2_wait(&done[it & (RING - 1)], (unsigned)(it >> 3) & 1u, abort)) {
+            const int ir = r - 10 > 0 ? r - 10 : 0;
+            if (!tb2_wait(&done[ir & (RING - 1)], (unsigned)(ir >> 3) & 1u, abort)) {
               ok = false;
               break;
             }
@@ -909,13 +931,45 @@ __global__ void __launch_bounds__(tb2::NT2, 1)
     k_step2_kahan(const __grid_constant__ Maps2 maps, float* __restrict__ po,
                   float* __restrict__ dout, float* __restrict__ eout, int n, int zc, int tiles_x,
                   int tiles_y, int nitems) {
-  step2_body<1>(maps, po, dout, eout, n, zc, tiles_x, tiles_y, nitems);
+  step2_body<1>(Step2One{&maps, po, dout, eout, n, zc, tiles_x, tiles_y}, nitems);
 }
 
 __global__ void __launch_bounds__(tb2::NT2, 1)
     k_step2_f32(const __grid_constant__ Maps2 maps, float* __restrict__ o1,
                 float* __restrict__ o2, int n, int zc, int tiles_x, int tiles_y, int nitems) {
-  step2_body<0>(maps, o1, o2, nullptr, n, zc, tiles_x, tiles_y, nitems);
+  step2_body<0>(Step2One{&maps, o1, o2, nullptr, n, zc, tiles_x, tiles_y}, nitems);
+}
+
+// ---- two FP32-Kahan steps per pass for several problems in one launch
+// (the serving path): the work items of all problems are concatenated; every
+// item carries its problem's tensor maps and outputs, so a problem's result
+// does not depend on which others share the launch.
+struct Batch2Req {
+  Maps2 maps;
+  float *o0, *o1, *o2;  // p, d, e of level n + 2
+  int n, zc, tiles_x, tiles_y;
+};
+
+struct Batch2Params {
+  int count;
+  int item_end[kMaxBatch];  // exclusive prefix of the problems' item counts
+  Batch2Req r[kMaxBatch];
+};
+
+struct Step2Batch {
+  const Batch2Params* bp;
+  __device__ Step2Item operator()(int item) const {
+    int r = 0;
+    while (item >= bp->item_end[r]) ++r;
+    const Batch2Req& q = bp->r[r];
+    const int local = item - (r ? bp->item_end[r - 1] : 0);
+    return Step2One{&q.maps, q.o0, q.o1, q.o2, q.n, q.zc, q.tiles_x, q.tiles_y}(local);
+  }
+};
+
+__global__ void __launch_bounds__(tb2::NT2, 1)
+    k_step2_batch(const __grid_constant__ Batch2Params bp) {
+  step2_body<1>(Step2Batch{&bp}, bp.item_end[bp.count - 1]);
 }
 
 // ------------------------------------ resident time loop (small grids) --
@@ -1491,6 +1545,59 @@ int launch_step2_f32(const Plan& pl, const void* pm, const void* p, void* o1, vo
   maps.q[2] = maps.q[1];
   return launch_step2(k_step2_f32, tb2::smem_bytes<0>(), "k_step2_f32", pl, maps, st,
                       (float*)o1, (float*)o2);
+}
+
+int launch_step2_batch(const BatchStep2* steps, int count, cudaStream_t st) {
+  if (count < 1) return FFPAT_OK;
+  if (count > kMaxBatch)
+    return report(FFPAT_EINVAL, "batched two-step pass: %d requests > %d", count, kMaxBatch);
+  const size_t smem = tb2::smem_bytes<1>() + 1024;
+  static cudaError_t attr = cudaErrorUnknown;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(k_step2_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  });
+  if (attr != cudaSuccess) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "k_step2_batch: %zu bytes of shared memory refused", smem);
+  }
+  static thread_local Batch2Params bp;
+  long long total_points = 0;
+  for (int i = 0; i < count; ++i) total_points += (long long)steps[i].n * steps[i].n * steps[i].n;
+  const int slots = kNumSMs;  // one CTA per SM
+  int total = 0;
+  bp.count = count;
+  for (int i = 0; i < count; ++i) {
+    const BatchStep2& b = steps[i];
+    Batch2Req& r = bp.r[i];
+    if (make_map_box(&r.maps.p, b.p, b.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
+        make_map_box(&r.maps.q[0], b.d, b.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
+        make_map_box(&r.maps.q[1], b.e, b.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
+        make_map_box(&r.maps.q[2], b.kap, b.n, 4, tb2::QW, tb2::QH) != FFPAT_OK)
+      return report(FFPAT_ECUDA, "batched two-step pass: tensor map");
+    r.o0 = b.pout;
+    r.o1 = b.dout;
+    r.o2 = b.eout;
+    r.n = b.n;
+    r.tiles_x = (b.n + TBX - 1) / TBX;
+    r.tiles_y = (b.n + tb2::TH2 - 1) / tb2::TH2;
+    // z-ranges in proportion to this problem's share of the points: about one
+    // round of items over the SMs (every item repeats 4 planes of step A)
+    const double share = (double)b.n * b.n * b.n / (double)total_points;
+    int zchunks = (int)((slots * share) / (r.tiles_x * r.tiles_y) + 1.0);
+    const int zmax = b.n / 8 > 0 ? b.n / 8 : 1;
+    if (zchunks > zmax) zchunks = zmax;
+    if (zchunks < 1) zchunks = 1;
+    r.zc = (b.n + zchunks - 1) / zchunks;
+    zchunks = (b.n + r.zc - 1) / r.zc;
+    total += r.tiles_x * r.tiles_y * zchunks;
+    bp.item_end[i] = total;
+  }
+  const int grid = total < slots ? total : slots;
+  k_step2_batch<<<grid, tb2::NT2, smem, st>>>(bp);
+  count_launch();
+  return check_launch("k_step2_batch");
 }
 
 // ---- the resident time loop (host side)
