@@ -95,7 +95,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// bounded wait: false if the phase did not complete within `cycles`
+// try_wait with a suspend-time hint: a thread whose phase has not completed
+// is suspended (it takes no issue slots) until the phase completes or about
+// `ns` nanoseconds have passed
+__device__ __forceinline__ bool mbar_try_wait_ns(uint64_t* bar, unsigned parity, unsigned ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false if the phase did not complete within `cycles` (the
+// latency-bound resident loop measured slower with the suspend-time hint of
+// mbar_try_wait_ns, 4.86 against 4.70 us per step at 128^3, so this one polls)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long cycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
@@ -637,20 +653,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// try_wait with a suspend-time hint: a thread whose phase has not completed
-// is suspended (it takes no issue slots) until the phase completes or about
-// `ns` nanoseconds have passed
-__device__ __forceinline__ bool mbar_try_wait_ns(uint64_t* bar, unsigned parity, unsigned ns) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
-      : "memory");
-  return ok != 0;
 }
 
 // Bounded wait that also gives up once another thread of the CTA recorded a
