@@ -228,6 +228,22 @@ def test_forward_adjoint_ragged(prec):
     assert rel(host(F.adjoint(prob, dev(c, prob), dev(g, prob))), o.adjoint(c, g, T)) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,nth", [(1, 1), (2, 1), (3, 2), (4, 1), (8, 1)])
+def test_degenerate_grids(prec, n, nth):
+    """The smallest grids and a single angle: one to three cells per axis
+    (the plain kernels, N_s = 2 samples per ray), 4^3 and 8^3 (the TMA and
+    resident paths) with one angle; forward and adjoint against the oracle."""
+    T = 0.3
+    c = as_input(random_speed(n, 650 + n), prec)
+    h = as_input(random_volume(n, 651 + n), prec)
+    g = as_input(random_data(nth, n, 652 + n), prec)
+    prob = F.problem(n, T, nth, prec)
+    assert rel(host(F.forward(prob, dev(c, prob), dev(h, prob))), o.forward(c, h, T, nth)) < TOL[prec]
+    assert rel(host(F.adjoint(prob, dev(c, prob), dev(g, prob))), o.adjoint(c, g, T)) < TOL[prec]
+    assert F.device_status() == 0
+
+
 def test_dot_product_gpu_fp64():
     n, nth, T = 36, 9, 0.7
     prob = F.problem(n, T, nth)
