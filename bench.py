@@ -353,7 +353,9 @@ def run_ours(args):
                                 "caches), DRAM read + write bytes per launch",
               "steps_per_pass": steps_per_pass, "launch_ms": launch_ms,
               "launches_timed": prof["step_launches"], "steps_timed": prof["steps"]}
-    rates = None if args.no_extras else fma_rates(F)
+    rates = None if args.no_extras else guarded(fma_rates, F)
+    if rates is not None and "error" in rates:
+        rates = None
     if kernel == "resident" and args.precision in FLOP_PER_POINT_STEP:
         # the resident time loop (one launch per W): the state never leaves
         # the chip, so HBM is not its bound; report its arithmetic against
@@ -395,16 +397,30 @@ def run_ours(args):
         "clocks": clocks,
     }
     if world == 1 and not args.no_extras:
+        # measured after the timed region; a failure here is recorded in the
+        # line instead of costing it
         line["fma_rates"] = rates
-        line["fp32_vs_fp64"] = extra_precision(F, dev, rates, args.extra_iters)
-        pool = serving_pool(F, dev, args.pool)
-        line["serving"] = extra_serving(F, pool, args)
-        line["serve_vs_fp64"] = extra_serve_vs_fp64(F, dev, pool[:args.fp64_pool], args)
+        line["fp32_vs_fp64"] = guarded(extra_precision, F, dev, rates, args.extra_iters)
+        pool = guarded(serving_pool, F, dev, args.pool)
+        if isinstance(pool, list):
+            line["serving"] = guarded(extra_serving, F, pool, args)
+            line["serve_vs_fp64"] = guarded(extra_serve_vs_fp64, F, dev, pool[:args.fp64_pool],
+                                            args)
+        else:
+            line["serving"] = line["serve_vs_fp64"] = pool
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def guarded(fn, *a):
+    """fn(*a), or {"error": ...} if it raises (for the optional keys of the line)."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
 def fma_rates(F):
