@@ -102,3 +102,9 @@ def test_stencil_path_range(L):
             assert b"stencil path" in L.ffpat_last_error()
     finally:
         L.ffpat_set_stencil_path(0)
+
+
+def test_fma_rate_probe_rejects_bad_arguments(L):
+    out = ctypes.c_double(0.0)
+    assert L.ffpat_debug_fma_rate(3, ctypes.byref(out), None) == F.EINVAL
+    assert L.ffpat_debug_fma_rate(0, None, None) == F.EINVAL
