@@ -285,10 +285,13 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
   if (path >= 2 && !tma)
     return fail(FFPAT_EINVAL, "TMA stencil requested but N = %d or an array alignment rules it out",
                 pl.n);
+  if (path == 3 && pl.prec != FFPAT_FP64 && pl.n > kTwoStepMaxN)
+    return fail(FFPAT_EINVAL, "two-step pass requested but N = %d > %d", pl.n, kTwoStepMaxN);
   long long launches = 0, pairs = 0;
   if (pl.prec == FFPAT_FP32_KAHAN) {
     // two steps per pass halve the HBM bytes (kTwoStepMinN)
-    const bool two = tma && (path == 3 || (path == 0 && pl.n >= kTwoStepMinN));
+    const bool two = tma && pl.n <= kTwoStepMaxN &&
+                     (path == 3 || (path == 0 && pl.n >= kTwoStepMinN));
     void* P[2] = {pl.s[0], pl.s[1]};
     void* D[2] = {pl.s[2], pl.s[4]};
     void* E[2] = {pl.s[3], pl.s[5]};
@@ -317,7 +320,7 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
       ++launches;
     }
     if (result) *result = cur;
-  } else if (pl.prec == FFPAT_FP32 && tma && nt >= 3 &&
+  } else if (pl.prec == FFPAT_FP32 && tma && nt >= 3 && pl.n <= kTwoStepMaxN &&
              (path == 3 || (path == 0 && pl.n >= kTwoStepMinN))) {
     // FP32 three-term, two steps per pass (kTwoStepMinN): 20 B per point per
     // two steps against 32 B.  The pairs (S0, S1) and (S2, S3) alternate as

@@ -141,6 +141,9 @@ struct BatchStep2 {
   int n;
 };
 int launch_step2_batch(const BatchStep2* steps, int count, cudaStream_t st);
+// The two-step passes address a grid with 32-bit offsets: N^3 < 2^32, N <= 1624
+// (larger grids take single steps, whose offsets are 64-bit).
+constexpr int kTwoStepMaxN = 1624;
 constexpr int kMaxBatchRequests = 28;
 
 // Two FP32-Kahan steps in one pass (temporal blocking): reads (p, d, e) at

@@ -177,7 +177,9 @@ int admit(ffpat_server* S, Req& r) {
 float* d_buf(const Req& r, int k) { return (float*)r.pl.s[k ? 4 : 2]; }
 float* e_buf(const Req& r, int k) { return (float*)r.pl.s[k ? 5 : 3]; }
 
-bool two_steps_next(const Req& r) { return r.wstep > 0 && r.pl.nt - r.wstep >= 2; }
+bool two_steps_next(const Req& r) {
+  return r.wstep > 0 && r.pl.nt - r.wstep >= 2 && r.pl.n <= kTwoStepMaxN;
+}
 
 // the single step of request r in this tick (start step or the last one)
 BatchStep next_step(Req& r) {

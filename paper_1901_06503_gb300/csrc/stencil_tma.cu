@@ -811,7 +811,8 @@ __device__ __forceinline__ void step2_body(const Items& items, int nitems) {
       float2 uq0 = zero, uq1 = zero, vq0 = zero, vq1 = zero, kq0 = zero, kq1 = zero;
       const int x = x0 + 2 * lane, y = y0 + warp;
       const bool store = inner && x < n && y < n;  // N % 4 == 0: x + 1 < n as well
-      // offset of plane z0 - 4 + i (unsigned arithmetic: early values wrap and are unused)
+      // offset of plane z0 - 4 + i (unsigned arithmetic: early values wrap and are
+      // unused; N <= kTwoStepMaxN keeps every used offset below 2^32)
       unsigned gi = (unsigned)z0 * plane + (unsigned)y * (unsigned)n + (unsigned)x - 4u * plane;
       for (int ib = 0; ib < M; ib += RING) {
 #pragma unroll
@@ -1527,6 +1528,8 @@ int launch_step2(Kern kern, size_t smem_need, const char* name, const Plan& pl, 
 
 int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void* e, void* po,
                        void* dout, void* eout, cudaStream_t st) {
+  if (pl.n > kTwoStepMaxN)
+    return report(FFPAT_EINVAL, "two-step pass: N = %d > %d (32-bit offsets)", pl.n, kTwoStepMaxN);
   Maps2 maps;
   if (make_map_box(&maps.p, p, pl.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
       make_map_box(&maps.q[0], d, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
@@ -1539,6 +1542,8 @@ int launch_step2_kahan(const Plan& pl, const void* p, const void* d, const void*
 
 int launch_step2_f32(const Plan& pl, const void* pm, const void* p, void* o1, void* o2,
                      cudaStream_t st) {
+  if (pl.n > kTwoStepMaxN)
+    return report(FFPAT_EINVAL, "two-step pass: N = %d > %d (32-bit offsets)", pl.n, kTwoStepMaxN);
   Maps2 maps;
   if (make_map_box(&maps.p, p, pl.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
       make_map_box(&maps.q[0], pm, pl.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
@@ -1572,6 +1577,9 @@ int launch_step2_batch(const BatchStep2* steps, int count, cudaStream_t st) {
   bp.count = count;
   for (int i = 0; i < count; ++i) {
     const BatchStep2& b = steps[i];
+    if (b.n > kTwoStepMaxN)
+      return report(FFPAT_EINVAL, "batched two-step pass: N = %d > %d (32-bit offsets)", b.n,
+                    kTwoStepMaxN);
     Batch2Req& r = bp.r[i];
     if (make_map_box(&r.maps.p, b.p, b.n, 4, tb2::PW, tb2::PH) != FFPAT_OK ||
         make_map_box(&r.maps.q[0], b.d, b.n, 4, tb2::QW, tb2::QH) != FFPAT_OK ||
