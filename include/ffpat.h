@@ -267,11 +267,11 @@ int64_t ffpat_launch_count(void);
  * when N % 4 == 0 for float or N % 2 == 0 for double and all arrays are
  * 16-byte aligned -- for FP32 and FP32-Kahan the whole time loop in one
  * cooperative launch where its work items fit the GPU at once (N <= 128 on
- * GB300) and the stream is not capturing, else two steps per pass from
- * N = 128 on -- else the plain 2.5D kernel), 1 = always the plain kernel,
- * 2 = the single-step TMA kernel, 3 = the two-step TMA kernels for FP32 and
- * FP32-Kahan (single steps for FP64), 4 = the resident time loop (FP32,
- * FP32-Kahan);
+ * GB300) and the stream is not capturing, else two steps per pass for
+ * 128 <= N <= 1624 -- else the plain 2.5D kernel), 1 = always the plain
+ * kernel, 2 = the single-step TMA kernel, 3 = the two-step TMA kernels for
+ * FP32 and FP32-Kahan (N <= 1624; single steps for FP64), 4 = the resident
+ * time loop (FP32, FP32-Kahan);
  * 2, 3 and 4 fail with FFPAT_EINVAL where their kernel cannot be used.  All
  * compute the same steps bit for bit (FP32, FP32-Kahan) or up to rounding
  * order (FP64 plain against TMA); this exists for testing and measurement. */
