@@ -1570,9 +1570,31 @@ int launch_step2_batch(const BatchStep2* steps, int count, cudaStream_t st) {
     return report(FFPAT_ECUDA, "k_step2_batch: %zu bytes of shared memory refused", smem);
   }
   static thread_local Batch2Params bp;
-  long long total_points = 0;
-  for (int i = 0; i < count; ++i) total_points += (long long)steps[i].n * steps[i].n * steps[i].n;
   const int slots = kNumSMs;  // one CTA per SM
+  // z-ranges: the shortest item length (in planes) at which the items of all
+  // requests fit one round over the SMs, so that the longest item -- the
+  // launch's duration -- is as short as one round allows (whole columns if
+  // even those take more than one round)
+  auto tiles_of = [](int n) {
+    return ((n + TBX - 1) / TBX) * ((n + tb2::TH2 - 1) / tb2::TH2);
+  };
+  auto items_at = [&](int len) {
+    long long t = 0;
+    for (int i = 0; i < count; ++i)
+      t += (long long)tiles_of(steps[i].n) * ((steps[i].n + len - 1) / len);
+    return t;
+  };
+  int nmax = 1;
+  for (int i = 0; i < count; ++i) nmax = steps[i].n > nmax ? steps[i].n : nmax;
+  int lo = 1, hi = nmax;  // items_at is non-increasing in len
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (items_at(mid) <= slots)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  const int len = lo;
   int total = 0;
   bp.count = count;
   for (int i = 0; i < count; ++i) {
@@ -1592,15 +1614,8 @@ int launch_step2_batch(const BatchStep2* steps, int count, cudaStream_t st) {
     r.n = b.n;
     r.tiles_x = (b.n + TBX - 1) / TBX;
     r.tiles_y = (b.n + tb2::TH2 - 1) / tb2::TH2;
-    // z-ranges in proportion to this problem's share of the points: about one
-    // round of items over the SMs (every item repeats 4 planes of step A)
-    const double share = (double)b.n * b.n * b.n / (double)total_points;
-    int zchunks = (int)((slots * share) / (r.tiles_x * r.tiles_y) + 1.0);
-    const int zmax = b.n / 8 > 0 ? b.n / 8 : 1;
-    if (zchunks > zmax) zchunks = zmax;
-    if (zchunks < 1) zchunks = 1;
-    r.zc = (b.n + zchunks - 1) / zchunks;
-    zchunks = (b.n + r.zc - 1) / r.zc;
+    r.zc = len < b.n ? len : b.n;
+    const int zchunks = (b.n + r.zc - 1) / r.zc;
     total += r.tiles_x * r.tiles_y * zchunks;
     bp.item_end[i] = total;
   }
