@@ -1326,6 +1326,53 @@ int choose_zchunk(int n, int tiles, int slots) {
   return (n + zchunks - 1) / zchunks;
 }
 
+// z-range (planes) of the items of a batched pass over several problems.
+// The persistent grid walks the items in rounds of `slots`, and an item costs
+// its planes plus a fixed halo of 4, so the launch takes about
+// ceil(items / slots) x (len + 4) plane times: take the len of least such
+// cost (the longest among equals: the least halo work).  Tiles are TBX points
+// wide and tile_h high.  The choice depends only on the sizes, which change
+// only when a request joins or leaves: the last two are kept.
+template <class Batch>
+int batch_zrange(const Batch* steps, int count, int tile_h, int slots) {
+  struct Memo {
+    int count, tile_h, slots, len;
+    int n[kMaxBatch];
+  };
+  static thread_local Memo memo[2] = {};
+  static thread_local int next = 0;
+  for (Memo& m : memo) {
+    if (m.count != count || m.tile_h != tile_h || m.slots != slots) continue;
+    bool same = true;
+    for (int i = 0; i < count && same; ++i) same = m.n[i] == steps[i].n;
+    if (same) return m.len;
+  }
+  int nmax = 1;
+  for (int i = 0; i < count; ++i) nmax = steps[i].n > nmax ? steps[i].n : nmax;
+  int best = nmax;
+  long long best_cost = -1;
+  for (int len = 1; len <= nmax; ++len) {
+    long long items = 0;
+    for (int i = 0; i < count; ++i) {
+      const int n = steps[i].n;
+      items += (long long)((n + TBX - 1) / TBX) * ((n + tile_h - 1) / tile_h) * ((n + len - 1) / len);
+    }
+    const long long cost = (items + slots - 1) / slots * (len + 4);
+    if (best_cost < 0 || cost <= best_cost) {
+      best = len;
+      best_cost = cost;
+    }
+  }
+  Memo& m = memo[next];
+  next ^= 1;
+  m.count = count;
+  m.tile_h = tile_h;
+  m.slots = slots;
+  m.len = best;
+  for (int i = 0; i < count; ++i) m.n[i] = steps[i].n;
+  return best;
+}
+
 template <typename T, int FORM, bool START, int RPT>
 int launch_one(const Plan& pl, const Maps& maps, void* o0, void* o1, void* o2, cudaStream_t st) {
   using G = Geo<T, RPT>;
@@ -1430,9 +1477,8 @@ int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
   });
   static thread_local BatchParams bp;
   int total = 0;
-  long long total_points = 0;
-  for (int i = 0; i < count; ++i) total_points += (long long)steps[i].n * steps[i].n * steps[i].n;
   const int slots = kNumSMs * occ;
+  const int len = batch_zrange(steps, count, G::TH, slots);
   bp.count = count;
   for (int i = 0; i < count; ++i) {
     const BatchStep& b = steps[i];
@@ -1455,14 +1501,8 @@ int launch_step_batch(const BatchStep* steps, int count, cudaStream_t st) {
     r.start = b.start ? 1 : 0;
     r.tiles_x = (b.n + TBX - 1) / TBX;
     r.tiles_y = (b.n + G::TH - 1) / G::TH;
-    // z-chunks in proportion to this request's share of the points
-    const double share = (double)b.n * b.n * b.n / (double)total_points;
-    int zchunks = (int)((4.0 * slots * share) / (r.tiles_x * r.tiles_y) + 1.0);
-    const int zmax = b.n / 8 > 0 ? b.n / 8 : 1;
-    if (zchunks > zmax) zchunks = zmax;
-    if (zchunks < 1) zchunks = 1;
-    r.zc = (b.n + zchunks - 1) / zchunks;
-    zchunks = (b.n + r.zc - 1) / r.zc;
+    r.zc = len < b.n ? len : b.n;
+    const int zchunks = (b.n + r.zc - 1) / r.zc;
     total += r.tiles_x * r.tiles_y * zchunks;
     bp.item_end[i] = total;
   }
@@ -1571,30 +1611,7 @@ int launch_step2_batch(const BatchStep2* steps, int count, cudaStream_t st) {
   }
   static thread_local Batch2Params bp;
   const int slots = kNumSMs;  // one CTA per SM
-  // z-ranges: the shortest item length (in planes) at which the items of all
-  // requests fit one round over the SMs, so that the longest item -- the
-  // launch's duration -- is as short as one round allows (whole columns if
-  // even those take more than one round)
-  auto tiles_of = [](int n) {
-    return ((n + TBX - 1) / TBX) * ((n + tb2::TH2 - 1) / tb2::TH2);
-  };
-  auto items_at = [&](int len) {
-    long long t = 0;
-    for (int i = 0; i < count; ++i)
-      t += (long long)tiles_of(steps[i].n) * ((steps[i].n + len - 1) / len);
-    return t;
-  };
-  int nmax = 1;
-  for (int i = 0; i < count; ++i) nmax = steps[i].n > nmax ? steps[i].n : nmax;
-  int lo = 1, hi = nmax;  // items_at is non-increasing in len
-  while (lo < hi) {
-    const int mid = (lo + hi) / 2;
-    if (items_at(mid) <= slots)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  const int len = lo;
+  const int len = batch_zrange(steps, count, tb2::TH2, slots);
   int total = 0;
   bp.count = count;
   for (int i = 0; i < count; ++i) {
