@@ -697,10 +697,11 @@ def run_op(args):
     for _ in range(args.repeat):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        run()
+        for _ in range(args.inner):
+            run()
         e1.record()
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
+        times.append(e0.elapsed_time(e1) / args.inner)
     prof = F.profile_read()
     F.profile_enable(False)
     res = {"mode": "op", "op": args.op, "path": args.path, "n": n, "angles": args.angles,
@@ -973,6 +974,8 @@ def main():
     ap.add_argument("--angles", type=int, default=90, help="op: projection angles")
     ap.add_argument("--op-steps", type=int, default=16, help="op: leapfrog steps of W")
     ap.add_argument("--repeat", type=int, default=3, help="op: timed repetitions")
+    ap.add_argument("--inner", type=int, default=1,
+                    help="op: calls per timed repetition (ms is per call; for short kernels)")
     ap.add_argument("--seed", type=int, default=0, help="op: random seed")
     ap.add_argument("--ramp", action="store_true", help="op: ramp preconditioner (Lambda)")
     ap.add_argument("--path", type=int, default=0,

@@ -30,6 +30,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -383,6 +384,226 @@ __global__ void __launch_bounds__(1024)
     if (sub) out = out - sub[oo];
     if (mask) out = out * mask[oo];
     g[oo] = out;
+  }
+}
+
+// FP32 P by angle classes (even N, even n_angles = 2h), the forward
+// counterpart of k_backproject_quad.  The bilinear samples of theta's
+// lattice serve four angles: (1) theta's ray k is the sum over its samples m
+// ("row" k); (2) theta + 90 deg's ray k' is the sum of "column" m = k' + koff
+// (koff = (Ns - N)/2) over the lattice points k = -koff .. N + koff - 1 (its
+// samples m' = (N + Ns)/2 - 1 - k); (3) pi - theta's ray k sums the mirror
+// image x -> N-1-x of theta's row k (its sample m' is theta's Ns-1-m', so
+// only the order of the terms differs); (4) pi/2 - theta's ray k' sums that
+// mirror image's column k' + koff, by (2) applied to the pair (pi/2 - theta,
+// pi - theta).  So the lattice spans Ns x Ns points, both indices shifted to
+// 0 .. Ns-1 (kidx = k + koff): rows kidx in [koff, koff + N) and columns m in
+// [koff, koff + N) are rays.  The mirror image of a sample uses the same
+// corner row, fractions and weights, read at the mirrored columns.  Classes
+// j = 0 and 2j = h have only the pair (1), (2).
+// One CTA per (class, plane).  Warp (kg, mg) owns the tiles of 32 lattice
+// rows (lane = row) x 32 samples whose k-tile is kg mod KG and m-tile mg mod
+// MG; tiles whose samples miss the plane (or the band) are skipped, and tiles
+// whose samples all lie on it take a path without per-sample tests.  A lane's
+// running sum over a tile is its row's partial sum; the column partials of an
+// m-tile accumulate per lane over the warp's k-tiles, then one transposed
+// butterfly over the lanes gives the 32 column sums.  The owner adds both to
+// its partial sums in shared memory (rows per m-group, columns per k-group),
+// and the groups are summed at the end.  The plane is staged band by band
+// (one band when it fits) behind a zero border of 4 points, with rows of a
+// pitch = 16 mod 32 words: the 32 lanes of a load lie along theta (direct
+// image) or along its mirror, and this pitch keeps both near two wavefronts
+// per load.  A sample belongs to the band of its lower corner row j0, the
+// first and last bands taking the rows beyond.  Fixed order everywhere:
+// deterministic, no atomics.
+constexpr int kQuadMaxWarps = 16;
+constexpr int kQPad = 4;  // zero border of the staged plane (keeps rows 16-byte aligned)
+
+__host__ __device__ inline int quad_pitch(int n) {
+  const int w = n + 2 * kQPad;
+  return w + ((48 - w % 32) % 32);
+}
+
+// 32 samples of one lattice row per lane (the lanes: 32 consecutive rows),
+// both images; CHECK: skip the samples that do not exist or miss the plane
+// or band (else every sample is known to touch it)
+template <bool CHECK>
+__device__ __forceinline__ void quad_tile(const float* __restrict__ sb, int W, int n,
+                                          long long GX, long long GY, long long dGX,
+                                          long long dGY, bool kin, int mlim, int jmin,
+                                          unsigned jspan, float (&cv)[32], float (&cm)[32],
+                                          float& rt, float& rm) {
+  const int nm1 = n - 1;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int i0 = (int)(GX >> 32), j0 = (int)(GY >> 32);
+    const unsigned lx = (unsigned)GX, ly = (unsigned)GY;
+    GX += dGX;
+    GY += dGY;
+    if (!CHECK ||
+        (kin && i < mlim && (unsigned)(j0 - jmin) <= jspan && (unsigned)(i0 + 1) <= (unsigned)n)) {
+      const float fx = __uint_as_float(0x3f800000u | (lx >> 9)) - 1.0f;
+      const float fy = __uint_as_float(0x3f800000u | (ly >> 9)) - 1.0f;
+      const float* q = sb + j0 * W;
+      const float v00 = q[i0], v10 = q[i0 + 1], v01 = q[i0 + W], v11 = q[i0 + W + 1];
+      const int im = nm1 - i0;  // the mirror column N - 1 - i0
+      const float a0 = q[im], b0 = q[im - 1], a1 = q[im + W], b1 = q[im + W - 1];
+      const float r0 = fmaf(fx, v10 - v00, v00), r1 = fmaf(fx, v11 - v01, v01);
+      const float q0 = fmaf(fx, b0 - a0, a0), q1 = fmaf(fx, b1 - a1, a1);
+      const float v = fmaf(fy, r1 - r0, r0), vm = fmaf(fy, q1 - q0, q0);
+      rt += v;
+      rm += vm;
+      cv[i] += v;
+      cm[i] += vm;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kQuadMaxWarps * 32, 1)
+    k_project_quad(const float* __restrict__ p, float* __restrict__ g,
+                   const float* __restrict__ sub, const float* __restrict__ mask,
+                   const int32_t* __restrict__ tabi, int n, int nth, int ns, int nimg, int tiles,
+                   int kg_n, int mg_n, int bh, int nb, int cpb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int W = quad_pitch(n);
+  const int HB = bh + 2 * kQPad;  // rows of the band buffer
+  const int TW = tiles * 32;      // lattice rows (and samples) rounded up to tiles
+  float* s = reinterpret_cast<float*>(smem_raw);
+  float* rowp = s + (size_t)HB * W;             // [mg][2][TW]: row sums of both images
+  float* colp = rowp + (size_t)mg_n * 2 * TW;   // [kg][2][TW]: column sums of both images
+  const int hh = nth / 2;
+  const int ncls = nth / 4 + 1;
+  const int l = blockIdx.y;  // plane
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthreads = blockDim.x, nwarps = nthreads / 32;
+  const int kg = warp % kg_n, mg = warp / kg_n;
+  const float* __restrict__ sl = p + (size_t)l * n * n;
+  const int koff = (ns - n) / 2;
+
+  // stage rows y_lo - 4 .. y_lo + bh + 3 of the plane (zero outside it)
+  auto stage = [&](int y_lo) {
+    if ((n & 3) == 0 && ((uintptr_t)p & 15) == 0) {
+      // rows of W / 4 float4: column 4q .. 4q+3 holds the plane's 4q-4 .. 4q-1
+      const int W4 = W / 4, n4 = n / 4;
+      for (int yy = warp; yy < HB; yy += nwarps) {
+        const int y = y_lo - kQPad + yy;
+        float4* dst = reinterpret_cast<float4*>(s + (size_t)yy * W);
+        if (y >= 0 && y < n) {
+          const float4* src = reinterpret_cast<const float4*>(sl + (size_t)y * n);
+          for (int q = lane; q < W4; q += 32)
+            dst[q] = (q >= 1 && q <= n4) ? __ldg(src + q - 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          for (int q = lane; q < W4; q += 32) dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    } else {
+      for (int yy = warp; yy < HB; yy += nwarps) {
+        const int y = y_lo - kQPad + yy;
+        for (int xx = lane; xx < W; xx += 32) {
+          const int x = xx - kQPad;
+          s[yy * W + xx] =
+              (x >= 0 && y >= 0 && x < n && y < n) ? __ldg(sl + (size_t)y * n + x) : 0.0f;
+        }
+      }
+    }
+  };
+  if (nb == 1) stage(0);  // one band: staged once for all classes of the CTA
+
+  const int c1 = min(ncls, (int)(blockIdx.x + 1) * cpb);
+  for (int j = blockIdx.x * cpb; j < c1; ++j) {  // angle class: theta_j in [0, 45] degrees
+    const bool four = j != 0 && 2 * j != hh;
+    __syncthreads();  // the previous class's sums are read
+    for (int i = tid; i < (mg_n + kg_n) * 2 * TW; i += nthreads) rowp[i] = 0.0f;
+    // fixed-point coordinates at twice the scale of the other FP32 kernels
+    // (2^32 per cell): the corner index is the high word and the fraction the
+    // low word, the same corners and fraction bits as frac31 of the 2^31 form.
+    // cos, sin >= 0: x grows along the rows and falls along the samples, y
+    // grows along both, so a tile's extremes sit at known corners
+    const long long CS = 2LL * tabi[j], SN = 2LL * tabi[nth + j];
+    const long long c2 = (long long)(n - 1) << 31;
+    const long long dGX = -2 * SN, dGY = 2 * CS;
+    for (int b = 0; b < nb; ++b) {
+      const int y_lo = b * bh;
+      if (nb > 1) {
+        __syncthreads();  // the previous band's readers are done
+        stage(y_lo);
+      }
+      __syncthreads();
+      // corner rows whose samples can be nonzero and belong to this band
+      const int jmin = b == 0 ? -1 : y_lo;
+      const int jmax = b == nb - 1 ? n - 1 : min(y_lo + bh, n) - 1;
+      const unsigned jspan = (unsigned)(jmax - jmin);
+      const float* sb = s + (kQPad - y_lo) * W + kQPad;  // element (row j0, column i0)
+      for (int mt = mg; mt < tiles; mt += mg_n) {
+        const int m0 = mt * 32;
+        const long long v2 = 2LL * m0 + 1 - ns, vb = v2 + 62;
+        const long long xa = c2 - vb * SN, xb = c2 - v2 * SN;  // x at the low / high samples
+        const long long ya = c2 + v2 * CS, yb = c2 + vb * CS;  // y at them
+        const int mlim = ns - m0;  // samples m0 + i with i < mlim exist
+        float cv[32], cm[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) cv[i] = cm[i] = 0.0f;
+        bool any = false;
+        for (int kt = kg; kt < tiles; kt += kg_n) {
+          const int r0i = kt * 32;  // first lattice row of the tile
+          const long long ua = 2LL * (r0i - koff) + 1 - n, ub = ua + 62;
+          const long long xlo = (xa + ua * CS) >> 32, xhi = (xb + ub * CS) >> 32;
+          const long long ylo = (ya + ua * SN) >> 32, yhi = (yb + ub * SN) >> 32;
+          // no sample of the tile touches the plane within this band
+          if (xhi < -1 || xlo > n - 1 || yhi < jmin || ylo > jmax) continue;
+          any = true;
+          const int kidx = r0i + lane;
+          const long long u2 = ua + 2 * lane;
+          const long long GX = c2 + u2 * CS - v2 * SN;
+          const long long GY = c2 + u2 * SN + v2 * CS;
+          float rt = 0.0f, rm = 0.0f;
+          if (xlo >= -1 && xhi <= n - 1 && ylo >= jmin && yhi <= jmax && r0i + 31 < ns &&
+              mlim >= 32)
+            quad_tile<false>(sb, W, n, GX, GY, dGX, dGY, true, 32, jmin, jspan, cv, cm, rt, rm);
+          else
+            quad_tile<true>(sb, W, n, GX, GY, dGX, dGY, kidx < ns, mlim, jmin, jspan, cv, cm, rt,
+                            rm);
+          float* rp = rowp + (size_t)mg * 2 * TW + kidx;
+          rp[0] += rt;
+          rp[TW] += rm;
+        }
+        if (!any) continue;
+        // transposed butterfly: afterwards lane t holds the sums over the 32
+        // lanes of cv[t] and cm[t]
+#pragma unroll
+        for (int sh = 16; sh >= 1; sh >>= 1) {
+          const bool up = (lane & sh) != 0;
+#pragma unroll
+          for (int i = 0; i < sh; ++i) {
+            const float sv = up ? cv[i] : cv[i + sh], kv = up ? cv[i + sh] : cv[i];
+            const float sm = up ? cm[i] : cm[i + sh], km = up ? cm[i + sh] : cm[i];
+            cv[i] = kv + __shfl_xor_sync(0xffffffffu, sv, sh);
+            cm[i] = km + __shfl_xor_sync(0xffffffffu, sm, sh);
+          }
+        }
+        float* cp = colp + (size_t)kg * 2 * TW + m0 + lane;
+        cp[0] += cv[0];
+        cp[TW] += cm[0];
+      }
+    }
+    __syncthreads();
+    const float scale = 2.0f / (float)nimg;
+    const int nout = four ? 4 : 2;
+    for (int w = tid; w < nout * n; w += nthreads) {
+      const int which = w / n, kk = w % n;
+      // row sums of theta and pi - theta; column sums of theta + 90 and pi/2 - theta
+      const bool row = which == 0 || which == 2;
+      const float* src = (row ? rowp : colp) + (which >= 2 ? TW : 0) + koff + kk;
+      const int groups = row ? mg_n : kg_n;
+      float acc = 0.0f;
+      for (int q = 0; q < groups; ++q) acc += src[(size_t)q * 2 * TW];
+      const int ang = which == 0 ? j : which == 1 ? j + hh : which == 2 ? nth - j : hh - j;
+      const size_t oo = ((size_t)ang * n + l) * n + kk;
+      float out = scale * acc;
+      if (sub) out = out - sub[oo];
+      if (mask) out = out * mask[oo];
+      g[oo] = out;
+    }
   }
 }
 
@@ -847,15 +1068,105 @@ static bool band_plan(const Plan& pl, int* group, int* bh, int* nb, size_t* sm) 
   return true;
 }
 
+// FFPAT_PROJECT_QUAD=0 turns the angle-class projection off, =1 uses it for
+// every even case (comparison knobs)
+static bool project_quad_off() {
+  static const bool off = [] {
+    const char* e = getenv("FFPAT_PROJECT_QUAD");
+    return e && e[0] == '0';
+  }();
+  return off;
+}
+static bool project_quad_forced() {
+  static const bool on = [] {
+    const char* e = getenv("FFPAT_PROJECT_QUAD");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+// Shape of the angle-class projection (FP32, even N, even angle count): a
+// lattice of `tiles` x `tiles` tiles of 32 x 32, warps kg x mg, and the plane
+// in nb bands of bh rows.  When the plane fits with the partial sums in half
+// the shared memory of an SM, one band and 2 x 4 warps (two CTAs per SM);
+// else 4 x 4 warps and bands as tall as the rest of 220 KB allows.
+constexpr size_t kQuadSmem = 220 * 1024;
+
+static bool quad_plan(const Plan& pl, int* tiles, int* kg, int* mg, int* bh, int* nb,
+                      size_t* sm, int* cpb) {
+  if (pl.esize != 4 || pl.n % 2 != 0 || pl.nth % 2 != 0 || project_quad_off()) return false;
+  // where the one-angle kernel keeps the whole plane at two CTAs per SM it is
+  // the faster one (measured on GB300 at 128^3: 269 against 325 us a launch)
+  if (project_smem_bytes(pl) <= 110 * 1024 && !project_quad_forced()) return false;
+  const int T = (pl.ns + 31) / 32;
+  const size_t W = (size_t)quad_pitch(pl.n);
+  auto state = [&](int g1, int g2) { return (size_t)(g1 + g2) * 2 * T * 32 * 4; };
+  int KG = 2, MG = 4, rows_b = pl.n, nbands = 1;
+  size_t need = (size_t)(pl.n + 2 * kQPad) * W * 4 + state(KG, MG);
+  if (need > 110 * 1024) {
+    KG = 4;
+    MG = 4;
+    const size_t st = state(KG, MG);
+    need = (size_t)(pl.n + 2 * kQPad) * W * 4 + st;
+    if (need > kQuadSmem) {
+      const long long rows = st < kQuadSmem ? (long long)((kQuadSmem - st) / (W * 4)) - 2 * kQPad : 0;
+      if (rows < 16) return false;
+      nbands = (int)((pl.n + rows - 1) / rows);
+      rows_b = (pl.n + nbands - 1) / nbands;
+      need = (size_t)(rows_b + 2 * kQPad) * W * 4 + st;
+    }
+  }
+  *tiles = T;
+  *kg = KG;
+  *mg = MG;
+  *bh = rows_b;
+  *nb = nbands;
+  *sm = need;
+  // one band: several classes per CTA share the staged plane, as long as the
+  // grid keeps about four CTAs per SM
+  const int ncls = pl.nth / 4 + 1;
+  int c = 1;
+  if (nbands == 1)
+    while (c < ncls && (long long)((ncls + 2 * c - 1) / (2 * c)) * pl.n >= 4LL * kNumSMs) c *= 2;
+  *cpb = c;
+  return true;
+}
+
 size_t project_scratch_bytes(const Plan& pl) {
-  int group, bh, nb;
+  int group, bh, nb, tl, kg, mg, cpb;
   size_t sm;
-  if (project_smem_bytes(pl) <= 200 * 1024 || band_plan(pl, &group, &bh, &nb, &sm)) return 0;
+  if (quad_plan(pl, &tl, &kg, &mg, &bh, &nb, &sm, &cpb) || project_smem_bytes(pl) <= 200 * 1024 ||
+      band_plan(pl, &group, &bh, &nb, &sm))
+    return 0;
   return (size_t)pl.n * pl.n * pl.n * pl.esize;
 }
 
 int launch_project(const Plan& pl, const void* p, void* g, const void* sub, cudaStream_t st,
                    const void* mask, void* scratch) {
+  {
+    // FP32, even N and angle count: one weight evaluation per four angles
+    int tl, kg, mg, bh, nb, cpb;
+    size_t sm;
+    if (quad_plan(pl, &tl, &kg, &mg, &bh, &nb, &sm, &cpb)) {
+      static std::once_flag once;
+      static cudaError_t attr = cudaSuccess;
+      std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_project_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kQuadSmem);
+      });
+      if (attr != cudaSuccess) {
+        cudaGetLastError();
+        return report(FFPAT_ECUDA, "k_project_quad: %zu bytes of shared memory refused", sm);
+      }
+      const dim3 grid((pl.nth / 4 + cpb) / cpb, pl.n);
+      k_project_quad<<<grid, kg * mg * 32, sm, st>>>((const float*)p, (float*)g,
+                                                     (const float*)sub, (const float*)mask,
+                                                     pl.tabi, pl.n, pl.nth, pl.ns, pl.nimg, tl,
+                                                     kg, mg, bh, nb, cpb);
+      count_launch();
+      return check_launch("k_project_quad");
+    }
+  }
   const size_t smem = project_smem_bytes(pl);
   if (smem <= 200 * 1024) {
     // one CTA per (plane, group of 8 angles); the padded plane is read once per CTA

@@ -121,13 +121,90 @@ def test_project_fp32_global_fallback(tmp_path):
     assert rel(g, o.project(p.astype(np.float64), nth)) < 5e-7
 
 
+# FP32 with even N and an even angle count 2h evaluates each bilinear sample
+# of theta's lattice once for the four angles theta, theta + 90, 180 - theta,
+# 90 - theta (k_project_quad) where the plane takes more than 110 KB (from N
+# ~ 160: (192, 12) in one band, the N = 232 case of the large planes band by
+# band); smaller planes and odd cases take the one-angle kernels.  The small
+# cases run the four-angle kernel as well, forced in a child process: several
+# 32 x 32 lattice tiles with ragged edges, h odd and even (the 45-degree
+# class), the pair 0 / 90 alone
+PROJ_CASES = [(24, 6), (33, 7), (40, 12), (64, 90), (24, 4), (48, 16), (16, 2), (100, 10),
+              (130, 14), (40, 13), (192, 12)]
+
+
+def _check_angles(g, want, tol=1e-6):
+    assert rel(g, want) < 5e-7
+    for a in range(want.shape[0]):  # every angle: each class writes four of them
+        assert rel(g[a], want[a]) < tol, a
+
+
 @pytest.mark.parametrize("prec", [F.FP32])
-@pytest.mark.parametrize("n,nth", [(24, 6), (33, 7)])
+@pytest.mark.parametrize("n,nth", PROJ_CASES)
 def test_project_fp32(n, nth, prec):
     p = random_volume(n, 200 + n)
     prob = F.problem(n, 1.0, nth, prec)
     g = host(F.project(prob, dev(p, prob)))
-    assert rel(g, o.project(as_input(p, prec), nth)) < 5e-7
+    _check_angles(g, o.project(as_input(p, prec), nth))
+
+
+def _project_child(tmp_path, cases, env_key, env_val, seed0):
+    """Run F.project in a child process with one environment knob set."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for i, (n, nth) in enumerate(cases):
+        np.save(tmp_path / f"p{i}.npy", random_volume(n, seed0 + n).astype(np.float32))
+    code = (
+        "import sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "from paper_1901_06503_gb300 import ffpat as F\n"
+        f"for i, (n, nth) in enumerate({cases!r}):\n"
+        f"    p = np.load({str(tmp_path)!r} + f'/p{{i}}.npy')\n"
+        "    prob = F.problem(n, 1.0, nth, F.FP32)\n"
+        "    g = F.project(prob, torch.as_tensor(p, device='cuda'))\n"
+        "    torch.cuda.synchronize()\n"
+        f"    np.save({str(tmp_path)!r} + f'/g{{i}}.npy', g.cpu().numpy())\n")
+    env = dict(os.environ, **{env_key: env_val})
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, timeout=300)
+    out = []
+    for i, (n, nth) in enumerate(cases):
+        p = np.load(tmp_path / f"p{i}.npy").astype(np.float64)
+        g = np.load(tmp_path / f"g{i}.npy").astype(np.float64)
+        out.append((p, g))
+    return out
+
+
+def test_project_fp32_four_angle_kernel_small(tmp_path):
+    """The four-angle projection on the small even cases (FFPAT_PROJECT_QUAD=1
+    in a child process), every angle against the oracle."""
+    cases = [(24, 6), (40, 12), (64, 90), (24, 4), (48, 16), (16, 2), (100, 10), (130, 14)]
+    for (n, nth), (p, g) in zip(cases, _project_child(tmp_path, cases, "FFPAT_PROJECT_QUAD", "1",
+                                                       230)):
+        _check_angles(g, o.project(p, nth))
+
+
+def test_project_fp32_one_angle_kernels(tmp_path):
+    """The one-angle FP32 projections on cases the four-angle kernel takes by
+    default (whole plane in shared memory at N = 192; band by band at 232),
+    forced with FFPAT_PROJECT_QUAD=0 in a child process."""
+    cases = [(24, 6), (192, 12), (232, 6)]
+    for (n, nth), (p, g) in zip(cases, _project_child(tmp_path, cases, "FFPAT_PROJECT_QUAD", "0",
+                                                       210)):
+        assert rel(g, o.project(p, nth)) < 5e-7, (n, nth)
+
+
+def test_project_fp32_deterministic():
+    """The four-angle projection sums in a fixed order: two calls agree bit
+    for bit (whole plane at N = 192, band by band at N = 232)."""
+    for n, nth in ((192, 12), (232, 6)):
+        p = random_volume(n, 220 + n)
+        prob = F.problem(n, 1.0, nth, F.FP32)
+        pd = dev(p, prob)
+        g1 = host(F.project(prob, pd))
+        g2 = host(F.project(prob, pd))
+        assert np.array_equal(g1, g2)
 
 
 # FP32 with even N and an even angle count 2h applies each weight set to the
