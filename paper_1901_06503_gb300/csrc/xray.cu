@@ -402,12 +402,12 @@ __global__ void __launch_bounds__(1024)
 // corner row, fractions and weights, read at the mirrored columns.  Classes
 // j = 0 and 2j = h have only the pair (1), (2).
 // One CTA per (class, plane).  Warp (kg, mg) owns the tiles of 32 lattice
-// rows (lane = row) x 32 samples whose k-tile is kg mod KG and m-tile mg mod
+// rows (lane = row) x 16 samples whose k-tile is kg mod KG and m-tile mg mod
 // MG; tiles whose samples miss the plane (or the band) are skipped, and tiles
 // whose samples all lie on it take a path without per-sample tests.  A lane's
 // running sum over a tile is its row's partial sum; the column partials of an
 // m-tile accumulate per lane over the warp's k-tiles, then one transposed
-// butterfly over the lanes gives the 32 column sums.  The owner adds both to
+// butterfly over the lanes gives the 16 column sums.  The owner adds both to
 // its partial sums in shared memory (rows per m-group, columns per k-group),
 // and the groups are summed at the end.  The plane is staged band by band
 // (one band when it fits) behind a zero border of 4 points, with rows of a
@@ -424,18 +424,20 @@ __host__ __device__ inline int quad_pitch(int n) {
   return w + ((48 - w % 32) % 32);
 }
 
-// 32 samples of one lattice row per lane (the lanes: 32 consecutive rows),
+constexpr int kQuadTM = 16;  // samples of a lattice tile (its rows: the 32 lanes)
+
+// kQuadTM samples of one lattice row per lane (the lanes: 32 consecutive rows),
 // both images; CHECK: skip the samples that do not exist or miss the plane
 // or band (else every sample is known to touch it)
 template <bool CHECK>
 __device__ __forceinline__ void quad_tile(const float* __restrict__ sb, int W, int n,
                                           long long GX, long long GY, long long dGX,
                                           long long dGY, bool kin, int mlim, int jmin,
-                                          unsigned jspan, float (&cv)[32], float (&cm)[32],
-                                          float& rt, float& rm) {
+                                          unsigned jspan, float (&cv)[kQuadTM],
+                                          float (&cm)[kQuadTM], float& rt, float& rm) {
   const int nm1 = n - 1;
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < kQuadTM; ++i) {
     const int i0 = (int)(GX >> 32), j0 = (int)(GY >> 32);
     const unsigned lx = (unsigned)GX, ly = (unsigned)GY;
     GX += dGX;
@@ -534,15 +536,16 @@ __global__ void __launch_bounds__(kQuadMaxWarps * 32, 1)
       const int jmax = b == nb - 1 ? n - 1 : min(y_lo + bh, n) - 1;
       const unsigned jspan = (unsigned)(jmax - jmin);
       const float* sb = s + (kQPad - y_lo) * W + kQPad;  // element (row j0, column i0)
-      for (int mt = mg; mt < tiles; mt += mg_n) {
-        const int m0 = mt * 32;
-        const long long v2 = 2LL * m0 + 1 - ns, vb = v2 + 62;
+      const int mtiles = (ns + kQuadTM - 1) / kQuadTM;
+      for (int mt = mg; mt < mtiles; mt += mg_n) {
+        const int m0 = mt * kQuadTM;
+        const long long v2 = 2LL * m0 + 1 - ns, vb = v2 + 2 * (kQuadTM - 1);
         const long long xa = c2 - vb * SN, xb = c2 - v2 * SN;  // x at the low / high samples
         const long long ya = c2 + v2 * CS, yb = c2 + vb * CS;  // y at them
         const int mlim = ns - m0;  // samples m0 + i with i < mlim exist
-        float cv[32], cm[32];
+        float cv[kQuadTM], cm[kQuadTM];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) cv[i] = cm[i] = 0.0f;
+        for (int i = 0; i < kQuadTM; ++i) cv[i] = cm[i] = 0.0f;
         bool any = false;
         for (int kt = kg; kt < tiles; kt += kg_n) {
           const int r0i = kt * 32;  // first lattice row of the tile
@@ -558,8 +561,9 @@ __global__ void __launch_bounds__(kQuadMaxWarps * 32, 1)
           const long long GY = c2 + u2 * SN + v2 * CS;
           float rt = 0.0f, rm = 0.0f;
           if (xlo >= -1 && xhi <= n - 1 && ylo >= jmin && yhi <= jmax && r0i + 31 < ns &&
-              mlim >= 32)
-            quad_tile<false>(sb, W, n, GX, GY, dGX, dGY, true, 32, jmin, jspan, cv, cm, rt, rm);
+              mlim >= kQuadTM)
+            quad_tile<false>(sb, W, n, GX, GY, dGX, dGY, true, kQuadTM, jmin, jspan, cv, cm, rt,
+                             rm);
           else
             quad_tile<true>(sb, W, n, GX, GY, dGX, dGY, kidx < ns, mlim, jmin, jspan, cv, cm, rt,
                             rm);
@@ -568,10 +572,16 @@ __global__ void __launch_bounds__(kQuadMaxWarps * 32, 1)
           rp[TW] += rm;
         }
         if (!any) continue;
-        // transposed butterfly: afterwards lane t holds the sums over the 32
-        // lanes of cv[t] and cm[t]
+        // column sums over the 32 lanes: fold the two half-warps, then a
+        // transposed butterfly over 16 lanes leaves the sum of sample t & 15
+        // in lane t
 #pragma unroll
-        for (int sh = 16; sh >= 1; sh >>= 1) {
+        for (int i = 0; i < kQuadTM; ++i) {
+          cv[i] += __shfl_xor_sync(0xffffffffu, cv[i], 16);
+          cm[i] += __shfl_xor_sync(0xffffffffu, cm[i], 16);
+        }
+#pragma unroll
+        for (int sh = kQuadTM / 2; sh >= 1; sh >>= 1) {
           const bool up = (lane & sh) != 0;
 #pragma unroll
           for (int i = 0; i < sh; ++i) {
@@ -581,9 +591,11 @@ __global__ void __launch_bounds__(kQuadMaxWarps * 32, 1)
             cm[i] = km + __shfl_xor_sync(0xffffffffu, sm, sh);
           }
         }
-        float* cp = colp + (size_t)kg * 2 * TW + m0 + lane;
-        cp[0] += cv[0];
-        cp[TW] += cm[0];
+        if (lane < kQuadTM) {
+          float* cp = colp + (size_t)kg * 2 * TW + m0 + lane;
+          cp[0] += cv[0];
+          cp[TW] += cm[0];
+        }
       }
     }
     __syncthreads();
@@ -1068,21 +1080,13 @@ static bool band_plan(const Plan& pl, int* group, int* bh, int* nb, size_t* sm) 
   return true;
 }
 
-// FFPAT_PROJECT_QUAD=0 turns the angle-class projection off, =1 uses it for
-// every even case (comparison knobs)
+// FFPAT_PROJECT_QUAD=0 turns the angle-class projection off (a comparison knob)
 static bool project_quad_off() {
   static const bool off = [] {
     const char* e = getenv("FFPAT_PROJECT_QUAD");
     return e && e[0] == '0';
   }();
   return off;
-}
-static bool project_quad_forced() {
-  static const bool on = [] {
-    const char* e = getenv("FFPAT_PROJECT_QUAD");
-    return e && e[0] == '1';
-  }();
-  return on;
 }
 
 // Shape of the angle-class projection (FP32, even N, even angle count): a
@@ -1095,9 +1099,6 @@ constexpr size_t kQuadSmem = 220 * 1024;
 static bool quad_plan(const Plan& pl, int* tiles, int* kg, int* mg, int* bh, int* nb,
                       size_t* sm, int* cpb) {
   if (pl.esize != 4 || pl.n % 2 != 0 || pl.nth % 2 != 0 || project_quad_off()) return false;
-  // where the one-angle kernel keeps the whole plane at two CTAs per SM it is
-  // the faster one (measured on GB300 at 128^3: 269 against 325 us a launch)
-  if (project_smem_bytes(pl) <= 110 * 1024 && !project_quad_forced()) return false;
   const int T = (pl.ns + 31) / 32;
   const size_t W = (size_t)quad_pitch(pl.n);
   auto state = [&](int g1, int g2) { return (size_t)(g1 + g2) * 2 * T * 32 * 4; };

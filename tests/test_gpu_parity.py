@@ -123,12 +123,10 @@ def test_project_fp32_global_fallback(tmp_path):
 
 # FP32 with even N and an even angle count 2h evaluates each bilinear sample
 # of theta's lattice once for the four angles theta, theta + 90, 180 - theta,
-# 90 - theta (k_project_quad) where the plane takes more than 110 KB (from N
-# ~ 160: (192, 12) in one band, the N = 232 case of the large planes band by
-# band); smaller planes and odd cases take the one-angle kernels.  The small
-# cases run the four-angle kernel as well, forced in a child process: several
-# 32 x 32 lattice tiles with ragged edges, h odd and even (the 45-degree
-# class), the pair 0 / 90 alone
+# 90 - theta (k_project_quad); odd cases take the one-angle kernels.  The
+# cases span several 32 x 16 lattice tiles with ragged edges, h odd and even
+# (the 45-degree class), the pair 0 / 90 alone, one band (up to N = 192) and
+# band by band (the N = 232 case of the large planes)
 PROJ_CASES = [(24, 6), (33, 7), (40, 12), (64, 90), (24, 4), (48, 16), (16, 2), (100, 10),
               (130, 14), (40, 13), (192, 12)]
 
@@ -176,20 +174,11 @@ def _project_child(tmp_path, cases, env_key, env_val, seed0):
     return out
 
 
-def test_project_fp32_four_angle_kernel_small(tmp_path):
-    """The four-angle projection on the small even cases (FFPAT_PROJECT_QUAD=1
-    in a child process), every angle against the oracle."""
-    cases = [(24, 6), (40, 12), (64, 90), (24, 4), (48, 16), (16, 2), (100, 10), (130, 14)]
-    for (n, nth), (p, g) in zip(cases, _project_child(tmp_path, cases, "FFPAT_PROJECT_QUAD", "1",
-                                                       230)):
-        _check_angles(g, o.project(p, nth))
-
-
 def test_project_fp32_one_angle_kernels(tmp_path):
     """The one-angle FP32 projections on cases the four-angle kernel takes by
-    default (whole plane in shared memory at N = 192; band by band at 232),
-    forced with FFPAT_PROJECT_QUAD=0 in a child process."""
-    cases = [(24, 6), (192, 12), (232, 6)]
+    default (whole plane in shared memory; band by band at N = 232), forced
+    with FFPAT_PROJECT_QUAD=0 in a child process."""
+    cases = [(24, 6), (64, 90), (192, 12), (232, 6)]
     for (n, nth), (p, g) in zip(cases, _project_child(tmp_path, cases, "FFPAT_PROJECT_QUAD", "0",
                                                        210)):
         assert rel(g, o.project(p, nth)) < 5e-7, (n, nth)
@@ -197,8 +186,8 @@ def test_project_fp32_one_angle_kernels(tmp_path):
 
 def test_project_fp32_deterministic():
     """The four-angle projection sums in a fixed order: two calls agree bit
-    for bit (whole plane at N = 192, band by band at N = 232)."""
-    for n, nth in ((192, 12), (232, 6)):
+    for bit (whole plane, and band by band at N = 232)."""
+    for n, nth in ((64, 90), (192, 12), (232, 6)):
         p = random_volume(n, 220 + n)
         prob = F.problem(n, 1.0, nth, F.FP32)
         pd = dev(p, prob)
