@@ -572,13 +572,16 @@ __global__ void __launch_bounds__(kQuadMaxWarps * 32, 1)
           rp[TW] += rm;
         }
         if (!any) continue;
-        // column sums over the 32 lanes: fold the two half-warps, then a
-        // transposed butterfly over 16 lanes leaves the sum of sample t & 15
-        // in lane t
+        // column sums over the 32 lanes: fold the lane groups above the tile
+        // length, then a transposed butterfly over the kQuadTM lanes of each
+        // group leaves the sum of sample t mod kQuadTM in lane t
 #pragma unroll
-        for (int i = 0; i < kQuadTM; ++i) {
-          cv[i] += __shfl_xor_sync(0xffffffffu, cv[i], 16);
-          cm[i] += __shfl_xor_sync(0xffffffffu, cm[i], 16);
+        for (int sh = 16; sh >= kQuadTM; sh >>= 1) {
+#pragma unroll
+          for (int i = 0; i < kQuadTM; ++i) {
+            cv[i] += __shfl_xor_sync(0xffffffffu, cv[i], sh);
+            cm[i] += __shfl_xor_sync(0xffffffffu, cm[i], sh);
+          }
         }
 #pragma unroll
         for (int sh = kQuadTM / 2; sh >= 1; sh >>= 1) {
