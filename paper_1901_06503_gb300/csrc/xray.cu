@@ -825,6 +825,10 @@ struct Sums3 {
   int kb, mb;
 };
 
+// IN: the voxel lies within (N - 6) / 2 grid units of the plane's centre,
+// where every candidate detector and sample of every angle exists (its
+// rotated coordinates stay within (N - 5) / 2), so no validity factors.
+template <bool IN>
 __device__ __forceinline__ Sums3 candidate_sums(long long KK, long long MM, float cs, float sn,
                                                 int ns, int mrot) {
   Sums3 o;
@@ -838,8 +842,10 @@ __device__ __forceinline__ Sums3 candidate_sums(long long KK, long long MM, floa
   float mv[3], mv2[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    mv[q] = (unsigned)(o.mb + q) < (unsigned)ns ? 1.0f : 0.0f;
-    mv2[q] = (unsigned)(mrot - (o.kb + q)) < (unsigned)ns ? 1.0f : 0.0f;
+    if (!IN) {
+      mv[q] = (unsigned)(o.mb + q) < (unsigned)ns ? 1.0f : 0.0f;
+      mv2[q] = (unsigned)(mrot - (o.kb + q)) < (unsigned)ns ? 1.0f : 0.0f;
+    }
     o.r[q] = 0.0f;
     o.c[q] = 0.0f;
   }
@@ -850,27 +856,75 @@ __device__ __forceinline__ Sums3 candidate_sums(long long KK, long long MM, floa
       const float a = a0 + (float)i * cs - (float)jj * sn;
       const float b = b0 + (float)i * sn + (float)jj * cs;
       const float w = hat1f(a) * hat1f(b);
-      o.r[i] = fmaf(w, mv[jj], o.r[i]);
-      o.c[jj] = fmaf(w, mv2[i], o.c[jj]);
+      if (IN) {
+        o.r[i] += w;
+        o.c[jj] += w;
+      } else {
+        o.r[i] = fmaf(w, mv[jj], o.r[i]);
+        o.c[jj] = fmaf(w, mv2[i], o.c[jj]);
+      }
     }
   return o;
 }
 
 // acc += sum_i r_i row[kb + i] + sum_j c_j row2[mb + j - koff] (valid detectors)
+template <bool IN>
 __device__ __forceinline__ float apply_sums(const Sums3& s, const float* __restrict__ row,
                                             const float* __restrict__ row2, int n, int koff,
                                             float acc) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const int k = s.kb + i;
-    if ((unsigned)k < (unsigned)n) acc = fmaf(s.r[i], __ldg(row + k), acc);
+    if (IN || (unsigned)k < (unsigned)n) acc = fmaf(s.r[i], __ldg(row + k), acc);
   }
 #pragma unroll
   for (int jj = 0; jj < 3; ++jj) {
     const int k2 = s.mb + jj - koff;
-    if ((unsigned)k2 < (unsigned)n) acc = fmaf(s.c[jj], __ldg(row2 + k2), acc);
+    if (IN || (unsigned)k2 < (unsigned)n) acc = fmaf(s.c[jj], __ldg(row2 + k2), acc);
   }
   return acc;
+}
+
+// The angle classes of k_backproject_quad for one voxel pair (u, u').
+template <bool IN>
+__device__ __forceinline__ void bp_quad_classes(const float* __restrict__ gl, size_t rows, int n,
+                                                int nth, int ns, int hh, int nclass, int koff,
+                                                int mrot, long long X2, long long Y2,
+                                                long long ck, long long cm, bool in, int tid,
+                                                const float* __restrict__ tabf,
+                                                const int32_t* __restrict__ tabi, float* s_cs,
+                                                float* s_sn, int* s_CS, int* s_SN, float& acc_u,
+                                                float& acc_m) {
+  for (int ja = 0; ja < nclass; ja += kAngleChunk) {
+    const int jn = min(kAngleChunk, nclass - ja);
+    __syncthreads();
+    for (int t = tid; t < jn; t += 256) {
+      s_cs[t] = tabf[ja + t];
+      s_sn[t] = tabf[nth + ja + t];
+      s_CS[t] = tabi[ja + t];
+      s_SN[t] = tabi[nth + ja + t];
+    }
+    __syncthreads();
+    if (!in) continue;
+    for (int t = 0; t < jn; ++t) {
+      const int j = ja + t;
+      const float cs = s_cs[t], sn = s_sn[t];
+      const long long CS = s_CS[t], SN = s_SN[t];
+      const long long A = X2 * CS, B = Y2 * SN, C = Y2 * CS, D = X2 * SN;
+      const Sums3 su = candidate_sums<IN>(A + B + ck, C - D + cm, cs, sn, ns, mrot);
+      const Sums3 sm = candidate_sums<IN>(-A + B + ck, C + D + cm, cs, sn, ns, mrot);
+      const float* __restrict__ r0 = gl + (size_t)j * rows;         // theta_j
+      const float* __restrict__ r1 = gl + (size_t)(j + hh) * rows;  // theta_j + 90
+      acc_u = apply_sums<IN>(su, r0, r1, n, koff, acc_u);
+      acc_m = apply_sums<IN>(sm, r0, r1, n, koff, acc_m);
+      if (j != 0 && 2 * j != hh) {
+        const float* __restrict__ r2 = gl + (size_t)(nth - j) * rows;  // pi - theta_j
+        const float* __restrict__ r3 = gl + (size_t)(hh - j) * rows;   // pi/2 - theta_j
+        acc_m = apply_sums<IN>(su, r2, r3, n, koff, acc_m);
+        acc_u = apply_sums<IN>(sm, r2, r3, n, koff, acc_u);
+      }
+    }
+  }
 }
 
 // FP32 P^T using two exact symmetries of the sample lattices (even N, even
@@ -909,37 +963,21 @@ __global__ void __launch_bounds__(256)
   const long long ck = (long long)(n - 1) << 30, cm = (long long)(ns - 1) << 30;
   const size_t rows = (size_t)n * n;    // stride between the angles' data
   const float* __restrict__ gl = g + (size_t)l * n;
+  // the CTA's voxels (and their mirrors) all within (N - 6) / 2 of the centre:
+  // the loop without validity tests
+  const float cc = 0.5f * (float)(n - 1);
+  const float x0 = (float)(blockIdx.x * 32), x1 = (float)min((int)blockIdx.x * 32 + 31, nh - 1);
+  const float y0 = (float)(blockIdx.y * 8), y1 = (float)min((int)blockIdx.y * 8 + 7, n - 1);
+  const float dxm = fmaxf(fabsf(x0 - cc), fabsf(x1 - cc)), dym = fmaxf(fabsf(y0 - cc), fabsf(y1 - cc));
+  const float rin = 0.5f * (float)(n - 6);
+  const bool inner = n > 6 && dxm * dxm + dym * dym <= rin * rin;
   float acc_u = 0.0f, acc_m = 0.0f;
-  for (int ja = 0; ja < nclass; ja += kAngleChunk) {
-    const int jn = min(kAngleChunk, nclass - ja);
-    __syncthreads();
-    for (int t = tid; t < jn; t += 256) {
-      s_cs[t] = tabf[ja + t];
-      s_sn[t] = tabf[nth + ja + t];
-      s_CS[t] = tabi[ja + t];
-      s_SN[t] = tabi[nth + ja + t];
-    }
-    __syncthreads();
-    if (!in) continue;
-    for (int t = 0; t < jn; ++t) {
-      const int j = ja + t;
-      const float cs = s_cs[t], sn = s_sn[t];
-      const long long CS = s_CS[t], SN = s_SN[t];
-      const long long A = X2 * CS, B = Y2 * SN, C = Y2 * CS, D = X2 * SN;
-      const Sums3 su = candidate_sums(A + B + ck, C - D + cm, cs, sn, ns, mrot);
-      const Sums3 sm = candidate_sums(-A + B + ck, C + D + cm, cs, sn, ns, mrot);
-      const float* __restrict__ r0 = gl + (size_t)j * rows;         // theta_j
-      const float* __restrict__ r1 = gl + (size_t)(j + hh) * rows;  // theta_j + 90
-      acc_u = apply_sums(su, r0, r1, n, koff, acc_u);
-      acc_m = apply_sums(sm, r0, r1, n, koff, acc_m);
-      if (j != 0 && 2 * j != hh) {
-        const float* __restrict__ r2 = gl + (size_t)(nth - j) * rows;  // pi - theta_j
-        const float* __restrict__ r3 = gl + (size_t)(hh - j) * rows;   // pi/2 - theta_j
-        acc_m = apply_sums(su, r2, r3, n, koff, acc_m);
-        acc_u = apply_sums(sm, r2, r3, n, koff, acc_u);
-      }
-    }
-  }
+  if (inner)
+    bp_quad_classes<true>(gl, rows, n, nth, ns, hh, nclass, koff, mrot, X2, Y2, ck, cm, in, tid,
+                          tabf, tabi, s_cs, s_sn, s_CS, s_SN, acc_u, acc_m);
+  else
+    bp_quad_classes<false>(gl, rows, n, nth, ns, hh, nclass, koff, mrot, X2, Y2, ck, cm, in, tid,
+                           tabf, tabi, s_cs, s_sn, s_CS, s_SN, acc_u, acc_m);
   if (!in) return;
   const float f = 2.0f / (float)nimg;
   const size_t ou = ((size_t)l * n + iy) * n + ix;
