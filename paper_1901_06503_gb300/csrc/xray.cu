@@ -995,17 +995,19 @@ __global__ void __launch_bounds__(256)
   h[om] = out_m;
 }
 
+// Lambda on rows of n detectors.  A CTA computes the taps once (FP64, then
+// rounded to T) and walks rows; each row sits in shared memory between n
+// zeros on either side, so out-of-range neighbours read as zero (the same
+// sums, term for term, as testing the range).
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_ramp(const T* __restrict__ r, T* __restrict__ out, const T* __restrict__ mask, int n,
-           int nimg) {
+           int nimg, int rows) {
   extern __shared__ unsigned char smem_raw[];
-  T* row = reinterpret_cast<T*>(smem_raw);
-  T* tap = row + n;  // tap[d] for d < n (odd d nonzero)
-  const size_t base = (size_t)blockIdx.x * n;
+  T* tap = reinterpret_cast<T*>(smem_raw);  // tap[d] for d < n (odd d nonzero)
+  T* row = tap + n;                         // zeros, the row, zeros: 3n
   const double dxi = 2.0 / nimg;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    row[i] = r[base + i];
     double t;
     if (i == 0)
       t = 1.0 / (8.0 * dxi);
@@ -1014,18 +1016,21 @@ __global__ void __launch_bounds__(128)
     else
       t = -1.0 / (2.0 * kPi * kPi * (double)i * (double)i * dxi);
     tap[i] = (T)t;
+    row[i] = T(0);
+    row[2 * n + i] = T(0);
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    T acc = tap[0] * row[k];
-    for (int d = 1; d < n; d += 2) {
-      T a = T(0);
-      if (k - d >= 0) a += row[k - d];
-      if (k + d < n) a += row[k + d];
-      acc += tap[d] * a;
+  const T* rc = row + n;
+  for (int rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+    const size_t base = (size_t)rw * n;
+    __syncthreads();  // the previous row is read (and the taps and zeros written)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) row[n + i] = r[base + i];
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      T acc = tap[0] * rc[k];
+      for (int d = 1; d < n; d += 2) acc += tap[d] * (rc[k - d] + rc[k + d]);
+      if (mask) acc = acc * mask[base + k];
+      out[base + k] = acc;
     }
-    if (mask) acc = acc * mask[base + k];
-    out[base + k] = acc;
   }
 }
 
@@ -1316,14 +1321,29 @@ int launch_backproject(const Plan& pl, const void* g, void* h, const void* scale
 }
 
 int launch_ramp(const Plan& pl, const void* r, void* out, cudaStream_t st, const void* mask) {
-  const unsigned rows = (unsigned)(pl.nth * pl.n);
-  const size_t smem = 2 * (size_t)pl.n * pl.esize;
+  const int rows = pl.nth * pl.n;
+  const size_t smem = 4 * (size_t)pl.n * pl.esize;
+  // eight 128-thread CTAs per SM walk the rows
+  const unsigned grid = (unsigned)(rows < 8 * kNumSMs ? rows : 8 * kNumSMs);
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_ramp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_ramp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024);
+  });
+  if (attr != cudaSuccess || smem > 200 * 1024) {
+    cudaGetLastError();
+    return report(FFPAT_ECUDA, "k_ramp: %zu bytes of shared memory refused", smem);
+  }
   if (pl.prec == FFPAT_FP64)
-    k_ramp<double><<<rows, 128, smem, st>>>((const double*)r, (double*)out, (const double*)mask,
-                                            pl.n, pl.nimg);
+    k_ramp<double><<<grid, 128, smem, st>>>((const double*)r, (double*)out, (const double*)mask,
+                                            pl.n, pl.nimg, rows);
   else
-    k_ramp<float><<<rows, 128, smem, st>>>((const float*)r, (float*)out, (const float*)mask, pl.n,
-                                           pl.nimg);
+    k_ramp<float><<<grid, 128, smem, st>>>((const float*)r, (float*)out, (const float*)mask, pl.n,
+                                           pl.nimg, rows);
   count_launch();
   return check_launch(__func__);
 }

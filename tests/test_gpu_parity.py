@@ -243,8 +243,9 @@ def test_backproject_fp32_other_kernels(tmp_path, knob):
         assert rel(h, o.backproject(g, n)) < 5e-7, (knob, n, nth)
 
 
+# (96, 20): 1920 rows, more than the grid's 1216 CTAs, so CTAs walk several rows
 @pytest.mark.parametrize("prec", [F.FP64, F.FP32])
-@pytest.mark.parametrize("n,nth", [(24, 6), (33, 3), (130, 2)])
+@pytest.mark.parametrize("n,nth", [(24, 6), (33, 3), (130, 2), (96, 20)])
 def test_ramp(n, nth, prec):
     r = random_data(nth, n, 400 + n)
     prob = F.problem(n, 1.0, nth, prec)
