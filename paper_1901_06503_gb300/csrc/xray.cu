@@ -401,9 +401,10 @@ __global__ void __launch_bounds__(1024)
 // [koff, koff + N) are rays.  The mirror image of a sample uses the same
 // corner row, fractions and weights, read at the mirrored columns.  Classes
 // j = 0 and 2j = h have only the pair (1), (2).
-// One CTA per (class, plane).  Warp (kg, mg) owns the tiles of 32 lattice
-// rows (lane = row) x 16 samples whose k-tile is kg mod KG and m-tile mg mod
-// MG; tiles whose samples miss the plane (or the band) are skipped, and tiles
+// A CTA takes one plane and one class (several classes, one after the
+// other, when the plane fits one band and is staged once).  Warp (kg, mg)
+// owns the tiles of 32 lattice rows (lane = row) x 16 samples whose k-tile
+// is kg mod KG and m-tile mg mod MG; tiles whose samples miss the plane (or the band) are skipped, and tiles
 // whose samples all lie on it take a path without per-sample tests.  A lane's
 // running sum over a tile is its row's partial sum; the column partials of an
 // m-tile accumulate per lane over the warp's k-tiles, then one transposed
