@@ -246,6 +246,15 @@ int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_
 // 15.4 / 46.9 / 135), and tie at 144^3, whose 64-wide tiles are a third empty
 constexpr int kTwoStepMinN = 128;
 
+// Whether a three-term FP32 time loop takes two steps per pass: the rule of
+// W's own loop (TMA layout, N in the two-step kernel's range, automatic
+// choice from kTwoStepMinN or the two-step path requested)
+bool two_step_three_term(const Plan& pl, bool tma) {
+  const int path = g_stencil_path.load();
+  return pl.prec == FFPAT_FP32 && tma && pl.n <= kTwoStepMaxN &&
+         (path == 3 || (path == 0 && pl.n >= kTwoStepMinN));
+}
+
 // algorithmic HBM bytes per point of a two-step pass beyond a single step's:
 // FP32-Kahan moves its 28 B once for both steps, FP32 20 B against 16 B
 static double pass_extra_bytes(const Plan& pl) { return pl.prec == FFPAT_FP32 ? 4.0 : 0.0; }
@@ -320,8 +329,7 @@ static int wave_sequence(const Plan& pl, const void* in, void* out, const void**
       ++launches;
     }
     if (result) *result = cur;
-  } else if (pl.prec == FFPAT_FP32 && tma && nt >= 3 && pl.n <= kTwoStepMaxN &&
-             (path == 3 || (path == 0 && pl.n >= kTwoStepMinN))) {
+  } else if (nt >= 3 && two_step_three_term(pl, tma)) {
     // FP32 three-term, two steps per pass (kTwoStepMinN): 20 B per point per
     // two steps against 32 B.  The pairs (S0, S1) and (S2, S3) alternate as
     // (p^{n-1}, p^n) inputs and (p^{n+1}, p^{n+2}) outputs

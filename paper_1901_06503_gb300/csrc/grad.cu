@@ -46,8 +46,14 @@ void as_three_term(Plan& pl) {
 }
 
 bool use_tma(const Plan& pl, const Ckpt& ck, const void* a, const void* b) {
-  const void* ptrs[8] = {a, b, pl.kap, pl.s[0], pl.s[1], pl.x, ck.base, nullptr};
-  return tma_supported(pl, ptrs, 7) && (ck.vol % 16) == 0;
+  const void* ptrs[9] = {a, b, pl.kap, pl.s[0], pl.s[1], pl.s[2], pl.s[3], pl.x, ck.base};
+  return tma_supported(pl, ptrs, 9) && (ck.vol % 16) == 0;
+}
+
+// two steps per pass in the checkpointed loops: W's rule, and checkpoints at
+// even steps (the passes advance the pair (p^m, p^{m+1}) by two)
+bool use_two(const Plan& pl, const Ckpt& ck, bool tma) {
+  return two_step_three_term(pl, tma) && ck.every % 2 == 0 && pl.s[2] && pl.s[3];
 }
 
 }  // namespace
@@ -80,28 +86,38 @@ int ffpat_forward_ckpt(const ffpat_problem* problem, const void* c, const void* 
   if (ckpt_bytes < ck.bytes())
     return report(FFPAT_ENOMEM, "checkpoint buffer %zu < %zu bytes", ckpt_bytes, ck.bytes());
   const bool tma = use_tma(pl, ck, h, g);
-  void* A = pl.s[0];
-  void* B = pl.s[1];
-  int rc = step3(pl, tma, true, h, nullptr, B, A, st);  // A = p^0, B = p^1
+  const bool two = use_two(pl, ck, tma);
+  // S[a] = p^m, S[b] = p^{m+1}; a two-step pass writes the other pair
+  void* S[4] = {pl.s[0], pl.s[1], pl.s[2], pl.s[3]};
+  int a = 0, b = 1;
+  int rc = step3(pl, tma, true, h, nullptr, S[b], S[a], st);  // p^0, p^1
   if (rc != FFPAT_OK) return rc;
   const size_t vb = pl.n3 * pl.esize;
-  if (cudaMemcpyAsync(ck.a(0), A, vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(ck.b(0), B, vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(ck.a(0), S[a], vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ck.b(0), S[b], vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return check_launch("checkpoint copy");
-  for (int n = 1; n < pl.nt; ++n) {
-    rc = step3(pl, tma, false, B, A, A, nullptr, st);  // A = p^{n+1}
+  for (int m = 0; m + 1 < pl.nt;) {
+    if (two && m + 3 <= pl.nt) {
+      rc = launch_step2_f32(pl, S[a], S[b], S[a ^ 2], S[b ^ 2], st);  // p^{m+2}, p^{m+3}
+      a ^= 2;
+      b ^= 2;
+      m += 2;
+    } else {
+      rc = step3(pl, tma, false, S[b], S[a], S[a], nullptr, st);  // p^{m+2} over p^m
+      const int t = a;
+      a = b;
+      b = t;
+      m += 1;
+    }
     if (rc != FFPAT_OK) return rc;
-    void* t = A;
-    A = B;
-    B = t;  // A = p^n, B = p^{n+1}
-    if (n % every == 0) {
-      const int s = n / every;
-      if (cudaMemcpyAsync(ck.a(s), A, vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-          cudaMemcpyAsync(ck.b(s), B, vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    if (m % every == 0) {
+      const int s = m / every;
+      if (cudaMemcpyAsync(ck.a(s), S[a], vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(ck.b(s), S[b], vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return check_launch("checkpoint copy");
     }
   }
-  return launch_project(pl, B, g, nullptr, st, nullptr, pl.x);
+  return launch_project(pl, S[b], g, nullptr, st, nullptr, pl.x);
 }
 
 int ffpat_backward(const ffpat_problem* problem, const void* c, const void* grad_g, void* grad_h,
@@ -118,6 +134,7 @@ int ffpat_backward(const ffpat_problem* problem, const void* c, const void* grad
   if (ckpt_bytes < ck.bytes())
     return report(FFPAT_ENOMEM, "checkpoint buffer %zu < %zu bytes", ckpt_bytes, ck.bytes());
   const bool tma = use_tma(pl, ck, grad_h, c);
+  const bool two = use_two(pl, ck, tma);
   const size_t vb = pl.n3 * pl.esize;
   // mu^{Nt} = (kappa / 12) P^T grad_g, mu^{Nt+1} = 0
   void* U = pl.x;
@@ -130,8 +147,16 @@ int ffpat_backward(const ffpat_problem* problem, const void* c, const void* grad
     const int lo = s * every;
     const int hi = (lo + every - 1 < pl.nt - 1) ? lo + every - 1 : pl.nt - 1;
     auto P = [&](int j) -> void* { return j == 0 ? ck.a(s) : (j == 1 ? ck.b(s) : ck.seg(j)); };
-    for (int j = 1; j + 1 <= hi - lo; ++j) {
-      rc = step3(pl, tma, false, P(j), P(j - 1), P(j + 1), nullptr, st);
+    // recompute p^{lo+2} .. p^{hi} from the checkpoint, two steps per pass
+    // where allowed
+    for (int j = 1; j + 1 <= hi - lo;) {
+      if (two && j + 2 <= hi - lo) {
+        rc = launch_step2_f32(pl, P(j - 1), P(j), P(j + 1), P(j + 2), st);
+        j += 2;
+      } else {
+        rc = step3(pl, tma, false, P(j), P(j - 1), P(j + 1), nullptr, st);
+        j += 1;
+      }
       if (rc != FFPAT_OK) return rc;
     }
     for (int n = hi; n >= lo; --n) {

@@ -68,6 +68,8 @@ int setup(const ffpat_problem* pr, Plan& pl, const void* c, void* ws, size_t ws_
 // one three-term leapfrog launch (TMA kernel when the layout allows)
 int step3(const Plan& pl, bool tma, bool start, const void* p, const void* qin, void* qout,
           void* copy0, cudaStream_t st);
+// whether a three-term FP32 time loop takes two steps per pass (W's own rule)
+bool two_step_three_term(const Plan& pl, bool tma);
 int attach(const ffpat_problem* pr, Plan& pl, void* ws, size_t ws_bytes);
 int time_steps(const Plan& pl, double cmax, int* nt, double* dt);
 void fill_tables_host(int nth, unsigned char* buf);  // table_bytes(nth) bytes

@@ -183,3 +183,30 @@ def test_config3_central_differences_fp32_192():
     print(f"config-3 FD: FP32 eps=1e-3 max rel err {max(errs32):.3e} median "
           f"{float(np.median(errs32)):.3e}; FP64 eps, eps/2 max "
           f"{max(e[0] for e in errs64):.3e}, {max(e[1] for e in errs64):.3e}")
+
+
+@pytest.mark.parametrize("n,every,path", [(128, 4, 0), (128, 16, 0), (128, 5, 0), (48, 6, 3)])
+def test_checkpointed_loops_two_step_bit_identical(n, every, path):
+    """The checkpointed forward and the segment recomputes take two leapfrog
+    steps per pass (FP32, from N = 128 or with the two-step path requested,
+    checkpoints at even steps); the loss and both gradients equal those of
+    the step-by-step loops bit for bit (an odd interval keeps single steps)."""
+    nth, T = 8, 0.1
+    c = random_speed(n, 1100 + n).astype(np.float32)
+    h = random_volume(n, 1101 + n).astype(np.float32)
+    w = torch.tensor(random_data(nth, n, 1102 + n), device="cuda", dtype=torch.float32)
+    prob = F.problem(n, T, nth, F.FP32)
+    out = {}
+    try:
+        for p in (path, 2):
+            F.set_stencil_path(p)
+            ht = torch.tensor(h, device="cuda", requires_grad=True)
+            ct = torch.tensor(c, device="cuda", requires_grad=True)
+            g = forward_op(ht, ct, prob, every)
+            (g * w).sum().backward()
+            torch.cuda.synchronize()
+            out[p] = (g.detach().cpu().numpy(), ht.grad.cpu().numpy(), ct.grad.cpu().numpy())
+    finally:
+        F.set_stencil_path(0)
+    for a, b in zip(out[path], out[2]):
+        assert np.array_equal(a, b)
