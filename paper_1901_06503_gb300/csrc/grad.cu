@@ -137,11 +137,15 @@ int ffpat_backward(const ffpat_problem* problem, const void* c, const void* grad
   const bool two = use_two(pl, ck, tma);
   const size_t vb = pl.n3 * pl.esize;
   // mu^{Nt} = (kappa / 12) P^T grad_g, mu^{Nt+1} = 0
-  void* U = pl.x;
-  void* V = pl.s[0];
-  int rc = launch_backproject(pl, grad_g, U, pl.kap, st);
+  // B[u] = mu^{n+1}, B[v] = mu^{n+2}; a two-step pass writes mu^n, mu^{n-1}
+  // into the other two buffers
+  void* B[4] = {pl.x, pl.s[0], pl.s[1], pl.s[2]};
+  const bool two_t = two_step_three_term(pl, tma) && pl.s[1] && pl.s[2];
+  int u = 0, v = 1;
+  int rc = launch_backproject(pl, grad_g, B[u], pl.kap, st);
   if (rc != FFPAT_OK) return rc;
-  if (cudaMemsetAsync(V, 0, vb, st) != cudaSuccess || cudaMemsetAsync(ck.acc(), 0, vb, st) != cudaSuccess)
+  if (cudaMemsetAsync(B[v], 0, vb, st) != cudaSuccess ||
+      cudaMemsetAsync(ck.acc(), 0, vb, st) != cudaSuccess)
     return check_launch("backward init");
   for (int s = ck.nseg - 1; s >= 0; --s) {
     const int lo = s * every;
@@ -159,21 +163,37 @@ int ffpat_backward(const ffpat_problem* problem, const void* c, const void* grad
       }
       if (rc != FFPAT_OK) return rc;
     }
-    for (int n = hi; n >= lo; --n) {
+    for (int n = hi; n >= lo;) {
       const void* pn = P(n - lo);
-      if (n >= 1) {
-        rc = launch_lap_accum(pl, ck.acc(), U, pn, 1.0, st);
-        if (rc == FFPAT_OK) rc = step3(pl, tma, false, U, V, V, nullptr, st);  // V = mu^n
+      if (two_t && n - 1 >= lo && n - 1 >= 1) {
+        // mu^n, mu^{n-1} in one pass; the accumulations in the order of
+        // the single steps (mu^{n+1} L(p^n), then mu^n L(p^{n-1}))
+        int x = 0;
+        while (x == u || x == v) ++x;
+        int y = x + 1;
+        while (y == u || y == v) ++y;
+        rc = launch_step2_f32(pl, B[v], B[u], B[x], B[y], st);
+        if (rc == FFPAT_OK) rc = launch_lap_accum(pl, ck.acc(), B[u], pn, 1.0, st);
+        if (rc == FFPAT_OK) rc = launch_lap_accum(pl, ck.acc(), B[x], P(n - 1 - lo), 1.0, st);
         if (rc != FFPAT_OK) return rc;
-        void* t = U;
-        U = V;
-        V = t;
+        u = y;  // mu^{n-1}
+        v = x;  // mu^n
+        n -= 2;
+      } else if (n >= 1) {
+        rc = launch_lap_accum(pl, ck.acc(), B[u], pn, 1.0, st);
+        if (rc == FFPAT_OK) rc = step3(pl, tma, false, B[u], B[v], B[v], nullptr, st);  // mu^n
+        if (rc != FFPAT_OK) return rc;
+        const int t = u;
+        u = v;
+        v = t;
+        n -= 1;
       } else {
-        rc = launch_lap_accum(pl, ck.acc(), U, pn, 0.5, st);
+        rc = launch_lap_accum(pl, ck.acc(), B[u], pn, 0.5, st);
         void* tmp = ck.seg(0);
-        if (rc == FFPAT_OK) rc = step3(pl, tma, true, U, nullptr, tmp, nullptr, st);
-        if (rc == FFPAT_OK && grad_h) rc = launch_sub_div(pl, tmp, V, grad_h, st);
+        if (rc == FFPAT_OK) rc = step3(pl, tma, true, B[u], nullptr, tmp, nullptr, st);
+        if (rc == FFPAT_OK && grad_h) rc = launch_sub_div(pl, tmp, B[v], grad_h, st);
         if (rc != FFPAT_OK) return rc;
+        n -= 1;
       }
     }
   }
